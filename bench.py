@@ -1,0 +1,336 @@
+"""Benchmark: LiDAR beams/s (waveforms + echoes) on the full-frame workload.
+
+Workload: 2048x1024 G-buffer over 120 x 30 deg (ground plane, 50 boxes at
+5-150 m, 5 % retroreflective faces, sun ambient), 16 x 1600 line scan
+(25 600 beams), 401x401 tabulated profile at 0.01 deg, 2048 bins of 0.1 ns.
+One step = one lidar_simulate call over the whole frame (every kernel of the
+path). Inputs are synthetic and seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one process per GPU): each rank simulates its own frame
+(weak scaling, no collective on the data path); value = all ranks' beams / max
+rank time. --impl reference times the FP64 CPU oracle on a bounded beam sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LiDAR beams/s (waveform+echoes) at <=1e-3 rel err vs FP64 oracle; % HBM roofline"
+UNIT = "beams/s"
+L2_BYTES = 129 * 1024 * 1024
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "footprint_wave_boxes2048x1024.traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2512_05932_gb300", "csrc", "lidar_kernels.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2512_05932_gb300 import scenes
+    return scenes.full_frame_boxes()
+
+
+def config_of(w, extra=None):
+    gb = w.gbuffer
+    c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "120x30", "beams": int(len(w.dirs)),
+         "pattern": "linescan 16x1600", "profile": "table 401x401 @0.01deg", "n_bins": int(w.pulse["n_bins"]),
+         "dt_ns": w.pulse["dt_s"] * 1e9, "max_echoes": int(w.calib["max_echoes"]), "seed": 2}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def algorithmic_bytes(w):
+    """HBM bytes one frame must move: the G-buffer read once (7 fp32 planes)
+    plus the waveforms, echoes and echo counts written once."""
+    gb = w.gbuffer
+    nb = len(w.dirs)
+    return gb.U * gb.V * 7 * 4 + nb * (w.pulse["n_bins"] * 4 + w.calib["max_echoes"] * 32 + 4)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(w, n_sample, nthreads):
+    """Oracle beams/s on an evenly spaced beam sample of the workload."""
+    from oracle import oracle as O
+    O.build()
+    nb = len(w.dirs)
+    beams = np.linspace(0, nb - 1, n_sample).round().astype(np.int32)
+    t = time.perf_counter()
+    O.simulate_workload(w, beams=beams, nthreads=nthreads, max_out=4)
+    dt = time.perf_counter() - t
+    return n_sample / dt, dt, beams
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for_current_kernel():
+    """dram bytes per launch of the footprint kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    with open(KERNEL_SRC, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if d.get("kernel_sha256") != sha:
+        return None
+    return d.get("bytes_per_launch")
+
+
+# --------------------------------------------------------------------------
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload()
+    cores = cpu_cores()
+    n_sample = 96
+    # warm-up steps are untimed samples of the same kind
+    from oracle import oracle as O
+    O.build()
+    nb = len(w.dirs)
+    times = []
+    for s in range(args.warmup + args.steps):
+        g = np.random.default_rng(1000 + s)
+        beams = np.sort(g.choice(nb, n_sample, replace=False)).astype(np.int32)
+        t = time.perf_counter()
+        O.simulate_workload(w, beams=beams, nthreads=cores, max_out=4)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = n_sample * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, {"sample_beams_per_step": n_sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sample} random beams of the frame per step, all pixels of each"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+    from paper_2512_05932_gb300 import lidar
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    planes = lidar.gbuffer_to_device(w.gbuffer, dev)
+    outs = L.alloc_outputs(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    clk = ClockSampler(local_rank).__enter__()
+    # warm-up: at least W steps and at least 1.5 s, so that the clock sampler
+    # (200 ms period) is running under load before the timed steps start
+    t_w = time.perf_counter()
+    n_w = 0
+    while n_w < args.warmup or time.perf_counter() - t_w < 1.5:
+        L.simulate(w.gbuffer, planes, w.pose, outs, stream)
+        n_w += 1
+        if n_w % 16 == 0:
+            torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed steps (inputs resident in HBM, L2 flushed between) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lidar.lidar_profile_enable(L.handle, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            L.simulate(w.gbuffer, planes, w.pose, outs, stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern = lidar.lidar_profile_read(L.handle)
+    lidar.lidar_profile_enable(L.handle, False)
+    t_total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_total, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t_total.item()) / args.steps
+    nbeams = len(w.dirs)
+    value = world * nbeams / (ms_per_step * 1e-3)
+
+    # ---- end to end through the host-memory entry point ----
+    host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
+    host_out = (torch.empty((nbeams, L.n_bins), dtype=torch.float32, pin_memory=True),
+                torch.empty((nbeams, L.max_echoes, 8), dtype=torch.int32, pin_memory=True),
+                torch.empty((nbeams,), dtype=torch.int32, pin_memory=True))
+    for _ in range(2):
+        L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = world * nbeams * args.steps / float(e2e_s.item())
+    h2d = sum(p.numel() * 4 for p in host_planes)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----
+    names = lidar.KERNELS
+    tot = {k: kern[k][0] for k in names}
+    dom = max(names, key=lambda k: tot[k])
+    launches = kern[dom][1]
+    avg_ms = tot[dom] / max(1, launches)
+    peak, peak_kind = load_peaks()
+    alg = algorithmic_bytes(w)
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    pix_samples = None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+            "traffic": traffic_for_current_kernel(), "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+            "kernel_share": {k: tot[k] / sum(tot.values()) for k in names}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = cpu_cores()
+        rate, dt, beams = oracle_rate(w, args.cpu_beams, cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_beams} evenly spaced beams of the frame, all pixels each ({dt:.1f} s wall)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(w, {"l2": "flushed between timed steps (258 MB write)",
+                                    "parallelism": f"replicas x{world}"}),
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),
+            "clocks": clk.summary(),
+            "kernel_ms": {k: tot[k] / max(1, kern[k][1]) for k in names}}
+    print(json.dumps(line), flush=True)
+    L.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gb300(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

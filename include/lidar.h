@@ -1,0 +1,237 @@
+/*
+ * lidar.h - C ABI of the GB300 (sm_103a) beam model library.
+ *
+ * The library computes, for every beam of a LiDAR steering pattern, the
+ * received time-of-flight waveform and its echoes from a near-infrared
+ * G-buffer, following Dudzik et al., "Physically-Based Simulation of
+ * Automotive LiDAR" (IAVVC 2025, arXiv 2512.05932):
+ *
+ *   xi_b(r) = iint d omega (kappa eta)(Phi - Psi_b) rho_hat(Phi) delta(r - r(Phi))
+ *                                          (Sec. II-B, centered-kernel equation)
+ *   xi_hat  = varpi * xi + ambient,  echoes = maximal intervals xi_hat > T
+ *                                          (Sec. II-C, EPW post-processing)
+ *
+ * discretised as the beam iteration of Alg. 1 over pixel centres, with each
+ * pixel's power spread uniformly over its range interval (pixelRangeInterval
+ * of Alg. 1, plane extrapolation of Sec. II-D) and projected onto linear hat
+ * functions centred on the range bins.
+ *
+ * Conventions used throughout
+ *   - Sensor frame: x forward, y left, z up. Directions are unit vectors.
+ *   - G-buffer: equirectangular; pixel (u, v), 0 <= u < U along azimuth,
+ *     0 <= v < V along elevation, centre at az = az0 + (u + 1/2) daz,
+ *     el = el0 + (v + 1/2) del, direction (cos el cos az, cos el sin az, sin el).
+ *     Planes are float32 [V][U], row v contiguous in u.
+ *   - Bins: bin k covers time of flight [t0 + k dt, t0 + (k + 1) dt), centre
+ *     t_k = t0 + (k + 1/2) dt, range r = c t / 2 (c = 299792458 m/s).
+ *   - All intensities are relative (Sec. I-A: intensities reduce to relative
+ *     values after calibration).
+ *
+ * Ownership: the caller owns every buffer it passes. The library copies the
+ * profile table, the beam directions and the pulse at lidar_create time and
+ * owns internal device scratch (per-pixel records and per-beam parameters),
+ * which it grows with cudaMalloc when a larger G-buffer arrives.
+ *
+ * Errors: every entry point returns a lidar_status_t and never aborts; a
+ * message for the last failure is available from lidar_last_error.
+ * Thread safety: one lidar_t may be used by one host thread at a time.
+ */
+#ifndef GB300_LIDAR_H
+#define GB300_LIDAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LIDAR_OK = 0,
+    LIDAR_EINVAL = 1,   /* invalid argument (message says which) */
+    LIDAR_ENOMEM = 2,   /* host or device allocation failed */
+    LIDAR_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    LIDAR_ETIMEOUT = 4, /* reserved: a bounded device wait gave up */
+    LIDAR_ENUMERIC = 5  /* calibration fit or normalisation failed */
+} lidar_status_t;
+
+/* Beam x sensitivity profile kappa*eta of Sec. III-C, centred on the beam
+ * (Sec. II-B, centered kernel). Offsets (u, v) are in degrees in the beam's
+ * local tangent frame (azimuthal-equidistant): u along e1 = z x dir
+ * (increasing azimuth), v along e2 = dir x e1 (increasing elevation), both
+ * taken in the sensor frame and rotated with the pose. The library
+ * normalises the profile to unit integral over the sphere at create time.
+ *
+ *   LIDAR_PROFILE_RADIAL: P(theta) = exp(-theta^2 / (2 sigma^2))
+ *                         + tail_amp * min(1, (theta / tail_core)^(-tail_pow))
+ *                         for theta <= trunc, 0 beyond (theta in degrees).
+ *   LIDAR_PROFILE_TABLE:  bilinear interpolation of table[h][w] (row j <-> v,
+ *                         column i <-> u), node (i, j) at
+ *                         u = (i - (w-1)/2) pitch, v = (j - (h-1)/2) pitch,
+ *                         extended by one ring of zeros (P falls linearly to 0
+ *                         one pitch beyond the edge nodes). Values >= 0. */
+typedef enum { LIDAR_PROFILE_RADIAL = 0, LIDAR_PROFILE_TABLE = 1 } lidar_profile_kind_t;
+
+typedef struct {
+    int32_t kind;          /* lidar_profile_kind_t */
+    double sigma_deg;      /* RADIAL */
+    double tail_amp;
+    double tail_core_deg;
+    double tail_pow;
+    double trunc_deg;      /* RADIAL support radius, (0, 10] degrees */
+    int32_t table_w;       /* TABLE: 2..4096 */
+    int32_t table_h;       /* TABLE: 2..4096 */
+    double pitch_deg;      /* TABLE node spacing; half-diagonal of the support <= 10 deg */
+    const float *table;    /* TABLE: host pointer, [table_h][table_w], copied at create */
+} lidar_profile_t;
+
+/* Beam set B with centre directions Psi_b (Sec. II-A), sensor frame.
+ * Beams are processed in groups of consecutive indices: listing spatially
+ * neighbouring beams next to each other (row-major scans, curve order) keeps
+ * the groups' footprints compact. */
+typedef struct {
+    int32_t n_beams;       /* >= 1 */
+    const float *dirs;     /* host pointer, [n_beams][3], nonzero (normalised inside) */
+} lidar_pattern_t;
+
+/* Range bins and emitted pulse varpi (Sec. II-C): Gaussian of the given FWHM
+ * sampled at integer bin offsets -M..M with M = ceil(trunc_sigmas * sigma/dt),
+ * normalised to unit sum. */
+typedef struct {
+    int32_t n_bins;        /* multiple of 32, 32..16384 */
+    double dt_s;           /* bin width (s), > 0 */
+    double t0_s;           /* time of flight at the start of bin 0 (range gate) */
+    double fwhm_s;         /* pulse FWHM (s), > 0 */
+    double trunc_sigmas;   /* truncation in standard deviations, (0, 12] */
+} lidar_pulse_t;
+
+/* Detection threshold, ambient scale and EPW -> intensity conversion
+ * (Sec. II-C EPW, Sec. III-C threshold calibration). The intensity of an echo
+ * is exp(c0 + c1 EPW^2 + c2 EPW^4) with EPW in metres. With fit_epw != 0,
+ * lidar_create fits (c0, c1, c2) in FP64 by least squares on a sweep of
+ * perpendicular point targets of energy a in [50 T, 1e6 T] (64 log-spaced
+ * amplitudes x 4 sub-bin phases, no ambient): ln a = c0 + c1 EPW^2 + c2 EPW^4. */
+typedef struct {
+    double threshold;      /* T > 0; an echo is a maximal run of bins with xi_hat > T */
+    double ambient_scale;  /* s_amb >= 0: xi_hat[k] += A_b * s_amb in every bin */
+    int32_t max_echoes;    /* 1..3, nearest first */
+    int32_t fit_epw;       /* != 0: fit epw_coef at create time */
+    double epw_coef[3];    /* used when fit_epw == 0 */
+} lidar_calib_t;
+
+/* NIR G-buffer (Alg. 1 inputs rho_hat, varrho, nu plus the material planes
+ * the library turns into rho_hat). Device pointers, float32 [V][U].
+ *   range: metres along the pixel-centre ray; a pixel without a hit has a
+ *          non-finite or non-positive range (it still receives ambient).
+ *   nx, ny, nz: unit surface normal (either orientation).
+ *   rho_d: NIR diffuse reflectance (BRDF rho_d / pi, Sec. I-A).
+ *   retro: retroreflective BRDF gain g (sr^-1, Sec. I-B); beta = rho_d/pi + g.
+ *   ambient: ambient radiance L_amb (relative), finite >= 0.
+ * The azimuth span U*daz must not exceed 2 pi (exactly 2 pi wraps around);
+ * the elevation span must stay within [-pi/2, pi/2]. */
+typedef struct {
+    int32_t U, V;
+    double az0, el0, daz, del;   /* radians */
+    const float *range, *nx, *ny, *nz, *rho_d, *retro, *ambient;
+} lidar_gbuffer_t;
+
+/* Sensor pose: rotation R (row-major 3x3) taking sensor-frame vectors into the
+ * G-buffer frame (a beam axis is R dir). Orthonormal with det +1 (1e-3). */
+typedef struct {
+    float R[9];
+} lidar_pose_t;
+
+enum {
+    LIDAR_ECHO_CLIPPED_START = 1u,  /* run starts at bin 0 */
+    LIDAR_ECHO_CLIPPED_END = 2u,    /* run ends at the last bin */
+    LIDAR_ECHO_NEAR_THRESHOLD = 4u  /* a crossing bin lies within 1e-4 T of T */
+};
+
+/* One echo (32 bytes). Ranges in metres. bin_start/bin_end: first/last bin
+ * above T; r0/r1 interpolate the two threshold crossings linearly, EPW =
+ * r1 - r0; bin_peak = argmax in the run (lowest bin on ties); range_m is the
+ * peak refined by a 3-point parabola on ln xi_hat (on xi_hat if a value is
+ * <= 0); peak = xi_hat[bin_peak]. */
+typedef struct {
+    float range_m;
+    float epw_m;
+    float intensity;
+    float peak;
+    int32_t bin_peak;
+    int32_t bin_start;
+    int32_t bin_end;
+    uint32_t flags;
+} lidar_echo_t;
+
+/* Echo outputs: device pointers. echoes[n_beams][max_echoes] (unused slots are
+ * zero-filled), counts[n_beams] = number of echoes written (<= max_echoes). */
+typedef struct {
+    lidar_echo_t *echoes;
+    int32_t *counts;
+} lidar_echoes_t;
+
+typedef struct lidar lidar_t;
+
+/* Creates a simulator for one sensor: copies the profile, pattern and pulse to
+ * the current CUDA device, normalises the profile (FP64) and, if asked, fits
+ * the EPW -> intensity coefficients (FP64). Returns LIDAR_EINVAL for invalid
+ * parameters without touching the GPU, LIDAR_ENOMEM/LIDAR_ECUDA on device
+ * failures, LIDAR_ENUMERIC if the profile integrates to zero or the fit is
+ * singular. On failure *out is NULL. */
+lidar_status_t lidar_create(const lidar_profile_t *profile, const lidar_pattern_t *pattern,
+                            const lidar_pulse_t *pulse, const lidar_calib_t *calib, lidar_t **out);
+
+/* Simulates all beams for one G-buffer and pose, enqueued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream). Asynchronous: returns after
+ * enqueueing; results are ready when the stream reaches this point.
+ * out_waveforms: device float32 [n_beams][n_bins], xi_hat in beam order.
+ * out_echoes: device echo arrays as described at lidar_echoes_t.
+ * The first call with a larger G-buffer than before grows the internal
+ * scratch with cudaMalloc (synchronising the device). Returns LIDAR_EINVAL for
+ * invalid arguments (nothing is enqueued) and LIDAR_ECUDA if a launch fails. */
+lidar_status_t lidar_simulate(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
+                              float *out_waveforms, lidar_echoes_t *out_echoes, void *stream);
+
+/* Same computation from host memory: the G-buffer plane pointers in `gbuffer`
+ * are HOST pointers, and the outputs are host arrays (waveforms
+ * [n_beams][n_bins], echoes [n_beams][max_echoes], counts [n_beams]). The
+ * library copies the inputs to device buffers it owns, simulates, copies the
+ * results back and synchronises `stream` before returning. Page-locked host
+ * memory gives asynchronous, full-bandwidth copies. */
+lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
+                                   float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
+                                   void *stream);
+
+/* Synchronises `stream` and reports any asynchronous CUDA error as LIDAR_ECUDA. */
+lidar_status_t lidar_sync(lidar_t *lidar, void *stream);
+
+/* Queries: number of beams, bins, echoes per beam, the profile normaliser Z
+ * (integral of the raw profile over the sphere, sr) and the EPW coefficients
+ * in use. Any output pointer may be NULL. */
+lidar_status_t lidar_get_info(const lidar_t *lidar, int32_t *n_beams, int32_t *n_bins, int32_t *max_echoes,
+                              double *profile_norm, double epw_coef[3]);
+
+/* Number of kernel launches one lidar_simulate call enqueues. */
+int32_t lidar_launches_per_simulate(const lidar_t *lidar);
+
+/* Per-kernel timing. While enabled, every lidar_simulate call records CUDA
+ * events on its stream around each of its kernels (setup, footprint_wave).
+ * lidar_profile_read synchronises those events, writes the summed device time
+ * (ms) and launch count of each kernel into total_ms[2] and launches[2]
+ * (either may be NULL), and clears the accumulated records. Enabling or
+ * disabling clears them too. */
+lidar_status_t lidar_profile_enable(lidar_t *lidar, int32_t enable);
+lidar_status_t lidar_profile_read(lidar_t *lidar, double total_ms[2], int32_t launches[2]);
+
+/* Message describing the last failure on `lidar` (or, for NULL, the last
+ * failure of lidar_create on this thread). Never NULL. */
+const char *lidar_last_error(const lidar_t *lidar);
+
+/* Frees the simulator and its device memory. NULL is ignored. */
+void lidar_destroy(lidar_t *lidar);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LIDAR_H */

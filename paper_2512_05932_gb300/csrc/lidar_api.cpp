@@ -1,0 +1,694 @@
+// Host side of the C ABI declared in include/lidar.h: argument validation,
+// create-time FP64 work (profile normalisation, pulse taps, EPW calibration
+// fit), device memory and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lidar_internal.h"
+
+namespace {
+
+constexpr double kC = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kDeg = kPi / 180.0;
+constexpr double kMaxSupportDeg = 10.0;
+
+thread_local char g_create_err[512] = "no error";
+
+}  // namespace
+
+struct lidar {
+    // sensor
+    int32_t n_beams = 0;
+    int32_t kind = 0;
+    double Z = 0.0;
+    double support_rad = 0.0;
+    // radial profile
+    float kg = 0.f, trunc2 = 0.f, tail_amp = 0.f, tc2_inv = 0.f, tail_hp = 0.f;
+    // table profile
+    int32_t qw = 0, qh = 0;
+    float tk = 0.f, tcu = 0.f, tcv = 0.f;
+    // pulse and calibration
+    int32_t n_bins = 0, M = 0, R = 0, tp_len = 0, tp_off = 0;
+    double dt = 0.0, t0 = 0.0;
+    double T = 0.0, s_amb = 0.0;
+    int32_t max_echoes = 0;
+    double coef[3] = {0, 0, 0};
+    // launch shape
+    int32_t G = 16, threads = 512;
+    size_t smem = 0;
+    int device = 0;
+    // device memory owned by the library
+    float *d_dirs = nullptr;
+    float4 *d_quads = nullptr;
+    float *d_taps = nullptr;
+    gbl::BeamParam *d_beams = nullptr;
+    float4 *d_rec = nullptr;
+    size_t rec_cap = 0;  // pixels
+    // host-memory entry point buffers
+    float *d_planes = nullptr;
+    size_t planes_cap = 0;  // pixels
+    float *d_wave = nullptr;
+    lidar_echo_t *d_echo = nullptr;
+    int32_t *d_counts = nullptr;
+    // per-kernel timing (lidar_profile_enable)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // 3 events per recorded simulate call
+    size_t ev_used = 0;
+    char err[512] = "no error";
+};
+
+namespace {
+
+lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...)
+{
+    char *buf = l ? l->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what)
+{
+    return fail(l, e == cudaErrorMemoryAllocation ? LIDAR_ENOMEM : LIDAR_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// ---------------------------------------------------------------------------
+// FP64 profile normalisation: Z = integral of the raw profile over the sphere
+// ---------------------------------------------------------------------------
+
+double radial_raw(const lidar_profile_t *p, double th_deg)
+{
+    if (th_deg > p->trunc_deg) return 0.0;
+    double g = std::exp(-0.5 * th_deg * th_deg / (p->sigma_deg * p->sigma_deg));
+    double t = th_deg > p->tail_core_deg ? std::pow(th_deg / p->tail_core_deg, -p->tail_pow) : 1.0;
+    return g + p->tail_amp * t;
+}
+
+// 2 pi int_0^trunc P(theta) sin(theta) dtheta with 8-point Gauss-Legendre on
+// 4096 panels per smooth piece (pieces split at the tail core).
+double radial_norm(const lidar_profile_t *p)
+{
+    static const double x8[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double w8[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    double cuts[3] = {0.0, std::min(p->tail_core_deg, p->trunc_deg), p->trunc_deg};
+    double acc = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        double a = cuts[s], b = cuts[s + 1];
+        if (!(b > a)) continue;
+        const int panels = 4096;
+        double h = (b - a) / panels;
+        for (int k = 0; k < panels; ++k) {
+            double mid = a + (k + 0.5) * h, half = 0.5 * h;
+            for (int q = 0; q < 4; ++q)
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    double th = mid + sg * x8[q] * half;
+                    acc += w8[q] * half * radial_raw(p, th) * std::sin(th * kDeg);
+                }
+        }
+    }
+    return 2.0 * kPi * acc * kDeg;
+}
+
+// Integral of the zero-extended bilinear table times the azimuthal-equidistant
+// area element sin(theta)/theta: 3x3 Gauss-Legendre per cell (exact for the
+// bilinear part, the area element is smooth).
+double table_norm(const lidar_profile_t *p, const std::vector<double> &padded, int pw, int ph)
+{
+    static const double xg[3] = {-0.7745966692414834, 0.0, 0.7745966692414834};
+    static const double wg[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    double pr = p->pitch_deg * kDeg;
+    double acc = 0.0;
+    for (int j = 0; j + 1 < ph; ++j)
+        for (int i = 0; i + 1 < pw; ++i) {
+            double t00 = padded[(size_t)j * pw + i], t10 = padded[(size_t)j * pw + i + 1];
+            double t01 = padded[(size_t)(j + 1) * pw + i], t11 = padded[(size_t)(j + 1) * pw + i + 1];
+            if (t00 == 0 && t10 == 0 && t01 == 0 && t11 == 0) continue;
+            for (int qy = 0; qy < 3; ++qy)
+                for (int qx = 0; qx < 3; ++qx) {
+                    double fx = 0.5 * (1 + xg[qx]), fy = 0.5 * (1 + xg[qy]);
+                    double val = (1 - fy) * ((1 - fx) * t00 + fx * t10) + fy * ((1 - fx) * t01 + fx * t11);
+                    // padded index i <-> table column i - 1
+                    double u = (i + fx - 1 - 0.5 * (p->table_w - 1)) * pr;
+                    double v = (j + fy - 1 - 0.5 * (p->table_h - 1)) * pr;
+                    double th = std::sqrt(u * u + v * v);
+                    double jac = th > 0 ? std::sin(th) / th : 1.0;
+                    acc += 0.25 * wg[qx] * wg[qy] * val * jac;
+                }
+        }
+    return acc * pr * pr;
+}
+
+// ---------------------------------------------------------------------------
+// Pulse taps and the EPW calibration fit (FP64)
+// ---------------------------------------------------------------------------
+
+std::vector<double> pulse_taps(const lidar_pulse_t *pu, int *Mout)
+{
+    double sigma = pu->fwhm_s / (2.0 * std::sqrt(2.0 * std::log(2.0))) / pu->dt_s;
+    int M = (int)std::ceil(pu->trunc_sigmas * sigma);
+    std::vector<double> t(2 * M + 1);
+    double s = 0.0;
+    for (int m = -M; m <= M; ++m) s += (t[m + M] = std::exp(-0.5 * (m / sigma) * (m / sigma)));
+    for (double &x : t) x /= s;
+    *Mout = M;
+    return t;
+}
+
+// EPW (m) of the single echo of a point target of energy `amp` at bin-centre
+// coordinate X (no ambient): the waveform is amp * (hat split of X onto the
+// two nearest bins) convolved with the pulse; the echo's edges are the linear
+// interpolations of the threshold crossings. Returns < 0 if there is not
+// exactly one run above T.
+double point_target_epw(const std::vector<double> &taps, int M, int n, double X, double amp, double T, double dt)
+{
+    int k0 = (int)std::floor(X);
+    double f = X - k0;
+    std::vector<double> xi(n, 0.0);
+    for (int m = -M; m <= M; ++m) {
+        int a = k0 + m, b = k0 + 1 + m;
+        if (a >= 0 && a < n) xi[a] += amp * (1 - f) * taps[m + M];
+        if (b >= 0 && b < n) xi[b] += amp * f * taps[m + M];
+    }
+    int first = -1, last = -1, runs = 0;
+    for (int k = 0; k < n; ++k) {
+        bool ab = xi[k] > T;
+        if (ab && (k == 0 || !(xi[k - 1] > T))) { ++runs; if (first < 0) first = k; }
+        if (ab) last = k;
+    }
+    if (runs != 1 || first <= 0 || last >= n - 1) return -1.0;
+    double x0 = (first - 1) + (T - xi[first - 1]) / (xi[first] - xi[first - 1]);
+    double x1 = last + (xi[last] - T) / (xi[last] - xi[last + 1]);
+    return (x1 - x0) * dt * kC * 0.5;
+}
+
+bool fit_epw(const lidar_pulse_t *pu, double T, double coef[3])
+{
+    int M = 0;
+    std::vector<double> taps = pulse_taps(pu, &M);
+    int n = 4 * M + 64;
+    // normal equations of ln a = c0 + c1 E^2 + c2 E^4
+    double A[3][4] = {{0}};
+    int used = 0;
+    for (int ia = 0; ia < 64; ++ia) {
+        double e = std::log10(50.0) + ia * (6.0 - std::log10(50.0)) / 63.0;
+        double amp = T * std::pow(10.0, e);
+        for (int ph = 0; ph < 4; ++ph) {
+            double E = point_target_epw(taps, M, n, n / 2 + 0.25 * ph, amp, T, pu->dt_s);
+            if (E < 0) continue;
+            double phi[3] = {1.0, E * E, E * E * E * E};
+            double y = std::log(amp);
+            for (int r = 0; r < 3; ++r) {
+                for (int q = 0; q < 3; ++q) A[r][q] += phi[r] * phi[q];
+                A[r][3] += phi[r] * y;
+            }
+            ++used;
+        }
+    }
+    if (used < 8) return false;
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r) if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        for (int q = 0; q < 4; ++q) std::swap(A[c][q], A[piv][q]);
+        if (A[c][c] == 0.0) return false;
+        for (int r = 0; r < 3; ++r) {
+            if (r == c) continue;
+            double f = A[r][c] / A[c][c];
+            for (int q = c; q < 4; ++q) A[r][q] -= f * A[c][q];
+        }
+    }
+    for (int r = 0; r < 3; ++r) coef[r] = A[r][3] / A[r][r];
+    return std::isfinite(coef[0]) && std::isfinite(coef[1]) && std::isfinite(coef[2]);
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+
+lidar_status_t check_create(const lidar_profile_t *p, const lidar_pattern_t *pat, const lidar_pulse_t *pu,
+                            const lidar_calib_t *ca)
+{
+    if (!p || !pat || !pu || !ca) return fail(nullptr, LIDAR_EINVAL, "null parameter struct");
+    if (p->kind == LIDAR_PROFILE_RADIAL) {
+        if (!finite_pos(p->sigma_deg)) return fail(nullptr, LIDAR_EINVAL, "profile.sigma_deg must be > 0");
+        if (!(std::isfinite(p->tail_amp) && p->tail_amp >= 0))
+            return fail(nullptr, LIDAR_EINVAL, "profile.tail_amp must be >= 0");
+        if (!finite_pos(p->tail_core_deg)) return fail(nullptr, LIDAR_EINVAL, "profile.tail_core_deg must be > 0");
+        if (!(std::isfinite(p->tail_pow) && p->tail_pow >= 0))
+            return fail(nullptr, LIDAR_EINVAL, "profile.tail_pow must be >= 0");
+        if (!finite_pos(p->trunc_deg) || p->trunc_deg > kMaxSupportDeg)
+            return fail(nullptr, LIDAR_EINVAL, "profile.trunc_deg must be in (0, 10]");
+    } else if (p->kind == LIDAR_PROFILE_TABLE) {
+        if (p->table_w < 2 || p->table_h < 2 || p->table_w > 4096 || p->table_h > 4096)
+            return fail(nullptr, LIDAR_EINVAL, "profile table size must be 2..4096 per side");
+        if (!p->table) return fail(nullptr, LIDAR_EINVAL, "profile.table is NULL");
+        if (!finite_pos(p->pitch_deg)) return fail(nullptr, LIDAR_EINVAL, "profile.pitch_deg must be > 0");
+        double hu = (0.5 * (p->table_w - 1) + 1) * p->pitch_deg, hv = (0.5 * (p->table_h - 1) + 1) * p->pitch_deg;
+        if (std::sqrt(hu * hu + hv * hv) > kMaxSupportDeg)
+            return fail(nullptr, LIDAR_EINVAL, "profile table support exceeds 10 degrees");
+        for (long i = 0; i < (long)p->table_w * p->table_h; ++i)
+            if (!(std::isfinite(p->table[i]) && p->table[i] >= 0.f))
+                return fail(nullptr, LIDAR_EINVAL, "profile.table[%ld] is negative or not finite", i);
+    } else {
+        return fail(nullptr, LIDAR_EINVAL, "profile.kind %d unknown", p->kind);
+    }
+    if (pat->n_beams < 1) return fail(nullptr, LIDAR_EINVAL, "pattern.n_beams must be >= 1");
+    if (!pat->dirs) return fail(nullptr, LIDAR_EINVAL, "pattern.dirs is NULL");
+    for (long b = 0; b < pat->n_beams; ++b) {
+        const float *d = pat->dirs + 3 * b;
+        double n = (double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2];
+        if (!(std::isfinite(n) && n > 1e-20))
+            return fail(nullptr, LIDAR_EINVAL, "pattern.dirs[%ld] is zero or not finite", b);
+    }
+    if (pu->n_bins < 32 || pu->n_bins > gbl::kMaxBins || pu->n_bins % 32 != 0)
+        return fail(nullptr, LIDAR_EINVAL, "pulse.n_bins must be a multiple of 32 in [32, %d]", gbl::kMaxBins);
+    if (!finite_pos(pu->dt_s)) return fail(nullptr, LIDAR_EINVAL, "pulse.dt_s must be > 0");
+    if (!std::isfinite(pu->t0_s)) return fail(nullptr, LIDAR_EINVAL, "pulse.t0_s must be finite");
+    if (!finite_pos(pu->fwhm_s)) return fail(nullptr, LIDAR_EINVAL, "pulse.fwhm_s must be > 0");
+    if (!finite_pos(pu->trunc_sigmas) || pu->trunc_sigmas > 12)
+        return fail(nullptr, LIDAR_EINVAL, "pulse.trunc_sigmas must be in (0, 12]");
+    double sigma = pu->fwhm_s / (2.0 * std::sqrt(2.0 * std::log(2.0))) / pu->dt_s;
+    if (std::ceil(pu->trunc_sigmas * sigma) > 2048)
+        return fail(nullptr, LIDAR_EINVAL, "pulse support exceeds 2048 bins");
+    if (!finite_pos(ca->threshold)) return fail(nullptr, LIDAR_EINVAL, "calib.threshold must be > 0");
+    if (!(std::isfinite(ca->ambient_scale) && ca->ambient_scale >= 0))
+        return fail(nullptr, LIDAR_EINVAL, "calib.ambient_scale must be >= 0");
+    if (ca->max_echoes < 1 || ca->max_echoes > 3) return fail(nullptr, LIDAR_EINVAL, "calib.max_echoes must be 1..3");
+    if (!ca->fit_epw)
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(ca->epw_coef[i])) return fail(nullptr, LIDAR_EINVAL, "calib.epw_coef not finite");
+    return LIDAR_OK;
+}
+
+lidar_status_t check_gbuffer(lidar_t *l, const lidar_gbuffer_t *g)
+{
+    if (!g) return fail(l, LIDAR_EINVAL, "gbuffer is NULL");
+    if (g->U < 1 || g->V < 1) return fail(l, LIDAR_EINVAL, "gbuffer U, V must be >= 1");
+    if ((long long)g->U * g->V > (1LL << 30)) return fail(l, LIDAR_EINVAL, "gbuffer has more than 2^30 pixels");
+    if (!finite_pos(g->daz) || !finite_pos(g->del) || !std::isfinite(g->az0) || !std::isfinite(g->el0))
+        return fail(l, LIDAR_EINVAL, "gbuffer angles must be finite with daz, del > 0");
+    if (g->U * g->daz > 2 * kPi * (1 + 1e-9)) return fail(l, LIDAR_EINVAL, "gbuffer azimuth span exceeds 2 pi");
+    if (g->el0 < -0.5 * kPi - 1e-9 || g->el0 + g->V * g->del > 0.5 * kPi + 1e-9)
+        return fail(l, LIDAR_EINVAL, "gbuffer elevation span leaves [-pi/2, pi/2]");
+    if (!g->range || !g->nx || !g->ny || !g->nz || !g->rho_d || !g->retro || !g->ambient)
+        return fail(l, LIDAR_EINVAL, "gbuffer plane pointer is NULL");
+    return LIDAR_OK;
+}
+
+lidar_status_t check_pose(lidar_t *l, const lidar_pose_t *p, double R[9])
+{
+    static const double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (!p) { std::memcpy(R, I, sizeof I); return LIDAR_OK; }
+    for (int i = 0; i < 9; ++i) {
+        R[i] = p->R[i];
+        if (!std::isfinite(R[i])) return fail(l, LIDAR_EINVAL, "pose.R not finite");
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
+            if (std::fabs(s - (a == b)) > 1e-3) return fail(l, LIDAR_EINVAL, "pose.R is not orthonormal");
+        }
+    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (det < 0) return fail(l, LIDAR_EINVAL, "pose.R is a reflection");
+    return LIDAR_OK;
+}
+
+lidar_status_t ensure_scratch(lidar_t *l, size_t pixels)
+{
+    if (pixels <= l->rec_cap) return LIDAR_OK;
+    if (l->d_rec) cudaFree(l->d_rec);
+    l->d_rec = nullptr;
+    l->rec_cap = 0;
+    cudaError_t e = cudaMalloc(&l->d_rec, pixels * 2 * sizeof(float4));
+    if (e != cudaSuccess) return cuda_fail(l, e, "cudaMalloc(per-pixel records)");
+    l->rec_cap = pixels;
+    return LIDAR_OK;
+}
+
+void free_events(lidar_t *l)
+{
+    for (cudaEvent_t e : l->ev) cudaEventDestroy(e);
+    l->ev.clear();
+    l->ev_used = 0;
+}
+
+// Returns the next event of the profiling pool (creating it if needed), or
+// nullptr when profiling is off.
+cudaEvent_t next_event(lidar_t *l)
+{
+    if (!l->prof) return nullptr;
+    if (l->ev_used == l->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        l->ev.push_back(e);
+    }
+    return l->ev[l->ev_used++];
+}
+
+void free_all(lidar_t *l)
+{
+    free_events(l);
+    cudaFree(l->d_dirs);
+    cudaFree(l->d_quads);
+    cudaFree(l->d_taps);
+    cudaFree(l->d_beams);
+    cudaFree(l->d_rec);
+    cudaFree(l->d_planes);
+    cudaFree(l->d_wave);
+    cudaFree(l->d_echo);
+    cudaFree(l->d_counts);
+}
+
+lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
+                       int32_t *counts, cudaStream_t s)
+{
+    size_t pixels = (size_t)g->U * g->V;
+    lidar_status_t st = ensure_scratch(l, pixels);
+    if (st != LIDAR_OK) return st;
+    bool panorama = std::fabs(g->U * g->daz - 2 * kPi) <= 1e-6;
+
+    gbl::SetupArgs sa{};
+    sa.U = g->U; sa.V = g->V;
+    sa.az0 = (float)g->az0; sa.el0 = (float)g->el0; sa.daz = (float)g->daz; sa.del = (float)g->del;
+    sa.ch = (float)std::cos(0.5 * g->daz); sa.sh = (float)std::sin(0.5 * g->daz);
+    sa.cv = (float)std::cos(0.5 * g->del); sa.sv = (float)std::sin(0.5 * g->del);
+    sa.range = g->range; sa.nx = g->nx; sa.ny = g->ny; sa.nz = g->nz;
+    sa.rho = g->rho_d; sa.retro = g->retro; sa.amb = g->ambient;
+    sa.rec = l->d_rec;
+    sa.x_scale = (float)(2.0 / (kC * l->dt));
+    sa.x_off = (float)(-l->t0 / l->dt - 0.5);
+    sa.n_bins = l->n_bins;
+    long pb = (long)((pixels + 255) / 256);
+    sa.pix_blocks = (int)std::min<long>(pb, 152L * 64);
+    sa.n_beams = l->n_beams;
+    sa.dirs = l->d_dirs;
+    for (int i = 0; i < 9; ++i) sa.R[i] = R[i];
+    sa.az0d = g->az0; sa.el0d = g->el0; sa.dazd = g->daz; sa.deld = g->del;
+    sa.panorama = panorama ? 1 : 0;
+    sa.support_rad = l->support_rad;
+    sa.beams = l->d_beams;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    if (l->prof) {
+        size_t mark = l->ev_used;
+        ev0 = next_event(l); ev1 = next_event(l); ev2 = next_event(l);
+        if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
+    }
+    if (ev0) cudaEventRecord(ev0, s);
+    cudaError_t e = gbl::launch_setup(sa, s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    if (ev1) cudaEventRecord(ev1, s);
+
+    gbl::FootprintArgs fa{};
+    fa.U = g->U; fa.V = g->V; fa.panorama = sa.panorama;
+    fa.az0 = sa.az0; fa.el0 = sa.el0; fa.daz = sa.daz; fa.del = sa.del;
+    fa.rec = l->d_rec;
+    fa.beams = l->d_beams;
+    fa.n_beams = l->n_beams;
+    fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
+    fa.invZ = (float)(1.0 / l->Z);
+    fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
+    fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
+    fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
+    fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
+    fa.T = (float)l->T; fa.s_amb = (float)l->s_amb; fa.max_echoes = l->max_echoes;
+    fa.c0 = (float)l->coef[0]; fa.c1 = (float)l->coef[1]; fa.c2 = (float)l->coef[2];
+    fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
+    fa.rB = (float)(0.5 * kC * l->dt);
+    fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
+    e = gbl::launch_footprint(l->kind, l->G, l->threads, l->smem, fa, s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
+    if (ev2) cudaEventRecord(ev2, s);
+    return LIDAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat, const lidar_pulse_t *pu,
+                            const lidar_calib_t *ca, lidar_t **out)
+{
+    if (!out) return fail(nullptr, LIDAR_EINVAL, "out is NULL");
+    *out = nullptr;
+    lidar_status_t st = check_create(p, pat, pu, ca);
+    if (st != LIDAR_OK) return st;
+    lidar_t *l = new (std::nothrow) lidar();
+    if (!l) return fail(nullptr, LIDAR_ENOMEM, "host allocation failed");
+    l->n_beams = pat->n_beams;
+    l->kind = p->kind;
+    l->n_bins = pu->n_bins;
+    l->dt = pu->dt_s;
+    l->t0 = pu->t0_s;
+    l->T = ca->threshold;
+    l->s_amb = ca->ambient_scale;
+    l->max_echoes = ca->max_echoes;
+
+    // profile normalisation and device form
+    std::vector<float4> quads;
+    if (p->kind == LIDAR_PROFILE_RADIAL) {
+        l->Z = radial_norm(p);
+        double s = p->sigma_deg * kDeg, tc = p->tail_core_deg * kDeg, tr = p->trunc_deg * kDeg;
+        l->kg = (float)(-1.0 / (2.0 * s * s * std::log(2.0)));
+        l->trunc2 = (float)(tr * tr);
+        l->tail_amp = (float)p->tail_amp;
+        l->tc2_inv = (float)(1.0 / (tc * tc));
+        l->tail_hp = (float)(-0.5 * p->tail_pow);
+        l->support_rad = tr;
+    } else {
+        int pw = p->table_w + 2, ph = p->table_h + 2;
+        std::vector<double> padded((size_t)pw * ph, 0.0);
+        for (int j = 0; j < p->table_h; ++j)
+            for (int i = 0; i < p->table_w; ++i)
+                padded[(size_t)(j + 1) * pw + i + 1] = p->table[(size_t)j * p->table_w + i];
+        l->Z = table_norm(p, padded, pw, ph);
+        l->qw = p->table_w + 1;
+        l->qh = p->table_h + 1;
+        quads.resize((size_t)l->qw * l->qh);
+        for (int j = 0; j < l->qh; ++j)
+            for (int i = 0; i < l->qw; ++i) {
+                auto at = [&](int ii, int jj) { return (float)(padded[(size_t)jj * pw + ii] / l->Z); };
+                quads[(size_t)j * l->qw + i] = make_float4(at(i, j), at(i + 1, j), at(i, j + 1), at(i + 1, j + 1));
+            }
+        l->tk = (float)(1.0 / (p->pitch_deg * kDeg));
+        l->tcu = (float)(0.5 * (p->table_w - 1) + 1.0);
+        l->tcv = (float)(0.5 * (p->table_h - 1) + 1.0);
+        double hu = (0.5 * (p->table_w - 1) + 1) * p->pitch_deg, hv = (0.5 * (p->table_h - 1) + 1) * p->pitch_deg;
+        l->support_rad = std::sqrt(hu * hu + hv * hv) * kDeg;
+    }
+    if (!(std::isfinite(l->Z) && l->Z > 0)) {
+        double Z = l->Z;
+        delete l;
+        return fail(nullptr, LIDAR_ENUMERIC, "profile integrates to %g", Z);
+    }
+
+    // pulse taps, zero-padded so that every tap index of the 32x32 blocks of
+    // the convolution is in range
+    int M = 0;
+    std::vector<double> taps = pulse_taps(pu, &M);
+    l->M = M;
+    l->R = (M + 31) / 32;
+    l->tp_off = 32 * l->R + 31;
+    l->tp_len = 64 * l->R + 63;
+    std::vector<float> tpad(l->tp_len, 0.f);
+    for (int m = -M; m <= M; ++m) tpad[l->tp_off + m] = (float)taps[m + M];
+
+    if (ca->fit_epw) {
+        if (!fit_epw(pu, ca->threshold, l->coef)) {
+            delete l;
+            return fail(nullptr, LIDAR_ENUMERIC, "EPW calibration fit failed");
+        }
+    } else {
+        for (int i = 0; i < 3; ++i) l->coef[i] = ca->epw_coef[i];
+    }
+
+    // launch shape: largest beam group whose histograms fit in shared memory
+    // while leaving at least two groups per SM of a 152-SM part
+    cudaError_t e = cudaGetDevice(&l->device);
+    if (e != cudaSuccess) { delete l; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    int smem_optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, l->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, l->device);
+    gbl::FootprintArgs probe{};
+    probe.n_bins = l->n_bins;
+    probe.M = l->M;
+    int chosen = 0;
+    for (int G : {8, 4, 2}) {
+        size_t need = gbl::footprint_smem_bytes(G, probe);
+        if ((long)need > smem_optin) continue;
+        long groups = (l->n_beams + G - 1) / G;
+        if (G > 2 && groups < 2L * sms) continue;
+        chosen = G;
+        break;
+    }
+    if (!chosen) {
+        chosen = 2;
+        if ((long)gbl::footprint_smem_bytes(2, probe) > smem_optin) {
+            delete l;
+            return fail(nullptr, LIDAR_EINVAL, "n_bins too large for shared memory");
+        }
+    }
+    l->G = chosen;
+    l->threads = 512;
+    l->smem = gbl::footprint_smem_bytes(l->G, probe);
+    e = gbl::prepare_footprint(l->kind, l->G, l->smem);
+    if (e != cudaSuccess) { delete l; return cuda_fail(nullptr, e, "cudaFuncSetAttribute"); }
+
+    // device copies
+    size_t nd = (size_t)pat->n_beams * 3 * sizeof(float);
+    if ((e = cudaMalloc(&l->d_dirs, nd)) != cudaSuccess ||
+        (e = cudaMemcpy(l->d_dirs, pat->dirs, nd, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&l->d_taps, tpad.size() * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemcpy(l->d_taps, tpad.data(), tpad.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&l->d_beams, (size_t)pat->n_beams * sizeof(gbl::BeamParam))) != cudaSuccess) {
+        free_all(l);
+        delete l;
+        return cuda_fail(nullptr, e, "device allocation at create");
+    }
+    if (!quads.empty()) {
+        if ((e = cudaMalloc(&l->d_quads, quads.size() * sizeof(float4))) != cudaSuccess ||
+            (e = cudaMemcpy(l->d_quads, quads.data(), quads.size() * sizeof(float4), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+            free_all(l);
+            delete l;
+            return cuda_fail(nullptr, e, "profile table upload");
+        }
+    }
+    *out = l;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_simulate(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
+                              lidar_echoes_t *echoes, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    lidar_status_t st = check_gbuffer(l, g);
+    if (st != LIDAR_OK) return st;
+    double R[9];
+    if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
+    if (!wave || !echoes || !echoes->echoes || !echoes->counts)
+        return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    return enqueue(l, g, R, wave, echoes->echoes, echoes->counts, (cudaStream_t)stream);
+}
+
+lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
+                                   lidar_echo_t *echoes, int32_t *counts, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    lidar_status_t st = check_gbuffer(l, g);
+    if (st != LIDAR_OK) return st;
+    double R[9];
+    if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
+    if (!wave || !echoes || !counts) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t pixels = (size_t)g->U * g->V;
+    cudaError_t e;
+    if (pixels > l->planes_cap) {
+        cudaFree(l->d_planes);
+        l->d_planes = nullptr;
+        l->planes_cap = 0;
+        if ((e = cudaMalloc(&l->d_planes, 7 * pixels * sizeof(float))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(G-buffer staging)");
+        l->planes_cap = pixels;
+    }
+    if (!l->d_wave) {
+        if ((e = cudaMalloc(&l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t))) != cudaSuccess ||
+            (e = cudaMalloc(&l->d_counts, (size_t)l->n_beams * sizeof(int32_t))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(output staging)");
+    }
+    const float *src[7] = {g->range, g->nx, g->ny, g->nz, g->rho_d, g->retro, g->ambient};
+    lidar_gbuffer_t dg = *g;
+    float *dst[7];
+    for (int i = 0; i < 7; ++i) {
+        dst[i] = l->d_planes + (size_t)i * pixels;
+        if ((e = cudaMemcpyAsync(dst[i], src[i], pixels * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(l, e, "G-buffer upload");
+    }
+    dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
+    dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
+    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s)) != LIDAR_OK) return st;
+    if ((e = cudaMemcpyAsync(wave, l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
+                             cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+        return cuda_fail(l, e, "result download");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_sync(lidar_t *l, void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(l, e, "asynchronous error");
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_get_info(const lidar_t *l, int32_t *n_beams, int32_t *n_bins, int32_t *max_echoes,
+                              double *profile_norm, double epw_coef[3])
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (n_beams) *n_beams = l->n_beams;
+    if (n_bins) *n_bins = l->n_bins;
+    if (max_echoes) *max_echoes = l->max_echoes;
+    if (profile_norm) *profile_norm = l->Z;
+    if (epw_coef) for (int i = 0; i < 3; ++i) epw_coef[i] = l->coef[i];
+    return LIDAR_OK;
+}
+
+int32_t lidar_launches_per_simulate(const lidar_t *l) { return l ? 2 : 0; }
+
+lidar_status_t lidar_profile_enable(lidar_t *l, int32_t enable)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    free_events(l);
+    l->prof = enable != 0;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_profile_read(lidar_t *l, double total_ms[2], int32_t launches[2])
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    double t[2] = {0, 0};
+    int32_t n[2] = {0, 0};
+    for (size_t i = 0; i + 3 <= l->ev_used; i += 3) {
+        cudaError_t e = cudaEventSynchronize(l->ev[i + 2]);
+        if (e != cudaSuccess) return cuda_fail(l, e, "cudaEventSynchronize");
+        float a = 0, b = 0;
+        if ((e = cudaEventElapsedTime(&a, l->ev[i], l->ev[i + 1])) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&b, l->ev[i + 1], l->ev[i + 2])) != cudaSuccess)
+            return cuda_fail(l, e, "cudaEventElapsedTime");
+        t[0] += a; t[1] += b; n[0] += 1; n[1] += 1;
+    }
+    l->ev_used = 0;
+    if (total_ms) { total_ms[0] = t[0]; total_ms[1] = t[1]; }
+    if (launches) { launches[0] = n[0]; launches[1] = n[1]; }
+    return LIDAR_OK;
+}
+
+const char *lidar_last_error(const lidar_t *l) { return l ? l->err : g_create_err; }
+
+void lidar_destroy(lidar_t *l)
+{
+    if (!l) return;
+    free_all(l);
+    delete l;
+}
+
+}  // extern "C"

@@ -1,0 +1,638 @@
+// sm_103a kernels of the beam model (Alg. 1 beam iteration with the EPW
+// post-processing of Sec. II-C).
+//
+//   setup_kernel      one launch, two roles:
+//                     - per pixel: rho_hat * d omega, the time-of-flight
+//                       interval from the plane extrapolation of Sec. II-D
+//                       (pixelRangeInterval of Alg. 1), ambient * d omega, and
+//                       the pixel's range-bin deposit written as difference
+//                       coefficients -> one 32-byte record;
+//                     - per beam (FP64): pose-rotated axis, its pixel-grid
+//                       coordinates, the local frame's roll and the candidate
+//                       pixel box.
+//   footprint_wave_kernel  one CTA per group of G consecutive beams:
+//                     - profile weight (Eq. centered kernel) for every
+//                       (beam, pixel) pair of the group's box, accumulated into
+//                       per-beam difference histograms in shared memory;
+//                     - prefix sum -> histogram xi_b;
+//                     - pulse convolution varpi * xi_b + ambient (Sec. II-C),
+//                       skipping 32-bin chunks that no deposit touched;
+//                     - echo intervals, EPW, peak and intensity.
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "lidar_internal.h"
+
+namespace gbl {
+
+// --------------------------------------------------------------------------
+// setup: per-pixel records
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ float hatf(float x) { return fmaxf(0.f, 1.f - fabsf(x)); }
+
+// Mean of hat(x - k) over [X0, X1] (bin-centre units): the interval is cut at
+// the kinks k-1, k, k+1; on each piece the hat is linear, so the piece's
+// contribution is its length times the hat at its midpoint.
+__device__ float mean_hat(float X0, float X1, float k)
+{
+    float W = X1 - X0;
+    if (!(W > 0.f)) return hatf(X0 - k);
+    float lo = X0, acc = 0.f;
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) {
+        float cut = k + (float)c;
+        if (cut > lo && cut < X1) {
+            acc += (cut - lo) * hatf(0.5f * (lo + cut) - k);
+            lo = cut;
+        }
+    }
+    acc += (X1 - lo) * hatf(0.5f * (lo + X1) - k);
+    return acc / W;
+}
+
+__device__ void setup_pixel(const SetupArgs &A, int idx)
+{
+    int v = idx / A.U;
+    int u = idx - v * A.U;
+    float az = A.az0 + ((float)u + 0.5f) * A.daz;
+    float el = A.el0 + ((float)v + 0.5f) * A.del;
+    float sa, ca, se, ce;
+    sincosf(az, &sa, &ca);
+    sincosf(el, &se, &ce);
+    // exact solid angle of the cell: daz (sin(el + del/2) - sin(el - del/2))
+    float domega = 2.f * A.daz * ce * A.sv;
+    float L = A.amb[idx];
+    float a = isfinite(L) ? L * domega : 0.f;
+    float rr = A.range[idx];
+    uint32_t kab = kNoDeposit;
+    float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, cr = 0.f;
+    if (isfinite(rr) && rr > 0.f) {
+        float nx = A.nx[idx], ny = A.ny[idx], nz = A.nz[idx];
+        float dn = ce * (ca * nx + sa * ny) + se * nz;
+        float beta = A.rho[idx] * (1.f / CUDART_PI_F) + A.retro[idx];
+        // rho_hat d omega = beta |cos theta_i| / R^2 * d omega
+        float w = beta * fabsf(dn) / (rr * rr) * domega;
+        // range interval: plane through the hit point, extrapolated to the four
+        // corner rays (r_c = r * (d.n) / (d_c.n)), normal facing the sensor
+        float sgn = dn > 0.f ? -1.f : 1.f;
+        float mup = fmaxf(-sgn * dn, kMuMin);
+        float rmin = rr, rmax = rr;
+#pragma unroll
+        for (int cj = -1; cj <= 1; cj += 2)
+#pragma unroll
+            for (int ci = -1; ci <= 1; ci += 2) {
+                float cac = ca * A.ch - (float)ci * sa * A.sh;
+                float sac = sa * A.ch + (float)ci * ca * A.sh;
+                float cec = ce * A.cv - (float)cj * se * A.sv;
+                float sec = se * A.cv + (float)cj * ce * A.sv;
+                float dcn = cec * (cac * nx + sac * ny) + sec * nz;
+                float rc = rr * mup / fmaxf(-sgn * dcn, kMuMin);
+                rmin = fminf(rmin, rc);
+                rmax = fmaxf(rmax, rc);
+            }
+        float X0 = rmin * A.x_scale + A.x_off;
+        float X1 = rmax * A.x_scale + A.x_off;
+        const float nb = (float)A.n_bins;
+        float f = floorf(X0);
+        // the hat functions of bins 0..n-1 cover (-1, n): anything else is dropped
+        if (w > 0.f && X1 > -1.f && X0 < nb) {
+            if (X1 <= f + 3.f) {
+                // narrow: at most 4 bins f..f+3 touched
+                if (f >= -3.f) {
+                    h0 = w * mean_hat(X0, X1, f);
+                    h1 = w * mean_hat(X0, X1, f + 1.f);
+                    h2 = w * mean_hat(X0, X1, f + 2.f);
+                    h3 = w * mean_hat(X0, X1, f + 3.f);
+                    kab = (uint32_t)((int)f + kBinBias) | (0xFFFFu << 16);
+                }
+            } else {
+                // wide (X1 - X0 > 2): partial bins f, f+1 and g, g+1, every bin
+                // in between fully covered with weight w / (X1 - X0)
+                float g = floorf(X1);
+                h0 = w * mean_hat(X0, X1, f);
+                h1 = w * mean_hat(X0, X1, f + 1.f);
+                h2 = w * mean_hat(X0, X1, g);
+                h3 = w * mean_hat(X0, X1, g + 1.f);
+                cr = w / (X1 - X0);
+                // bins far outside the window: zero weight, parked next to it
+                // (the run between them keeps its extent)
+                if (f < -4.f) { f = -4.f; h0 = 0.f; h1 = 0.f; }
+                if (g > nb + 2.f) { g = nb + 2.f; h2 = 0.f; h3 = 0.f; }
+                kab = (uint32_t)((int)f + kBinBias) | ((uint32_t)((int)g + kBinBias) << 16);
+            }
+        }
+    }
+    float4 r0 = make_float4(__uint_as_float(kab), a, h0, h1);
+    float4 r1 = make_float4(h2, h3, cr, 0.f);
+    A.rec[2 * (size_t)idx] = r0;
+    A.rec[2 * (size_t)idx + 1] = r1;
+}
+
+// --------------------------------------------------------------------------
+// setup: per-beam parameters (FP64)
+// --------------------------------------------------------------------------
+
+__device__ void setup_beam(const SetupArgs &A, int b)
+{
+    double d[3] = {A.dirs[3 * b], A.dirs[3 * b + 1], A.dirs[3 * b + 2]};
+    double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    d[0] /= nd; d[1] /= nd; d[2] /= nd;
+    double e1[3] = {-d[1], d[0], 0.0};
+    double ne = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    if (ne < 1e-12) { e1[0] = 0.0; e1[1] = 1.0; ne = 1.0; }
+    e1[0] /= ne; e1[1] /= ne;
+    double a[3], E1[3];
+    for (int r = 0; r < 3; ++r) {
+        a[r] = A.R[3 * r] * d[0] + A.R[3 * r + 1] * d[1] + A.R[3 * r + 2] * d[2];
+        E1[r] = A.R[3 * r] * e1[0] + A.R[3 * r + 1] * e1[1] + A.R[3 * r + 2] * e1[2];
+    }
+    double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    a[0] /= na; a[1] /= na; a[2] /= na;
+    double el_b = asin(fmin(1.0, fmax(-1.0, a[2])));
+    double az_b = atan2(a[1], a[0]);
+    const double two_pi = 2.0 * CUDART_PI;
+    if (A.panorama) {
+        while (az_b < A.az0d) az_b += two_pi;
+        while (az_b >= A.az0d + two_pi) az_b -= two_pi;
+    }
+    double sab, cab, seb, ceb;
+    sincos(az_b, &sab, &cab);
+    sincos(el_b, &seb, &ceb);
+    // east/north frame of the axis in the G-buffer frame
+    double g1[3] = {-sab, cab, 0.0};
+    double g2[3] = {-seb * cab, -seb * sab, ceb};
+    double cg = E1[0] * g1[0] + E1[1] * g1[1] + E1[2] * g1[2];
+    double sg = E1[0] * g2[0] + E1[1] * g2[1] + E1[2] * g2[2];
+    double ng = sqrt(cg * cg + sg * sg);
+    if (ng > 0) { cg /= ng; sg /= ng; } else { cg = 1.0; sg = 0.0; }
+    double ua = (az_b - A.az0d) / A.dazd - 0.5;
+    double va = (el_b - A.el0d) / A.deld - 0.5;
+    BeamParam P;
+    P.ci = (int)floor(ua);
+    P.cf = (float)(ua - floor(ua));
+    P.ri = (int)floor(va);
+    P.rf = (float)(va - floor(va));
+    P.sin_elb = (float)seb;
+    P.cos_elb = (float)ceb;
+    P.cg = (float)cg;
+    P.sg = (float)sg;
+    double th = A.support_rad;
+    long r0 = (long)ceil((el_b - th - A.el0d) / A.deld - 0.5) - 1;
+    long r1 = (long)floor((el_b + th - A.el0d) / A.deld - 0.5) + 1;
+    if (r0 < 0) r0 = 0;
+    if (r1 > A.V - 1) r1 = A.V - 1;
+    long c0, c1;
+    bool full = fabs(el_b) + th >= 0.5 * CUDART_PI - 1e-9;
+    if (!full) {
+        double dl = asin(fmin(1.0, sin(th) / ceb));
+        c0 = (long)ceil((az_b - dl - A.az0d) / A.dazd - 0.5) - 1;
+        c1 = (long)floor((az_b + dl - A.az0d) / A.dazd - 0.5) + 1;
+        if (A.panorama && c1 - c0 + 1 >= A.U) full = true;
+    }
+    if (full) {
+        if (A.panorama) { c0 = P.ci - A.U / 2; c1 = c0 + A.U - 1; }
+        else { c0 = 0; c1 = A.U - 1; }
+    }
+    if (!A.panorama) {
+        if (c0 < 0) c0 = 0;
+        if (c1 > A.U - 1) c1 = A.U - 1;
+    }
+    P.row0 = (int)r0; P.row1 = (int)r1;
+    P.col0 = (int)c0; P.col1 = (int)c1;
+    P.valid = (r0 <= r1 && c0 <= c1) ? 1 : 0;
+    P.pad0 = 0; P.pad1 = 0.f; P.pad2 = 0.f;
+    A.beams[b] = P;
+}
+
+__global__ void __launch_bounds__(256) setup_kernel(SetupArgs A)
+{
+    if ((int)blockIdx.x < A.pix_blocks) {
+        int n = A.U * A.V;
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += A.pix_blocks * blockDim.x)
+            setup_pixel(A, idx);
+    } else {
+        int b = (blockIdx.x - A.pix_blocks) * blockDim.x + threadIdx.x;
+        if (b < A.n_beams) setup_beam(A, b);
+    }
+}
+
+cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s)
+{
+    int beam_blocks = (a.n_beams + 255) / 256;
+    setup_kernel<<<a.pix_blocks + beam_blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// footprint + waveform + echoes
+// --------------------------------------------------------------------------
+
+constexpr int kSeg = 32;     // columns per work unit
+constexpr int kBlk = 256;    // waveform bins per convolution work item (8 per lane)
+
+// Per-beam histogram buffer: bins [-pad, n_bins + pad) at positions
+// x = bin + pad, stored at x + (x >> 5) so that lanes reading bins 8 apart hit
+// distinct banks. pad >= M + 16 and is a multiple of 32.
+struct Layout {
+    int pad;       // zero padding on each side, in bins
+    int HB;        // floats per beam buffer (odd)
+    int taps_off;  // tap m lives at index taps_off + m
+    int taps_len;
+    size_t off_taps, off_amb, off_supp, off_bp, total;
+};
+
+__host__ __device__ inline int skew(int x) { return x + (x >> 5); }
+
+__host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
+{
+    Layout L;
+    L.pad = 32 * ((M + 16 + 31) / 32);
+    int span = n_bins + 2 * L.pad;
+    L.HB = skew(span) + 1;
+    if ((L.HB & 1) == 0) L.HB += 1;
+    L.taps_off = M + 8;
+    L.taps_len = 2 * M + 17;
+    size_t off = (size_t)G * L.HB * 4;
+    L.off_taps = off; off += (size_t)L.taps_len * 4;
+    L.off_amb = off; off += (size_t)G * 4;
+    L.off_supp = off; off += (size_t)G * 8;
+    off = (off + 15) & ~(size_t)15;
+    L.off_bp = off; off += (size_t)G * sizeof(BeamParam);
+    L.total = off;
+    return L;
+}
+
+// Profile weight of a local offset (x, y) = (sin theta) * (unit offset
+// direction), i.e. the components of the pixel direction along the beam's
+// local axes. s2 = x^2 + y^2 = sin^2 theta.
+template <int KIND>
+__device__ __forceinline__ float profile_weight(const FootprintArgs &A, float x, float y)
+{
+    float s2 = fmaf(x, x, y * y);
+    if (KIND == LIDAR_PROFILE_RADIAL) {
+        // theta^2 = asin(s)^2 = s^2 (1 + s^2/3 + 8 s^4/45 + ...)
+        float t2 = s2 * fmaf(s2, fmaf(s2, 8.f / 45.f, 1.f / 3.f), 1.f);
+        if (t2 > A.trunc2) return 0.f;
+        float g = exp2f(t2 * A.kg);
+        float r = t2 * A.tc2_inv;
+        float tail = r <= 1.f ? 1.f : exp2f(A.tail_hp * __log2f(r));
+        return fmaf(A.tail_amp, tail, g) * A.invZ;
+    } else {
+        // azimuthal-equidistant coordinates: (x, y) * theta / sin theta,
+        // theta / sin theta = asin(s)/s = 1 + s^2/6 + 3 s^4/40 + ...
+        float f = fmaf(s2, fmaf(s2, 3.f / 40.f, 1.f / 6.f), 1.f) * A.tk;
+        float fu = fmaf(x, f, A.tcu);
+        float fv = fmaf(y, f, A.tcv);
+        float iu = floorf(fu), iv = floorf(fv);
+        int i = (int)iu, j = (int)iv;
+        if ((unsigned)i >= (unsigned)A.qw || (unsigned)j >= (unsigned)A.qh) return 0.f;
+        float fx = fu - iu, fy = fv - iv;
+        float4 q = __ldg(A.quads + (size_t)j * A.qw + i);
+        float top = fmaf(fx, q.y - q.x, q.x);
+        float bot = fmaf(fx, q.w - q.z, q.z);
+        return fmaf(fy, bot - top, top);
+    }
+}
+
+template <int KIND, int G>
+__global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = A.n_bins, M = A.M;
+    const Layout Ly = make_layout(G, nb, M);
+    const int pad = Ly.pad;
+    float *hbuf = reinterpret_cast<float *>(smem_raw);
+    float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
+    float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
+    int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
+    BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int b0 = blockIdx.x * G;
+    const int gcount = min(G, A.n_beams - b0);
+
+    // ---- phase 0: clear, load parameters, union box ----------------------
+    for (int i = tid; i < G * Ly.HB; i += blockDim.x) hbuf[i] = 0.f;
+    for (int i = tid; i < Ly.taps_len; i += blockDim.x) {
+        int m = i - Ly.taps_off;
+        taps[i] = (m >= -M && m <= M) ? A.taps_pad[A.tp_off + m] : 0.f;
+    }
+    if (tid < G) {
+        amb_s[tid] = 0.f;
+        BeamParam P;
+        if (tid < gcount) P = A.beams[b0 + tid];
+        else { P = BeamParam{}; P.valid = 0; }
+        bp[tid] = P;
+    }
+    __syncthreads();
+    if (tid < G && A.panorama) {
+        // keep all boxes of the group in the unwrapped period of the first valid beam
+        int ref = -1;
+        for (int j = 0; j < gcount; ++j) if (bp[j].valid) { ref = bp[j].ci; break; }
+        BeamParam &P = bp[tid];
+        if (P.valid && ref >= 0) {
+            int sh = 0;
+            while (P.ci + sh - ref > A.U / 2) sh -= A.U;
+            while (P.ci + sh - ref < -A.U / 2) sh += A.U;
+            P.ci += sh; P.col0 += sh; P.col1 += sh;
+        }
+    }
+    __syncthreads();
+    int R0 = 1 << 30, R1 = -(1 << 30), C0 = 1 << 30, C1 = -(1 << 30);
+    for (int j = 0; j < gcount; ++j) {
+        const BeamParam &P = bp[j];
+        if (!P.valid) continue;
+        R0 = min(R0, P.row0); R1 = max(R1, P.row1);
+        C0 = min(C0, P.col0); C1 = max(C1, P.col1);
+    }
+
+    // ---- phase 1: profile-weighted deposits into the range bins -----------
+    constexpr int LR = kWarp / G;  // work units per warp step
+    const int j = lane % G;
+    const int rsub = lane / G;
+    float amb_acc = 0.f;
+    if (R0 <= R1) {
+        const int nseg = (C1 - C0 + kSeg) / kSeg;
+        const int nunits = (R1 - R0 + 1) * nseg;
+        const BeamParam P = bp[j];
+        const bool jok = (j < gcount) && P.valid;
+        float *hj = hbuf + j * Ly.HB;
+        for (int ubase = warp * LR; ubase < nunits; ubase += nwarps * LR) {
+            int unit = ubase + rsub;
+            if (unit >= nunits || !jok) continue;
+            int row = R0 + unit / nseg;
+            int seg = unit - (unit / nseg) * nseg;
+            if (row < P.row0 || row > P.row1) continue;
+            int cbeg = max(C0 + seg * kSeg, P.col0);
+            int cend = min(C0 + seg * kSeg + kSeg - 1, P.col1);
+            if (cbeg > cend) continue;
+            float el = A.el0 + ((float)row + 0.5f) * A.del;
+            float cosEl = cosf(el);
+            float dEl = ((float)(row - P.ri) - P.rf) * A.del;
+            float sdEl = sinf(dEl), cdEl = cosf(dEl);
+            float Kv = P.sin_elb * cosEl;
+            float Kc = P.cos_elb * cosEl;
+            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
+            float daz0 = ((float)(cbeg - P.ci) - P.cf) * A.daz;
+            for (int c = cbeg; c <= cend; ++c) {
+                int cw = c;
+                if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                float4 r0 = __ldg(recrow + 2 * cw);
+                uint32_t kab = __float_as_uint(r0.x);
+                float a = r0.y;
+                if (kab == kNoDeposit && a == 0.f) continue;
+                float dAz = fmaf((float)(c - cbeg), A.daz, daz0);
+                float sD, vers;
+                if (fabsf(dAz) <= 0.1f) {
+                    float z2 = dAz * dAz;
+                    sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
+                    vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
+                } else {
+                    float cD;
+                    __sincosf(dAz, &sD, &cD);
+                    vers = 1.f - cD;
+                    // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
+                    if (fmaf(-Kc, vers, cdEl) <= 0.f) continue;
+                }
+                float xg = cosEl * sD;
+                float yg = fmaf(Kv, vers, sdEl);
+                float x = fmaf(P.cg, xg, P.sg * yg);
+                float y = fmaf(P.cg, yg, -P.sg * xg);
+                float Pw = profile_weight<KIND>(A, x, y);
+                if (!(Pw > 0.f)) continue;
+                amb_acc = fmaf(Pw, a, amb_acc);
+                if (kab == kNoDeposit) continue;
+                float4 r1 = __ldg(recrow + 2 * cw + 1);
+                int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
+                uint32_t gq = kab >> 16;
+                if (gq == 0xFFFFu) {
+                    // narrow: hat weights on 4 consecutive bins
+                    if (r0.z != 0.f) atomicAdd(hj + skew(xf), Pw * r0.z);
+                    if (r0.w != 0.f) atomicAdd(hj + skew(xf + 1), Pw * r0.w);
+                    if (r1.x != 0.f) atomicAdd(hj + skew(xf + 2), Pw * r1.x);
+                    if (r1.y != 0.f) atomicAdd(hj + skew(xf + 3), Pw * r1.y);
+                } else {
+                    // wide: two partial bins at each end, a constant run between
+                    int xg2 = (int)gq - kBinBias + pad;
+                    atomicAdd(hj + skew(xf), Pw * r0.z);
+                    atomicAdd(hj + skew(xf + 1), Pw * r0.w);
+                    atomicAdd(hj + skew(xg2), Pw * r1.x);
+                    atomicAdd(hj + skew(xg2 + 1), Pw * r1.y);
+                    float cv = Pw * r1.z;
+                    int xs = max(xf + 2, pad), xe = min(xg2 - 1, pad + nb - 1);
+                    for (int x2 = xs; x2 <= xe; ++x2) atomicAdd(hj + skew(x2), cv);
+                }
+            }
+        }
+    }
+    // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
+#pragma unroll
+    for (int o = G; o < kWarp; o <<= 1) amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, o);
+    if (lane < G && amb_acc != 0.f) atomicAdd(amb_s + lane, amb_acc);
+    __syncthreads();
+
+    // ---- phase 2: drop contributions outside the window, support ----------
+    for (int jj = warp; jj < G; jj += nwarps) {
+        float *hj = hbuf + jj * Ly.HB;
+        if (lane < 4) {
+            hj[skew(pad - 4 + lane)] = 0.f;
+            hj[skew(pad + nb + lane)] = 0.f;
+        }
+        __syncwarp();
+        int lo = 1 << 30, hi = -1;
+        for (int k = lane; k < nb; k += 32) {
+            if (hj[skew(k + pad)] != 0.f) { lo = min(lo, k); hi = max(hi, k); }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) { supp[2 * jj] = lo; supp[2 * jj + 1] = hi; }
+    }
+    __syncthreads();
+
+    // ---- phase 3: pulse convolution + ambient, waveform to HBM -------------
+    // Lane L of an item owns bins o0 + 8L .. o0 + 8L + 7; the 8 inputs it needs
+    // for tap m are a window that slides by one bin per tap, kept in registers.
+    const int nblk = (nb + kBlk - 1) / kBlk;
+    for (int it = warp; it < gcount * nblk; it += nwarps) {
+        int jj = it / nblk;
+        int o0 = (it - jj * nblk) * kBlk;
+        const float *hj = hbuf + jj * Ly.HB;
+        const int lo = supp[2 * jj], hi = supp[2 * jj + 1];
+        const float ambv = amb_s[jj] * A.s_amb;
+        float acc[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] = ambv;
+        int m_lo = max(-M, o0 - hi), m_hi = min(M, o0 + kBlk - 1 - lo);
+        const int kb = min(o0 + 8 * lane, nb - 8);  // lanes past the end compute a copy, not stored
+        if (hi >= 0 && m_lo <= m_hi) {
+            m_lo = (m_lo >> 3) << 3;  // floor to a multiple of 8
+            const float *hb = hj;
+            float win[8];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) win[r] = hb[skew(kb + r - m_lo + pad)];
+            for (int m0 = m_lo; m0 <= m_hi; m0 += 8) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int m = m0 + i;
+                    win[(8 - i) & 7] = hb[skew(kb - m + pad)];
+                    const float t = taps[Ly.taps_off + m];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, win[(r - i) & 7], acc[r]);
+                }
+            }
+        }
+        if (o0 + 8 * lane < nb) {
+            float4 *dst = reinterpret_cast<float4 *>(A.wave + (size_t)(b0 + jj) * nb + o0 + 8 * lane);
+            dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 4: echoes ---------------------------------------------------
+    const int nch = nb / 32;
+    for (int jj = warp; jj < gcount; jj += nwarps) {
+        const int beam = b0 + jj;
+        const float *xw = A.wave + (size_t)beam * nb;
+        lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
+        const float T = A.T;
+        int count = 0;
+        bool open = false;
+        int bs = 0, pk = 0;
+        float pv = 0.f;
+        for (int c = 0; c < nch && count < A.max_echoes; ++c) {
+            int k = 32 * c + lane;
+            float v = xw[k];
+            float vn = (k + 1 < nb) ? xw[k + 1] : 0.f;
+            float vp = (k > 0) ? xw[k - 1] : 0.f;
+            bool ab = v > T;
+            bool st = ab && !(k > 0 && vp > T);
+            bool en = ab && !(k + 1 < nb && vn > T);
+            uint32_t Sm = __ballot_sync(0xffffffffu, st);
+            uint32_t Em = __ballot_sync(0xffffffffu, en);
+            int seg_lo = 0;
+            uint32_t ev = Sm | Em;
+            while (ev && count < A.max_echoes) {
+                int i = __ffs(ev) - 1;
+                ev &= ev - 1;
+                if ((Sm >> i) & 1u) { open = true; bs = 32 * c + i; pv = -1.f; pk = bs; seg_lo = i; }
+                if ((Em >> i) & 1u) {
+                    // argmax over [seg_lo, i] of this chunk, lowest bin on ties
+                    float mv = (lane >= seg_lo && lane <= i) ? v : -1.f;
+                    int mi = k;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float ov = __shfl_xor_sync(0xffffffffu, mv, o);
+                        int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+                        if (ov > mv || (ov == mv && oi < mi)) { mv = ov; mi = oi; }
+                    }
+                    if (mv > pv) { pv = mv; pk = mi; }
+                    int be = 32 * c + i;
+                    if (lane == 0) {
+                        lidar_echo_t e;
+                        uint32_t fl = 0;
+                        float x0, x1;
+                        float vbs = xw[bs], vbe = xw[be];
+                        float eps = kNearRel * T;
+                        if (bs > 0) {
+                            float vm = xw[bs - 1];
+                            x0 = (float)(bs - 1) + (T - vm) / (vbs - vm);
+                            if (fabsf(vm - T) <= eps) fl |= LIDAR_ECHO_NEAR_THRESHOLD;
+                        } else { x0 = 0.f; fl |= LIDAR_ECHO_CLIPPED_START; }
+                        if (be < nb - 1) {
+                            float vq = xw[be + 1];
+                            x1 = (float)be + (vbe - T) / (vbe - vq);
+                            if (fabsf(vq - T) <= eps) fl |= LIDAR_ECHO_NEAR_THRESHOLD;
+                        } else { x1 = (float)(nb - 1); fl |= LIDAR_ECHO_CLIPPED_END; }
+                        if (fabsf(vbs - T) <= eps || fabsf(vbe - T) <= eps) fl |= LIDAR_ECHO_NEAR_THRESHOLD;
+                        float dl = 0.f;
+                        if (pk > 0 && pk < nb - 1) {
+                            float va = xw[pk - 1], vb = xw[pk], vc = xw[pk + 1];
+                            if (va > 0.f && vb > 0.f && vc > 0.f) {
+                                float la = logf(va), lb = logf(vb), lc = logf(vc);
+                                float den = la - 2.f * lb + lc;
+                                if (den < 0.f) dl = 0.5f * (la - lc) / den;
+                            } else {
+                                float den = va - 2.f * vb + vc;
+                                if (den < 0.f) dl = 0.5f * (va - vc) / den;
+                            }
+                            dl = fminf(0.5f, fmaxf(-0.5f, dl));
+                        }
+                        float r0m = fmaf(x0, A.rB, A.rA), r1m = fmaf(x1, A.rB, A.rA);
+                        float epw = r1m - r0m;
+                        float E2 = epw * epw;
+                        e.range_m = fmaf((float)pk + dl, A.rB, A.rA);
+                        e.epw_m = epw;
+                        e.intensity = expf(fmaf(A.c2 * E2, E2, fmaf(A.c1, E2, A.c0)));
+                        e.peak = pv;
+                        e.bin_peak = pk;
+                        e.bin_start = bs;
+                        e.bin_end = be;
+                        e.flags = fl;
+                        eo[count] = e;
+                    }
+                    ++count;
+                    open = false;
+                    seg_lo = i + 1;
+                }
+            }
+            if (open) {
+                float mv = (lane >= seg_lo) ? v : -1.f;
+                int mi = k;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float ov = __shfl_xor_sync(0xffffffffu, mv, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+                    if (ov > mv || (ov == mv && oi < mi)) { mv = ov; mi = oi; }
+                }
+                if (mv > pv) { pv = mv; pk = mi; }
+            }
+        }
+        if (lane == 0) {
+            for (int e = count; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
+            A.counts[beam] = count;
+        }
+    }
+}
+
+size_t footprint_smem_bytes(int G, const FootprintArgs &a)
+{
+    return make_layout(G, a.n_bins, a.M).total;
+}
+
+template <int KIND, int G>
+static cudaError_t prep_one(size_t smem)
+{
+    return cudaFuncSetAttribute(footprint_wave_kernel<KIND, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t prepare_footprint(int kind, int G, size_t smem)
+{
+#define GBL_CASE(K, GG) if (kind == K && G == GG) return prep_one<K, GG>(smem);
+    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
+    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_footprint(int kind, int G, int threads, size_t smem, const FootprintArgs &a, cudaStream_t s)
+{
+    int groups = (a.n_beams + G - 1) / G;
+#define GBL_CASE(K, GG)                                                              \
+    if (kind == K && G == GG) {                                                      \
+        footprint_wave_kernel<K, GG><<<groups, threads, smem, s>>>(a);               \
+        return cudaGetLastError();                                                   \
+    }
+    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
+    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gbl

@@ -1,0 +1,322 @@
+"""Thin Python binding of the C ABI in include/lidar.h (argument marshalling
+only). Every step of the computation runs in the sm_103a library
+``liblidar_gb300.so``; there is no other code path. Loading fails loudly if
+the library has not been built.
+
+Functions keep the C names (lidar_create, lidar_simulate, ...). ``Lidar`` is a
+small convenience wrapper that owns a handle and allocates outputs as torch
+CUDA tensors (PyTorch provides device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblidar_gb300.so")
+
+LIDAR_OK, LIDAR_EINVAL, LIDAR_ENOMEM, LIDAR_ECUDA, LIDAR_ETIMEOUT, LIDAR_ENUMERIC = range(6)
+LIDAR_PROFILE_RADIAL, LIDAR_PROFILE_TABLE = 0, 1
+ECHO_CLIPPED_START, ECHO_CLIPPED_END, ECHO_NEAR_THRESHOLD = 1, 2, 4
+
+
+class lidar_profile_t(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("sigma_deg", C.c_double), ("tail_amp", C.c_double),
+                ("tail_core_deg", C.c_double), ("tail_pow", C.c_double), ("trunc_deg", C.c_double),
+                ("table_w", C.c_int32), ("table_h", C.c_int32), ("pitch_deg", C.c_double),
+                ("table", C.POINTER(C.c_float))]
+
+
+class lidar_pattern_t(C.Structure):
+    _fields_ = [("n_beams", C.c_int32), ("dirs", C.POINTER(C.c_float))]
+
+
+class lidar_pulse_t(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("dt_s", C.c_double), ("t0_s", C.c_double), ("fwhm_s", C.c_double),
+                ("trunc_sigmas", C.c_double)]
+
+
+class lidar_calib_t(C.Structure):
+    _fields_ = [("threshold", C.c_double), ("ambient_scale", C.c_double), ("max_echoes", C.c_int32),
+                ("fit_epw", C.c_int32), ("epw_coef", C.c_double * 3)]
+
+
+class lidar_gbuffer_t(C.Structure):
+    _fields_ = [("U", C.c_int32), ("V", C.c_int32), ("az0", C.c_double), ("el0", C.c_double),
+                ("daz", C.c_double), ("del_", C.c_double)] + [
+        (n, C.c_void_p) for n in ("range", "nx", "ny", "nz", "rho_d", "retro", "ambient")]
+
+
+class lidar_pose_t(C.Structure):
+    _fields_ = [("R", C.c_float * 9)]
+
+
+class lidar_echo_t(C.Structure):
+    _fields_ = [("range_m", C.c_float), ("epw_m", C.c_float), ("intensity", C.c_float), ("peak", C.c_float),
+                ("bin_peak", C.c_int32), ("bin_start", C.c_int32), ("bin_end", C.c_int32), ("flags", C.c_uint32)]
+
+
+class lidar_echoes_t(C.Structure):
+    _fields_ = [("echoes", C.c_void_p), ("counts", C.c_void_p)]
+
+
+ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), ("peak", "f4"),
+                       ("bin_peak", "i4"), ("bin_start", "i4"), ("bin_end", "i4"), ("flags", "u4")])
+assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
+
+# exported symbols (every function declared in include/lidar.h)
+SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_sync", "lidar_get_info",
+           "lidar_launches_per_simulate", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
+           "lidar_destroy")
+KERNELS = ("setup", "footprint_wave")
+
+_lib = None
+
+
+class LidarError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lidar status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2512_05932_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    lib.lidar_create.restype = C.c_int
+    lib.lidar_create.argtypes = [P(lidar_profile_t), P(lidar_pattern_t), P(lidar_pulse_t), P(lidar_calib_t),
+                                 P(C.c_void_p)]
+    lib.lidar_simulate.restype = C.c_int
+    lib.lidar_simulate.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
+                                   P(lidar_echoes_t), C.c_void_p]
+    lib.lidar_simulate_host.restype = C.c_int
+    lib.lidar_simulate_host.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+    lib.lidar_sync.restype = C.c_int
+    lib.lidar_sync.argtypes = [C.c_void_p, C.c_void_p]
+    lib.lidar_get_info.restype = C.c_int
+    lib.lidar_get_info.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_double),
+                                   P(C.c_double)]
+    lib.lidar_launches_per_simulate.restype = C.c_int32
+    lib.lidar_launches_per_simulate.argtypes = [C.c_void_p]
+    lib.lidar_profile_enable.restype = C.c_int
+    lib.lidar_profile_enable.argtypes = [C.c_void_p, C.c_int32]
+    lib.lidar_profile_read.restype = C.c_int
+    lib.lidar_profile_read.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32)]
+    lib.lidar_last_error.restype = C.c_char_p
+    lib.lidar_last_error.argtypes = [C.c_void_p]
+    lib.lidar_destroy.restype = None
+    lib.lidar_destroy.argtypes = [C.c_void_p]
+    _lib = lib
+    return lib
+
+
+# --------------------------------------------------------------------------
+# struct builders from the plain dicts of the input generators
+# --------------------------------------------------------------------------
+
+
+def make_profile(prof: dict, keep: list) -> lidar_profile_t:
+    p = lidar_profile_t()
+    p.kind = int(prof["kind"])
+    if p.kind == LIDAR_PROFILE_RADIAL:
+        for k in ("sigma_deg", "tail_amp", "tail_core_deg", "tail_pow", "trunc_deg"):
+            setattr(p, k, float(prof[k]))
+    else:
+        t = np.ascontiguousarray(prof["table"], dtype=np.float32)
+        keep.append(t)
+        p.table_w, p.table_h = t.shape[1], t.shape[0]
+        p.pitch_deg = float(prof["pitch_deg"])
+        p.table = t.ctypes.data_as(C.POINTER(C.c_float))
+    return p
+
+
+def make_pattern(dirs, keep: list) -> lidar_pattern_t:
+    d = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 3)
+    keep.append(d)
+    return lidar_pattern_t(len(d), d.ctypes.data_as(C.POINTER(C.c_float)))
+
+
+def make_pulse(pu: dict) -> lidar_pulse_t:
+    return lidar_pulse_t(int(pu["n_bins"]), float(pu["dt_s"]), float(pu["t0_s"]), float(pu["fwhm_s"]),
+                         float(pu["trunc_sigmas"]))
+
+
+def make_calib(ca: dict) -> lidar_calib_t:
+    c = lidar_calib_t()
+    c.threshold = float(ca["threshold"])
+    c.ambient_scale = float(ca["ambient_scale"])
+    c.max_echoes = int(ca["max_echoes"])
+    c.fit_epw = int(ca["fit_epw"])
+    for i, v in enumerate(ca.get("epw_coef", (0.0, 0.0, 0.0))):
+        c.epw_coef[i] = float(v)
+    return c
+
+
+def make_gbuffer(geom, planes) -> lidar_gbuffer_t:
+    """geom: object with U, V, az0, el0, daz, dele; planes: 7 pointers (ints)."""
+    g = lidar_gbuffer_t()
+    g.U, g.V = int(geom.U), int(geom.V)
+    g.az0, g.el0, g.daz, g.del_ = float(geom.az0), float(geom.el0), float(geom.daz), float(geom.dele)
+    for name, ptr in zip(("range", "nx", "ny", "nz", "rho_d", "retro", "ambient"), planes):
+        setattr(g, name, ptr)
+    return g
+
+
+def make_pose(R) -> lidar_pose_t:
+    p = lidar_pose_t()
+    R = np.asarray(R, dtype=np.float32).ravel()
+    for i in range(9):
+        p.R[i] = float(R[i])
+    return p
+
+
+# --------------------------------------------------------------------------
+# C-named functions
+# --------------------------------------------------------------------------
+
+
+def lidar_last_error(handle=None) -> str:
+    return load().lidar_last_error(handle).decode()
+
+
+def _check(st, handle=None):
+    if st != LIDAR_OK:
+        raise LidarError(st, lidar_last_error(handle))
+
+
+def lidar_create(profile: dict, dirs, pulse: dict, calib: dict) -> int:
+    keep = []
+    lib = load()
+    out = C.c_void_p()
+    st = lib.lidar_create(C.byref(make_profile(profile, keep)), C.byref(make_pattern(dirs, keep)),
+                          C.byref(make_pulse(pulse)), C.byref(make_calib(calib)), C.byref(out))
+    _check(st)
+    return out.value
+
+
+def lidar_simulate(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_waveforms: int,
+                   out_echoes: int, out_counts: int, stream: int = 0) -> None:
+    e = lidar_echoes_t(out_echoes, out_counts)
+    st = load().lidar_simulate(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
+    _check(st, handle)
+
+
+def lidar_simulate_host(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_waveforms: int,
+                        out_echoes: int, out_counts: int, stream: int = 0) -> None:
+    st = load().lidar_simulate_host(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, out_echoes,
+                                    out_counts, stream)
+    _check(st, handle)
+
+
+def lidar_sync(handle, stream: int = 0) -> None:
+    _check(load().lidar_sync(handle, stream), handle)
+
+
+def lidar_get_info(handle) -> dict:
+    nb, nbin, me = C.c_int32(), C.c_int32(), C.c_int32()
+    Z = C.c_double()
+    coef = (C.c_double * 3)()
+    _check(load().lidar_get_info(handle, C.byref(nb), C.byref(nbin), C.byref(me), C.byref(Z), coef), handle)
+    return dict(n_beams=nb.value, n_bins=nbin.value, max_echoes=me.value, profile_norm=Z.value,
+                epw_coef=np.array(coef[:]))
+
+
+def lidar_launches_per_simulate(handle) -> int:
+    return int(load().lidar_launches_per_simulate(handle))
+
+
+def lidar_profile_enable(handle, enable: bool) -> None:
+    _check(load().lidar_profile_enable(handle, int(bool(enable))), handle)
+
+
+def lidar_profile_read(handle) -> dict:
+    """{kernel name: (total ms, launches)} accumulated since the last read."""
+    t = (C.c_double * 2)()
+    n = (C.c_int32 * 2)()
+    _check(load().lidar_profile_read(handle, t, n), handle)
+    return {k: (t[i], n[i]) for i, k in enumerate(KERNELS)}
+
+
+def lidar_destroy(handle) -> None:
+    if handle:
+        load().lidar_destroy(handle)
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper over torch CUDA tensors
+# --------------------------------------------------------------------------
+
+
+def gbuffer_to_device(gb, device="cuda"):
+    """Copies the 7 float32 planes of a scenes.GBuffer to torch CUDA tensors."""
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(p, dtype=np.float32)).to(device) for p in gb.planes()]
+
+
+class Lidar:
+    def __init__(self, profile, dirs, pulse, calib):
+        self.handle = lidar_create(profile, dirs, pulse, calib)
+        info = lidar_get_info(self.handle)
+        self.n_beams, self.n_bins, self.max_echoes = info["n_beams"], info["n_bins"], info["max_echoes"]
+        self.profile_norm, self.epw_coef = info["profile_norm"], info["epw_coef"]
+
+    def alloc_outputs(self, device="cuda"):
+        import torch
+        wave = torch.empty((self.n_beams, self.n_bins), dtype=torch.float32, device=device)
+        echoes = torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, device=device)
+        counts = torch.empty((self.n_beams,), dtype=torch.int32, device=device)
+        return wave, echoes, counts
+
+    def simulate(self, geom, planes, pose=None, outputs=None, stream=None):
+        """planes: 7 CUDA tensors [V, U] float32. Returns (waveforms, echoes, counts)
+        as torch tensors; echoes is int32 [n_beams, max_echoes, 8] holding
+        lidar_echo_t records (view with ECHO_DTYPE after .cpu().numpy())."""
+        import torch
+        if outputs is None:
+            outputs = self.alloc_outputs(planes[0].device)
+        wave, echoes, counts = outputs
+        for p in planes:
+            assert p.is_cuda and p.dtype == torch.float32 and p.is_contiguous()
+        g = make_gbuffer(geom, [p.data_ptr() for p in planes])
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        lidar_simulate(self.handle, g, make_pose(np.eye(3) if pose is None else pose), wave.data_ptr(),
+                       echoes.data_ptr(), counts.data_ptr(), s)
+        return wave, echoes, counts
+
+    def simulate_host(self, geom, host_planes, pose=None, outputs=None, stream=None):
+        """Host-memory entry point: planes and outputs are (pinned) CPU tensors."""
+        import torch
+        if outputs is None:
+            outputs = (torch.empty((self.n_beams, self.n_bins), dtype=torch.float32, pin_memory=True),
+                       torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, pin_memory=True),
+                       torch.empty((self.n_beams,), dtype=torch.int32, pin_memory=True))
+        wave, echoes, counts = outputs
+        g = make_gbuffer(geom, [p.data_ptr() for p in host_planes])
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        lidar_simulate_host(self.handle, g, make_pose(np.eye(3) if pose is None else pose), wave.data_ptr(),
+                            echoes.data_ptr(), counts.data_ptr(), s)
+        return wave, echoes, counts
+
+    def close(self):
+        if self.handle:
+            lidar_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def echoes_numpy(echoes_tensor) -> np.ndarray:
+    a = echoes_tensor.detach().cpu().numpy()
+    return np.ascontiguousarray(a).view(ECHO_DTYPE).reshape(a.shape[:-1])
