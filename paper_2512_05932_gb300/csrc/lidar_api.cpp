@@ -391,6 +391,7 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     sa.x_scale = (float)(2.0 / (kC * l->dt));
     sa.x_off = (float)(-l->t0 / l->dt - 0.5);
     sa.n_bins = l->n_bins;
+    sa.pad = gbl::footprint_pad(l->M);
     long pb = (long)((pixels + 255) / 256);
     sa.pix_blocks = (int)std::min<long>(pb, 152L * 64);
     sa.n_beams = l->n_beams;

@@ -40,6 +40,7 @@ struct SetupArgs {
     float4 *rec;             // [U*V][2]: 32-byte per-pixel records
     float x_scale, x_off;    // bin-centre coordinate X = r * x_scale + x_off
     int n_bins;
+    int pad;                 // zero padding (bins) of the footprint kernel's histogram buffer
     int pix_blocks;
     // beams
     int n_beams;
@@ -83,6 +84,7 @@ struct FootprintArgs {
 // Launch helpers (lidar_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s);
 size_t footprint_smem_bytes(int G, const FootprintArgs &a);
+int footprint_pad(int M);
 cudaError_t prepare_footprint(int kind, int G, size_t smem);
 cudaError_t launch_footprint(int kind, int G, int threads, size_t smem, const FootprintArgs &a, cudaStream_t s);
 

@@ -31,6 +31,10 @@ namespace gbl {
 
 __device__ __forceinline__ float hatf(float x) { return fmaxf(0.f, 1.f - fabsf(x)); }
 
+// Position of padded bin index x in the footprint kernel's histogram buffer:
+// one unused slot after every 32, so that lanes 8 bins apart hit distinct banks.
+__host__ __device__ __forceinline__ int skew_pos(int x) { return x + (x >> 5); }
+
 // Mean of hat(x - k) over [X0, X1] (bin-centre units): the interval is cut at
 // the kinks k-1, k, k+1; on each piece the hat is linear, so the piece's
 // contribution is its length times the hat at its midpoint.
@@ -65,7 +69,7 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
     float L = A.amb[idx];
     float a = isfinite(L) ? L * domega : 0.f;
     float rr = A.range[idx];
-    uint32_t kab = kNoDeposit;
+    uint32_t kab = kNoDeposit, kq = kNoDeposit;
     float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, cr = 0.f;
     if (isfinite(rr) && rr > 0.f) {
         float nx = A.nx[idx], ny = A.ny[idx], nz = A.nz[idx];
@@ -98,13 +102,16 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
         // the hat functions of bins 0..n-1 cover (-1, n): anything else is dropped
         if (w > 0.f && X1 > -1.f && X0 < nb) {
             if (X1 <= f + 3.f) {
-                // narrow: at most 4 bins f..f+3 touched
+                // narrow: at most 4 bins f..f+3 touched; the record holds their
+                // positions in the footprint kernel's skewed histogram buffer
                 if (f >= -3.f) {
                     h0 = w * mean_hat(X0, X1, f);
                     h1 = w * mean_hat(X0, X1, f + 1.f);
                     h2 = w * mean_hat(X0, X1, f + 2.f);
                     h3 = w * mean_hat(X0, X1, f + 3.f);
-                    kab = (uint32_t)((int)f + kBinBias) | (0xFFFFu << 16);
+                    int x = (int)f + A.pad;
+                    kab = (uint32_t)skew_pos(x) | ((uint32_t)skew_pos(x + 1) << 16);
+                    kq = (uint32_t)skew_pos(x + 2) | ((uint32_t)skew_pos(x + 3) << 16);
                 }
             } else {
                 // wide (X1 - X0 > 2): partial bins f, f+1 and g, g+1, every bin
@@ -124,7 +131,7 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
         }
     }
     float4 r0 = make_float4(__uint_as_float(kab), a, h0, h1);
-    float4 r1 = make_float4(h2, h3, cr, 0.f);
+    float4 r1 = make_float4(__uint_as_float(kq), h2, h3, cr);
     A.rec[2 * (size_t)idx] = r0;
     A.rec[2 * (size_t)idx + 1] = r1;
 }
@@ -234,22 +241,23 @@ constexpr int kBlk = 256;    // waveform bins per convolution work item (8 per l
 // Per-beam histogram buffer: bins [-pad, n_bins + pad) at positions
 // x = bin + pad, stored at x + (x >> 5) so that lanes reading bins 8 apart hit
 // distinct banks. pad >= M + 16 and is a multiple of 32.
+constexpr int kTC = 257;     // columns per offset-table stripe (odd: conflict-free float2 rows)
+
 struct Layout {
     int pad;       // zero padding on each side, in bins
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_supp, off_bp, total;
+    size_t off_taps, off_amb, off_supp, off_tab, off_bp, total;
 };
 
-__host__ __device__ inline int skew(int x) { return x + (x >> 5); }
 
 __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
 {
     Layout L;
     L.pad = 32 * ((M + 16 + 31) / 32);
     int span = n_bins + 2 * L.pad;
-    L.HB = skew(span) + 1;
+    L.HB = skew_pos(span) + 1;
     if ((L.HB & 1) == 0) L.HB += 1;
     L.taps_off = M + 8;
     L.taps_len = 2 * M + 17;
@@ -258,6 +266,8 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     L.off_amb = off; off += (size_t)G * 4;
     L.off_supp = off; off += (size_t)G * 8;
     off = (off + 15) & ~(size_t)15;
+    L.off_tab = off; off += (size_t)G * kTC * sizeof(float2);
+    off = (off + 15) & ~(size_t)15;
     L.off_bp = off; off += (size_t)G * sizeof(BeamParam);
     L.total = off;
     return L;
@@ -265,19 +275,30 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
 
 // Profile weight of a local offset (x, y) = (sin theta) * (unit offset
 // direction), i.e. the components of the pixel direction along the beam's
-// local axes. s2 = x^2 + y^2 = sin^2 theta.
+// local axes; s2 = x^2 + y^2 = sin^2 theta. Split in two stages so that the
+// table load of several samples can be in flight together:
+// profile_fetch issues the load (table) or evaluates the weight (radial),
+// profile_finish interpolates.
+struct ProfFetch {
+    float4 q;      // table: the 4 corner values; radial: q.x = weight
+    float fx, fy;
+    bool ok;
+};
+
 template <int KIND>
-__device__ __forceinline__ float profile_weight(const FootprintArgs &A, float x, float y)
+__device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float x, float y, bool act)
 {
+    ProfFetch r;
     float s2 = fmaf(x, x, y * y);
     if (KIND == LIDAR_PROFILE_RADIAL) {
         // theta^2 = asin(s)^2 = s^2 (1 + s^2/3 + 8 s^4/45 + ...)
         float t2 = s2 * fmaf(s2, fmaf(s2, 8.f / 45.f, 1.f / 3.f), 1.f);
-        if (t2 > A.trunc2) return 0.f;
+        r.ok = act && t2 <= A.trunc2;
         float g = exp2f(t2 * A.kg);
-        float r = t2 * A.tc2_inv;
-        float tail = r <= 1.f ? 1.f : exp2f(A.tail_hp * __log2f(r));
-        return fmaf(A.tail_amp, tail, g) * A.invZ;
+        float rr = t2 * A.tc2_inv;
+        float tail = rr <= 1.f ? 1.f : exp2f(A.tail_hp * __log2f(rr));
+        r.q.x = fmaf(A.tail_amp, tail, g) * A.invZ;
+        r.fx = r.fy = 0.f;
     } else {
         // azimuthal-equidistant coordinates: (x, y) * theta / sin theta,
         // theta / sin theta = asin(s)/s = 1 + s^2/6 + 3 s^4/40 + ...
@@ -286,13 +307,22 @@ __device__ __forceinline__ float profile_weight(const FootprintArgs &A, float x,
         float fv = fmaf(y, f, A.tcv);
         float iu = floorf(fu), iv = floorf(fv);
         int i = (int)iu, j = (int)iv;
-        if ((unsigned)i >= (unsigned)A.qw || (unsigned)j >= (unsigned)A.qh) return 0.f;
-        float fx = fu - iu, fy = fv - iv;
-        float4 q = __ldg(A.quads + (size_t)j * A.qw + i);
-        float top = fmaf(fx, q.y - q.x, q.x);
-        float bot = fmaf(fx, q.w - q.z, q.z);
-        return fmaf(fy, bot - top, top);
+        r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
+        r.fx = fu - iu;
+        r.fy = fv - iv;
+        r.q = r.ok ? __ldg(A.quads + (size_t)j * A.qw + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ float profile_finish(const ProfFetch &r)
+{
+    if (!r.ok) return 0.f;
+    if (KIND == LIDAR_PROFILE_RADIAL) return r.q.x;
+    float top = fmaf(r.fx, r.q.y - r.q.x, r.q.x);
+    float bot = fmaf(r.fx, r.q.w - r.q.z, r.q.z);
+    return fmaf(r.fy, bot - top, top);
 }
 
 template <int KIND, int G>
@@ -306,6 +336,7 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
     float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
     int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
+    float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
     BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -349,81 +380,130 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     }
 
     // ---- phase 1: profile-weighted deposits into the range bins -----------
+    // The group's pixel box is walked in stripes of kTC columns. For each
+    // stripe, tab[j][c] holds sin(dAz) and 1 - cos(dAz) of column c relative
+    // to beam j; work units are (row, 32-column segment) pairs; lane (j, rsub)
+    // of a warp handles beam j on unit rsub, all lanes stepping through the
+    // same columns so that lanes on the same row share each record load.
     constexpr int LR = kWarp / G;  // work units per warp step
     const int j = lane % G;
     const int rsub = lane / G;
     float amb_acc = 0.f;
-    if (R0 <= R1) {
-        const int nseg = (C1 - C0 + kSeg) / kSeg;
+    const BeamParam P = bp[j];
+    const bool jok = (j < gcount) && P.valid;
+    float *hj = hbuf + j * Ly.HB;
+    const float2 *tj = tab + j * kTC;
+    for (int cs = C0; cs <= C1; cs += kTC) {
+        const int ce = min(C1, cs + kTC - 1);
+        const int ncs = ce - cs + 1;
+        __syncthreads();  // previous stripe's table no longer read
+        for (int i = tid; i < G * ncs; i += blockDim.x) {
+            int jj = i / ncs, cc = i - jj * ncs;
+            const BeamParam &Q = bp[jj];
+            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
+            float sD, vers;
+            if (fabsf(dAz) <= 0.1f) {
+                // Taylor series (relative accuracy ~1e-12 for |dAz| <= 0.1)
+                float z2 = dAz * dAz;
+                sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
+                vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
+            } else {
+                float cD;
+                sincosf(dAz, &sD, &cD);
+                vers = 1.f - cD;
+            }
+            tab[jj * kTC + cc] = make_float2(sD, vers);
+        }
+        __syncthreads();
+        if (R0 > R1) continue;
+        const int nseg = (ncs + kSeg - 1) / kSeg;
         const int nunits = (R1 - R0 + 1) * nseg;
-        const BeamParam P = bp[j];
-        const bool jok = (j < gcount) && P.valid;
-        float *hj = hbuf + j * Ly.HB;
         for (int ubase = warp * LR; ubase < nunits; ubase += nwarps * LR) {
             int unit = ubase + rsub;
-            if (unit >= nunits || !jok) continue;
             int row = R0 + unit / nseg;
             int seg = unit - (unit / nseg) * nseg;
-            if (row < P.row0 || row > P.row1) continue;
-            int cbeg = max(C0 + seg * kSeg, P.col0);
-            int cend = min(C0 + seg * kSeg + kSeg - 1, P.col1);
-            if (cbeg > cend) continue;
+            bool act = jok && unit < nunits && row >= P.row0 && row <= P.row1;
+            int c_lo = cs + seg * kSeg, c_hi = min(ce, c_lo + kSeg - 1);
+            int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
+            if (!act) { my_lo = 1; my_hi = 0; }
             float el = A.el0 + ((float)row + 0.5f) * A.del;
             float cosEl = cosf(el);
             float dEl = ((float)(row - P.ri) - P.rf) * A.del;
             float sdEl = sinf(dEl), cdEl = cosf(dEl);
             float Kv = P.sin_elb * cosEl;
             float Kc = P.cos_elb * cosEl;
-            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
-            float daz0 = ((float)(cbeg - P.ci) - P.cf) * A.daz;
-            for (int c = cbeg; c <= cend; ++c) {
-                int cw = c;
-                if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
-                float4 r0 = __ldg(recrow + 2 * cw);
-                uint32_t kab = __float_as_uint(r0.x);
-                float a = r0.y;
-                if (kab == kNoDeposit && a == 0.f) continue;
-                float dAz = fmaf((float)(c - cbeg), A.daz, daz0);
-                float sD, vers;
-                if (fabsf(dAz) <= 0.1f) {
-                    float z2 = dAz * dAz;
-                    sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
-                    vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
-                } else {
-                    float cD;
-                    __sincosf(dAz, &sD, &cD);
-                    vers = 1.f - cD;
+            const float4 *recrow = A.rec + 2 * (size_t)min(row, A.V - 1) * A.U;
+            // narrow deposits of consecutive pixels that hit the same 4 bins are
+            // summed in registers and written with one set of atomics
+            uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
+            float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
+            // two columns per step: both samples' loads are issued before use
+            for (int c2 = c_lo; c2 <= c_lo + kSeg - 1; c2 += 2) {
+                float4 r0[2], r1[2];
+                ProfFetch pf[2];
+                bool act[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c2 + u;
+                    act[u] = c >= my_lo && c <= my_hi;
+                    int cw = c;
+                    if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    cw = act[u] ? cw : 0;
+                    r0[u] = __ldg(recrow + 2 * cw);
+                    r1[u] = __ldg(recrow + 2 * cw + 1);
+                    float2 t = tj[act[u] ? c - cs : 0];
                     // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
-                    if (fmaf(-Kc, vers, cdEl) <= 0.f) continue;
+                    act[u] = act[u] && fmaf(-Kc, t.y, cdEl) > 0.f;
+                    float xg = cosEl * t.x;
+                    float yg = fmaf(Kv, t.y, sdEl);
+                    float x = fmaf(P.cg, xg, P.sg * yg);
+                    float y = fmaf(P.cg, yg, -P.sg * xg);
+                    pf[u] = profile_fetch<KIND>(A, x, y, act[u]);
                 }
-                float xg = cosEl * sD;
-                float yg = fmaf(Kv, vers, sdEl);
-                float x = fmaf(P.cg, xg, P.sg * yg);
-                float y = fmaf(P.cg, yg, -P.sg * xg);
-                float Pw = profile_weight<KIND>(A, x, y);
-                if (!(Pw > 0.f)) continue;
-                amb_acc = fmaf(Pw, a, amb_acc);
-                if (kab == kNoDeposit) continue;
-                float4 r1 = __ldg(recrow + 2 * cw + 1);
-                int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
-                uint32_t gq = kab >> 16;
-                if (gq == 0xFFFFu) {
-                    // narrow: hat weights on 4 consecutive bins
-                    if (r0.z != 0.f) atomicAdd(hj + skew(xf), Pw * r0.z);
-                    if (r0.w != 0.f) atomicAdd(hj + skew(xf + 1), Pw * r0.w);
-                    if (r1.x != 0.f) atomicAdd(hj + skew(xf + 2), Pw * r1.x);
-                    if (r1.y != 0.f) atomicAdd(hj + skew(xf + 3), Pw * r1.y);
-                } else {
-                    // wide: two partial bins at each end, a constant run between
-                    int xg2 = (int)gq - kBinBias + pad;
-                    atomicAdd(hj + skew(xf), Pw * r0.z);
-                    atomicAdd(hj + skew(xf + 1), Pw * r0.w);
-                    atomicAdd(hj + skew(xg2), Pw * r1.x);
-                    atomicAdd(hj + skew(xg2 + 1), Pw * r1.y);
-                    float cv = Pw * r1.z;
-                    int xs = max(xf + 2, pad), xe = min(xg2 - 1, pad + nb - 1);
-                    for (int x2 = xs; x2 <= xe; ++x2) atomicAdd(hj + skew(x2), cv);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    uint32_t kab = __float_as_uint(r0[u].x);
+                    float a = r0[u].y;
+                    float Pw = profile_finish<KIND>(pf[u]);
+                    if (!(Pw > 0.f)) continue;
+                    amb_acc = fmaf(Pw, a, amb_acc);
+                    if (kab == kNoDeposit) continue;
+                    uint32_t kq = __float_as_uint(r1[u].x);
+                    if (kq != kNoDeposit) {
+                        // narrow: hat weights on 4 consecutive bins at precomputed positions
+                        if (kab != wk0 || kq != wk1) {
+                            if (wk0 != kNoDeposit) {
+                                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
+                                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
+                                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
+                                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
+                            }
+                            wk0 = kab; wk1 = kq;
+                            wa0 = 0.f; wa1 = 0.f; wa2 = 0.f; wa3 = 0.f;
+                        }
+                        wa0 = fmaf(Pw, r0[u].z, wa0);
+                        wa1 = fmaf(Pw, r0[u].w, wa1);
+                        wa2 = fmaf(Pw, r1[u].y, wa2);
+                        wa3 = fmaf(Pw, r1[u].z, wa3);
+                    } else {
+                        // wide: two partial bins at each end, a constant run between
+                        int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
+                        int xg2 = (int)(kab >> 16) - kBinBias + pad;
+                        atomicAdd(hj + skew_pos(xf), Pw * r0[u].z);
+                        atomicAdd(hj + skew_pos(xf + 1), Pw * r0[u].w);
+                        atomicAdd(hj + skew_pos(xg2), Pw * r1[u].y);
+                        atomicAdd(hj + skew_pos(xg2 + 1), Pw * r1[u].z);
+                        float cv = Pw * r1[u].w;
+                        int xs = max(xf + 2, pad), xe = min(xg2 - 1, pad + nb - 1);
+                        for (int x3 = xs; x3 <= xe; ++x3) atomicAdd(hj + skew_pos(x3), cv);
+                    }
                 }
+            }
+            if (wk0 != kNoDeposit) {
+                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
+                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
+                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
+                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
             }
         }
     }
@@ -437,13 +517,13 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     for (int jj = warp; jj < G; jj += nwarps) {
         float *hj = hbuf + jj * Ly.HB;
         if (lane < 4) {
-            hj[skew(pad - 4 + lane)] = 0.f;
-            hj[skew(pad + nb + lane)] = 0.f;
+            hj[skew_pos(pad - 4 + lane)] = 0.f;
+            hj[skew_pos(pad + nb + lane)] = 0.f;
         }
         __syncwarp();
         int lo = 1 << 30, hi = -1;
         for (int k = lane; k < nb; k += 32) {
-            if (hj[skew(k + pad)] != 0.f) { lo = min(lo, k); hi = max(hi, k); }
+            if (hj[skew_pos(k + pad)] != 0.f) { lo = min(lo, k); hi = max(hi, k); }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -474,12 +554,12 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
             const float *hb = hj;
             float win[8];
 #pragma unroll
-            for (int r = 1; r < 8; ++r) win[r] = hb[skew(kb + r - m_lo + pad)];
+            for (int r = 1; r < 8; ++r) win[r] = hb[skew_pos(kb + r - m_lo + pad)];
             for (int m0 = m_lo; m0 <= m_hi; m0 += 8) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int m = m0 + i;
-                    win[(8 - i) & 7] = hb[skew(kb - m + pad)];
+                    win[(8 - i) & 7] = hb[skew_pos(kb - m + pad)];
                     const float t = taps[Ly.taps_off + m];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, win[(r - i) & 7], acc[r]);
@@ -495,21 +575,38 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     __syncthreads();
 
     // ---- phase 4: echoes ---------------------------------------------------
-    const int nch = nb / 32;
+    // With the ambient level at or below T, bins farther than M from the
+    // histogram's support hold the ambient level only and cannot be part of a
+    // run, so the scan covers [lo - M - 1, hi + M + 1]. Loads run one chunk ahead.
     for (int jj = warp; jj < gcount; jj += nwarps) {
         const int beam = b0 + jj;
         const float *xw = A.wave + (size_t)beam * nb;
         lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
         const float T = A.T;
+        const float ambv = amb_s[jj] * A.s_amb;
+        const int lo = supp[2 * jj], hi = supp[2 * jj + 1];
+        int kbeg, kend;
+        if (ambv > T) { kbeg = 0; kend = nb - 1; }
+        else if (hi < 0) { kbeg = 1; kend = 0; }
+        else { kbeg = max(0, lo - M - 1); kend = min(nb - 1, hi + M + 1); }
         int count = 0;
         bool open = false;
         int bs = 0, pk = 0;
         float pv = 0.f;
-        for (int c = 0; c < nch && count < A.max_echoes; ++c) {
-            int k = 32 * c + lane;
-            float v = xw[k];
-            float vn = (k + 1 < nb) ? xw[k + 1] : 0.f;
-            float vp = (k > 0) ? xw[k - 1] : 0.f;
+        const int cfirst = kbeg >> 5, clast = kend >> 5;
+        float v = 0.f, prev_last = 0.f;
+        if (kbeg <= kend) {
+            v = xw[32 * cfirst + lane];
+            prev_last = cfirst > 0 ? xw[32 * cfirst - 1] : 0.f;
+        }
+        for (int c = cfirst; c <= clast && kbeg <= kend && count < A.max_echoes; ++c) {
+            const int k = 32 * c + lane;
+            const float v_next = (k + 32 < nb) ? xw[k + 32] : 0.f;
+            float vn = __shfl_down_sync(0xffffffffu, v, 1);
+            float vnn = __shfl_sync(0xffffffffu, v_next, 0);
+            if (lane == 31) vn = vnn;
+            float vp = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0) vp = prev_last;
             bool ab = v > T;
             bool st = ab && !(k > 0 && vp > T);
             bool en = ab && !(k + 1 < nb && vn > T);
@@ -592,6 +689,8 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                 }
                 if (mv > pv) { pv = mv; pk = mi; }
             }
+            prev_last = __shfl_sync(0xffffffffu, v, 31);
+            v = v_next;
         }
         if (lane == 0) {
             for (int e = count; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
@@ -604,6 +703,8 @@ size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 {
     return make_layout(G, a.n_bins, a.M).total;
 }
+
+int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
 
 template <int KIND, int G>
 static cudaError_t prep_one(size_t smem)
