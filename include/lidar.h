@@ -202,6 +202,30 @@ lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffe
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);
 
+/* Same computation as lidar_simulate, for callers that cannot let the library
+ * allocate device memory during a call: a host whose memory pool has already
+ * reserved the GPU, or a real-time loop that must not allocate once running
+ * (a cudaMalloc can fail, stall or synchronise the device mid-frame). The
+ * paper has no counterpart; this is a property of the library only.
+ * Instead of library-allocated scratch, the per-pixel records live in a fixed
+ * device array of 2^20 records (32 MiB) that the library declares statically,
+ * so every GPU that loads the library holds it until the process exits. This
+ * call never calls cudaMalloc or cudaFree.
+ *   - G-buffers with more than 2^20 pixels (U * V) are rejected with
+ *     LIDAR_EINVAL and a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls, from every lidar_t in the process, share the one array on a
+ *     device. Calls whose kernels overlap on the GPU (different streams or
+ *     threads without ordering) race on it and give wrong results; order them
+ *     on one stream or synchronise between them. Each call rewrites every
+ *     record it reads, so the previous call's contents do no harm.
+ *   - Profiling (lidar_profile_enable) does not record this call.
+ * Arguments, outputs and errors are otherwise those of lidar_simulate. */
+lidar_status_t lidar_simulate_noalloc(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
+                                      float *out_waveforms, lidar_echoes_t *out_echoes, void *stream);
+
 /* Synchronises `stream` and reports any asynchronous CUDA error as LIDAR_ECUDA. */
 lidar_status_t lidar_sync(lidar_t *lidar, void *stream);
 

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblidar_gb300.so")
-SOURCES = ["lidar_api.cpp", "lidar_kernels.cu"]
+SOURCES = ["lidar_api.cpp", "lidar_kernels.cu", "lidar_noalloc.cu"]
 HEADERS = [os.path.join(INCLUDE, "lidar.h"), os.path.join(CSRC, "lidar_internal.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

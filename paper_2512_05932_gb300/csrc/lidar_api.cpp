@@ -632,6 +632,39 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     return LIDAR_OK;
 }
 
+lidar_status_t lidar_simulate_noalloc(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
+                                      lidar_echoes_t *echoes, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    lidar_status_t st = check_gbuffer(l, g);
+    if (st != LIDAR_OK) return st;
+    if ((long)g->U * g->V > gbl::kNoAllocMaxPixels)
+        return fail(l, LIDAR_EINVAL, "gbuffer has %ld pixels; lidar_simulate_noalloc takes at most %ld",
+                    (long)g->U * g->V, gbl::kNoAllocMaxPixels);
+    double R[9];
+    if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
+    if (!wave || !echoes || !echoes->echoes || !echoes->counts)
+        return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    float4 *rec = nullptr;
+    cudaError_t e = gbl::noalloc_records(&rec);
+    if (e != cudaSuccess) return cuda_fail(l, e, "cudaGetSymbolAddress(no-alloc scratch)");
+    // Run the regular path with the fixed array as its per-pixel scratch: its
+    // capacity covers the G-buffer, so nothing is allocated; profiling events
+    // (which would be created on demand) are off for this call. Every pixel's
+    // record is rewritten before it is read, so nothing needs clearing.
+    float4 *own = l->d_rec;
+    size_t own_cap = l->rec_cap;
+    bool prof = l->prof;
+    l->d_rec = rec;
+    l->rec_cap = (size_t)gbl::kNoAllocMaxPixels;
+    l->prof = false;
+    st = enqueue(l, g, R, wave, echoes->echoes, echoes->counts, (cudaStream_t)stream);
+    l->d_rec = own;
+    l->rec_cap = own_cap;
+    l->prof = prof;
+    return st;
+}
+
 lidar_status_t lidar_sync(lidar_t *l, void *stream)
 {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

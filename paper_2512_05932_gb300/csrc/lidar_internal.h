@@ -10,6 +10,7 @@
 namespace gbl {
 
 constexpr int kMaxBins = 16384;
+constexpr long kNoAllocMaxPixels = 1L << 20;  // G-buffer size limit of lidar_simulate_noalloc
 constexpr int kWarp = 32;
 constexpr uint32_t kNoDeposit = 0xFFFFFFFFu;
 constexpr int kBinBias = 8;           // bin indices in records are stored + kBinBias (>= 0)
@@ -80,6 +81,10 @@ struct FootprintArgs {
     lidar_echo_t *echoes;
     int32_t *counts;
 };
+
+// Device address of the fixed scratch of lidar_simulate_noalloc on the current
+// device (lidar_noalloc.cu); looked up on first use per device.
+cudaError_t noalloc_records(float4 **out);
 
 // Launch helpers (lidar_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s);

@@ -67,7 +67,8 @@ ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), 
 assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 
 # exported symbols (every function declared in include/lidar.h)
-SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_sync", "lidar_get_info",
+SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_simulate_noalloc", "lidar_sync",
+           "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
 KERNELS = ("setup", "footprint_wave")
@@ -99,6 +100,9 @@ def load(path: str = LIB_PATH):
     lib.lidar_simulate_host.restype = C.c_int
     lib.lidar_simulate_host.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
+    lib.lidar_simulate_noalloc.restype = C.c_int
+    lib.lidar_simulate_noalloc.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
+                                           P(lidar_echoes_t), C.c_void_p]
     lib.lidar_sync.restype = C.c_int
     lib.lidar_sync.argtypes = [C.c_void_p, C.c_void_p]
     lib.lidar_get_info.restype = C.c_int
@@ -213,6 +217,15 @@ def lidar_simulate_host(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, ou
                         out_echoes: int, out_counts: int, stream: int = 0) -> None:
     st = load().lidar_simulate_host(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, out_echoes,
                                     out_counts, stream)
+    _check(st, handle)
+
+
+def lidar_simulate_noalloc(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_waveforms: int,
+                           out_echoes: int, out_counts: int, stream: int = 0) -> None:
+    """lidar_simulate without any device allocation inside the call (fixed
+    32 MiB scratch, G-buffers up to 2^20 pixels; see include/lidar.h)."""
+    e = lidar_echoes_t(out_echoes, out_counts)
+    st = load().lidar_simulate_noalloc(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
     _check(st, handle)
 
 
