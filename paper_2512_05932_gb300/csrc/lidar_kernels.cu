@@ -416,14 +416,16 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
         }
         __syncthreads();
         if (R0 > R1) continue;
+        // columns split into nseg segments of (nearly) equal width <= kSeg
         const int nseg = (ncs + kSeg - 1) / kSeg;
+        const int segw = (ncs + nseg - 1) / nseg;
         const int nunits = (R1 - R0 + 1) * nseg;
         for (int ubase = warp * LR; ubase < nunits; ubase += nwarps * LR) {
             int unit = ubase + rsub;
             int row = R0 + unit / nseg;
             int seg = unit - (unit / nseg) * nseg;
             bool act = jok && unit < nunits && row >= P.row0 && row <= P.row1;
-            int c_lo = cs + seg * kSeg, c_hi = min(ce, c_lo + kSeg - 1);
+            int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
             int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
             if (!act) { my_lo = 1; my_hi = 0; }
             float el = A.el0 + ((float)row + 0.5f) * A.del;
@@ -432,16 +434,22 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
             float sdEl = sinf(dEl), cdEl = cosf(dEl);
             float Kv = P.sin_elb * cosEl;
             float Kc = P.cos_elb * cosEl;
+            // x = cg xg + sg yg, y = cg yg - sg xg with xg = cosEl sD and
+            // yg = sdEl + Kv vers: per-row coefficients of (sD, vers, 1)
+            const float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
+            const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
             const float4 *recrow = A.rec + 2 * (size_t)min(row, A.V - 1) * A.U;
             // narrow deposits of consecutive pixels that hit the same 4 bins are
             // summed in registers and written with one set of atomics
             uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
             float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
             // two columns per step: both samples' loads are issued before use
-            for (int c2 = c_lo; c2 <= c_lo + kSeg - 1; c2 += 2) {
-                float4 r0[2], r1[2];
+            for (int c2 = c_lo; c2 <= c_lo + segw - 1; c2 += 2) {
+                float4 r0[2];
+                int cws[2];
                 ProfFetch pf[2];
                 bool act[2];
+                bool any_need = false;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int c = c2 + u;
@@ -449,15 +457,21 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                     int cw = c;
                     if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
                     cw = act[u] ? cw : 0;
+                    cws[u] = cw;
                     r0[u] = __ldg(recrow + 2 * cw);
-                    r1[u] = __ldg(recrow + 2 * cw + 1);
+                    // a pixel with neither a return nor ambient light adds nothing
+                    act[u] = act[u] && !(__float_as_uint(r0[u].x) == kNoDeposit && r0[u].y == 0.f);
+                    any_need |= act[u];
+                }
+                if (!__any_sync(0xffffffffu, any_need)) continue;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c2 + u;
                     float2 t = tj[act[u] ? c - cs : 0];
                     // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
                     act[u] = act[u] && fmaf(-Kc, t.y, cdEl) > 0.f;
-                    float xg = cosEl * t.x;
-                    float yg = fmaf(Kv, t.y, sdEl);
-                    float x = fmaf(P.cg, xg, P.sg * yg);
-                    float y = fmaf(P.cg, yg, -P.sg * xg);
+                    float x = fmaf(ax, t.x, fmaf(bx, t.y, cx));
+                    float y = fmaf(ay, t.x, fmaf(by, t.y, cy));
                     pf[u] = profile_fetch<KIND>(A, x, y, act[u]);
                 }
 #pragma unroll
@@ -468,7 +482,9 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                     if (!(Pw > 0.f)) continue;
                     amb_acc = fmaf(Pw, a, amb_acc);
                     if (kab == kNoDeposit) continue;
-                    uint32_t kq = __float_as_uint(r1[u].x);
+                    // second half of the record (same 32-byte sector as the first)
+                    const float4 r1u = __ldg(recrow + 2 * cws[u] + 1);
+                    uint32_t kq = __float_as_uint(r1u.x);
                     if (kq != kNoDeposit) {
                         // narrow: hat weights on 4 consecutive bins at precomputed positions
                         if (kab != wk0 || kq != wk1) {
@@ -483,17 +499,17 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                         }
                         wa0 = fmaf(Pw, r0[u].z, wa0);
                         wa1 = fmaf(Pw, r0[u].w, wa1);
-                        wa2 = fmaf(Pw, r1[u].y, wa2);
-                        wa3 = fmaf(Pw, r1[u].z, wa3);
+                        wa2 = fmaf(Pw, r1u.y, wa2);
+                        wa3 = fmaf(Pw, r1u.z, wa3);
                     } else {
                         // wide: two partial bins at each end, a constant run between
                         int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
                         int xg2 = (int)(kab >> 16) - kBinBias + pad;
                         atomicAdd(hj + skew_pos(xf), Pw * r0[u].z);
                         atomicAdd(hj + skew_pos(xf + 1), Pw * r0[u].w);
-                        atomicAdd(hj + skew_pos(xg2), Pw * r1[u].y);
-                        atomicAdd(hj + skew_pos(xg2 + 1), Pw * r1[u].z);
-                        float cv = Pw * r1[u].w;
+                        atomicAdd(hj + skew_pos(xg2), Pw * r1u.y);
+                        atomicAdd(hj + skew_pos(xg2 + 1), Pw * r1u.z);
+                        float cv = Pw * r1u.w;
                         int xs = max(xf + 2, pad), xe = min(xg2 - 1, pad + nb - 1);
                         for (int x3 = xs; x3 <= xe; ++x3) atomicAdd(hj + skew_pos(x3), cv);
                     }
