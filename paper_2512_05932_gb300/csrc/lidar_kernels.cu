@@ -235,7 +235,7 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s)
 // footprint + waveform + echoes
 // --------------------------------------------------------------------------
 
-constexpr int kSeg = 32;     // columns per work unit
+constexpr int kSeg = 64;     // columns per work unit (one row)
 constexpr int kBlk = 256;    // waveform bins per convolution work item (8 per lane)
 
 // Per-beam histogram buffer: bins [-pad, n_bins + pad) at positions
@@ -382,12 +382,13 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     // ---- phase 1: profile-weighted deposits into the range bins -----------
     // The group's pixel box is walked in stripes of kTC columns. For each
     // stripe, tab[j][c] holds sin(dAz) and 1 - cos(dAz) of column c relative
-    // to beam j; work units are (row, 32-column segment) pairs; lane (j, rsub)
-    // of a warp handles beam j on unit rsub, all lanes stepping through the
-    // same columns so that lanes on the same row share each record load.
-    constexpr int LR = kWarp / G;  // work units per warp step
+    // to beam j. A work unit is one row x kSeg columns, taken by one warp:
+    // lane (j, q) handles beam j on columns q, q + CQ, q + 2 CQ, ... so that a
+    // warp's profile lookups stay within one row of the table and lanes on the
+    // same pixel share its record load.
+    constexpr int CQ = kWarp / G;  // columns handled side by side per beam
     const int j = lane % G;
-    const int rsub = lane / G;
+    const int q = lane / G;
     float amb_acc = 0.f;
     const BeamParam P = bp[j];
     const bool jok = (j < gcount) && P.valid;
@@ -420,14 +421,13 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
         const int nseg = (ncs + kSeg - 1) / kSeg;
         const int segw = (ncs + nseg - 1) / nseg;
         const int nunits = (R1 - R0 + 1) * nseg;
-        for (int ubase = warp * LR; ubase < nunits; ubase += nwarps * LR) {
-            int unit = ubase + rsub;
-            int row = R0 + unit / nseg;
-            int seg = unit - (unit / nseg) * nseg;
-            bool act = jok && unit < nunits && row >= P.row0 && row <= P.row1;
-            int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
+        for (int unit = warp; unit < nunits; unit += nwarps) {
+            const int row = R0 + unit / nseg;
+            const int seg = unit - (unit / nseg) * nseg;
+            const bool act_row = jok && row >= P.row0 && row <= P.row1;
+            const int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
             int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
-            if (!act) { my_lo = 1; my_hi = 0; }
+            if (!act_row) { my_lo = 1; my_hi = 0; }
             float el = A.el0 + ((float)row + 0.5f) * A.del;
             float cosEl = cosf(el);
             float dEl = ((float)(row - P.ri) - P.rf) * A.del;
@@ -438,13 +438,10 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
             // yg = sdEl + Kv vers: per-row coefficients of (sD, vers, 1)
             const float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
             const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
-            const float4 *recrow = A.rec + 2 * (size_t)min(row, A.V - 1) * A.U;
-            // narrow deposits of consecutive pixels that hit the same 4 bins are
-            // summed in registers and written with one set of atomics
-            uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
-            float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
+            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
             // two columns per step: both samples' loads are issued before use
-            for (int c2 = c_lo; c2 <= c_lo + segw - 1; c2 += 2) {
+            for (int cb = c_lo; cb <= c_hi; cb += 2 * CQ) {  // warp-uniform trip count
+                const int c2 = cb + q;
                 float4 r0[2];
                 int cws[2];
                 ProfFetch pf[2];
@@ -452,7 +449,7 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                 bool any_need = false;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int c = c2 + u;
+                    const int c = c2 + u * CQ;
                     act[u] = c >= my_lo && c <= my_hi;
                     int cw = c;
                     if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
@@ -466,7 +463,7 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                 if (!__any_sync(0xffffffffu, any_need)) continue;
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int c = c2 + u;
+                    const int c = c2 + u * CQ;
                     float2 t = tj[act[u] ? c - cs : 0];
                     // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
                     act[u] = act[u] && fmaf(-Kc, t.y, cdEl) > 0.f;
@@ -487,20 +484,10 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                     uint32_t kq = __float_as_uint(r1u.x);
                     if (kq != kNoDeposit) {
                         // narrow: hat weights on 4 consecutive bins at precomputed positions
-                        if (kab != wk0 || kq != wk1) {
-                            if (wk0 != kNoDeposit) {
-                                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
-                                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
-                                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
-                                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
-                            }
-                            wk0 = kab; wk1 = kq;
-                            wa0 = 0.f; wa1 = 0.f; wa2 = 0.f; wa3 = 0.f;
-                        }
-                        wa0 = fmaf(Pw, r0[u].z, wa0);
-                        wa1 = fmaf(Pw, r0[u].w, wa1);
-                        wa2 = fmaf(Pw, r1u.y, wa2);
-                        wa3 = fmaf(Pw, r1u.z, wa3);
+                        atomicAdd(hj + (kab & 0xFFFFu), Pw * r0[u].z);
+                        if (r0[u].w != 0.f) atomicAdd(hj + (kab >> 16), Pw * r0[u].w);
+                        if (r1u.y != 0.f) atomicAdd(hj + (kq & 0xFFFFu), Pw * r1u.y);
+                        if (r1u.z != 0.f) atomicAdd(hj + (kq >> 16), Pw * r1u.z);
                     } else {
                         // wide: two partial bins at each end, a constant run between
                         int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
@@ -514,12 +501,6 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
                         for (int x3 = xs; x3 <= xe; ++x3) atomicAdd(hj + skew_pos(x3), cv);
                     }
                 }
-            }
-            if (wk0 != kNoDeposit) {
-                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
-                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
-                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
-                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
             }
         }
     }
