@@ -226,6 +226,40 @@ lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffe
 lidar_status_t lidar_simulate_noalloc(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                       float *out_waveforms, lidar_echoes_t *out_echoes, void *stream);
 
+/* One frame of a batch: a rendering (G-buffer) seen by one sensor at one pose.
+ * A batch simulates many frames in one pass; this amortises the per-launch cost
+ * the way one rendering serves all beams of a sensor (Sec. II-B). All sensors
+ * of a batch must share the executor's sensor model (the same profile, pulse
+ * and calibration given to lidar_create); their beam patterns may differ. */
+typedef struct {
+    const lidar_t *sensor;        /* beam pattern of this frame */
+    lidar_gbuffer_t gbuffer;      /* device planes, as for lidar_simulate */
+    lidar_pose_t pose;
+    float *out_waveforms;         /* device [sensor's n_beams][n_bins] */
+    lidar_echoes_t out_echoes;    /* device, as for lidar_simulate */
+} lidar_frame_t;
+
+/* Simulates n_frames frames, enqueued on `stream`, as two kernel launches: one
+ * setup launch over every frame's pixels and beams, and one persistent
+ * footprint launch whose CTAs take (frame, beam group) items from a device
+ * counter, largest footprints first. The descriptor upload and both launches
+ * are captured once into a CUDA graph per batch shape (frame count, sizes,
+ * beam counts, tuning) and replayed; a new shape is captured anew. The call
+ * waits (host side) until the previous batch of this executor has finished
+ * reading its descriptors. Scratch for all frames (32 bytes per pixel, 64 per
+ * beam) is grown with cudaMalloc when needed. Errors as lidar_simulate, plus
+ * LIDAR_EINVAL if a frame's sensor has a different sensor model. */
+lidar_status_t lidar_simulate_batch(lidar_t *executor, const lidar_frame_t *frames, int32_t n_frames, void *stream);
+
+/* Autotuner for lidar_simulate_batch: times the batch (CUDA events on `stream`)
+ * for every beam-group size (beams per CTA) that fits shared memory and for
+ * 1 or 2 resident CTAs per SM, keeps the fastest for this executor, and
+ * leaves the outputs of the last run in the frames' buffers. */
+lidar_status_t lidar_autotune_batch(lidar_t *executor, const lidar_frame_t *frames, int32_t n_frames, void *stream);
+
+/* Current batch tuning: beams per CTA and resident CTAs per SM. */
+lidar_status_t lidar_batch_config(const lidar_t *executor, int32_t *beams_per_cta, int32_t *ctas_per_sm);
+
 /* Synchronises `stream` and reports any asynchronous CUDA error as LIDAR_ECUDA. */
 lidar_status_t lidar_sync(lidar_t *lidar, void *stream);
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <string>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -58,6 +60,22 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
+    // sensor-model fingerprint (batch compatibility) and table hash
+    uint64_t model_hash = 0;
+    // batched execution
+    int32_t batch_G = 8, batch_cps = 0;  // beams per CTA, CTAs per SM (0 = occupancy maximum)
+    float4 *d_brec = nullptr;
+    size_t brec_cap = 0;  // pixels
+    gbl::BeamParam *d_bbeams = nullptr;
+    size_t bbeams_cap = 0;  // beams
+    unsigned char *d_blob = nullptr, *h_blob = nullptr;
+    size_t blob_cap = 0;
+    int *d_counter = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t blob_free = nullptr;
+    bool blob_pending = false;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> gkey;
     // per-kernel timing (lidar_profile_enable)
     bool prof = false;
     std::vector<cudaEvent_t> ev;  // 3 events per recorded simulate call
@@ -358,8 +376,26 @@ cudaEvent_t next_event(lidar_t *l)
     return l->ev[l->ev_used++];
 }
 
+void free_batch(lidar_t *l)
+{
+    if (l->gexec) cudaGraphExecDestroy(l->gexec);
+    l->gexec = nullptr;
+    l->gkey.clear();
+    cudaFree(l->d_brec);
+    cudaFree(l->d_bbeams);
+    cudaFree(l->d_blob);
+    cudaFreeHost(l->h_blob);
+    cudaFree(l->d_counter);
+    if (l->cap_stream) cudaStreamDestroy(l->cap_stream);
+    if (l->blob_free) cudaEventDestroy(l->blob_free);
+    l->d_brec = nullptr; l->d_bbeams = nullptr; l->d_blob = nullptr; l->h_blob = nullptr; l->d_counter = nullptr;
+    l->cap_stream = nullptr; l->blob_free = nullptr;
+    l->brec_cap = l->bbeams_cap = l->blob_cap = 0;
+}
+
 void free_all(lidar_t *l)
 {
+    free_batch(l);
     free_events(l);
     cudaFree(l->d_dirs);
     cudaFree(l->d_quads);
@@ -372,35 +408,61 @@ void free_all(lidar_t *l)
     cudaFree(l->d_counts);
 }
 
-lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
-                       int32_t *counts, cudaStream_t s)
-{
-    size_t pixels = (size_t)g->U * g->V;
-    lidar_status_t st = ensure_scratch(l, pixels);
-    if (st != LIDAR_OK) return st;
-    bool panorama = std::fabs(g->U * g->daz - 2 * kPi) <= 1e-6;
+bool is_panorama(const lidar_gbuffer_t *g) { return std::fabs(g->U * g->daz - 2 * kPi) <= 1e-6; }
 
+// Setup-kernel arguments of one frame (geometry, planes, pose, scratch).
+gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_gbuffer_t *g, const double R[9],
+                          float4 *rec, gbl::BeamParam *beams)
+{
     gbl::SetupArgs sa{};
+    size_t pixels = (size_t)g->U * g->V;
     sa.U = g->U; sa.V = g->V;
     sa.az0 = (float)g->az0; sa.el0 = (float)g->el0; sa.daz = (float)g->daz; sa.del = (float)g->del;
     sa.ch = (float)std::cos(0.5 * g->daz); sa.sh = (float)std::sin(0.5 * g->daz);
     sa.cv = (float)std::cos(0.5 * g->del); sa.sv = (float)std::sin(0.5 * g->del);
     sa.range = g->range; sa.nx = g->nx; sa.ny = g->ny; sa.nz = g->nz;
     sa.rho = g->rho_d; sa.retro = g->retro; sa.amb = g->ambient;
-    sa.rec = l->d_rec;
+    sa.rec = rec;
     sa.x_scale = (float)(2.0 / (kC * l->dt));
     sa.x_off = (float)(-l->t0 / l->dt - 0.5);
     sa.n_bins = l->n_bins;
     sa.pad = gbl::footprint_pad(l->M);
     long pb = (long)((pixels + 255) / 256);
     sa.pix_blocks = (int)std::min<long>(pb, 152L * 64);
-    sa.n_beams = l->n_beams;
-    sa.dirs = l->d_dirs;
+    sa.n_beams = sensor->n_beams;
+    sa.dirs = sensor->d_dirs;
     for (int i = 0; i < 9; ++i) sa.R[i] = R[i];
     sa.az0d = g->az0; sa.el0d = g->el0; sa.dazd = g->daz; sa.deld = g->del;
-    sa.panorama = panorama ? 1 : 0;
+    sa.panorama = is_panorama(g) ? 1 : 0;
     sa.support_rad = l->support_rad;
-    sa.beams = l->d_beams;
+    sa.beams = beams;
+    return sa;
+}
+
+// Footprint-kernel arguments that depend on the sensor model only.
+gbl::FootprintArgs model_args(const lidar_t *l)
+{
+    gbl::FootprintArgs fa{};
+    fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
+    fa.invZ = (float)(1.0 / l->Z);
+    fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
+    fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
+    fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
+    fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
+    fa.T = (float)l->T; fa.s_amb = (float)l->s_amb; fa.max_echoes = l->max_echoes;
+    fa.c0 = (float)l->coef[0]; fa.c1 = (float)l->coef[1]; fa.c2 = (float)l->coef[2];
+    fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
+    fa.rB = (float)(0.5 * kC * l->dt);
+    return fa;
+}
+
+lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
+                       int32_t *counts, cudaStream_t s)
+{
+    size_t pixels = (size_t)g->U * g->V;
+    lidar_status_t st = ensure_scratch(l, pixels);
+    if (st != LIDAR_OK) return st;
+    gbl::SetupArgs sa = setup_args(l, l, g, R, l->d_rec, l->d_beams);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     if (l->prof) {
         size_t mark = l->ev_used;
@@ -412,26 +474,189 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
     if (ev1) cudaEventRecord(ev1, s);
 
-    gbl::FootprintArgs fa{};
+    gbl::FootprintArgs fa = model_args(l);
     fa.U = g->U; fa.V = g->V; fa.panorama = sa.panorama;
     fa.az0 = sa.az0; fa.el0 = sa.el0; fa.daz = sa.daz; fa.del = sa.del;
     fa.rec = l->d_rec;
     fa.beams = l->d_beams;
     fa.n_beams = l->n_beams;
-    fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
-    fa.invZ = (float)(1.0 / l->Z);
-    fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
-    fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
-    fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
-    fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
-    fa.T = (float)l->T; fa.s_amb = (float)l->s_amb; fa.max_echoes = l->max_echoes;
-    fa.c0 = (float)l->coef[0]; fa.c1 = (float)l->coef[1]; fa.c2 = (float)l->coef[2];
-    fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
-    fa.rB = (float)(0.5 * kC * l->dt);
     fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
     e = gbl::launch_footprint(l->kind, l->G, l->threads, l->smem, fa, s);
     if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     if (ev2) cudaEventRecord(ev2, s);
+    return LIDAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched execution
+// ---------------------------------------------------------------------------
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename T>
+lidar_status_t grow(lidar_t *l, T **p, size_t *cap, size_t need, const char *what)
+{
+    if (need <= *cap) return LIDAR_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, need * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(l, e, what);
+    *cap = need;
+    return LIDAR_OK;
+}
+
+// Builds the descriptor blob of a batch (host copy) and returns its layout.
+struct BlobLayout {
+    size_t off_setup, off_pix, off_beam, off_frames, off_items, size;
+    int n_items, total_blocks;
+};
+
+lidar_status_t batch_validate(lidar_t *l, const lidar_frame_t *fr, int n, std::vector<std::array<double, 9>> &Rs)
+{
+    if (!fr || n < 1) return fail(l, LIDAR_EINVAL, "batch needs at least one frame");
+    Rs.resize(n);
+    for (int f = 0; f < n; ++f) {
+        const lidar_frame_t &F = fr[f];
+        if (!F.sensor) return fail(l, LIDAR_EINVAL, "frame %d: sensor is NULL", f);
+        if (F.sensor->model_hash != l->model_hash)
+            return fail(l, LIDAR_EINVAL, "frame %d: sensor model differs from the executor's", f);
+        lidar_status_t st = check_gbuffer(l, &F.gbuffer);
+        if (st != LIDAR_OK) return fail(l, st, "frame %d: %s", f, std::string(l->err).c_str());
+        if ((st = check_pose(l, &F.pose, Rs[f].data())) != LIDAR_OK) return fail(l, st, "frame %d: %s", f, std::string(l->err).c_str());
+        if (!F.out_waveforms || !F.out_echoes.echoes || !F.out_echoes.counts)
+            return fail(l, LIDAR_EINVAL, "frame %d: output pointer is NULL", f);
+    }
+    return LIDAR_OK;
+}
+
+lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_t s, int G, int cps)
+{
+    std::vector<std::array<double, 9>> Rs;
+    lidar_status_t st = batch_validate(l, fr, n, Rs);
+    if (st != LIDAR_OK) return st;
+    cudaError_t e;
+    if (!l->cap_stream) {
+        if ((e = cudaStreamCreateWithFlags(&l->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&l->blob_free, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaEventCreate");
+        if ((e = cudaMalloc(&l->d_counter, sizeof(int))) != cudaSuccess) return cuda_fail(l, e, "cudaMalloc(counter)");
+    }
+    // scratch for all frames
+    size_t tot_pix = 0, tot_beams = 0;
+    std::vector<size_t> pix_off(n), beam_off(n);
+    for (int f = 0; f < n; ++f) {
+        pix_off[f] = tot_pix;
+        beam_off[f] = tot_beams;
+        tot_pix += (size_t)fr[f].gbuffer.U * fr[f].gbuffer.V;
+        tot_beams += (size_t)fr[f].sensor->n_beams;
+    }
+    if ((st = grow(l, &l->d_brec, &l->brec_cap, 2 * tot_pix, "cudaMalloc(batch records)")) != LIDAR_OK) return st;
+    if ((st = grow(l, &l->d_bbeams, &l->bbeams_cap, tot_beams, "cudaMalloc(batch beams)")) != LIDAR_OK) return st;
+    // items: (frame, group), frames with the widest footprints (pixels per beam) first
+    std::vector<int> order(n);
+    for (int f = 0; f < n; ++f) order[f] = f;
+    auto cost = [&](int f) {
+        const lidar_gbuffer_t &g = fr[f].gbuffer;
+        return l->support_rad * l->support_rad / (g.daz * g.del);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<int2> items;
+    for (int f : order) {
+        int groups = (fr[f].sensor->n_beams + G - 1) / G;
+        for (int g = 0; g < groups; ++g) items.push_back(make_int2(f, g));
+    }
+    BlobLayout B;
+    B.off_setup = 0;
+    B.off_pix = align16(B.off_setup + n * sizeof(gbl::SetupArgs));
+    B.off_beam = align16(B.off_pix + (n + 1) * sizeof(int));
+    B.off_frames = align16(B.off_beam + (n + 1) * sizeof(int));
+    B.off_items = align16(B.off_frames + n * sizeof(gbl::FrameDesc));
+    B.size = align16(B.off_items + items.size() * sizeof(int2));
+    B.n_items = (int)items.size();
+    // the previous batch's graph may still be reading the pinned staging copy
+    if (l->blob_pending) {
+        if ((e = cudaEventSynchronize(l->blob_free)) != cudaSuccess) return cuda_fail(l, e, "cudaEventSynchronize");
+        l->blob_pending = false;
+    }
+    if (B.size > l->blob_cap) {
+        if (l->gexec) { cudaGraphExecDestroy(l->gexec); l->gexec = nullptr; l->gkey.clear(); }
+        cudaFree(l->d_blob);
+        cudaFreeHost(l->h_blob);
+        l->d_blob = nullptr; l->h_blob = nullptr; l->blob_cap = 0;
+        size_t cap = B.size * 2;
+        if ((e = cudaMalloc(&l->d_blob, cap)) != cudaSuccess) return cuda_fail(l, e, "cudaMalloc(batch descriptors)");
+        if ((e = cudaMallocHost(&l->h_blob, cap)) != cudaSuccess) return cuda_fail(l, e, "cudaMallocHost(batch descriptors)");
+        l->blob_cap = cap;
+    }
+    unsigned char *hb = l->h_blob;
+    gbl::SetupArgs *hs = reinterpret_cast<gbl::SetupArgs *>(hb + B.off_setup);
+    int *hpix = reinterpret_cast<int *>(hb + B.off_pix);
+    int *hbeam = reinterpret_cast<int *>(hb + B.off_beam);
+    gbl::FrameDesc *hf = reinterpret_cast<gbl::FrameDesc *>(hb + B.off_frames);
+    int pb = 0, bb = 0;
+    for (int f = 0; f < n; ++f) {
+        const lidar_frame_t &F = fr[f];
+        float4 *rec = l->d_brec + 2 * pix_off[f];
+        gbl::BeamParam *bp = l->d_bbeams + beam_off[f];
+        hs[f] = setup_args(l, F.sensor, &F.gbuffer, Rs[f].data(), rec, bp);
+        hpix[f] = pb;
+        hbeam[f] = bb;
+        pb += (int)(((size_t)F.gbuffer.U * F.gbuffer.V + 255) / 256);
+        bb += (F.sensor->n_beams + 255) / 256;
+        gbl::FrameDesc D{};
+        D.U = F.gbuffer.U; D.V = F.gbuffer.V; D.panorama = hs[f].panorama; D.n_beams = F.sensor->n_beams;
+        D.az0 = hs[f].az0; D.el0 = hs[f].el0; D.daz = hs[f].daz; D.del = hs[f].del;
+        D.rec = rec; D.beams = bp;
+        D.wave = F.out_waveforms; D.echoes = F.out_echoes.echoes; D.counts = F.out_echoes.counts;
+        hf[f] = D;
+    }
+    hpix[n] = pb;
+    hbeam[n] = bb;
+    B.total_blocks = pb + bb;
+    std::memcpy(hb + B.off_items, items.data(), items.size() * sizeof(int2));
+
+    // persistent grid size
+    size_t smem = gbl::footprint_smem_bytes(G, model_args(l));
+    if ((e = gbl::prepare_footprint_batch(l->kind, G, smem)) != cudaSuccess) return cuda_fail(l, e, "cudaFuncSetAttribute");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, l->device);
+    int per_sm = cps > 0 ? cps : 2;
+    int grid = std::max(1, std::min(B.n_items, per_sm * sms));
+
+    // graph keyed on everything the captured launches depend on
+    std::vector<long long> key = {n, (long long)B.size, B.n_items, B.total_blocks, G, grid, (long long)smem,
+                                  (long long)(uintptr_t)l->d_blob, (long long)(uintptr_t)l->h_blob};
+    if (!l->gexec || key != l->gkey) {
+        if (l->gexec) { cudaGraphExecDestroy(l->gexec); l->gexec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(l->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamBeginCapture");
+        cudaError_t e1 = cudaMemcpyAsync(l->d_blob, l->h_blob, B.size, cudaMemcpyHostToDevice, l->cap_stream);
+        const unsigned char *db = l->d_blob;
+        cudaError_t e2 = gbl::launch_setup_batch(reinterpret_cast<const gbl::SetupArgs *>(db + B.off_setup),
+                                                 reinterpret_cast<const int *>(db + B.off_pix),
+                                                 reinterpret_cast<const int *>(db + B.off_beam), n, B.total_blocks,
+                                                 l->d_counter, l->cap_stream);
+        gbl::FootprintArgs base = model_args(l);
+        cudaError_t e3 = gbl::launch_footprint_batch(l->kind, G, l->threads, grid, smem, base,
+                                                     reinterpret_cast<const gbl::FrameDesc *>(db + B.off_frames),
+                                                     reinterpret_cast<const int2 *>(db + B.off_items), B.n_items,
+                                                     l->d_counter, l->cap_stream);
+        e = cudaStreamEndCapture(l->cap_stream, &graph);
+        if (e1 != cudaSuccess) return cuda_fail(l, e1, "descriptor upload capture");
+        if (e2 != cudaSuccess) return cuda_fail(l, e2, "batch setup launch capture");
+        if (e3 != cudaSuccess) return cuda_fail(l, e3, "batch footprint launch capture");
+        if (e != cudaSuccess) return cuda_fail(l, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&l->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { l->gexec = nullptr; return cuda_fail(l, e, "cudaGraphInstantiate"); }
+        l->gkey = key;
+    }
+    if ((e = cudaGraphLaunch(l->gexec, s)) != cudaSuccess) return cuda_fail(l, e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(l->blob_free, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+    l->blob_pending = true;
     return LIDAR_OK;
 }
 
@@ -513,6 +738,29 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         }
     } else {
         for (int i = 0; i < 3; ++i) l->coef[i] = ca->epw_coef[i];
+    }
+
+    // fingerprint of the sensor model (profile, pulse, calibration): frames of a
+    // batch must share the executor's model
+    {
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](const void *p, size_t n) {
+            const unsigned char *c = static_cast<const unsigned char *>(p);
+            for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+        };
+        double md[12] = {l->Z, l->dt, l->t0, l->T, l->s_amb, l->coef[0], l->coef[1], l->coef[2],
+                         (double)l->kg, (double)l->trunc2, (double)l->tail_amp, (double)l->tail_hp};
+        int32_t mi[6] = {l->kind, l->n_bins, l->M, l->max_echoes, l->qw, l->qh};
+        mix(md, sizeof md);
+        mix(mi, sizeof mi);
+        if (p->kind == LIDAR_PROFILE_TABLE) {
+            mix(p->table, (size_t)p->table_w * p->table_h * sizeof(float));
+            mix(&p->pitch_deg, sizeof p->pitch_deg);
+        } else {
+            double pr[5] = {p->sigma_deg, p->tail_amp, p->tail_core_deg, p->tail_pow, p->trunc_deg};
+            mix(pr, sizeof pr);
+        }
+        l->model_hash = h;
     }
 
     // launch shape: largest beam group whose histograms fit in shared memory
@@ -663,6 +911,59 @@ lidar_status_t lidar_simulate_noalloc(lidar_t *l, const lidar_gbuffer_t *g, cons
     l->rec_cap = own_cap;
     l->prof = prof;
     return st;
+}
+
+lidar_status_t lidar_simulate_batch(lidar_t *l, const lidar_frame_t *frames, int32_t n_frames, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "executor is NULL");
+    return batch_run(l, frames, n_frames, (cudaStream_t)stream, l->batch_G, l->batch_cps);
+}
+
+lidar_status_t lidar_autotune_batch(lidar_t *l, const lidar_frame_t *frames, int32_t n_frames, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "executor is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, l->device);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess)
+        return cuda_fail(l, e, "cudaEventCreate");
+    float best = 1e30f;
+    int bestG = l->batch_G, bestC = l->batch_cps;
+    lidar_status_t st = LIDAR_OK;
+    for (int G : {2, 4, 8, 16}) {
+        size_t smem = gbl::footprint_smem_bytes(G, model_args(l));
+        if ((long)smem > smem_optin) continue;
+        for (int cps : {1, 2}) {
+            if (cps * smem > 228 * 1024) continue;
+            // one untimed run (graph capture), then two timed runs
+            if ((st = batch_run(l, frames, n_frames, s, G, cps)) != LIDAR_OK) break;
+            cudaEventRecord(a, s);
+            for (int r = 0; r < 2 && st == LIDAR_OK; ++r) st = batch_run(l, frames, n_frames, s, G, cps);
+            cudaEventRecord(b, s);
+            if (st != LIDAR_OK) break;
+            if ((e = cudaEventSynchronize(b)) != cudaSuccess) { st = cuda_fail(l, e, "cudaEventSynchronize"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best) { best = ms; bestG = G; bestC = cps; }
+        }
+        if (st != LIDAR_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != LIDAR_OK) return st;
+    l->batch_G = bestG;
+    l->batch_cps = bestC;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_batch_config(const lidar_t *l, int32_t *beams_per_cta, int32_t *ctas_per_sm)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "executor is NULL");
+    if (beams_per_cta) *beams_per_cta = l->batch_G;
+    if (ctas_per_sm) *ctas_per_sm = l->batch_cps > 0 ? l->batch_cps : 2;
+    return LIDAR_OK;
 }
 
 lidar_status_t lidar_sync(lidar_t *l, void *stream)

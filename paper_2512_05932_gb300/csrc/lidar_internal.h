@@ -82,6 +82,17 @@ struct FootprintArgs {
     int32_t *counts;
 };
 
+// Per-frame fields of the batched footprint kernel.
+struct FrameDesc {
+    int U, V, panorama, n_beams;
+    float az0, el0, daz, del;
+    const float4 *rec;
+    const BeamParam *beams;
+    float *wave;
+    lidar_echo_t *echoes;
+    int32_t *counts;
+};
+
 // Device address of the fixed scratch of lidar_simulate_noalloc on the current
 // device (lidar_noalloc.cu); looked up on first use per device.
 cudaError_t noalloc_records(float4 **out);
@@ -92,5 +103,11 @@ size_t footprint_smem_bytes(int G, const FootprintArgs &a);
 int footprint_pad(int M);
 cudaError_t prepare_footprint(int kind, int G, size_t smem);
 cudaError_t launch_footprint(int kind, int G, int threads, size_t smem, const FootprintArgs &a, cudaStream_t s);
+cudaError_t launch_setup_batch(const SetupArgs *frames, const int *pix_blk, const int *beam_blk, int n_frames,
+                               int total_blocks, int *counter, cudaStream_t s);
+cudaError_t prepare_footprint_batch(int kind, int G, size_t smem);
+cudaError_t launch_footprint_batch(int kind, int G, int threads, int grid, size_t smem, const FootprintArgs &base,
+                                   const FrameDesc *frames, const int2 *items, int n_items, int *counter,
+                                   cudaStream_t s);
 
 }  // namespace gbl

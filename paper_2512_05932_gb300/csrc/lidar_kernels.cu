@@ -224,6 +224,44 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A)
     }
 }
 
+// Batched setup: frame f owns pixel blocks [pix_blk[f], pix_blk[f+1]) and beam
+// blocks [beam_blk[f], beam_blk[f+1]) (pixel blocks first). Block 0 also resets
+// the work counter of the batched footprint kernel that follows on the stream.
+__global__ void __launch_bounds__(256) setup_batch_kernel(const SetupArgs *frames, const int *pix_blk,
+                                                          const int *beam_blk, int n_frames, int *counter)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    const int b = blockIdx.x;
+    const int total_pix_blk = pix_blk[n_frames];
+    if (b < total_pix_blk) {
+        int lo = 0, hi = n_frames - 1;  // last f with pix_blk[f] <= b
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (pix_blk[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        const SetupArgs &A = frames[lo];
+        int idx = (b - pix_blk[lo]) * blockDim.x + threadIdx.x;
+        if (idx < A.U * A.V) setup_pixel(A, idx);
+    } else {
+        const int bb = b - total_pix_blk;
+        int lo = 0, hi = n_frames - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (beam_blk[mid] <= bb) lo = mid; else hi = mid - 1;
+        }
+        const SetupArgs &A = frames[lo];
+        int beam = (bb - beam_blk[lo]) * blockDim.x + threadIdx.x;
+        if (beam < A.n_beams) setup_beam(A, beam);
+    }
+}
+
+cudaError_t launch_setup_batch(const SetupArgs *frames, const int *pix_blk, const int *beam_blk, int n_frames,
+                               int total_blocks, int *counter, cudaStream_t s)
+{
+    setup_batch_kernel<<<total_blocks, 256, 0, s>>>(frames, pix_blk, beam_blk, n_frames, counter);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s)
 {
     int beam_blocks = (a.n_beams + 255) / 256;
@@ -325,10 +363,11 @@ __device__ __forceinline__ float profile_finish(const ProfFetch &r)
     return fmaf(r.fy, bot - top, top);
 }
 
+// One group of G consecutive beams of one frame (the whole per-CTA pipeline).
+// Every thread of the CTA must call it (it contains block barriers).
 template <int KIND, int G>
-__global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
+__device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nb = A.n_bins, M = A.M;
     const Layout Ly = make_layout(G, nb, M);
     const int pad = Ly.pad;
@@ -341,7 +380,7 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int b0 = blockIdx.x * G;
+    const int b0 = group * G;
     const int gcount = min(G, A.n_beams - b0);
 
     // ---- phase 0: clear, load parameters, union box ----------------------
@@ -696,6 +735,39 @@ __global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
     }
 }
 
+template <int KIND, int G>
+__global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    footprint_group<KIND, G>(A, blockIdx.x, smem_raw);
+}
+
+// Batched form: a persistent grid whose CTAs take (frame, group) items, in the
+// order of `items`, from a counter that the batch setup kernel resets.
+template <int KIND, int G>
+__global__ void __launch_bounds__(512) footprint_batch_kernel(FootprintArgs base, const FrameDesc *frames,
+                                                              const int2 *items, int n_items, int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (it >= n_items) break;
+        const int2 fg = items[it];
+        const FrameDesc F = frames[fg.x];
+        FootprintArgs A = base;
+        A.U = F.U; A.V = F.V; A.panorama = F.panorama;
+        A.az0 = F.az0; A.el0 = F.el0; A.daz = F.daz; A.del = F.del;
+        A.rec = F.rec; A.beams = F.beams; A.n_beams = F.n_beams;
+        A.wave = F.wave; A.echoes = F.echoes; A.counts = F.counts;
+        footprint_group<KIND, G>(A, fg.y, smem_raw);
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
 size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 {
     return make_layout(G, a.n_bins, a.M).total;
@@ -708,6 +780,37 @@ static cudaError_t prep_one(size_t smem)
 {
     return cudaFuncSetAttribute(footprint_wave_kernel<KIND, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+}
+
+template <int KIND, int G>
+static cudaError_t prep_batch_one(size_t smem)
+{
+    return cudaFuncSetAttribute(footprint_batch_kernel<KIND, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+cudaError_t prepare_footprint_batch(int kind, int G, size_t smem)
+{
+#define GBL_CASE(K, GG) if (kind == K && G == GG) return prep_batch_one<K, GG>(smem);
+    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
+    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_footprint_batch(int kind, int G, int threads, int grid, size_t smem, const FootprintArgs &base,
+                                   const FrameDesc *frames, const int2 *items, int n_items, int *counter,
+                                   cudaStream_t s)
+{
+#define GBL_CASE(K, GG)                                                                                    \
+    if (kind == K && G == GG) {                                                                            \
+        footprint_batch_kernel<K, GG><<<grid, threads, smem, s>>>(base, frames, items, n_items, counter); \
+        return cudaGetLastError();                                                                         \
+    }
+    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
+    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t prepare_footprint(int kind, int G, size_t smem)

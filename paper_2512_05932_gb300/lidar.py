@@ -62,13 +62,18 @@ class lidar_echoes_t(C.Structure):
     _fields_ = [("echoes", C.c_void_p), ("counts", C.c_void_p)]
 
 
+class lidar_frame_t(C.Structure):
+    _fields_ = [("sensor", C.c_void_p), ("gbuffer", lidar_gbuffer_t), ("pose", lidar_pose_t),
+                ("out_waveforms", C.c_void_p), ("out_echoes", lidar_echoes_t)]
+
+
 ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), ("peak", "f4"),
                        ("bin_peak", "i4"), ("bin_start", "i4"), ("bin_end", "i4"), ("flags", "u4")])
 assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 
 # exported symbols (every function declared in include/lidar.h)
 SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_simulate_noalloc", "lidar_sync",
-           "lidar_get_info",
+           "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
 KERNELS = ("setup", "footprint_wave")
@@ -103,6 +108,12 @@ def load(path: str = LIB_PATH):
     lib.lidar_simulate_noalloc.restype = C.c_int
     lib.lidar_simulate_noalloc.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                            P(lidar_echoes_t), C.c_void_p]
+    lib.lidar_simulate_batch.restype = C.c_int
+    lib.lidar_simulate_batch.argtypes = [C.c_void_p, P(lidar_frame_t), C.c_int32, C.c_void_p]
+    lib.lidar_autotune_batch.restype = C.c_int
+    lib.lidar_autotune_batch.argtypes = [C.c_void_p, P(lidar_frame_t), C.c_int32, C.c_void_p]
+    lib.lidar_batch_config.restype = C.c_int
+    lib.lidar_batch_config.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int32)]
     lib.lidar_sync.restype = C.c_int
     lib.lidar_sync.argtypes = [C.c_void_p, C.c_void_p]
     lib.lidar_get_info.restype = C.c_int
@@ -227,6 +238,33 @@ def lidar_simulate_noalloc(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t,
     e = lidar_echoes_t(out_echoes, out_counts)
     st = load().lidar_simulate_noalloc(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
     _check(st, handle)
+
+
+def make_frames(items) -> "C.Array":
+    """items: list of (sensor handle, gbuffer struct, pose struct, waveforms ptr,
+    echoes ptr, counts ptr)."""
+    arr = (lidar_frame_t * len(items))()
+    for i, (h, g, p, w, e, c) in enumerate(items):
+        arr[i].sensor = h
+        arr[i].gbuffer = g
+        arr[i].pose = p
+        arr[i].out_waveforms = w
+        arr[i].out_echoes = lidar_echoes_t(e, c)
+    return arr
+
+
+def lidar_simulate_batch(executor, frames, stream: int = 0) -> None:
+    _check(load().lidar_simulate_batch(executor, frames, len(frames), stream), executor)
+
+
+def lidar_autotune_batch(executor, frames, stream: int = 0) -> None:
+    _check(load().lidar_autotune_batch(executor, frames, len(frames), stream), executor)
+
+
+def lidar_batch_config(executor) -> tuple:
+    g, c = C.c_int32(), C.c_int32()
+    _check(load().lidar_batch_config(executor, C.byref(g), C.byref(c)), executor)
+    return g.value, c.value
 
 
 def lidar_sync(handle, stream: int = 0) -> None:

@@ -414,3 +414,61 @@ def tiny_case(seed: int = 3, U: int = 37, V: int = 29, n_beams: int = 5, n_bins:
     prof = radial_profile(0.08, 1e-3, 0.08, 3.0, 0.4)
     return Workload("tiny", gb, dirs, prof, pulse(n_bins, 0.1e-9), calib(2e-4, 1e-3, 3, True),
                     pose_ypr(0.002, -0.001, 0.3))
+
+
+# ----------------------------------------------------------------------------
+# batched workload: many frames of uneven size, pattern and pose
+# ----------------------------------------------------------------------------
+
+SIZE_CLASSES = ((512, 256), (1024, 512), (2048, 1024), (4096, 2048))
+
+
+def _boresight_frame(R):
+    """Azimuth and elevation of the sensor boresight R x in the G-buffer frame."""
+    a = np.asarray(R, np.float64) @ np.array([1.0, 0.0, 0.0])
+    return math.atan2(a[1], a[0]), math.asin(max(-1.0, min(1.0, a[2])))
+
+
+def plane_retro_frame(g, U, V, R, pitch_deg=0.02):
+    """One frame of the plane + retro-patch scene family seen by a posed sensor:
+    a Lambertian plane across the boresight at 6-14 m (reflectance 0.3-0.7),
+    a 0.5 x 0.5 m retro patch (gain 100) placed within a few degrees of the
+    boresight, uniform ambient 0.01; the G-buffer is centred on the boresight."""
+    R = np.asarray(R, np.float64)
+    bx, by, bz = R[:, 0], R[:, 1], R[:, 2]
+    dist = g.uniform(6.0, 14.0)
+    rho = g.uniform(0.3, 0.7)
+    off = g.uniform(-2.5, 2.5, size=2) * DEG * dist
+    decal = Rect(dist * bx + off[0] * by + off[1] * bz, by, bz, 0.25, 0.25, rho_d=rho, retro=100.0)
+    scene = Scene(planes=[Plane(bx, dist, rho, 0.0, decal)], ambient="uniform", ambient_level=0.01)
+    az_c, el_c = _boresight_frame(R)
+    pitch = pitch_deg * DEG
+    return raycast(scene, U, V, az_c - U * pitch / 2, el_c - V * pitch / 2, pitch, pitch)
+
+
+def batched_frames(seed: int = 4, n_frames: int = 64, size_classes=SIZE_CLASSES, beams=(1_000, 100_000)):
+    """Batched workload: n_frames frames, each with a G-buffer size drawn from
+    size_classes, a beam count log-uniform in `beams`, a line-scan or a MEMS
+    Lissajous (7:9) pattern over 80 % of its field of view, and a random pose
+    (yaw +-180 deg, pitch +-5 deg, roll +-2 deg). All frames share the sensor
+    model of the small plane/retro instance (radial profile, 1024 bins of 0.1 ns).
+    Returns a list of Workload."""
+    g = rng(seed)
+    base = small_plane_retro()
+    out = []
+    for f in range(n_frames):
+        U, V = size_classes[int(g.integers(len(size_classes)))]
+        R = pose_ypr(g.uniform(-math.pi, math.pi), g.uniform(-5, 5) * DEG, g.uniform(-2, 2) * DEG)
+        gb = plane_retro_frame(g, U, V, R)
+        nb = int(round(math.exp(g.uniform(math.log(beams[0]), math.log(beams[1])))))
+        fov_az, fov_el = 0.8 * U * 0.02 * DEG, 0.8 * V * 0.02 * DEG
+        if g.uniform() < 0.5:
+            rows = max(4, int(round(math.sqrt(nb * fov_el / fov_az))))
+            cols = max(1, nb // rows)
+            dirs = linescan_pattern(rows, cols, fov_az, fov_el)
+            kind = f"linescan{rows}x{cols}"
+        else:
+            dirs = lissajous_pattern(nb, fov_az, fov_el, 7, 9, phase=g.uniform(0, 2 * math.pi))
+            kind = f"lissajous{nb}"
+        out.append(Workload(f"frame{f}_{U}x{V}_{kind}", gb, dirs, base.profile, base.pulse, base.calib, R))
+    return out
