@@ -46,19 +46,33 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch64", "wide"],
+                    help="frame: the full-frame workload (the headline line); batch64: 64 frames of uneven "
+                         "size, pattern and pose through lidar_simulate_batch")
     return ap.parse_args()
+
+
+WORKLOAD = "frame"
 
 
 def workload():
     from paper_2512_05932_gb300 import scenes
+    if WORKLOAD == "wide":
+        return scenes.wide_frame()
     return scenes.full_frame_boxes()
 
 
 def config_of(w, extra=None):
     gb = w.gbuffer
-    c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "120x30", "beams": int(len(w.dirs)),
-         "pattern": "linescan 16x1600", "profile": "table 401x401 @0.01deg", "n_bins": int(w.pulse["n_bins"]),
-         "dt_ns": w.pulse["dt_s"] * 1e9, "max_echoes": int(w.calib["max_echoes"]), "seed": 2}
+    if WORKLOAD == "wide":
+        c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "163.84x81.92", "beams": int(len(w.dirs)),
+             "pattern": "grid 500x400", "profile": "radial sigma 0.05 deg + tail, truncated at 2 deg",
+             "n_bins": int(w.pulse["n_bins"]), "dt_ns": w.pulse["dt_s"] * 1e9,
+             "max_echoes": int(w.calib["max_echoes"]), "seed": 5}
+    else:
+        c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "120x30", "beams": int(len(w.dirs)),
+             "pattern": "linescan 16x1600", "profile": "table 401x401 @0.01deg", "n_bins": int(w.pulse["n_bins"]),
+             "dt_ns": w.pulse["dt_s"] * 1e9, "max_echoes": int(w.calib["max_echoes"]), "seed": 2}
     if extra:
         c.update(extra)
     return c
@@ -321,13 +335,92 @@ def run_gb300(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world, local_rank):
+    """64-frame batched workload through lidar_simulate_batch (autotuned)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2512_05932_gb300 import lidar, scenes
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    frames = scenes.batched_frames()
+    sensors = [lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib) for w in frames]
+    planes = [lidar.gbuffer_to_device(w.gbuffer, dev) for w in frames]
+    outs = [s_.alloc_outputs(dev) for s_ in sensors]
+    arr = lidar.make_frames([
+        (s_.handle, lidar.make_gbuffer(w.gbuffer, [p.data_ptr() for p in pl]), lidar.make_pose(w.pose),
+         o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr()) for s_, w, pl, o in zip(sensors, frames, planes, outs)])
+    ex = sensors[0].handle
+    stream = torch.cuda.current_stream(dev)
+    lidar.lidar_autotune_batch(ex, arr, stream.cuda_stream)
+    G, cps = lidar.lidar_batch_config(ex)
+    clk = ClockSampler(local_rank).__enter__()
+    t_w = time.perf_counter()
+    n_w = 0
+    while n_w < args.warmup or time.perf_counter() - t_w < 1.5:
+        lidar.lidar_simulate_batch(ex, arr, stream.cuda_stream)
+        n_w += 1
+        torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with clk:
+        for i in range(args.steps):
+            starts[i].record(stream)
+            lidar.lidar_simulate_batch(ex, arr, stream.cuda_stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
+    nbeams = sum(len(w.dirs) for w in frames)
+    pix = sum(w.gbuffer.U * w.gbuffer.V for w in frames)
+    alg = sum(algorithmic_bytes(w) for w in frames)
+    peak, peak_kind = load_peaks()
+    achieved = alg / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        from oracle import oracle as O
+        O.build()
+        g = np.random.default_rng(0)
+        t = time.perf_counter()
+        n_s = 0
+        for f in g.choice(len(frames), 8, replace=False):
+            b = np.sort(g.choice(len(frames[f].dirs), 24, replace=False)).astype(np.int32)
+            O.simulate_workload(frames[f], beams=b, nthreads=cpu_cores(), max_out=4)
+            n_s += len(b)
+        dt = time.perf_counter() - t
+        cpu = {"value": n_s / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{n_s} random beams from 8 random frames ({dt:.1f} s wall)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * nbeams / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"batch of {len(frames)} frames (512x256..4096x2048, 1k..100k beams, "
+                                       "line scan + 7:9 Lissajous, random poses), 1024 bins",
+                           "frames": len(frames), "beams": nbeams, "pixels": pix, "beams_per_cta": G,
+                           "ctas_per_sm": cps, "l2": "inputs (%.1f GB) exceed L2" % (pix * 28 / 1e9)},
+                "roofline": {"bound": "hbm", "kernel": "batch step (setup + persistent footprint)",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None,
+                             "algorithmic_bytes": alg},
+                "cpu_baseline": cpu, "e2e": None,
+                "gpu_launches": int(args.steps * 2), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    for s_ in sensors:
+        s_.close()
+
+
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch64":
+        run_batch(args, rank, world, local_rank)
     else:
         run_gb300(args, rank, world, local_rank)
 

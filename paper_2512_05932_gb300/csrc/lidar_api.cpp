@@ -773,15 +773,19 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     gbl::FootprintArgs probe{};
     probe.n_bins = l->n_bins;
     probe.M = l->M;
+    // prefer the largest group that still lets two CTAs share an SM, then
+    // the largest group that fits at all
     int chosen = 0;
-    for (int G : {8, 4, 2}) {
-        size_t need = gbl::footprint_smem_bytes(G, probe);
-        if ((long)need > smem_optin) continue;
-        long groups = (l->n_beams + G - 1) / G;
-        if (G > 2 && groups < 2L * sms) continue;
-        chosen = G;
-        break;
-    }
+    for (int pass = 0; pass < 2 && !chosen; ++pass)
+        for (int G : {8, 4, 2}) {
+            size_t need = gbl::footprint_smem_bytes(G, probe);
+            if ((long)need > smem_optin) continue;
+            if (pass == 0 && 2 * need > 226 * 1024) continue;
+            long groups = (l->n_beams + G - 1) / G;
+            if (G > 2 && groups < 2L * sms) continue;
+            chosen = G;
+            break;
+        }
     if (!chosen) {
         chosen = 2;
         if ((long)gbl::footprint_smem_bytes(2, probe) > smem_optin) {

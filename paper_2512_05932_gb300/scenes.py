@@ -472,3 +472,38 @@ def batched_frames(seed: int = 4, n_frames: int = 64, size_classes=SIZE_CLASSES,
             kind = f"lissajous{nb}"
         out.append(Workload(f"frame{f}_{U}x{V}_{kind}", gb, dirs, base.profile, base.pulse, base.calib, R))
     return out
+
+
+def wide_frame(seed: int = 5, U: int = 8192, V: int = 4096, n_az: int = 500, n_el: int = 400,
+               n_boxes: int = 24) -> Workload:
+    """Wide-tail instance: 8192x4096 G-buffer at 0.02 deg (163.84 x 81.92 deg)
+    of the plane/retro scene family (a plane at 10 m across the boresight with
+    retro patches, a ground plane 2 m below, boxes at 5-25 m, uniform ambient
+    0.01), 500 x 400 = 200k grid beams over 90 % of the field of view, the
+    radial profile of the small instance with its tail truncated at 2 deg, and
+    4096 bins of 0.05 ns."""
+    g = rng(seed)
+    pitch = 0.02 * DEG
+    planes = [Plane(np.array([1.0, 0.0, 0.0]), 10.0, 0.5, 0.0,
+                    Rect(np.array([10.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]),
+                         0.25, 0.25, rho_d=0.5, retro=100.0)),
+              Plane(np.array([0.0, 0.0, 1.0]), -2.0, 0.2, 0.0)]
+    rects = []
+    for _ in range(6):  # extra retro patches on the front plane
+        c = np.array([9.999, g.uniform(-8, 8), g.uniform(-1.5, 4)])
+        rects.append(Rect(c, np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]), 0.2, 0.2, 0.5, 100.0))
+    for _ in range(n_boxes):
+        rr = g.uniform(5.0, 25.0)
+        az = g.uniform(-75, 75) * DEG
+        half = g.uniform(0.25, 1.5, size=3)
+        rho = math.exp(g.uniform(math.log(0.05), math.log(0.9)))
+        retro = np.where(g.uniform(size=6) < 0.05, 100.0, 0.0)
+        d = max(rr, float(np.linalg.norm(half)) + 1.5)
+        c = np.array([d * math.cos(az), d * math.sin(az), -2.0 + half[2]])
+        rects += box_rects(c, half, g.uniform(-math.pi, math.pi), rho, retro)
+    scene = Scene(planes=planes, rects=rects, ambient="uniform", ambient_level=0.01)
+    gb = raycast(scene, U, V, -U * pitch / 2, -V * pitch / 2, pitch, pitch)
+    dirs = grid_pattern(n_az, n_el, 0.9 * U * 0.02 * DEG, 0.9 * V * 0.02 * DEG)
+    prof = radial_profile(0.05, 1e-4, 0.05, 3.0, 2.0)
+    return Workload(f"wide_{U}x{V}_{n_az * n_el}beams_4096bins", gb, dirs, prof, pulse(4096, 0.05e-9),
+                    calib(1e-5, 1e-4, 3, True))

@@ -241,3 +241,15 @@ def test_invalid_gbuffer_rejected_on_device_call():
     with pytest.raises(lidar.LidarError, match="orthonormal"):
         L.simulate(w.gbuffer, planes, np.diag([1.0, 2.0, 1.0]))
     L.close()
+
+
+def test_wide_tail_frame_sampled_beams():
+    """8192x4096 G-buffer, 200k beams, tail truncated at 2 deg, 4096 bins of
+    0.05 ns: the full-size instance, sampled beams against the oracle."""
+    w = S.wide_frame()
+    g = S.rng(31)
+    n = len(w.dirs)
+    rows, cols = g.integers(120, 280, 16), g.integers(100, 400, 16)
+    beams = np.unique(np.concatenate([rows * 500 + cols, g.choice(n, 8, replace=False), [0, n - 1]])).astype(np.int32)
+    st = check_workload(w, beams=beams)
+    assert st["echoes"] >= 8
