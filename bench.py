@@ -167,16 +167,17 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for_current_kernel():
+def traffic_for_current_kernel(workload_name):
     """dram bytes per launch of the footprint kernel from the committed ncu
-    summary, or None if absent or taken on a different kernel source."""
+    summary, or None if absent, taken on another workload or on a different
+    kernel source."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         d = json.load(f)
     with open(KERNEL_SRC, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    if d.get("kernel_sha256") != sha:
+    if d.get("kernel_sha256") != sha or not d.get("workload", "").startswith(workload_name):
         return None
     return d.get("bytes_per_launch")
 
@@ -309,7 +310,7 @@ def run_gb300(args, rank, world, local_rank):
     pix_samples = None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-            "traffic": traffic_for_current_kernel(), "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+            "traffic": traffic_for_current_kernel(w.name), "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
             "kernel_share": {k: tot[k] / sum(tot.values()) for k in names}}
 
     cpu = None

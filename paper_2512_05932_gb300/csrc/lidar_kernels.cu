@@ -317,6 +317,13 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
 // table load of several samples can be in flight together:
 // profile_fetch issues the load (table) or evaluates the weight (radial),
 // profile_finish interpolates.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct ProfFetch {
     float4 q;      // table: the 4 corner values; radial: q.x = weight
     float fx, fy;
@@ -332,9 +339,15 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
         // theta^2 = asin(s)^2 = s^2 (1 + s^2/3 + 8 s^4/45 + ...)
         float t2 = s2 * fmaf(s2, fmaf(s2, 8.f / 45.f, 1.f / 3.f), 1.f);
         r.ok = act && t2 <= A.trunc2;
-        float g = exp2f(t2 * A.kg);
+        // Gaussian: 2^(t2 kg) with the hardware base-2 exponential (relative
+        // error ~2^-22); tail: (theta/theta_c)^-p = rr^(-p/2), with the common
+        // p = 3 as rr^-1.5 = rsqrt(rr)^3
+        float g = ex2_approx(t2 * A.kg);
         float rr = t2 * A.tc2_inv;
-        float tail = rr <= 1.f ? 1.f : exp2f(A.tail_hp * __log2f(rr));
+        float tail;
+        if (rr <= 1.f) tail = 1.f;
+        else if (A.tail_hp == -1.5f) { float q = rsqrtf(rr); tail = q * q * q; }
+        else tail = ex2_approx(A.tail_hp * __log2f(rr));
         r.q.x = fmaf(A.tail_amp, tail, g) * A.invZ;
         r.fx = r.fy = 0.f;
     } else {
@@ -433,6 +446,13 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     const bool jok = (j < gcount) && P.valid;
     float *hj = hbuf + j * Ly.HB;
     const float2 *tj = tab + j * kTC;
+    // Narrow deposits of this lane's successive pixels (all of its beam) that
+    // land on the same 4 bins, as a surface at near-constant range does, are
+    // summed in registers and written with one set of atomics when the bins
+    // change or at the end; this keeps lanes of one beam from hitting the same
+    // addresses at the same time.
+    uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
+    float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
     for (int cs = C0; cs <= C1; cs += kTC) {
         const int ce = min(C1, cs + kTC - 1);
         const int ncs = ce - cs + 1;
@@ -523,10 +543,20 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                     uint32_t kq = __float_as_uint(r1u.x);
                     if (kq != kNoDeposit) {
                         // narrow: hat weights on 4 consecutive bins at precomputed positions
-                        atomicAdd(hj + (kab & 0xFFFFu), Pw * r0[u].z);
-                        if (r0[u].w != 0.f) atomicAdd(hj + (kab >> 16), Pw * r0[u].w);
-                        if (r1u.y != 0.f) atomicAdd(hj + (kq & 0xFFFFu), Pw * r1u.y);
-                        if (r1u.z != 0.f) atomicAdd(hj + (kq >> 16), Pw * r1u.z);
+                        if (kab != wk0 || kq != wk1) {
+                            if (wk0 != kNoDeposit) {
+                                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
+                                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
+                                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
+                                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
+                            }
+                            wk0 = kab; wk1 = kq;
+                            wa0 = 0.f; wa1 = 0.f; wa2 = 0.f; wa3 = 0.f;
+                        }
+                        wa0 = fmaf(Pw, r0[u].z, wa0);
+                        wa1 = fmaf(Pw, r0[u].w, wa1);
+                        wa2 = fmaf(Pw, r1u.y, wa2);
+                        wa3 = fmaf(Pw, r1u.z, wa3);
                     } else {
                         // wide: two partial bins at each end, a constant run between
                         int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
@@ -542,6 +572,12 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 }
             }
         }
+    }
+    if (wk0 != kNoDeposit) {
+        atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
+        if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
+        if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
+        if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
     }
     // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
 #pragma unroll
