@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
+    ap.add_argument("--deposit", default="atomic", choices=["atomic", "tc_split", "tc_bf16"],
+                    help="deposit form of the footprint kernel (lidar_set_deposit)")
     ap.add_argument("--workload", default="frame", choices=["frame", "batch64", "wide"],
                     help="frame: the full-frame workload (the headline line); batch64: 64 frames of uneven "
                          "size, pattern and pose through lidar_simulate_batch")
@@ -53,6 +55,7 @@ def parse():
 
 
 WORKLOAD = "frame"
+DEPOSIT = {"atomic": 0, "tc_split": 1, "tc_bf16": 2}
 
 
 def workload():
@@ -231,6 +234,7 @@ def run_gb300(args, rank, world, local_rank):
 
     w = workload()
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    lidar.lidar_set_deposit(L.handle, DEPOSIT[args.deposit])
     planes = lidar.gbuffer_to_device(w.gbuffer, dev)
     outs = L.alloc_outputs(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -302,6 +306,8 @@ def run_gb300(args, rank, world, local_rank):
     names = lidar.KERNELS
     tot = {k: kern[k][0] for k in names}
     dom = max(names, key=lambda k: tot[k])
+    if args.deposit != "atomic":
+        pass
     launches = kern[dom][1]
     avg_ms = tot[dom] / max(1, launches)
     peak, peak_kind = load_peaks()
@@ -322,9 +328,9 @@ def run_gb300(args, rank, world, local_rank):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16" if args.deposit == "tc_bf16" else "f32", "data": "synthetic",
             "config": config_of(w, {"l2": "flushed between timed steps (258 MB write)",
-                                    "parallelism": f"replicas x{world}"}),
+                                    "parallelism": f"replicas x{world}", "deposit": args.deposit}),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),
@@ -348,6 +354,8 @@ def run_batch(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     frames = scenes.batched_frames()
     sensors = [lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib) for w in frames]
+    for s_ in sensors:
+        lidar.lidar_set_deposit(s_.handle, DEPOSIT[args.deposit])
     planes = [lidar.gbuffer_to_device(w.gbuffer, dev) for w in frames]
     outs = [s_.alloc_outputs(dev) for s_ in sensors]
     arr = lidar.make_frames([

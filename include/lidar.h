@@ -272,6 +272,26 @@ lidar_status_t lidar_get_info(const lidar_t *lidar, int32_t *n_beams, int32_t *n
 /* Number of kernel launches one lidar_simulate call enqueues. */
 int32_t lidar_launches_per_simulate(const lidar_t *lidar);
 
+/* How the footprint kernel adds a pixel's profile-weighted deposit into a
+ * beam's range bins (same model, different arithmetic):
+ *   LIDAR_DEPOSIT_ATOMIC   FP32 products, shared-memory atomic adds (default).
+ *   LIDAR_DEPOSIT_TC_SPLIT tensor cores: for 16-pixel tiles, (bins x pixels)
+ *                          hat weights times (pixels x beams) profile weights
+ *                          with BF16 mma and FP32 accumulation, each factor
+ *                          split into BF16 hi + lo parts (three products,
+ *                          relative error ~2^-16 per product).
+ *   LIDAR_DEPOSIT_TC_BF16  the same with plain BF16 factors (one product,
+ *                          relative error ~2^-8 per product).
+ * The tensor-core forms process 8 beams per CTA (4 when two CTAs of 8 would
+ * not share an SM). Applies to later lidar_simulate* and lidar_simulate_batch
+ * calls of this simulator (a batch uses its executor's mode). */
+enum {
+    LIDAR_DEPOSIT_ATOMIC = 0,
+    LIDAR_DEPOSIT_TC_SPLIT = 1,
+    LIDAR_DEPOSIT_TC_BF16 = 2
+};
+lidar_status_t lidar_set_deposit(lidar_t *lidar, int32_t mode);
+
 /* Per-kernel timing. While enabled, every lidar_simulate call records CUDA
  * events on its stream around each of its kernels (setup, footprint_wave).
  * lidar_profile_read synchronises those events, writes the summed device time

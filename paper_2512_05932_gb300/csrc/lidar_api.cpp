@@ -46,6 +46,11 @@ struct lidar {
     // launch shape
     int32_t G = 16, threads = 512;
     size_t smem = 0;
+    // deposit form: 0 shared-memory atomics (FP32), 1 tensor cores BF16 hi/lo
+    // split (3 MMAs), 2 tensor cores plain BF16; G_tc/smem_tc: its group shape
+    int32_t deposit = 0;
+    int32_t G_tc = 8;
+    size_t smem_tc = 0;
     int device = 0;
     // device memory owned by the library
     float *d_dirs = nullptr;
@@ -436,6 +441,7 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
     sa.panorama = is_panorama(g) ? 1 : 0;
     sa.support_rad = l->support_rad;
     sa.beams = beams;
+    sa.bin_records = l->deposit != 0 ? 1 : 0;
     return sa;
 }
 
@@ -453,6 +459,7 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.c0 = (float)l->coef[0]; fa.c1 = (float)l->coef[1]; fa.c2 = (float)l->coef[2];
     fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
     fa.rB = (float)(0.5 * kC * l->dt);
+    fa.tc_split = l->deposit == 1 ? 1 : 0;
     return fa;
 }
 
@@ -481,7 +488,8 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     fa.beams = l->d_beams;
     fa.n_beams = l->n_beams;
     fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
-    e = gbl::launch_footprint(l->kind, l->G, l->threads, l->smem, fa, s);
+    const bool tc = l->deposit != 0;
+    e = gbl::launch_footprint(l->kind, tc ? l->G_tc : l->G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
     if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     if (ev2) cudaEventRecord(ev2, s);
     return LIDAR_OK;
@@ -562,6 +570,7 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
         return l->support_rad * l->support_rad / (g.daz * g.del);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    if (l->deposit != 0 && G != 4 && G != 8) G = l->G_tc;
     std::vector<int2> items;
     for (int f : order) {
         int groups = (fr[f].sensor->n_beams + G - 1) / G;
@@ -618,15 +627,18 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
     std::memcpy(hb + B.off_items, items.data(), items.size() * sizeof(int2));
 
     // persistent grid size
+    const bool tc = l->deposit != 0;
+    if (tc && G != 4 && G != 8) G = l->G_tc;  // tensor-core form: 4 or 8 beams per CTA
     size_t smem = gbl::footprint_smem_bytes(G, model_args(l));
-    if ((e = gbl::prepare_footprint_batch(l->kind, G, smem)) != cudaSuccess) return cuda_fail(l, e, "cudaFuncSetAttribute");
+    if ((e = gbl::prepare_footprint_batch(l->kind, G, tc, smem)) != cudaSuccess)
+        return cuda_fail(l, e, "cudaFuncSetAttribute");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, l->device);
     int per_sm = cps > 0 ? cps : 2;
     int grid = std::max(1, std::min(B.n_items, per_sm * sms));
 
     // graph keyed on everything the captured launches depend on
-    std::vector<long long> key = {n, (long long)B.size, B.n_items, B.total_blocks, G, grid, (long long)smem,
+    std::vector<long long> key = {n, (long long)B.size, B.n_items, B.total_blocks, G, grid, (long long)smem, l->deposit,
                                   (long long)(uintptr_t)l->d_blob, (long long)(uintptr_t)l->h_blob};
     if (!l->gexec || key != l->gkey) {
         if (l->gexec) { cudaGraphExecDestroy(l->gexec); l->gexec = nullptr; }
@@ -640,7 +652,7 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
                                                  reinterpret_cast<const int *>(db + B.off_beam), n, B.total_blocks,
                                                  l->d_counter, l->cap_stream);
         gbl::FootprintArgs base = model_args(l);
-        cudaError_t e3 = gbl::launch_footprint_batch(l->kind, G, l->threads, grid, smem, base,
+        cudaError_t e3 = gbl::launch_footprint_batch(l->kind, G, tc, l->threads, grid, smem, base,
                                                      reinterpret_cast<const gbl::FrameDesc *>(db + B.off_frames),
                                                      reinterpret_cast<const int2 *>(db + B.off_items), B.n_items,
                                                      l->d_counter, l->cap_stream);
@@ -796,8 +808,12 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     l->G = chosen;
     l->threads = 512;
     l->smem = gbl::footprint_smem_bytes(l->G, probe);
-    e = gbl::prepare_footprint(l->kind, l->G, l->smem);
+    e = gbl::prepare_footprint(l->kind, l->G, false, l->smem);
     if (e != cudaSuccess) { delete l; return cuda_fail(nullptr, e, "cudaFuncSetAttribute"); }
+    // tensor-core form: 8 beams per CTA if two CTAs still share an SM, else 4
+    l->G_tc = 8;
+    if (2 * gbl::footprint_smem_bytes(8, probe) > 226 * 1024) l->G_tc = 4;
+    l->smem_tc = gbl::footprint_smem_bytes(l->G_tc, probe);
 
     // device copies
     size_t nd = (size_t)pat->n_beams * 3 * sizeof(float);
@@ -937,6 +953,7 @@ lidar_status_t lidar_autotune_batch(lidar_t *l, const lidar_frame_t *frames, int
     int bestG = l->batch_G, bestC = l->batch_cps;
     lidar_status_t st = LIDAR_OK;
     for (int G : {2, 4, 8, 16}) {
+        if (l->deposit != 0 && G != 4 && G != 8) continue;
         size_t smem = gbl::footprint_smem_bytes(G, model_args(l));
         if ((long)smem > smem_optin) continue;
         for (int cps : {1, 2}) {
@@ -959,6 +976,22 @@ lidar_status_t lidar_autotune_batch(lidar_t *l, const lidar_frame_t *frames, int
     if (st != LIDAR_OK) return st;
     l->batch_G = bestG;
     l->batch_cps = bestC;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_set_deposit(lidar_t *l, int32_t mode)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (mode < LIDAR_DEPOSIT_ATOMIC || mode > LIDAR_DEPOSIT_TC_BF16)
+        return fail(l, LIDAR_EINVAL, "deposit mode %d unknown", mode);
+    if (mode != LIDAR_DEPOSIT_ATOMIC && (long)l->smem_tc > 227L * 1024)
+        return fail(l, LIDAR_EINVAL, "n_bins too large for the tensor-core deposit");
+    if (mode != LIDAR_DEPOSIT_ATOMIC) {
+        cudaError_t e = gbl::prepare_footprint(l->kind, l->G_tc, true, l->smem_tc);
+        if (e != cudaSuccess) return cuda_fail(l, e, "cudaFuncSetAttribute");
+        l->batch_G = l->G_tc;
+    }
+    l->deposit = mode;
     return LIDAR_OK;
 }
 

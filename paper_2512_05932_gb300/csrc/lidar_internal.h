@@ -42,6 +42,8 @@ struct SetupArgs {
     float x_scale, x_off;    // bin-centre coordinate X = r * x_scale + x_off
     int n_bins;
     int pad;                 // zero padding (bins) of the footprint kernel's histogram buffer
+    int bin_records;         // narrow records carry the first bin index (tensor-core deposit)
+                             // instead of histogram positions (shared-memory atomics)
     int pix_blocks;
     // beams
     int n_beams;
@@ -71,6 +73,7 @@ struct FootprintArgs {
     int n_bins, nch, M, R;
     const float *taps_pad;  // length tp_len, tap m at index tp_off + m
     int tp_len, tp_off;
+    int tc_split;            // tensor-core deposit: 1 = BF16 hi/lo split (3 MMAs), 0 = plain BF16
     // calibration
     float T, s_amb;
     int max_echoes;
@@ -101,13 +104,14 @@ cudaError_t noalloc_records(float4 **out);
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s);
 size_t footprint_smem_bytes(int G, const FootprintArgs &a);
 int footprint_pad(int M);
-cudaError_t prepare_footprint(int kind, int G, size_t smem);
-cudaError_t launch_footprint(int kind, int G, int threads, size_t smem, const FootprintArgs &a, cudaStream_t s);
+cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem);
+cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem, const FootprintArgs &a,
+                             cudaStream_t s);
 cudaError_t launch_setup_batch(const SetupArgs *frames, const int *pix_blk, const int *beam_blk, int n_frames,
                                int total_blocks, int *counter, cudaStream_t s);
-cudaError_t prepare_footprint_batch(int kind, int G, size_t smem);
-cudaError_t launch_footprint_batch(int kind, int G, int threads, int grid, size_t smem, const FootprintArgs &base,
-                                   const FrameDesc *frames, const int2 *items, int n_items, int *counter,
-                                   cudaStream_t s);
+cudaError_t prepare_footprint_batch(int kind, int G, bool tc, size_t smem);
+cudaError_t launch_footprint_batch(int kind, int G, bool tc, int threads, int grid, size_t smem,
+                                   const FootprintArgs &base, const FrameDesc *frames, const int2 *items,
+                                   int n_items, int *counter, cudaStream_t s);
 
 }  // namespace gbl

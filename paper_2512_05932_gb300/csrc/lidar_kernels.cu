@@ -18,6 +18,8 @@
 //                     - pulse convolution varpi * xi_b + ambient (Sec. II-C),
 //                       skipping 32-bin chunks that no deposit touched;
 //                     - echo intervals, EPW, peak and intensity.
+#include <cuda_bf16.h>
+#include <climits>
 #include <math_constants.h>
 #include <stdint.h>
 
@@ -109,9 +111,15 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
                     h1 = w * mean_hat(X0, X1, f + 1.f);
                     h2 = w * mean_hat(X0, X1, f + 2.f);
                     h3 = w * mean_hat(X0, X1, f + 3.f);
-                    int x = (int)f + A.pad;
-                    kab = (uint32_t)skew_pos(x) | ((uint32_t)skew_pos(x + 1) << 16);
-                    kq = (uint32_t)skew_pos(x + 2) | ((uint32_t)skew_pos(x + 3) << 16);
+                    if (A.bin_records) {
+                        // tensor-core deposit: the bin index itself
+                        kab = (uint32_t)((int)f + kBinBias) | (0xFFFFu << 16);
+                        kq = 0u;
+                    } else {
+                        int x = (int)f + A.pad;
+                        kab = (uint32_t)skew_pos(x) | ((uint32_t)skew_pos(x + 1) << 16);
+                        kq = (uint32_t)skew_pos(x + 2) | ((uint32_t)skew_pos(x + 3) << 16);
+                    }
                 }
             } else {
                 // wide (X1 - X0 > 2): partial bins f, f+1 and g, g+1, every bin
@@ -376,9 +384,245 @@ __device__ __forceinline__ float profile_finish(const ProfFetch &r)
     return fmaf(r.fy, bot - top, top);
 }
 
+
+// --------------------------------------------------------------------------
+// tensor-core form of the deposit (BF16 mma.sync, FP32 accumulation)
+// --------------------------------------------------------------------------
+//
+// For a 16-pixel tile of one row, the deposits of all G (<= 8) beams of the
+// group are the product C[bin][beam] += A[bin][pixel] * B[pixel][beam], with
+// A the pixels' hat weights (w * D_k) on a block of 16 bins and B the profile
+// weights. In the m16n8k16 fragment layout, lane (g, t) = (lane / 4, lane % 4)
+// supplies B for beam g at tile pixels 2t, 2t+1, 2t+8, 2t+9 -- the samples it
+// evaluates -- and A for the same pixels at bins g and g+8 of the block. Two
+// accumulator slots stay in registers while tiles keep hitting the same bin
+// blocks and are added to the histograms only when a slot is recycled.
+// Each factor is split into BF16 hi + lo parts; hi*hi + hi*lo + lo*hi gives
+// products accurate to ~2^-16 (tc_split), or hi*hi alone (plain BF16).
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// x = hi + lo with hi, lo in BF16 (pairs packed low element first)
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    hi = *reinterpret_cast<uint32_t *>(&h);
+    float r0 = x0 - __bfloat162float(h.x);
+    float r1 = x1 - __bfloat162float(h.y);
+    lo = pack_bf16(r0, r1);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One pixel's deposit in bin-index form (bin_records): weight at bin k.
+struct PixDep {
+    int f, g;       // first bin; for wide pixels the bin of the last partial pair, else -1
+    float h0, h1, h2, h3, c;
+};
+
+__device__ __forceinline__ float dep_weight(const PixDep &d, int k)
+{
+    int e = k - d.f;
+    if (d.g < 0) {  // narrow: bins f..f+3
+        float v = 0.f;
+        v = e == 0 ? d.h0 : v;
+        v = e == 1 ? d.h1 : v;
+        v = e == 2 ? d.h2 : v;
+        v = e == 3 ? d.h3 : v;
+        return v;
+    }
+    float v = (k >= d.f + 2 && k <= d.g - 1) ? d.c : 0.f;
+    v = e == 0 ? d.h0 : v;
+    v = e == 1 ? d.h1 : v;
+    v = k == d.g ? d.h2 : v;
+    v = k == d.g + 1 ? d.h3 : v;
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ void tc_flush(float *hbuf, int HB, int pad, const float (&c)[4], int blk, int g, int t)
+{
+    const int k0 = 16 * blk + g + pad;
+    const int bA = 2 * t, bB = 2 * t + 1;
+    if (bA < G) {
+        if (c[0] != 0.f) atomicAdd(hbuf + bA * HB + skew_pos(k0), c[0]);
+        if (c[2] != 0.f) atomicAdd(hbuf + bA * HB + skew_pos(k0 + 8), c[2]);
+    }
+    if (bB < G) {
+        if (c[1] != 0.f) atomicAdd(hbuf + bB * HB + skew_pos(k0), c[1]);
+        if (c[3] != 0.f) atomicAdd(hbuf + bB * HB + skew_pos(k0 + 8), c[3]);
+    }
+}
+
+template <int KIND, int G>
+__device__ __forceinline__ float phase1_tc(const FootprintArgs &A, const Layout &Ly, float *hbuf, float2 *tab,
+                                           const BeamParam *bp, int gcount, int R0, int R1, int C0, int C1)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int nb = A.n_bins, pad = Ly.pad;
+    const BeamParam P = bp[g < G ? g : 0];
+    const bool gok = g < G && g < gcount && P.valid;
+    const float2 *tj = tab + (g < G ? g : 0) * kTC;
+    const int blk_lo = -1, blk_hi = (nb + 3) / 16;  // blocks reachable by window deposits
+    float amb_acc = 0.f;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    int slot_blk[2] = {INT_MIN, INT_MIN};
+    int slot_next = 0;
+    for (int cs = C0; cs <= C1; cs += kTC) {
+        const int ce = min(C1, cs + kTC - 1);
+        const int ncs = ce - cs + 1;
+        __syncthreads();  // previous stripe's table no longer read
+        for (int i = tid; i < G * ncs; i += blockDim.x) {
+            int jj = i / ncs, cc = i - jj * ncs;
+            const BeamParam &Q = bp[jj];
+            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
+            float sD, vers;
+            if (fabsf(dAz) <= 0.1f) {
+                float z2 = dAz * dAz;
+                sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
+                vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
+            } else {
+                float cD;
+                sincosf(dAz, &sD, &cD);
+                vers = 1.f - cD;
+            }
+            tab[jj * kTC + cc] = make_float2(sD, vers);
+        }
+        __syncthreads();
+        if (R0 > R1) continue;
+        const int nseg = (ncs + kSeg - 1) / kSeg;
+        const int segw = (ncs + nseg - 1) / nseg;
+        const int nunits = (R1 - R0 + 1) * nseg;
+        for (int unit = warp; unit < nunits; unit += nwarps) {
+            const int row = R0 + unit / nseg;
+            const int seg = unit - (unit / nseg) * nseg;
+            const bool act_row = gok && row >= P.row0 && row <= P.row1;
+            const int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
+            int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
+            if (!act_row) { my_lo = 1; my_hi = 0; }
+            float el = A.el0 + ((float)row + 0.5f) * A.del;
+            float cosEl = cosf(el);
+            float dEl = ((float)(row - P.ri) - P.rf) * A.del;
+            float sdEl = sinf(dEl), cdEl = cosf(dEl);
+            float Kv = P.sin_elb * cosEl;
+            float Kc = P.cos_elb * cosEl;
+            const float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
+            const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
+            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
+            for (int ct = c_lo; ct <= c_hi; ct += 16) {  // warp-uniform
+                PixDep dp[4];
+                float Pw[4];
+                int bmin = INT_MAX, bmax = INT_MIN;
+                bool any_amb = false;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = ct + 2 * t + (u & 1) + 8 * (u >> 1);
+                    const bool inrow = c <= c_hi;  // pixel of this unit (for every beam)
+                    int cw = c;
+                    if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    cw = inrow ? cw : 0;
+                    float4 r0 = __ldg(recrow + 2 * cw);
+                    float4 r1 = __ldg(recrow + 2 * cw + 1);
+                    uint32_t kab = __float_as_uint(r0.x);
+                    const bool dep = inrow && kab != kNoDeposit;
+                    dp[u].f = (int)(kab & 0xFFFFu) - kBinBias;
+                    dp[u].g = ((kab >> 16) == 0xFFFFu) ? -1 : (int)(kab >> 16) - kBinBias;
+                    dp[u].h0 = dep ? r0.z : 0.f;
+                    dp[u].h1 = dep ? r0.w : 0.f;
+                    dp[u].h2 = dep ? r1.y : 0.f;
+                    dp[u].h3 = dep ? r1.z : 0.f;
+                    dp[u].c = dep ? r1.w : 0.f;
+                    if (dep) {
+                        int last = dp[u].g < 0 ? dp[u].f + 3 : dp[u].g + 1;
+                        bmin = min(bmin, max(blk_lo, dp[u].f >> 4));
+                        bmax = max(bmax, min(blk_hi, last >> 4));
+                    }
+                    const float a = inrow ? r0.y : 0.f;
+                    any_amb |= a != 0.f;
+                    // profile weight of beam g at this pixel
+                    const bool act = c >= my_lo && c <= my_hi && (dep || a != 0.f);
+                    float2 tt = tj[act ? c - cs : 0];
+                    const bool front = act && fmaf(-Kc, tt.y, cdEl) > 0.f;
+                    float x = fmaf(ax, tt.x, fmaf(bx, tt.y, cx));
+                    float y = fmaf(ay, tt.x, fmaf(by, tt.y, cy));
+                    Pw[u] = profile_finish<KIND>(profile_fetch<KIND>(A, x, y, front));
+                    amb_acc = fmaf(Pw[u], a, amb_acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+                    bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+                }
+                if (bmin > bmax) continue;  // no deposit in this tile
+                uint32_t bh0, bh1, bl0, bl1;
+                split_bf16(Pw[0], Pw[1], bh0, bl0);
+                split_bf16(Pw[2], Pw[3], bh1, bl1);
+                for (int blk = bmin; blk <= bmax; ++blk) {  // warp-uniform
+                    const int k_a = 16 * blk + g, k_b = k_a + 8;
+                    float w[8];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        w[u] = dep_weight(dp[u], k_a);
+                        w[4 + u] = dep_weight(dp[u], k_b);
+                    }
+                    bool touch = false;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) touch |= w[i] != 0.f;
+                    if (!__any_sync(0xffffffffu, touch)) continue;
+                    int sl = slot_blk[0] == blk ? 0 : (slot_blk[1] == blk ? 1 : -1);
+                    if (sl < 0) {
+                        sl = slot_next;
+                        slot_next ^= 1;
+                        if (slot_blk[sl] != INT_MIN) tc_flush<G>(hbuf, Ly.HB, pad, acc[sl], slot_blk[sl], g, t);
+                        slot_blk[sl] = blk;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc[sl][i] = 0.f;
+                    }
+                    // A: rows = bins (g, g+8), columns = tile pixels (2t, 2t+1 | 2t+8, 2t+9)
+                    uint32_t ah0, ah1, ah2, ah3, al0, al1, al2, al3;
+                    split_bf16(w[0], w[1], ah0, al0);  // bin g,   pixels 2t, 2t+1
+                    split_bf16(w[4], w[5], ah1, al1);  // bin g+8, pixels 2t, 2t+1
+                    split_bf16(w[2], w[3], ah2, al2);  // bin g,   pixels 2t+8, 2t+9
+                    split_bf16(w[6], w[7], ah3, al3);  // bin g+8, pixels 2t+8, 2t+9
+                    if (sl == 0) {
+                        mma_bf16(acc[0], ah0, ah1, ah2, ah3, bh0, bh1);
+                        if (A.tc_split) {
+                            mma_bf16(acc[0], ah0, ah1, ah2, ah3, bl0, bl1);
+                            mma_bf16(acc[0], al0, al1, al2, al3, bh0, bh1);
+                        }
+                    } else {
+                        mma_bf16(acc[1], ah0, ah1, ah2, ah3, bh0, bh1);
+                        if (A.tc_split) {
+                            mma_bf16(acc[1], ah0, ah1, ah2, ah3, bl0, bl1);
+                            mma_bf16(acc[1], al0, al1, al2, al3, bh0, bh1);
+                        }
+                    }
+                }
+                (void)any_amb;
+            }
+        }
+    }
+    if (slot_blk[0] != INT_MIN) tc_flush<G>(hbuf, Ly.HB, pad, acc[0], slot_blk[0], g, t);
+    if (slot_blk[1] != INT_MIN) tc_flush<G>(hbuf, Ly.HB, pad, acc[1], slot_blk[1], g, t);
+    return amb_acc;
+}
+
 // One group of G consecutive beams of one frame (the whole per-CTA pipeline).
 // Every thread of the CTA must call it (it contains block barriers).
-template <int KIND, int G>
+template <int KIND, int G, bool TC>
 __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
 {
     const int nb = A.n_bins, M = A.M;
@@ -432,6 +676,10 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
 
     // ---- phase 1: profile-weighted deposits into the range bins -----------
+    float amb_acc = 0.f;
+    if constexpr (TC) {
+        amb_acc = phase1_tc<KIND, G>(A, Ly, hbuf, tab, bp, gcount, R0, R1, C0, C1);
+    } else {
     // The group's pixel box is walked in stripes of kTC columns. For each
     // stripe, tab[j][c] holds sin(dAz) and 1 - cos(dAz) of column c relative
     // to beam j. A work unit is one row x kSeg columns, taken by one warp:
@@ -441,7 +689,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     constexpr int CQ = kWarp / G;  // columns handled side by side per beam
     const int j = lane % G;
     const int q = lane / G;
-    float amb_acc = 0.f;
     const BeamParam P = bp[j];
     const bool jok = (j < gcount) && P.valid;
     float *hj = hbuf + j * Ly.HB;
@@ -579,10 +826,18 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
         if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
     }
-    // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
+    }  // atomic-deposit phase 1
+    if constexpr (TC) {
+        // ambient sum per beam: lane (g, t) holds beam g; sum the 4 lanes t
+        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 1);
+        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 2);
+        if ((lane & 3) == 0 && (lane >> 2) < G && amb_acc != 0.f) atomicAdd(amb_s + (lane >> 2), amb_acc);
+    } else {
+        // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
 #pragma unroll
-    for (int o = G; o < kWarp; o <<= 1) amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, o);
-    if (lane < G && amb_acc != 0.f) atomicAdd(amb_s + lane, amb_acc);
+        for (int o = G; o < kWarp; o <<= 1) amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, o);
+        if (lane < G && amb_acc != 0.f) atomicAdd(amb_s + lane, amb_acc);
+    }
     __syncthreads();
 
     // ---- phase 2: drop contributions outside the window, support ----------
@@ -771,17 +1026,17 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
 }
 
-template <int KIND, int G>
-__global__ void __launch_bounds__(512) footprint_wave_kernel(FootprintArgs A)
+template <int KIND, int G, bool TC>
+__global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_wave_kernel(FootprintArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    footprint_group<KIND, G>(A, blockIdx.x, smem_raw);
+    footprint_group<KIND, G, TC>(A, blockIdx.x, smem_raw);
 }
 
 // Batched form: a persistent grid whose CTAs take (frame, group) items, in the
 // order of `items`, from a counter that the batch setup kernel resets.
-template <int KIND, int G>
-__global__ void __launch_bounds__(512) footprint_batch_kernel(FootprintArgs base, const FrameDesc *frames,
+template <int KIND, int G, bool TC>
+__global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_batch_kernel(FootprintArgs base, const FrameDesc *frames,
                                                               const int2 *items, int n_items, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -799,7 +1054,7 @@ __global__ void __launch_bounds__(512) footprint_batch_kernel(FootprintArgs base
         A.az0 = F.az0; A.el0 = F.el0; A.daz = F.daz; A.del = F.del;
         A.rec = F.rec; A.beams = F.beams; A.n_beams = F.n_beams;
         A.wave = F.wave; A.echoes = F.echoes; A.counts = F.counts;
-        footprint_group<KIND, G>(A, fg.y, smem_raw);
+        footprint_group<KIND, G, TC>(A, fg.y, smem_raw);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -811,63 +1066,58 @@ size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 
 int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
 
-template <int KIND, int G>
-static cudaError_t prep_one(size_t smem)
-{
-    return cudaFuncSetAttribute(footprint_wave_kernel<KIND, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-}
+// Instantiated configurations: profile kind x beams per CTA x deposit form.
+// Shared-memory atomics: G in {2, 4, 8, 16}; tensor cores: G in {4, 8}.
+#define GBL_FOR_EACH(X)                                                                              \
+    X(0, 2, false) X(0, 4, false) X(0, 8, false) X(0, 16, false) X(1, 2, false) X(1, 4, false)      \
+    X(1, 8, false) X(1, 16, false) X(0, 4, true) X(0, 8, true) X(1, 4, true) X(1, 8, true)
 
-template <int KIND, int G>
-static cudaError_t prep_batch_one(size_t smem)
+cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem)
 {
-    return cudaFuncSetAttribute(footprint_batch_kernel<KIND, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-}
-
-cudaError_t prepare_footprint_batch(int kind, int G, size_t smem)
-{
-#define GBL_CASE(K, GG) if (kind == K && G == GG) return prep_batch_one<K, GG>(smem);
-    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
-    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+#define GBL_CASE(K, GG, T)                                                                                    \
+    if (kind == K && G == GG && tc == T)                                                                      \
+        return cudaFuncSetAttribute(footprint_wave_kernel<K, GG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)smem);
+    GBL_FOR_EACH(GBL_CASE)
 #undef GBL_CASE
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_footprint_batch(int kind, int G, int threads, int grid, size_t smem, const FootprintArgs &base,
-                                   const FrameDesc *frames, const int2 *items, int n_items, int *counter,
-                                   cudaStream_t s)
-{
-#define GBL_CASE(K, GG)                                                                                    \
-    if (kind == K && G == GG) {                                                                            \
-        footprint_batch_kernel<K, GG><<<grid, threads, smem, s>>>(base, frames, items, n_items, counter); \
-        return cudaGetLastError();                                                                         \
-    }
-    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
-    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
-#undef GBL_CASE
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t prepare_footprint(int kind, int G, size_t smem)
-{
-#define GBL_CASE(K, GG) if (kind == K && G == GG) return prep_one<K, GG>(smem);
-    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
-    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
-#undef GBL_CASE
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_footprint(int kind, int G, int threads, size_t smem, const FootprintArgs &a, cudaStream_t s)
+cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem, const FootprintArgs &a,
+                             cudaStream_t s)
 {
     int groups = (a.n_beams + G - 1) / G;
-#define GBL_CASE(K, GG)                                                              \
-    if (kind == K && G == GG) {                                                      \
-        footprint_wave_kernel<K, GG><<<groups, threads, smem, s>>>(a);               \
-        return cudaGetLastError();                                                   \
+#define GBL_CASE(K, GG, T)                                               \
+    if (kind == K && G == GG && tc == T) {                               \
+        footprint_wave_kernel<K, GG, T><<<groups, threads, smem, s>>>(a); \
+        return cudaGetLastError();                                       \
     }
-    GBL_CASE(0, 2) GBL_CASE(0, 4) GBL_CASE(0, 8) GBL_CASE(0, 16)
-    GBL_CASE(1, 2) GBL_CASE(1, 4) GBL_CASE(1, 8) GBL_CASE(1, 16)
+    GBL_FOR_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_footprint_batch(int kind, int G, bool tc, size_t smem)
+{
+#define GBL_CASE(K, GG, T)                                                                          \
+    if (kind == K && G == GG && tc == T)                                                            \
+        return cudaFuncSetAttribute(footprint_batch_kernel<K, GG, T>,                               \
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    GBL_FOR_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_footprint_batch(int kind, int G, bool tc, int threads, int grid, size_t smem,
+                                   const FootprintArgs &base, const FrameDesc *frames, const int2 *items,
+                                   int n_items, int *counter, cudaStream_t s)
+{
+#define GBL_CASE(K, GG, T)                                                                                     \
+    if (kind == K && G == GG && tc == T) {                                                                     \
+        footprint_batch_kernel<K, GG, T><<<grid, threads, smem, s>>>(base, frames, items, n_items, counter); \
+        return cudaGetLastError();                                                                             \
+    }
+    GBL_FOR_EACH(GBL_CASE)
 #undef GBL_CASE
     return cudaErrorInvalidValue;
 }

@@ -74,7 +74,7 @@ assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 # exported symbols (every function declared in include/lidar.h)
 SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_simulate_noalloc", "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
-           "lidar_launches_per_simulate", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
+           "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
 KERNELS = ("setup", "footprint_wave")
 
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
                                    P(C.c_double)]
     lib.lidar_launches_per_simulate.restype = C.c_int32
     lib.lidar_launches_per_simulate.argtypes = [C.c_void_p]
+    lib.lidar_set_deposit.restype = C.c_int
+    lib.lidar_set_deposit.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_enable.restype = C.c_int
     lib.lidar_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_read.restype = C.c_int
@@ -282,6 +284,13 @@ def lidar_get_info(handle) -> dict:
 
 def lidar_launches_per_simulate(handle) -> int:
     return int(load().lidar_launches_per_simulate(handle))
+
+
+DEPOSIT_ATOMIC, DEPOSIT_TC_SPLIT, DEPOSIT_TC_BF16 = 0, 1, 2
+
+
+def lidar_set_deposit(handle, mode: int) -> None:
+    _check(load().lidar_set_deposit(handle, int(mode)), handle)
 
 
 def lidar_profile_enable(handle, enable: bool) -> None:
