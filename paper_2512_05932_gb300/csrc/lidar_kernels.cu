@@ -288,13 +288,14 @@ constexpr int kBlk = 256;    // waveform bins per convolution work item (8 per l
 // x = bin + pad, stored at x + (x >> 5) so that lanes reading bins 8 apart hit
 // distinct banks. pad >= M + 16 and is a multiple of 32.
 constexpr int kTC = 257;     // columns per offset-table stripe (odd: conflict-free float2 rows)
+constexpr int kRT = 256;     // rows of the per-(beam, row) elevation table; taller boxes compute on the fly
 
 struct Layout {
     int pad;       // zero padding on each side, in bins
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_supp, off_tab, off_bp, total;
+    size_t off_taps, off_amb, off_supp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
 };
 
 
@@ -313,6 +314,9 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     L.off_supp = off; off += (size_t)G * 8;
     off = (off + 15) & ~(size_t)15;
     L.off_tab = off; off += (size_t)G * kTC * sizeof(float2);
+    L.off_rtab = off; off += (size_t)G * kRT * sizeof(float2);
+    L.off_ctab = off; off += (size_t)kRT * sizeof(float);
+    L.off_ctr = off; off += 16;
     off = (off + 15) & ~(size_t)15;
     L.off_bp = off; off += (size_t)G * sizeof(BeamParam);
     L.total = off;
@@ -633,6 +637,9 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
     int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
+    float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
+    float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
+    int *uctr = reinterpret_cast<int *>(smem_raw + Ly.off_ctr);
     BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -673,6 +680,20 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         if (!P.valid) continue;
         R0 = min(R0, P.row0); R1 = max(R1, P.row1);
         C0 = min(C0, P.col0); C1 = max(C1, P.col1);
+    }
+    // per-(beam, row) sin and cos of the elevation offset and per-row cos(el)
+    const bool use_rtab = R0 <= R1 && R1 - R0 + 1 <= kRT;
+    if (use_rtab) {
+        const int nr = R1 - R0 + 1;
+        for (int i = tid; i < G * nr; i += blockDim.x) {
+            int jj = i / nr, rr = i - jj * nr;
+            const BeamParam &Q = bp[jj];
+            float dEl = ((float)(R0 + rr - Q.ri) - Q.rf) * A.del;
+            float sv, cv;
+            sincosf(dEl, &sv, &cv);
+            rtab[jj * kRT + rr] = make_float2(sv, cv);
+            if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
+        }
     }
 
     // ---- phase 1: profile-weighted deposits into the range bins -----------
@@ -721,23 +742,31 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             }
             tab[jj * kTC + cc] = make_float2(sD, vers);
         }
+        if (tid == 0) *uctr = nwarps;
         __syncthreads();
         if (R0 > R1) continue;
         // columns split into nseg segments of (nearly) equal width <= kSeg
         const int nseg = (ncs + kSeg - 1) / kSeg;
         const int segw = (ncs + nseg - 1) / nseg;
         const int nunits = (R1 - R0 + 1) * nseg;
-        for (int unit = warp; unit < nunits; unit += nwarps) {
+        // units are handed out to warps from a counter (costs differ: sky
+        // units are cheap), the first nwarps directly
+        for (int unit = warp; unit < nunits;) {
             const int row = R0 + unit / nseg;
             const int seg = unit - (unit / nseg) * nseg;
             const bool act_row = jok && row >= P.row0 && row <= P.row1;
             const int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
             int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
             if (!act_row) { my_lo = 1; my_hi = 0; }
-            float el = A.el0 + ((float)row + 0.5f) * A.del;
-            float cosEl = cosf(el);
-            float dEl = ((float)(row - P.ri) - P.rf) * A.del;
-            float sdEl = sinf(dEl), cdEl = cosf(dEl);
+            float cosEl, sdEl, cdEl;
+            if (use_rtab) {
+                const float2 rt = rtab[j * kRT + (row - R0)];
+                sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
+            } else {
+                cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
+                float dEl = ((float)(row - P.ri) - P.rf) * A.del;
+                sincosf(dEl, &sdEl, &cdEl);
+            }
             float Kv = P.sin_elb * cosEl;
             float Kc = P.cos_elb * cosEl;
             // x = cg xg + sg yg, y = cg yg - sg xg with xg = cosEl sD and
@@ -818,6 +847,9 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                     }
                 }
             }
+            int nu = 0;
+            if (lane == 0) nu = atomicAdd(uctr, 1);
+            unit = __shfl_sync(0xffffffffu, nu, 0);
         }
     }
     if (wk0 != kNoDeposit) {
