@@ -378,6 +378,22 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
     return r;
 }
 
+// Adds an accumulated wide deposit (end bins packed in key as for records):
+// partial bins f, f+1 and g, g+1, and the run value on f+2 .. g-1 (clipped to
+// the window; bins just outside it fall in the buffer's zeroed padding).
+__device__ __forceinline__ void wide_flush(float *hj, uint32_t key, float a0, float a1, float a2, float a3, float c,
+                                           int pad, int nb)
+{
+    int xf = (int)(key & 0xFFFFu) - kBinBias + pad;
+    int xg = (int)(key >> 16) - kBinBias + pad;
+    atomicAdd(hj + skew_pos(xf), a0);
+    atomicAdd(hj + skew_pos(xf + 1), a1);
+    atomicAdd(hj + skew_pos(xg), a2);
+    atomicAdd(hj + skew_pos(xg + 1), a3);
+    int xs = max(xf + 2, pad), xe = min(xg - 1, pad + nb - 1);
+    for (int x3 = xs; x3 <= xe; ++x3) atomicAdd(hj + skew_pos(x3), c);
+}
+
 template <int KIND>
 __device__ __forceinline__ float profile_finish(const ProfFetch &r)
 {
@@ -721,6 +737,10 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     // addresses at the same time.
     uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
     float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
+    // the same for wide deposits with the same end bins: 4 edge weights and
+    // the run value
+    uint32_t vk = kNoDeposit;
+    float va0 = 0.f, va1 = 0.f, va2 = 0.f, va3 = 0.f, vc = 0.f;
     for (int cs = C0; cs <= C1; cs += kTC) {
         const int ce = min(C1, cs + kTC - 1);
         const int ncs = ce - cs + 1;
@@ -835,15 +855,16 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                         wa3 = fmaf(Pw, r1u.z, wa3);
                     } else {
                         // wide: two partial bins at each end, a constant run between
-                        int xf = (int)(kab & 0xFFFFu) - kBinBias + pad;
-                        int xg2 = (int)(kab >> 16) - kBinBias + pad;
-                        atomicAdd(hj + skew_pos(xf), Pw * r0[u].z);
-                        atomicAdd(hj + skew_pos(xf + 1), Pw * r0[u].w);
-                        atomicAdd(hj + skew_pos(xg2), Pw * r1u.y);
-                        atomicAdd(hj + skew_pos(xg2 + 1), Pw * r1u.z);
-                        float cv = Pw * r1u.w;
-                        int xs = max(xf + 2, pad), xe = min(xg2 - 1, pad + nb - 1);
-                        for (int x3 = xs; x3 <= xe; ++x3) atomicAdd(hj + skew_pos(x3), cv);
+                        if (kab != vk) {
+                            if (vk != kNoDeposit) wide_flush(hj, vk, va0, va1, va2, va3, vc, pad, nb);
+                            vk = kab;
+                            va0 = 0.f; va1 = 0.f; va2 = 0.f; va3 = 0.f; vc = 0.f;
+                        }
+                        va0 = fmaf(Pw, r0[u].z, va0);
+                        va1 = fmaf(Pw, r0[u].w, va1);
+                        va2 = fmaf(Pw, r1u.y, va2);
+                        va3 = fmaf(Pw, r1u.z, va3);
+                        vc = fmaf(Pw, r1u.w, vc);
                     }
                 }
             }
@@ -858,6 +879,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
         if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
     }
+    if (vk != kNoDeposit) wide_flush(hj, vk, va0, va1, va2, va3, vc, pad, nb);
     }  // atomic-deposit phase 1
     if constexpr (TC) {
         // ambient sum per beam: lane (g, t) holds beam g; sum the 4 lanes t
