@@ -97,3 +97,21 @@ def test_no_fallback_when_library_missing(tmp_path):
             lidar.load(str(tmp_path / "nope.so"))
     finally:
         lidar._lib = saved
+
+
+def test_new_entry_points_reject_null(lib):
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_set_deposit(None, 1)
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_batch_config(None)
+    arr = lidar.make_frames([])
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_simulate_batch(None, arr, 0)
+    g = lidar.lidar_gbuffer_t()
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_simulate_noalloc(None, g, lidar.make_pose(np.eye(3)), 0, 0, 0, 0)
+
+
+def test_frame_struct_layout(lib):
+    # lidar_frame_t: sensor pointer, gbuffer, pose, waveforms pointer, echoes
+    assert C.sizeof(lidar.lidar_frame_t) == 8 + C.sizeof(lidar.lidar_gbuffer_t) + 36 + 4 + 8 + 16
