@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
     ap.add_argument("--deposit", default="atomic", choices=["atomic", "tc_split", "tc_bf16"],
                     help="deposit form of the footprint kernel (lidar_set_deposit)")
-    ap.add_argument("--workload", default="frame", choices=["frame", "batch64", "wide"],
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch64", "wide", "split"],
                     help="frame: the full-frame workload (the headline line); batch64: 64 frames of uneven "
-                         "size, pattern and pose through lidar_simulate_batch")
+                         "size, pattern and pose through lidar_simulate_batch; wide: the 8192x4096 wide-tail "
+                         "frame; split: the wide frame with an exact core and an estimated tail "
+                         "(lidar_tail_features + lidar_simulate_split)")
+    ap.add_argument("--core-deg", type=float, default=0.3, help="exact core radius of --workload split")
     return ap.parse_args()
 
 
@@ -60,14 +63,14 @@ DEPOSIT = {"atomic": 0, "tc_split": 1, "tc_bf16": 2}
 
 def workload():
     from paper_2512_05932_gb300 import scenes
-    if WORKLOAD == "wide":
+    if WORKLOAD in ("wide", "split"):
         return scenes.wide_frame()
     return scenes.full_frame_boxes()
 
 
 def config_of(w, extra=None):
     gb = w.gbuffer
-    if WORKLOAD == "wide":
+    if WORKLOAD in ("wide", "split"):
         c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "163.84x81.92", "beams": int(len(w.dirs)),
              "pattern": "grid 500x400", "profile": "radial sigma 0.05 deg + tail, truncated at 2 deg",
              "n_bins": int(w.pulse["n_bins"]), "dt_ns": w.pulse["dt_s"] * 1e9,
@@ -342,6 +345,86 @@ def run_gb300(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_split(args, rank, world, local_rank):
+    """Wide-tail frame with the core/tail split: per step, the tail features
+    (cell sums, bounds, prior) and the split simulation (exact core + tail
+    estimate, acceptance test, exact re-run of the beams that fail it)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2512_05932_gb300 import lidar
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    nc = 256
+    lidar.lidar_tail_configure(L.handle, args.core_deg, nc)
+    planes = lidar.gbuffer_to_device(w.gbuffer, dev)
+    g = lidar.make_gbuffer(w.gbuffer, [p.data_ptr() for p in planes])
+    pose = lidar.make_pose(w.pose)
+    wave, ech, cnt = L.alloc_outputs(dev)
+    rows = torch.zeros((L.n_beams, nc + 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        lidar.lidar_tail_features(L.handle, g, pose, rows.data_ptr(), 0, s)
+        if evs:
+            evs[1].record(stream)
+        n = lidar.lidar_simulate_split(L.handle, g, pose, rows.data_ptr(), wave.data_ptr(), ech.data_ptr(),
+                                       cnt.data_ptr(), s)
+        if evs:
+            evs[2].record(stream)
+        return n
+
+    clk = ClockSampler(local_rank).__enter__()
+    t_w = time.perf_counter()
+    n_w = 0
+    while n_w < args.warmup or time.perf_counter() - t_w < 1.5:
+        step()
+        n_w += 1
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    nfb = []
+    with clk:
+        for i in range(args.steps):
+            nfb.append(step(evs[i]))
+        torch.cuda.synchronize(dev)
+    feat = [e[0].elapsed_time(e[1]) for e in evs]
+    spl = [e[1].elapsed_time(e[2]) for e in evs]
+    ms = (sum(feat) + sum(spl)) / args.steps
+    nbeams = len(w.dirs)
+    peak, peak_kind = load_peaks()
+    alg = algorithmic_bytes(w)
+    achieved = alg / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        rate, dt, _ = oracle_rate(w, 96, cpu_cores())
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"96 evenly spaced beams of the frame, full profile ({dt:.1f} s wall)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * nbeams / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(w, {"split": f"exact core {args.core_deg} deg, tail: physics prior on "
+                                                 f"{nc} coarse bins, exact re-run of beams failing the test",
+                                        "l2": "inputs (0.94 GB) and waveforms (3.3 GB) exceed L2"}),
+                "roofline": {"bound": "hbm", "kernel": "split step (features + split simulation)",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None,
+                             "algorithmic_bytes": alg},
+                "stage_ms": {"features": sum(feat) / args.steps, "split": sum(spl) / args.steps},
+                "fallback_beams": int(np.median(nfb)), "cpu_baseline": cpu, "e2e": None,
+                "gpu_launches": int(args.steps * (7 + (4 if np.median(nfb) > 0 else 0))),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    L.close()
+
+
 def run_batch(args, rank, world, local_rank):
     """64-frame batched workload through lidar_simulate_batch (autotuned)."""
     import torch
@@ -430,6 +513,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch64":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "split":
+        run_split(args, rank, world, local_rank)
     else:
         run_gb300(args, rank, world, local_rank)
 

@@ -13,82 +13,13 @@
 #include <new>
 #include <vector>
 
+#include "lidar_host.h"
 #include "lidar_internal.h"
 
-namespace {
-
-constexpr double kC = 299792458.0;
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kDeg = kPi / 180.0;
-constexpr double kMaxSupportDeg = 10.0;
+namespace gblh {
 
 thread_local char g_create_err[512] = "no error";
 
-}  // namespace
-
-struct lidar {
-    // sensor
-    int32_t n_beams = 0;
-    int32_t kind = 0;
-    double Z = 0.0;
-    double support_rad = 0.0;
-    // radial profile
-    float kg = 0.f, trunc2 = 0.f, tail_amp = 0.f, tc2_inv = 0.f, tail_hp = 0.f;
-    // table profile
-    int32_t qw = 0, qh = 0;
-    float tk = 0.f, tcu = 0.f, tcv = 0.f;
-    // pulse and calibration
-    int32_t n_bins = 0, M = 0, R = 0, tp_len = 0, tp_off = 0;
-    double dt = 0.0, t0 = 0.0;
-    double T = 0.0, s_amb = 0.0;
-    int32_t max_echoes = 0;
-    double coef[3] = {0, 0, 0};
-    // launch shape
-    int32_t G = 16, threads = 512;
-    size_t smem = 0;
-    // deposit form: 0 shared-memory atomics (FP32), 1 tensor cores BF16 hi/lo
-    // split (3 MMAs), 2 tensor cores plain BF16; G_tc/smem_tc: its group shape
-    int32_t deposit = 0;
-    int32_t G_tc = 8;
-    size_t smem_tc = 0;
-    int device = 0;
-    // device memory owned by the library
-    float *d_dirs = nullptr;
-    float4 *d_quads = nullptr;
-    float *d_taps = nullptr;
-    gbl::BeamParam *d_beams = nullptr;
-    float4 *d_rec = nullptr;
-    size_t rec_cap = 0;  // pixels
-    // host-memory entry point buffers
-    float *d_planes = nullptr;
-    size_t planes_cap = 0;  // pixels
-    float *d_wave = nullptr;
-    lidar_echo_t *d_echo = nullptr;
-    int32_t *d_counts = nullptr;
-    // sensor-model fingerprint (batch compatibility) and table hash
-    uint64_t model_hash = 0;
-    // batched execution
-    int32_t batch_G = 8, batch_cps = 0;  // beams per CTA, CTAs per SM (0 = occupancy maximum)
-    float4 *d_brec = nullptr;
-    size_t brec_cap = 0;  // pixels
-    gbl::BeamParam *d_bbeams = nullptr;
-    size_t bbeams_cap = 0;  // beams
-    unsigned char *d_blob = nullptr, *h_blob = nullptr;
-    size_t blob_cap = 0;
-    int *d_counter = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    cudaEvent_t blob_free = nullptr;
-    bool blob_pending = false;
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<long long> gkey;
-    // per-kernel timing (lidar_profile_enable)
-    bool prof = false;
-    std::vector<cudaEvent_t> ev;  // 3 events per recorded simulate call
-    size_t ev_used = 0;
-    char err[512] = "no error";
-};
-
-namespace {
 
 lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...)
 {
@@ -411,6 +342,7 @@ void free_all(lidar_t *l)
     cudaFree(l->d_wave);
     cudaFree(l->d_echo);
     cudaFree(l->d_counts);
+    tail_free(l);
 }
 
 bool is_panorama(const lidar_gbuffer_t *g) { return std::fabs(g->U * g->daz - 2 * kPi) <= 1e-6; }
@@ -460,6 +392,7 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
     fa.rB = (float)(0.5 * kC * l->dt);
     fa.tc_split = l->deposit == 1 ? 1 : 0;
+    fa.inner2 = -1.f;  // no annulus: the whole profile
     return fa;
 }
 
@@ -672,7 +605,9 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
     return LIDAR_OK;
 }
 
-}  // namespace
+}  // namespace gblh
+
+using namespace gblh;
 
 extern "C" {
 

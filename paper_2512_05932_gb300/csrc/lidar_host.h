@@ -1,0 +1,97 @@
+// Host-side state of a sensor and the helpers shared by the host API files
+// (lidar_api.cpp, lidar_tail_api.cpp). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "lidar_internal.h"
+
+namespace gbl {
+struct TailState;
+}
+
+struct lidar {
+    // sensor
+    int32_t n_beams = 0;
+    int32_t kind = 0;
+    double Z = 0.0;
+    double support_rad = 0.0;
+    // radial profile
+    float kg = 0.f, trunc2 = 0.f, tail_amp = 0.f, tc2_inv = 0.f, tail_hp = 0.f;
+    // table profile
+    int32_t qw = 0, qh = 0;
+    float tk = 0.f, tcu = 0.f, tcv = 0.f;
+    // pulse and calibration
+    int32_t n_bins = 0, M = 0, R = 0, tp_len = 0, tp_off = 0;
+    double dt = 0.0, t0 = 0.0;
+    double T = 0.0, s_amb = 0.0;
+    int32_t max_echoes = 0;
+    double coef[3] = {0, 0, 0};
+    // launch shape
+    int32_t G = 16, threads = 512;
+    size_t smem = 0;
+    // deposit form: 0 shared-memory atomics (FP32), 1 tensor cores BF16 hi/lo
+    // split (3 MMAs), 2 tensor cores plain BF16; G_tc/smem_tc: its group shape
+    int32_t deposit = 0;
+    int32_t G_tc = 8;
+    size_t smem_tc = 0;
+    int device = 0;
+    // device memory owned by the library
+    float *d_dirs = nullptr;
+    float4 *d_quads = nullptr;
+    float *d_taps = nullptr;
+    gbl::BeamParam *d_beams = nullptr;
+    float4 *d_rec = nullptr;
+    size_t rec_cap = 0;  // pixels
+    // host-memory entry point buffers
+    float *d_planes = nullptr;
+    size_t planes_cap = 0;  // pixels
+    float *d_wave = nullptr;
+    lidar_echo_t *d_echo = nullptr;
+    int32_t *d_counts = nullptr;
+    // sensor-model fingerprint (batch compatibility) and table hash
+    uint64_t model_hash = 0;
+    // batched execution
+    int32_t batch_G = 8, batch_cps = 0;  // beams per CTA, CTAs per SM (0 = occupancy maximum)
+    float4 *d_brec = nullptr;
+    size_t brec_cap = 0;  // pixels
+    gbl::BeamParam *d_bbeams = nullptr;
+    size_t bbeams_cap = 0;  // beams
+    unsigned char *d_blob = nullptr, *h_blob = nullptr;
+    size_t blob_cap = 0;
+    int *d_counter = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t blob_free = nullptr;
+    bool blob_pending = false;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> gkey;
+    // per-kernel timing (lidar_profile_enable)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // 3 events per recorded simulate call
+    size_t ev_used = 0;
+    // core/tail split (lidar_tail_api.cpp)
+    gbl::TailState *tail = nullptr;
+    char err[512] = "no error";
+};
+
+namespace gblh {
+
+constexpr double kC = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kDeg = kPi / 180.0;
+constexpr double kMaxSupportDeg = 10.0;
+
+lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...);
+lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what);
+lidar_status_t check_gbuffer(lidar_t *l, const lidar_gbuffer_t *g);
+lidar_status_t check_pose(lidar_t *l, const lidar_pose_t *p, double R[9]);
+lidar_status_t ensure_scratch(lidar_t *l, size_t pixels);
+bool is_panorama(const lidar_gbuffer_t *g);
+gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_gbuffer_t *g, const double R[9],
+                          float4 *rec, gbl::BeamParam *beams);
+gbl::FootprintArgs model_args(const lidar_t *l);
+void tail_free(lidar_t *l);  // lidar_tail_api.cpp
+
+}  // namespace gblh

@@ -42,6 +42,9 @@ struct SetupArgs {
     float x_scale, x_off;    // bin-centre coordinate X = r * x_scale + x_off
     int n_bins;
     int pad;                 // zero padding (bins) of the footprint kernel's histogram buffer
+    const uint8_t *core_only;  // per beam: 1 = only the core of the profile (box radius core_rad)
+    double core_rad;
+    const int *beam_ids;     // beam slot b takes pattern direction beam_ids[b] (NULL: b)
     int bin_records;         // narrow records carry the first bin index (tensor-core deposit)
                              // instead of histogram positions (shared-memory atomics)
     int pix_blocks;
@@ -74,6 +77,26 @@ struct FootprintArgs {
     const float *taps_pad;  // length tp_len, tap m at index tp_off + m
     int tp_len, tp_off;
     int tc_split;            // tensor-core deposit: 1 = BF16 hi/lo split (3 MMAs), 0 = plain BF16
+    // core/tail split of a radial profile (learned tail surrogate)
+    float core2;             // support radius^2 (rad^2) of beams flagged core-only
+    float inner2;            // samples with theta^2 <= inner2 are left out (annulus), < 0: none
+    // Rows of tail_in / coarse_out have tail_stride = n_coarse + 4 floats:
+    //   [0, n_coarse)  coarse histogram (n_bins / n_coarse fine bins per coarse bin)
+    //   [n_coarse]     ambient sum
+    //   tail_in only:  [n_coarse + 1] bound on the tail's deposited mass,
+    //                  [n_coarse + 2] bound on the ambient estimate's error
+    const float *tail_in;    // coarse tail of core-only beams (convolved with tail_box); NULL: none
+    const float *tail_box;   // pulse averaged over cf fine bins, B(x) at index x + tb_off,
+                             // x in [-M - 7, M + cf + 6] (zero outside [-M, M + cf - 1])
+    int tb_off;
+    float *coarse_out;       // coarse histogram and ambient sum of every beam; NULL: none
+    int n_coarse, tail_stride;
+    // acceptance test of core-only beams (pulse constants of the FP32 taps:
+    // max tap, L2 norm, max |p[i+1]-p[i]|, max |p[i+2]-p[i]|, max |p[i+1]-2p[i]+p[i-1]|)
+    float g_pmax, g_pl2, g_d1, g_d2, g_dd;
+    float g_l2, g_dr;        // relative L2 budget of the tail error; range / EPW budget (m)
+    uint8_t *fb_flags;       // [n_beams]: set to 1 for beams that fail the test (cleared by the caller)
+    const int *out_ids;      // beam slot b writes output row out_ids[b] (NULL: b)
     // calibration
     float T, s_amb;
     int max_echoes;

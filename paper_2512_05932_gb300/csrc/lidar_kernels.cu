@@ -150,7 +150,8 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
 
 __device__ void setup_beam(const SetupArgs &A, int b)
 {
-    double d[3] = {A.dirs[3 * b], A.dirs[3 * b + 1], A.dirs[3 * b + 2]};
+    const int src = A.beam_ids ? A.beam_ids[b] : b;
+    double d[3] = {A.dirs[3 * src], A.dirs[3 * src + 1], A.dirs[3 * src + 2]};
     double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     d[0] /= nd; d[1] /= nd; d[2] /= nd;
     double e1[3] = {-d[1], d[0], 0.0};
@@ -192,7 +193,8 @@ __device__ void setup_beam(const SetupArgs &A, int b)
     P.cos_elb = (float)ceb;
     P.cg = (float)cg;
     P.sg = (float)sg;
-    double th = A.support_rad;
+    const int core = A.core_only ? (int)A.core_only[src] : 0;
+    double th = core ? A.core_rad : A.support_rad;
     long r0 = (long)ceil((el_b - th - A.el0d) / A.deld - 0.5) - 1;
     long r1 = (long)floor((el_b + th - A.el0d) / A.deld - 0.5) + 1;
     if (r0 < 0) r0 = 0;
@@ -216,7 +218,7 @@ __device__ void setup_beam(const SetupArgs &A, int b)
     P.row0 = (int)r0; P.row1 = (int)r1;
     P.col0 = (int)c0; P.col1 = (int)c1;
     P.valid = (r0 <= r1 && c0 <= c1) ? 1 : 0;
-    P.pad0 = 0; P.pad1 = 0.f; P.pad2 = 0.f;
+    P.pad0 = core; P.pad1 = 0.f; P.pad2 = 0.f;
     A.beams[b] = P;
 }
 
@@ -295,7 +297,7 @@ struct Layout {
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_supp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
+    size_t off_taps, off_amb, off_nrm, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
 };
 
 
@@ -311,7 +313,9 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     size_t off = (size_t)G * L.HB * 4;
     L.off_taps = off; off += (size_t)L.taps_len * 4;
     L.off_amb = off; off += (size_t)G * 4;
+    L.off_nrm = off; off += (size_t)G * 4;
     L.off_supp = off; off += (size_t)G * 8;
+    L.off_tsupp = off; off += (size_t)G * 8;
     off = (off + 15) & ~(size_t)15;
     L.off_tab = off; off += (size_t)G * kTC * sizeof(float2);
     L.off_rtab = off; off += (size_t)G * kRT * sizeof(float2);
@@ -343,14 +347,15 @@ struct ProfFetch {
 };
 
 template <int KIND>
-__device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float x, float y, bool act)
+__device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float x, float y, bool act,
+                                                   float t2max = -1.f)
 {
     ProfFetch r;
     float s2 = fmaf(x, x, y * y);
     if (KIND == LIDAR_PROFILE_RADIAL) {
         // theta^2 = asin(s)^2 = s^2 (1 + s^2/3 + 8 s^4/45 + ...)
         float t2 = s2 * fmaf(s2, fmaf(s2, 8.f / 45.f, 1.f / 3.f), 1.f);
-        r.ok = act && t2 <= A.trunc2;
+        r.ok = act && t2 <= (t2max >= 0.f ? t2max : A.trunc2) && t2 > A.inner2;
         // Gaussian: 2^(t2 kg) with the hardware base-2 exponential (relative
         // error ~2^-22); tail: (theta/theta_c)^-p = rr^(-p/2), with the common
         // p = 3 as rr^-1.5 = rsqrt(rr)^3
@@ -652,6 +657,8 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
     float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
     int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
+    int *tsupp = reinterpret_cast<int *>(smem_raw + Ly.off_tsupp);  // coarse support of an added tail
+    float *nrm2_s = reinterpret_cast<float *>(smem_raw + Ly.off_nrm);
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
     float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
     float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
@@ -671,6 +678,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
     if (tid < G) {
         amb_s[tid] = 0.f;
+        nrm2_s[tid] = 0.f;
         BeamParam P;
         if (tid < gcount) P = A.beams[b0 + tid];
         else { P = BeamParam{}; P.valid = 0; }
@@ -727,6 +735,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     const int j = lane % G;
     const int q = lane / G;
     const BeamParam P = bp[j];
+    const float t2max = P.pad0 ? A.core2 : A.trunc2;
     const bool jok = (j < gcount) && P.valid;
     float *hj = hbuf + j * Ly.HB;
     const float2 *tj = tab + j * kTC;
@@ -824,7 +833,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                     act[u] = act[u] && fmaf(-Kc, t.y, cdEl) > 0.f;
                     float x = fmaf(ax, t.x, fmaf(bx, t.y, cx));
                     float y = fmaf(ay, t.x, fmaf(by, t.y, cy));
-                    pf[u] = profile_fetch<KIND>(A, x, y, act[u]);
+                    pf[u] = profile_fetch<KIND>(A, x, y, act[u], t2max);
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
@@ -902,6 +911,41 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             hj[skew_pos(pad + nb + lane)] = 0.f;
         }
         __syncwarp();
+        int tlo = 1 << 30, thi = -1;
+        if (jj < gcount && (A.tail_in || A.coarse_out)) {
+            const int cf = nb / A.n_coarse;
+            const size_t row = (size_t)(b0 + jj) * A.tail_stride;
+            if (A.tail_in && bp[jj].pad0) {
+                // added tail of a core-only beam: its coarse support and ambient sum
+                // (the coarse histogram itself enters in the convolution phase)
+                for (int c = lane; c < A.n_coarse; c += 32)
+                    if (A.tail_in[row + c] != 0.f) { tlo = min(tlo, c); thi = max(thi, c); }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    tlo = min(tlo, __shfl_xor_sync(0xffffffffu, tlo, o));
+                    thi = max(thi, __shfl_xor_sync(0xffffffffu, thi, o));
+                }
+                if (lane == 0) amb_s[jj] += A.tail_in[row + A.n_coarse];
+            }
+            if (A.coarse_out) {
+                float tot = 0.f;
+                for (int cb = 0; cb < A.n_coarse; ++cb) {
+                    float v = 0.f;
+                    for (int k = cb * cf + lane; k < (cb + 1) * cf; k += 32) v += hj[skew_pos(k + pad)];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) A.coarse_out[row + cb] = v;
+                    tot += v;
+                }
+                if (lane == 0) {
+                    A.coarse_out[row + A.n_coarse] = amb_s[jj];
+                    A.coarse_out[row + A.n_coarse + 1] = 0.f;
+                    A.coarse_out[row + A.n_coarse + 2] = 0.f;
+                    A.coarse_out[row + A.n_coarse + 3] = tot;
+                }
+            }
+            __syncwarp();
+        }
         int lo = 1 << 30, hi = -1;
         for (int k = lane; k < nb; k += 32) {
             if (hj[skew_pos(k + pad)] != 0.f) { lo = min(lo, k); hi = max(hi, k); }
@@ -911,7 +955,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
-        if (lane == 0) { supp[2 * jj] = lo; supp[2 * jj + 1] = hi; }
+        if (lane == 0) { supp[2 * jj] = lo; supp[2 * jj + 1] = hi; tsupp[2 * jj] = tlo; tsupp[2 * jj + 1] = thi; }
     }
     __syncthreads();
 
@@ -947,10 +991,39 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 }
             }
         }
+        const int tlo = tsupp[2 * jj], thi = tsupp[2 * jj + 1];
+        if (thi >= 0) {
+            // added coarse tail: mass T_c spread evenly over the cf fine bins of
+            // coarse bin c, convolved with the pulse = sum_c T_c B(k - c cf),
+            // B(x) = (1/cf) sum_{j<cf} p(x - j) (tail_box, index x + tb_off)
+            const int cf = nb / A.n_coarse;
+            const float *Tr = A.tail_in + (size_t)(b0 + jj) * A.tail_stride;
+            // first coarse bin reaching output kb: ceil((kb - M - cf + 1) / cf) = floor((kb - M) / cf)
+            const int c0 = max(tlo, (kb - M + cf * (M + 1)) / cf - (M + 1));
+            const int c1 = min(thi, (kb + 7 + M) / cf);
+            for (int c = c0; c <= c1; ++c) {
+                const float t = __ldg(Tr + c);
+                const float *bx = A.tail_box + A.tb_off + kb - c * cf;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, __ldg(bx + r), acc[r]);
+            }
+        }
         if (o0 + 8 * lane < nb) {
-            float4 *dst = reinterpret_cast<float4 *>(A.wave + (size_t)(b0 + jj) * nb + o0 + 8 * lane);
+            const size_t orow = A.out_ids ? (size_t)A.out_ids[b0 + jj] : (size_t)(b0 + jj);
+            float4 *dst = reinterpret_cast<float4 *>(A.wave + orow * nb + o0 + 8 * lane);
             dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        }
+        if (A.tail_in && bp[jj].pad0) {
+            // squared L2 norm of the waveform (acceptance test of the tail)
+            float s2 = 0.f;
+            if (o0 + 8 * lane < nb) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) s2 = fmaf(acc[r], acc[r], s2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            if (lane == 0) atomicAdd(nrm2_s + jj, s2);
         }
     }
     __syncthreads();
@@ -960,7 +1033,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     // histogram's support hold the ambient level only and cannot be part of a
     // run, so the scan covers [lo - M - 1, hi + M + 1]. Loads run one chunk ahead.
     for (int jj = warp; jj < gcount; jj += nwarps) {
-        const int beam = b0 + jj;
+        const int beam = A.out_ids ? A.out_ids[b0 + jj] : b0 + jj;
         const float *xw = A.wave + (size_t)beam * nb;
         lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
         const float T = A.T;
@@ -970,6 +1043,32 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         if (ambv > T) { kbeg = 0; kend = nb - 1; }
         else if (hi < 0) { kbeg = 1; kend = 0; }
         else { kbeg = max(0, lo - M - 1); kend = min(nb - 1, hi + M + 1); }
+        if (tsupp[2 * jj + 1] >= 0 && !(ambv > T)) {
+            const int cf = nb / A.n_coarse;
+            const int tb = max(0, tsupp[2 * jj] * cf - M - 1), te = min(nb - 1, (tsupp[2 * jj + 1] + 1) * cf + M);
+            if (kbeg > kend) { kbeg = tb; kend = te; }
+            else { kbeg = min(kbeg, tb); kend = max(kend, te); }
+        }
+        // Acceptance test of a core-only beam whose tail was predicted: the
+        // exact tail and the prediction are both non-negative with mass at
+        // most Eub, so the difference moves any bin by at most eps and bin
+        // differences by at most 2 Eub times the pulse's differences. The beam
+        // is re-run exactly unless neither can change a bin's side of T, the
+        // peak bin, or move the waveform, a crossing or the peak vertex by more
+        // than the budgets.
+        const bool gated = A.tail_in != nullptr && bp[jj].pad0 != 0;
+        float g_eub = 0.f, g_eps = 0.f;
+        bool gfail = false;
+        if (gated) {
+            const float *trow = A.tail_in + (size_t)beam * A.tail_stride;
+            g_eub = trow[A.n_coarse + 1];
+            const float dAs = trow[A.n_coarse + 2] * A.s_amb;
+            g_eps = 1.01f * fmaf(g_eub, A.g_pmax, dAs);
+            const float l2err = 1.01f * (1.4142136f * g_eub * A.g_pl2 + dAs * sqrtf((float)nb));
+            gfail = !(l2err <= A.g_l2 * sqrtf(nrm2_s[jj]));
+            if (ambv <= T) gfail |= !(T - ambv > g_eps);  // bins outside the scan
+            gfail |= !(isfinite(g_eub) && isfinite(g_eps));
+        }
         int count = 0;
         bool open = false;
         int bs = 0, pk = 0;
@@ -988,6 +1087,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             if (lane == 31) vn = vnn;
             float vp = __shfl_up_sync(0xffffffffu, v, 1);
             if (lane == 0) vp = prev_last;
+            if (gated) gfail |= __any_sync(0xffffffffu, k >= kbeg && k <= kend && fabsf(v - T) <= g_eps);
             bool ab = v > T;
             bool st = ab && !(k > 0 && vp > T);
             bool en = ab && !(k + 1 < nb && vn > T);
@@ -1035,15 +1135,51 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                                 float la = logf(va), lb = logf(vb), lc = logf(vc);
                                 float den = la - 2.f * lb + lc;
                                 if (den < 0.f) dl = 0.5f * (la - lc) / den;
+                                if (gated) {
+                                    // first-order change of the log-parabola vertex, plus
+                                    // the second-order term of each log
+                                    const float D = 2.02f * g_eub;
+                                    const float q = g_eps / fminf(va, fminf(vb, vc));
+                                    const float dnum = D * A.g_d2 / va + g_eps * fabsf(1.f / va - 1.f / vc) + 2.f * q * q;
+                                    const float dden = D * A.g_dd / vb +
+                                                       g_eps * (fabsf(1.f / va - 1.f / vb) + fabsf(1.f / vc - 1.f / vb)) +
+                                                       4.f * q * q;
+                                    const float ad = fabsf(den);
+                                    if (!(ad > 2.f * dden)) gfail = true;
+                                    else {
+                                        float ddl = 0.5f * (dnum * ad + fabsf(la - lc) * dden) / (ad * (ad - dden));
+                                        if (!(ddl * A.rB <= A.g_dr)) gfail = true;
+                                    }
+                                    // the bins next to the peak must stay below it
+                                    if (pk - 1 >= bs && !(vb - va > D * A.g_d1)) gfail = true;
+                                    if (pk + 1 <= be && !(vb - vc > D * A.g_d1)) gfail = true;
+                                }
                             } else {
                                 float den = va - 2.f * vb + vc;
                                 if (den < 0.f) dl = 0.5f * (va - vc) / den;
+                                if (gated) gfail = true;
                             }
                             dl = fminf(0.5f, fmaxf(-0.5f, dl));
                         }
                         float r0m = fmaf(x0, A.rB, A.rA), r1m = fmaf(x1, A.rB, A.rA);
                         float epw = r1m - r0m;
                         float E2 = epw * epw;
+                        if (gated) {
+                            // crossings: x = k + (T - a) / (b - a) moves by at most
+                            // (|b - T| + |T - a|) eps / (b - a)^2 to first order
+                            float dx = 0.f;
+                            if (bs > 0) {
+                                float vm = xw[bs - 1], w = vbs - vm, q = g_eps / w;
+                                dx += (fabsf(vbs - T) + fabsf(T - vm)) * g_eps / (w * w) + 4.f * q * q;
+                            }
+                            if (be < nb - 1) {
+                                float vq = xw[be + 1], w = vbe - vq, q = g_eps / w;
+                                dx += (fabsf(vbe - T) + fabsf(T - vq)) * g_eps / (w * w) + 4.f * q * q;
+                            }
+                            const float dE = dx * A.rB;
+                            const float slope = fabsf(2.f * A.c1 * epw + 4.f * A.c2 * epw * E2);
+                            if (!(dE <= A.g_dr && slope * dE <= 3e-4f && g_eps <= 3e-4f * pv)) gfail = true;
+                        }
                         e.range_m = fmaf((float)pk + dl, A.rB, A.rA);
                         e.epw_m = epw;
                         e.intensity = expf(fmaf(A.c2 * E2, E2, fmaf(A.c1, E2, A.c0)));
@@ -1053,6 +1189,15 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                         e.bin_end = be;
                         e.flags = fl;
                         eo[count] = e;
+                    }
+                    if (gated) {
+                        // every other bin of the run must stay below the peak
+                        float m2 = -1.f;
+                        for (int qb = bs + lane; qb <= be; qb += 32)
+                            if (qb < pk - 1 || qb > pk + 1) m2 = fmaxf(m2, xw[qb]);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                        if (m2 >= 0.f && !(pv - m2 > 2.02f * g_eub * A.g_pmax)) gfail = true;
                     }
                     ++count;
                     open = false;
@@ -1077,6 +1222,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             for (int e = count; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
             A.counts[beam] = count;
         }
+        if (gated && __any_sync(0xffffffffu, gfail) && lane == 0) A.fb_flags[beam] = 1;
     }
 }
 

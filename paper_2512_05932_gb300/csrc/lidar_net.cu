@@ -1,0 +1,408 @@
+// FP16 kernels of the tail network (training and inference): a tiled tensor-
+// core GEMM (mma.sync m16n8k16, FP16 operands, FP32 accumulation) in three
+// operand layouts, im2col / col2im for the 3x3 stride-2 convolutions, and the
+// element-wise steps (bias, ReLU, loss, Adam).
+//
+// Network (per beam; x = the 4-level input pyramid, levels L0..L3 of
+// 64^2, 32^2, 16^2, 8^2 cells x 2 channels):
+//   a1 = relu(conv3x3/2(L0))                      32^2 x 32
+//   a2 = relu(conv3x3/2([a1, L1]))                16^2 x 32
+//   a3 = relu(conv3x3/2([a2, L2]))                 8^2 x 32
+//   f  = [a3, L3, prior / s]                       2048 + 128 + n_coarse
+//   h  = relu(W1 f + b1)                           256
+//   y  = relu(prior / s + W2 h + b2)               n_coarse   (tail / s)
+// with s the beam's scale (prior mass, at least 0.1 x the tail bound).
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lidar_net_internal.h"
+
+namespace gbl {
+
+// ---------------------------------------------------------------------------
+// GEMM: C[m][n] = sum_k A(m, k) B(n, k)
+//   A(m, k) = A[m * lda + k] (TA = false) or A[k * lda + m] (TA = true)
+//   B(n, k) = B[n * ldb + k] (TB = false) or B[k * ldb + n] (TB = true)
+// 64 x 64 x 32 tiles, 4 warps of 32 x 32; K a multiple of 8, leading
+// dimensions multiples of 8 (16-byte rows). blockIdx.z splits K.
+// ---------------------------------------------------------------------------
+
+constexpr int kBM = 64, kBN = 64, kBK = 32, kSP = kBK + 8;  // smem row pitch (halves): conflict-free ldmatrix
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __half *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Loads a rows x 32 (k) tile of an operand into shared memory as [row][k].
+template <bool T>
+__device__ __forceinline__ void load_tile(__half *s, const __half *g, int ld, int r0, int nrows, int k0, int K)
+{
+    const int tid = threadIdx.x;
+    if (!T) {
+        // row-major: 4 chunks of 8 halves per row
+        for (int i = tid; i < 64 * 4; i += 128) {
+            const int r = i >> 2, kq = (i & 3) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r0 + r < nrows && k0 + kq < K) v = *reinterpret_cast<const uint4 *>(g + (size_t)(r0 + r) * ld + k0 + kq);
+            *reinterpret_cast<uint4 *>(s + r * kSP + kq) = v;
+        }
+    } else {
+        // k-major: 8 chunks of 8 rows per k
+        for (int i = tid; i < 32 * 8; i += 128) {
+            const int kk = i >> 3, rq = (i & 7) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k0 + kk < K) {
+                if (r0 + rq + 8 <= nrows) {
+                    v = *reinterpret_cast<const uint4 *>(g + (size_t)(k0 + kk) * ld + r0 + rq);
+                } else {
+                    __half tmp[8];
+                    for (int j = 0; j < 8; ++j)
+                        tmp[j] = (r0 + rq + j < nrows) ? g[(size_t)(k0 + kk) * ld + r0 + rq + j] : __float2half(0.f);
+                    v = *reinterpret_cast<uint4 *>(tmp);
+                }
+            }
+            const __half *h = reinterpret_cast<const __half *>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[(rq + j) * kSP + kk] = h[j];
+        }
+    }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
+{
+    __shared__ __align__(16) __half sA[kBM * kSP];
+    __shared__ __align__(16) __half sB[kBN * kSP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+    const int kbeg = blockIdx.z * g.k_split;
+    const int kend = min(g.K, kbeg + g.k_split);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+        __syncthreads();
+        load_tile<TA>(sA, g.A, g.lda, m0, g.M, k0, kend);
+        load_tile<TB>(sB, g.B, g.ldb, n0, g.N, k0, kend);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; kk += 16) {
+            uint32_t a[2][4], b[2][4];
+            const int q = lane >> 3, r = lane & 7;
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm_x4(a[mi], sA + (wm * 32 + mi * 16 + (q & 1) * 8 + r) * kSP + kk + (q >> 1) * 8);
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj)
+                ldsm_x4(b[nj], sB + (wn * 32 + nj * 16 + (q >> 1) * 8 + r) * kSP + kk + (q & 1) * 8);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    mma_f16(acc[mi][ni], a[mi], b[ni >> 1][(ni & 1) * 2], b[ni >> 1][(ni & 1) * 2 + 1]);
+        }
+    }
+    // epilogue
+    const int gq = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm * 32 + mi * 16 + gq + 8 * h;
+                const int n = n0 + wn * 32 + ni * 8 + 2 * t4;
+                if (m >= g.M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (n + e >= g.N) continue;
+                    float v = acc[mi][ni][2 * h + e];
+                    if (g.mode == kGemmStore) {
+                        g.C[(size_t)m * g.ldc + n + e] = v;
+                    } else if (g.mode == kGemmAtomic) {
+                        atomicAdd(g.C + (size_t)m * g.ldc + n + e, v);
+                    } else {
+                        v += g.bias[n + e];
+                        if (g.mode == kGemmBiasRelu) v = fmaxf(v, 0.f);
+                        if (g.Ch) g.Ch[(size_t)m * g.ldc + n + e] = __float2half_rn(v);
+                        if (g.C && g.mode == kGemmBias) g.C[(size_t)m * g.ldc + n + e] = v;
+                    }
+                }
+            }
+}
+
+cudaError_t launch_gemm(bool ta, bool tb, const GemmArgs &g, int splits, cudaStream_t s)
+{
+    dim3 grid((g.M + kBM - 1) / kBM, (g.N + kBN - 1) / kBN, splits);
+    if (!ta && !tb) gemm_kernel<false, false><<<grid, 128, 0, s>>>(g);
+    else if (!ta && tb) gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);
+    else if (ta && !tb) gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
+    else gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// convolution plumbing
+// ---------------------------------------------------------------------------
+
+// im2col of a 3x3 stride-2 convolution with one pixel of zero padding:
+// row (b, oy, ox) of Xc ([B * Ho * Wo][Kp]), column k = tap * Cin + c
+// (tap = ky * 3 + kx), input pixel (2 oy + ky - 1, 2 ox + kx - 1); channels
+// c < Ca from act ([B][Hi][Wi][Ca]), the next 2 from the pyramid level
+// (x + level_off cells, [B][Hi][Wi][2] within each beam's input of
+// in_stride cells); columns k >= 9 Cin are zero.
+__global__ void im2col_kernel(Im2colArgs a)
+{
+    const int Cin = a.Ca + 2;
+    const size_t total = (size_t)a.B * a.Ho * a.Wo * a.Kp;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % a.Kp);
+        const size_t row = i / a.Kp;
+        const int ox = (int)(row % a.Wo), oy = (int)((row / a.Wo) % a.Ho);
+        const int b = (int)(row / ((size_t)a.Wo * a.Ho));
+        __half v = __float2half(0.f);
+        if (k < 9 * Cin) {
+            const int tap = k / Cin, c = k - tap * Cin;
+            const int iy = 2 * oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
+            if (iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi) {
+                if (c < a.Ca) v = a.act[(((size_t)b * a.Hi + iy) * a.Wi + ix) * a.Ca + c];
+                else v = a.x[(size_t)b * a.in_stride + a.level_off + ((size_t)iy * a.Wi + ix) * 2 + (c - a.Ca)];
+            }
+        }
+        a.out[i] = v;
+    }
+}
+
+// Gradient of im2col for the activation channels: dA[b][iy][ix][c] = sum over
+// the (<= 4) output pixels and taps that read (iy, ix) of dXc, times the ReLU
+// mask of the activation (a > 0), scaled; written as FP16.
+__global__ void col2im_kernel(Col2imArgs a)
+{
+    const int Cin = a.Ca + 2;
+    const size_t total = (size_t)a.B * a.Hi * a.Wi * a.Ca;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % a.Ca);
+        const size_t pix = i / a.Ca;
+        const int ix = (int)(pix % a.Wi), iy = (int)((pix / a.Wi) % a.Hi);
+        const int b = (int)(pix / ((size_t)a.Wi * a.Hi));
+        float s = 0.f;
+        if (__half2float(a.act[i]) > 0.f) {
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                const int ty = iy + 1 - ky;
+                if (ty < 0 || (ty & 1) || (ty >> 1) >= a.Ho) continue;
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int tx = ix + 1 - kx;
+                    if (tx < 0 || (tx & 1) || (tx >> 1) >= a.Wo) continue;
+                    const size_t row = ((size_t)b * a.Ho + (ty >> 1)) * a.Wo + (tx >> 1);
+                    s += a.dcol[row * a.Kp + (ky * 3 + kx) * Cin + c];
+                }
+            }
+        }
+        a.dact[i] = __float2half_rn(s);
+    }
+}
+
+// f = [a3 (n_a), level 3 of x (n_l), prior / s (n_coarse)] per beam, and the
+// per-beam scale s.
+__global__ void flatten_kernel(FlattenArgs a)
+{
+    const size_t total = (size_t)a.B * a.F;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % a.F);
+        const int b = (int)(i / a.F);
+        __half v;
+        if (j < a.n_a) {
+            v = a.a3[(size_t)b * a.n_a + j];
+        } else if (j < a.n_a + a.n_l) {
+            v = a.x[(size_t)b * a.in_stride + a.level_off + (j - a.n_a)];
+        } else {
+            const int c = j - a.n_a - a.n_l;
+            const float *row = a.rows + (size_t)b * a.row_stride;
+            const float s = net_scale(row, a.n_coarse);
+            v = __float2half_rn(s > 0.f ? row[c] / s : 0.f);
+        }
+        a.f[i] = v;
+    }
+}
+
+// Output, loss and the output gradient:
+//   y_hat = relu(prior / s + d), loss = mean_b sum_c |y_hat - target / s|,
+//   dd = d loss / d d x loss_scale (FP16)
+__global__ void head_kernel(HeadArgs a)
+{
+    const size_t total = (size_t)a.B * a.n_coarse;
+    float part = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % a.n_coarse);
+        const int b = (int)(i / a.n_coarse);
+        const float *row = a.rows + (size_t)b * a.row_stride;
+        const float s = net_scale(row, a.n_coarse);
+        const float pn = s > 0.f ? row[c] / s : 0.f;
+        const float z = pn + a.d[i];
+        const float yh = fmaxf(z, 0.f);
+        if (a.out) a.out[(size_t)b * a.row_stride + c] = yh * s;
+        if (a.target) {
+            const float y = s > 0.f ? a.target[(size_t)b * a.row_stride + c] / s : 0.f;
+            const float e = yh - y;
+            part += s > 0.f ? fabsf(e) : 0.f;
+            const float g = (s > 0.f && z > 0.f) ? (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) : 0.f;
+            a.dd[i] = __float2half_rn(g * a.grad_scale);
+        }
+    }
+    if (a.loss) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, part / (float)a.B);
+    }
+}
+
+// Final rows of a prediction: clip the tail to the bound and copy the
+// ambient entry and the bounds.
+__global__ void finish_rows_kernel(const float *rows, float *out, int B, int n_coarse)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const float *r = rows + (size_t)b * (n_coarse + 4);
+    float *o = out + (size_t)b * (n_coarse + 4);
+    float s = 0.f;
+    for (int c = lane; c < n_coarse; c += 32) s += fmaxf(o[c], 0.f);
+#pragma unroll
+    for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
+    const float E = r[n_coarse + 1];
+    const float f = (s > E && s > 0.f) ? E / s * (1.f - 1e-6f) : 1.f;
+    for (int c = lane; c < n_coarse; c += 32) o[c] = fmaxf(o[c], 0.f) * f;
+    if (lane == 0) {
+        o[n_coarse] = r[n_coarse];
+        o[n_coarse + 1] = E;
+        o[n_coarse + 2] = r[n_coarse + 2];
+        o[n_coarse + 3] = s * f;
+    }
+}
+
+// dZ = dA * (a > 0) for a row-major activation (FP16 in, FP16 out), used
+// between the fully connected layers.
+__global__ void relu_grad_kernel(const float *da, const __half *a, __half *dz, size_t n, float scale)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dz[i] = __float2half_rn(__half2float(a[i]) > 0.f ? da[i] * scale : 0.f);
+}
+
+// db[n] += sum_m dz[m][n] (FP32 atomics, one thread per (m-chunk, n))
+__global__ void bias_grad_kernel(const __half *dz, int M, int N, float *db)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int chunk = (M + gridDim.y - 1) / gridDim.y;
+    const int m0 = blockIdx.y * chunk, m1 = min(M, m0 + chunk);
+    float s = 0.f;
+    for (int m = m0; m < m1; ++m) s += __half2float(dz[(size_t)m * N + n]);
+    atomicAdd(db + n, s);
+}
+
+// Adam with bias correction; grads are divided by the loss scale; writes the
+// FP16 copy of the weights. A non-finite gradient skips the step (flag set).
+__global__ void adam_kernel(AdamArgs a)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (size_t)gridDim.x * blockDim.x) {
+        if (*a.skip) return;
+        const float g = a.grad[i] * a.inv_scale;
+        const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+        const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+        a.m[i] = m;
+        a.v[i] = v;
+        const float w = a.w[i] - a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+        a.w[i] = w;
+        a.wh[i] = __float2half_rn(w);
+    }
+}
+
+__global__ void finite_check_kernel(const float *g, size_t n, int *flag)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(g[i])) *flag = 1;
+}
+
+__global__ void to_half_kernel(const float *w, __half *wh, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        wh[i] = __float2half_rn(w[i]);
+}
+
+namespace {
+int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 32); }
+}  // namespace
+
+cudaError_t launch_im2col(const Im2colArgs &a, cudaStream_t s)
+{
+    im2col_kernel<<<grid_for((size_t)a.B * a.Ho * a.Wo * a.Kp), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_col2im(const Col2imArgs &a, cudaStream_t s)
+{
+    col2im_kernel<<<grid_for((size_t)a.B * a.Hi * a.Wi * a.Ca), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_flatten(const FlattenArgs &a, cudaStream_t s)
+{
+    flatten_kernel<<<grid_for((size_t)a.B * a.F), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_head(const HeadArgs &a, cudaStream_t s)
+{
+    head_kernel<<<grid_for((size_t)a.B * a.n_coarse), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_finish_rows(const float *rows, float *out, int B, int n_coarse, cudaStream_t s)
+{
+    finish_rows_kernel<<<(B + 7) / 8, 256, 0, s>>>(rows, out, B, n_coarse);
+    return cudaGetLastError();
+}
+cudaError_t launch_relu_grad(const float *da, const __half *a, __half *dz, size_t n, float scale, cudaStream_t s)
+{
+    relu_grad_kernel<<<grid_for(n), 256, 0, s>>>(da, a, dz, n, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_bias_grad(const __half *dz, int M, int N, float *db, cudaStream_t s)
+{
+    dim3 grid((N + 127) / 128, std::min(256, std::max(1, M / 256)));
+    bias_grad_kernel<<<grid, 128, 0, s>>>(dz, M, N, db);
+    return cudaGetLastError();
+}
+cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s)
+{
+    adam_kernel<<<grid_for(a.n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_finite_check(const float *g, size_t n, int *flag, cudaStream_t s)
+{
+    finite_check_kernel<<<grid_for(n), 256, 0, s>>>(g, n, flag);
+    return cudaGetLastError();
+}
+cudaError_t launch_to_half(const float *w, __half *wh, size_t n, cudaStream_t s)
+{
+    to_half_kernel<<<grid_for(n), 256, 0, s>>>(w, wh, n);
+    return cudaGetLastError();
+}
+
+}  // namespace gbl

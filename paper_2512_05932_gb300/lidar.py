@@ -76,7 +76,14 @@ SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_simul
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
+# include/lidar_tail.h
+TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact", "lidar_simulate_split",
+                "lidar_tailnet_create", "lidar_tailnet_destroy", "lidar_tailnet_last_error", "lidar_tailnet_num_params",
+                "lidar_tailnet_get_params", "lidar_tailnet_set_params", "lidar_tailnet_predict",
+                "lidar_tailnet_train_step", "lidar_tailnet_grads", "lidar_tailnet_save", "lidar_tailnet_load",
+                "lidar_simulate_surrogate")
 KERNELS = ("setup", "footprint_wave")
+TAIL_INPUT_CELLS = 5440
 
 _lib = None
 
@@ -131,6 +138,43 @@ def load(path: str = LIB_PATH):
     lib.lidar_last_error.argtypes = [C.c_void_p]
     lib.lidar_destroy.restype = None
     lib.lidar_destroy.argtypes = [C.c_void_p]
+    lib.lidar_tail_configure.restype = C.c_int
+    lib.lidar_tail_configure.argtypes = [C.c_void_p, C.c_double, C.c_int32]
+    lib.lidar_tail_features.restype = C.c_int
+    lib.lidar_tail_features.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
+    lib.lidar_tail_exact.restype = C.c_int
+    lib.lidar_tail_exact.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p]
+    lib.lidar_simulate_split.restype = C.c_int
+    lib.lidar_simulate_split.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
+                                         P(lidar_echoes_t), P(C.c_int32), C.c_void_p]
+    lib.lidar_tailnet_create.restype = C.c_int
+    lib.lidar_tailnet_create.argtypes = [C.c_int32, C.c_uint64, P(C.c_void_p)]
+    lib.lidar_tailnet_destroy.restype = None
+    lib.lidar_tailnet_destroy.argtypes = [C.c_void_p]
+    lib.lidar_tailnet_last_error.restype = C.c_char_p
+    lib.lidar_tailnet_last_error.argtypes = [C.c_void_p]
+    lib.lidar_tailnet_num_params.restype = C.c_int64
+    lib.lidar_tailnet_num_params.argtypes = [C.c_void_p]
+    lib.lidar_tailnet_get_params.restype = C.c_int
+    lib.lidar_tailnet_get_params.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.lidar_tailnet_set_params.restype = C.c_int
+    lib.lidar_tailnet_set_params.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.lidar_tailnet_predict.restype = C.c_int
+    lib.lidar_tailnet_predict.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+    lib.lidar_tailnet_train_step.restype = C.c_int
+    lib.lidar_tailnet_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                             P(C.c_float), C.c_void_p]
+    lib.lidar_tailnet_grads.restype = C.c_int
+    lib.lidar_tailnet_grads.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                        P(C.c_float), C.c_void_p]
+    lib.lidar_tailnet_save.restype = C.c_int
+    lib.lidar_tailnet_save.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
+    lib.lidar_tailnet_load.restype = C.c_int
+    lib.lidar_tailnet_load.argtypes = [C.c_void_p, C.c_char_p]
+    lib.lidar_simulate_surrogate.restype = C.c_int
+    lib.lidar_simulate_surrogate.argtypes = [C.c_void_p, C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
+                                             P(lidar_echoes_t), P(C.c_int32), C.c_void_p]
     _lib = lib
     return lib
 
@@ -240,6 +284,110 @@ def lidar_simulate_noalloc(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t,
     e = lidar_echoes_t(out_echoes, out_counts)
     st = load().lidar_simulate_noalloc(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
     _check(st, handle)
+
+
+def lidar_tail_configure(handle, core_deg: float, n_coarse: int) -> None:
+    """Core/tail split of a radial profile (include/lidar_tail.h)."""
+    _check(load().lidar_tail_configure(handle, float(core_deg), int(n_coarse)), handle)
+
+
+def lidar_tail_features(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, rows: int, inputs: int = 0,
+                        stream: int = 0) -> None:
+    st = load().lidar_tail_features(handle, C.byref(gbuffer), C.byref(pose), rows, inputs or None, stream)
+    _check(st, handle)
+
+
+def lidar_tail_exact(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, rows: int, stream: int = 0) -> None:
+    _check(load().lidar_tail_exact(handle, C.byref(gbuffer), C.byref(pose), rows, stream), handle)
+
+
+def lidar_simulate_split(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, tail: int, out_waveforms: int,
+                         out_echoes: int, out_counts: int, stream: int = 0) -> int:
+    """Returns the number of beams re-run with the exact profile."""
+    e = lidar_echoes_t(out_echoes, out_counts)
+    n = C.c_int32(-1)
+    st = load().lidar_simulate_split(handle, C.byref(gbuffer), C.byref(pose), tail, out_waveforms, C.byref(e),
+                                     C.byref(n), stream)
+    _check(st, handle)
+    return n.value
+
+
+def lidar_simulate_surrogate(handle, net, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_waveforms: int,
+                             out_echoes: int, out_counts: int, stream: int = 0) -> int:
+    """Tail features, network prediction (net None: the physics prior) and the
+    split simulation; returns the number of beams re-run exactly."""
+    e = lidar_echoes_t(out_echoes, out_counts)
+    n = C.c_int32(-1)
+    st = load().lidar_simulate_surrogate(handle, net or None, C.byref(gbuffer), C.byref(pose), out_waveforms,
+                                         C.byref(e), C.byref(n), stream)
+    _check(st, handle)
+    return n.value
+
+
+class TailNet:
+    """The learned tail estimator (include/lidar_tail.h): thin wrapper over
+    the lidar_tailnet_* functions; device arrays are torch CUDA tensors."""
+
+    def __init__(self, n_coarse: int = 256, seed: int = 0):
+        lib = load()
+        h = C.c_void_p()
+        st = lib.lidar_tailnet_create(int(n_coarse), int(seed), C.byref(h))
+        if st != 0:
+            raise LidarError(st, lib.lidar_tailnet_last_error(None).decode())
+        self.handle = h.value
+        self.n_coarse = n_coarse
+
+    def _check(self, st):
+        if st != 0:
+            raise LidarError(st, load().lidar_tailnet_last_error(self.handle).decode())
+
+    @property
+    def num_params(self) -> int:
+        return int(load().lidar_tailnet_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.num_params, np.float32)
+        self._check(load().lidar_tailnet_get_params(self.handle, p.ctypes.data, p.size))
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, np.float32)
+        self._check(load().lidar_tailnet_set_params(self.handle, p.ctypes.data, p.size))
+
+    def predict(self, inputs, rows, out, stream: int = 0) -> None:
+        self._check(load().lidar_tailnet_predict(self.handle, inputs.data_ptr(), rows.data_ptr(), rows.shape[0],
+                                                 out.data_ptr(), stream))
+
+    def train_step(self, inputs, rows, target, lr: float, want_loss: bool = True, stream: int = 0):
+        loss = C.c_float(float("nan"))
+        self._check(load().lidar_tailnet_train_step(self.handle, inputs.data_ptr(), rows.data_ptr(), target.data_ptr(),
+                                                    rows.shape[0], float(lr), C.byref(loss) if want_loss else None,
+                                                    stream))
+        return loss.value if want_loss else None
+
+    def grads(self, inputs, rows, target, stream: int = 0):
+        g = np.zeros(self.num_params, np.float32)
+        loss = C.c_float(0.0)
+        self._check(load().lidar_tailnet_grads(self.handle, inputs.data_ptr(), rows.data_ptr(), target.data_ptr(),
+                                               rows.shape[0], g.ctypes.data, C.byref(loss), stream))
+        return float(loss.value), g
+
+    def save(self, path: str, with_state: bool = True) -> None:
+        self._check(load().lidar_tailnet_save(self.handle, os.fsencode(path), int(bool(with_state))))
+
+    def load(self, path: str) -> None:
+        self._check(load().lidar_tailnet_load(self.handle, os.fsencode(path)))
+
+    def close(self):
+        if self.handle:
+            load().lidar_tailnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def make_frames(items) -> "C.Array":

@@ -20,14 +20,20 @@ def lib():
     return lidar.load()
 
 
-def declared_functions():
-    txt = open(os.path.join(ROOT, "include", "lidar.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(lidar_[a-z_]+)\s*\(", txt)))
+def declared_functions(header=None):
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h") or (header and h != header):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(lidar_[a-z_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_header_declares_binding_symbols():
-    assert declared_functions() == sorted(lidar.SYMBOLS)
+    assert declared_functions("lidar.h") == sorted(lidar.SYMBOLS)
+    assert declared_functions("lidar_tail.h") == sorted(lidar.TAIL_SYMBOLS)
 
 
 def test_library_exports_every_declared_symbol(lib):
