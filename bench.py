@@ -54,6 +54,10 @@ def parse():
                          "frame; split: the wide frame with an exact core and an estimated tail "
                          "(lidar_tail_features + lidar_simulate_split)")
     ap.add_argument("--core-deg", type=float, default=0.3, help="exact core radius of --workload split")
+    ap.add_argument("--tail", default="prior", choices=["prior", "net"],
+                    help="tail estimate of --workload split: the physics prior or the learned network")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
+                    help="network weights of --tail net")
     return ap.parse_args()
 
 
@@ -368,14 +372,27 @@ def run_split(args, rank, world, local_rank):
     rows = torch.zeros((L.n_beams, nc + 4), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
+    net = None
+    if args.tail == "net":
+        net = lidar.TailNet(nc)
+        net.load(args.weights)
+        inputs = torch.empty((L.n_beams, lidar.TAIL_INPUT_CELLS, 2), dtype=torch.float16, device=dev)
+        pred = torch.zeros_like(rows)
 
     def step(evs=None):
+        # the stages of lidar_simulate_surrogate, called one by one to time them
         if evs:
             evs[0].record(stream)
-        lidar.lidar_tail_features(L.handle, g, pose, rows.data_ptr(), 0, s)
+        lidar.lidar_tail_features(L.handle, g, pose, rows.data_ptr(), inputs.data_ptr() if net else 0, s)
+        tail = rows
+        if net:
+            if evs:
+                evs[3].record(stream)
+            net.predict(inputs, rows, pred, s)
+            tail = pred
         if evs:
             evs[1].record(stream)
-        n = lidar.lidar_simulate_split(L.handle, g, pose, rows.data_ptr(), wave.data_ptr(), ech.data_ptr(),
+        n = lidar.lidar_simulate_split(L.handle, g, pose, tail.data_ptr(), wave.data_ptr(), ech.data_ptr(),
                                        cnt.data_ptr(), s)
         if evs:
             evs[2].record(stream)
@@ -388,15 +405,20 @@ def run_split(args, rank, world, local_rank):
         step()
         n_w += 1
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     nfb = []
     with clk:
         for i in range(args.steps):
             nfb.append(step(evs[i]))
         torch.cuda.synchronize(dev)
-    feat = [e[0].elapsed_time(e[1]) for e in evs]
+    if net:
+        feat = [e[0].elapsed_time(e[3]) for e in evs]
+        prd = [e[3].elapsed_time(e[1]) for e in evs]
+    else:
+        feat = [e[0].elapsed_time(e[1]) for e in evs]
+        prd = [0.0]
     spl = [e[1].elapsed_time(e[2]) for e in evs]
-    ms = (sum(feat) + sum(spl)) / args.steps
+    ms = (sum(feat) + sum(prd) + sum(spl)) / args.steps
     nbeams = len(w.dirs)
     peak, peak_kind = load_peaks()
     alg = algorithmic_bytes(w)
@@ -410,18 +432,25 @@ def run_split(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": world * nbeams / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(w, {"split": f"exact core {args.core_deg} deg, tail: physics prior on "
-                                                 f"{nc} coarse bins, exact re-run of beams failing the test",
+                "config": config_of(w, {"split": f"exact core {args.core_deg} deg, tail: "
+                                                 + ("learned network (FP16)" if net else "physics prior")
+                                                 + f" on {nc} coarse bins, exact re-run of beams failing the test",
                                         "l2": "inputs (0.94 GB) and waveforms (3.3 GB) exceed L2"}),
                 "roofline": {"bound": "hbm", "kernel": "split step (features + split simulation)",
                              "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None,
                              "algorithmic_bytes": alg},
-                "stage_ms": {"features": sum(feat) / args.steps, "split": sum(spl) / args.steps},
+                "stage_ms": {"features": sum(feat) / args.steps, "network": sum(prd) / max(1, len(prd)),
+                             "split": sum(spl) / args.steps},
                 "fallback_beams": int(np.median(nfb)), "cpu_baseline": cpu, "e2e": None,
-                "gpu_launches": int(args.steps * (7 + (4 if np.median(nfb) > 0 else 0))),
+                # features: setup + 4 cell-sum levels + prep; network: 11 per 8192-beam chunk;
+                # split: setup + footprint + compaction (+ setup + footprint of the re-run)
+                "gpu_launches": int(args.steps * (6 + (11 * -(-nbeams // 8192) if net else 0) + 3
+                                                  + (2 if np.median(nfb) > 0 else 0))),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+    if net:
+        net.close()
     L.close()
 
 

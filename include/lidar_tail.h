@@ -114,8 +114,8 @@ lidar_status_t lidar_simulate_split(lidar_t *l, const lidar_gbuffer_t *g, const 
  * ------------------------------------------------------------------------ */
 typedef struct lidar_tailnet lidar_tailnet_t;
 
-/* New network with He-uniform weights from `seed` (output layer x 0.1, so that
- * it starts close to the prior) and zero Adam state. n_coarse: a multiple of 8
+/* New network with He-uniform weights from `seed`, a zero output layer (the
+ * first prediction is the prior) and zero Adam state. n_coarse: a multiple of 8
  * in [8, 1024], equal to the sensor's. Errors: LIDAR_EINVAL, LIDAR_ENOMEM,
  * LIDAR_ECUDA. */
 lidar_status_t lidar_tailnet_create(int32_t n_coarse, uint64_t seed, lidar_tailnet_t **out);

@@ -405,4 +405,247 @@ cudaError_t launch_to_half(const float *w, __half *wh, size_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference of the three convolutions (persistent; one beam at a time
+// per CTA, 8 warps). Shared memory holds the FP16 conv weights (re-laid out
+// so that every 16-column k-step is aligned), the beam's input pyramid
+// (double-buffered with cp.async) and the activations: a1 and a2 split by
+// pixel parity into four sub-images with an 80-byte pixel pitch, so that the
+// stride-2 window rows of the next layer are contiguous and ldmatrix reads
+// them without bank conflicts. Writes the fully connected layer's input row
+// f = [a3, L3, prior / s] per beam.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kCP = 40;                        // activation pixel pitch (halves)
+constexpr int kW1P = 40, kW23P = 328;           // weight row pitches (halves)
+constexpr int kInHalves = 2 * 5440;             // one beam's input
+constexpr int kL1Off = 2 * 4096, kL2Off = kL1Off + 2 * 1024, kL3Off = kL2Off + 2 * 256;
+
+struct ConvSmem {
+    __half w1[32 * kW1P];
+    __half w2[32 * kW23P];
+    __half w3[32 * kW23P];
+    float bias[96];
+    __half x[2][kInHalves];
+    __half a1[4 * 256 * kCP];
+    __half a2[4 * 64 * kCP];
+    __half a3[64 * 32];
+    __half zero[16];
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// A fragment (rows g and g + 8 of a 16-row tile, k-step of 16) of the
+// 2-channel pyramid part of a convolution's K: column tap * 2 + c, taps
+// 0..7 in chunk 0 and tap 8 in chunk 1. lv: the level [S][S][2]; (oy, ox)
+// of the two rows; chunk 0 or 1.
+__device__ __forceinline__ void pyr_frag(uint32_t (&a)[4], const __half *lv, int S, int oy0, int ox0, int oy1,
+                                         int ox1, int chunk, int t)
+{
+    auto pair = [&](int oy, int ox, int tap) -> uint32_t {
+        const int iy = 2 * oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
+        if (tap > 8 || iy < 0 || iy >= S || ix < 0 || ix >= S) return 0u;
+        return *reinterpret_cast<const uint32_t *>(lv + 2 * (iy * S + ix));
+    };
+    if (chunk == 0) {
+        a[0] = pair(oy0, ox0, t); a[1] = pair(oy1, ox1, t);
+        a[2] = pair(oy0, ox0, t + 4); a[3] = pair(oy1, ox1, t + 4);
+    } else {
+        a[0] = pair(oy0, ox0, t == 0 ? 8 : 99); a[1] = pair(oy1, ox1, t == 0 ? 8 : 99);
+        a[2] = 0u; a[3] = 0u;
+    }
+}
+
+// Stores bias + ReLU of a 16 x 32 accumulator tile (rows g, g + 8) as FP16
+// pairs at dst(row) + channel.
+template <typename Dst>
+__device__ __forceinline__ void store_relu(const float (&acc)[4][4], const float *bias, int g, int t, Dst dst)
+{
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = ni * 8 + 2 * t;
+            const float v0 = fmaxf(acc[ni][2 * h] + bias[c], 0.f), v1 = fmaxf(acc[ni][2 * h + 1] + bias[c + 1], 0.f);
+            *reinterpret_cast<__half2 *>(dst(g + 8 * h) + c) = __floats2half2_rn(v0, v1);
+        }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ConvSmem &S = *reinterpret_cast<ConvSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3, q = lane >> 3, r8 = lane & 7;
+
+    // weights: conv1 as is (columns 0..31); conv2 / conv3 reordered to
+    // column tap * 32 + c for the 32 activation channels, then 288 + tap * 2 + c
+    for (int i = tid; i < 32 * 32; i += 256) S.w1[(i >> 5) * kW1P + (i & 31)] = A.w1[i];
+    for (int i = tid; i < 32 * 320; i += 256) {
+        const int n = i / 320, k = i - n * 320;
+        int src;
+        if (k < 288) src = (k >> 5) * 34 + (k & 31);
+        else if (k < 306) src = ((k - 288) >> 1) * 34 + 32 + ((k - 288) & 1);
+        else src = -1;
+        S.w2[n * kW23P + k] = src >= 0 ? A.w2[n * 320 + src] : __float2half(0.f);
+        S.w3[n * kW23P + k] = src >= 0 ? A.w3[n * 320 + src] : __float2half(0.f);
+    }
+    for (int i = tid; i < 96; i += 256) S.bias[i] = i < 32 ? A.b1[i] : (i < 64 ? A.b2[i - 32] : A.b3[i - 64]);
+    if (tid < 16) S.zero[tid] = __float2half(0.f);
+
+    auto prefetch = [&](int b, int buf) {
+        const __half *src = A.x + (size_t)b * kInHalves;
+        for (int i = tid; i < kInHalves / 8; i += 256) cp_async16(S.x[buf] + 8 * i, src + 8 * i);
+        cp_async_commit();
+    };
+    int buf = 0;
+    if ((int)blockIdx.x < A.n) prefetch(blockIdx.x, 0);
+
+    for (int b = blockIdx.x; b < A.n; b += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        if (b + (int)gridDim.x < A.n) prefetch(b + gridDim.x, buf ^ 1);
+        const __half *X = S.x[buf];
+
+        // ---- conv1: 64^2 x 2 -> 32^2 x 32; warp w takes m-tiles w, w + 8, ...
+        {
+            uint32_t bw[2][2][4];  // [k-step][n-pair]
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                for (int nj = 0; nj < 2; ++nj)
+                    ldsm_x4(bw[ks][nj], S.w1 + (nj * 16 + (q >> 1) * 8 + r8) * kW1P + ks * 16 + (q & 1) * 8);
+            for (int mt = warp; mt < 64; mt += 8) {
+                const int oy = mt >> 1, ox0 = (mt & 1) * 16;
+                float acc[4][4] = {};
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    uint32_t a[4];
+                    pyr_frag(a, X, 64, oy, ox0 + g, oy, ox0 + g + 8, ks, t);
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni)
+                        mma_f16(acc[ni], a, bw[ks][ni >> 1][(ni & 1) * 2], bw[ks][ni >> 1][(ni & 1) * 2 + 1]);
+                }
+                store_relu(acc, S.bias, g, t, [&](int row) {
+                    const int ox = ox0 + row;
+                    return S.a1 + (((oy & 1) * 2 + (ox & 1)) * 256 + (oy >> 1) * 16 + (ox >> 1)) * kCP;
+                });
+            }
+        }
+        __syncthreads();
+
+        // ---- conv2: [a1, L1] -> 16^2 x 32; warp w takes output rows w, w + 8
+        {
+            float acc[2][4][4] = {};
+            for (int ks = 0; ks < 20; ++ks) {
+                uint32_t bw[2][4];
+#pragma unroll
+                for (int nj = 0; nj < 2; ++nj)
+                    ldsm_x4(bw[nj], S.w2 + (nj * 16 + (q >> 1) * 8 + r8) * kW23P + ks * 16 + (q & 1) * 8);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    const int oy = warp + 8 * mi;
+                    uint32_t a[4];
+                    if (ks < 18) {
+                        const int tap = ks >> 1, c0 = (ks & 1) * 16;
+                        const int ky = tap / 3, kx = tap % 3;
+                        const int sy = ky == 0 ? oy - 1 : oy;
+                        const int ox = (q & 1) * 8 + r8;
+                        const int sx = kx == 0 ? ox - 1 : ox;
+                        const int sub = ((ky + 1) & 1) * 2 + ((kx + 1) & 1);
+                        const __half *p = (sy < 0 || sx < 0) ? S.zero
+                                                             : S.a1 + (sub * 256 + sy * 16 + sx) * kCP + c0 + (q >> 1) * 8;
+                        ldsm_x4(a, p);
+                    } else {
+                        pyr_frag(a, X + kL1Off, 32, oy, g, oy, g + 8, ks - 18, t);
+                    }
+#pragma unroll
+                    for (int ni = 0; ni < 4; ++ni)
+                        mma_f16(acc[mi][ni], a, bw[ni >> 1][(ni & 1) * 2], bw[ni >> 1][(ni & 1) * 2 + 1]);
+                }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int oy = warp + 8 * mi;
+                store_relu(acc[mi], S.bias + 32, g, t, [&](int ox) {
+                    return S.a2 + (((oy & 1) * 2 + (ox & 1)) * 64 + (oy >> 1) * 8 + (ox >> 1)) * kCP;
+                });
+            }
+        }
+        __syncthreads();
+
+        // ---- conv3: [a2, L2] -> 8^2 x 32; warp w: m-tile w / 2 (output rows
+        // 2 mt, 2 mt + 1), n-tiles 2 (w % 2) .. + 1
+        {
+            const int mt = warp >> 1, nh = warp & 1;
+            float acc[2][4] = {};
+            for (int ks = 0; ks < 20; ++ks) {
+                uint32_t bw[4];
+                ldsm_x4(bw, S.w3 + (nh * 16 + (q >> 1) * 8 + r8) * kW23P + ks * 16 + (q & 1) * 8);
+                uint32_t a[4];
+                if (ks < 18) {
+                    const int tap = ks >> 1, c0 = (ks & 1) * 16;
+                    const int ky = tap / 3, kx = tap % 3;
+                    const int oy = 2 * mt + (q & 1), ox = r8;
+                    const int sy = ky == 0 ? oy - 1 : oy, sx = kx == 0 ? ox - 1 : ox;
+                    const int sub = ((ky + 1) & 1) * 2 + ((kx + 1) & 1);
+                    const __half *p = (sy < 0 || sx < 0) ? S.zero
+                                                         : S.a2 + (sub * 64 + sy * 8 + sx) * kCP + c0 + (q >> 1) * 8;
+                    ldsm_x4(a, p);
+                } else {
+                    pyr_frag(a, X + kL2Off, 16, 2 * mt, g, 2 * mt + 1, g, ks - 18, t);
+                }
+#pragma unroll
+                for (int ni = 0; ni < 2; ++ni) mma_f16(acc[ni], a, bw[(ni & 1) * 2], bw[(ni & 1) * 2 + 1]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = nh * 16 + ni * 8 + 2 * t;
+                    const int pix = (2 * mt + h) * 8 + g;  // row g (+8) of the tile = (oy, ox = g)
+                    const float v0 = fmaxf(acc[ni][2 * h] + S.bias[64 + c], 0.f);
+                    const float v1 = fmaxf(acc[ni][2 * h + 1] + S.bias[64 + c + 1], 0.f);
+                    *reinterpret_cast<__half2 *>(S.a3 + pix * 32 + c) = __floats2half2_rn(v0, v1);
+                }
+        }
+        __syncthreads();
+
+        // ---- f = [a3, L3, prior / s]
+        {
+            __half *f = A.f + (size_t)b * A.F;
+            for (int i = tid; i < 2048 / 8; i += 256)
+                reinterpret_cast<uint4 *>(f)[i] = reinterpret_cast<const uint4 *>(S.a3)[i];
+            for (int i = tid; i < 128 / 8; i += 256)
+                reinterpret_cast<uint4 *>(f + 2048)[i] = reinterpret_cast<const uint4 *>(X + kL3Off)[i];
+            const float *row = A.rows + (size_t)b * (A.n_coarse + 4);
+            const float sc = net_scale(row, A.n_coarse);
+            for (int c = tid; c < A.n_coarse; c += 256) f[2176 + c] = __float2half_rn(sc > 0.f ? row[c] / sc : 0.f);
+        }
+        buf ^= 1;
+    }
+    cp_async_wait_all();
+}
+
+size_t conv_smem_bytes() { return sizeof(ConvSmem); }
+
+cudaError_t launch_conv(const ConvArgs &a, int grid, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(tailnet_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(ConvSmem));
+    if (e != cudaSuccess) return e;
+    tailnet_conv_kernel<<<grid, 256, sizeof(ConvSmem), s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace gbl

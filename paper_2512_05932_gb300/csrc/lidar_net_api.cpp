@@ -46,6 +46,11 @@ struct lidar_tailnet {
     __half *X1 = nullptr, *A1 = nullptr, *X2 = nullptr, *A2 = nullptr, *X3 = nullptr, *A3 = nullptr, *Fm = nullptr,
            *H = nullptr, *dD = nullptr, *dZh = nullptr, *dZ3 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *D = nullptr, *dH = nullptr, *dA3 = nullptr, *dX = nullptr;
+    // prediction scratch for `pcap` beams (fused convolutions)
+    int pcap = 0;
+    __half *pF = nullptr, *pH = nullptr;
+    float *pD = nullptr;
+    int sms = 0;
     char err[512] = "no error";
 };
 
@@ -64,6 +69,26 @@ lidar_status_t nfail(lidar_tailnet_t *n, lidar_status_t st, const char *fmt, ...
 lidar_status_t ncuda(lidar_tailnet_t *n, cudaError_t e, const char *what)
 {
     return nfail(n, e == cudaErrorMemoryAllocation ? LIDAR_ENOMEM : LIDAR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void free_pred(lidar_tailnet_t *n)
+{
+    cudaFree(n->pF); cudaFree(n->pH); cudaFree(n->pD);
+    n->pF = nullptr; n->pH = nullptr; n->pD = nullptr;
+    n->pcap = 0;
+}
+
+lidar_status_t ensure_pred(lidar_tailnet_t *n, int B)
+{
+    if (B <= n->pcap) return LIDAR_OK;
+    free_pred(n);
+    cudaError_t e;
+    if ((e = cudaMalloc(&n->pF, (size_t)B * n->F * sizeof(__half))) != cudaSuccess ||
+        (e = cudaMalloc(&n->pH, (size_t)B * 256 * sizeof(__half))) != cudaSuccess ||
+        (e = cudaMalloc(&n->pD, (size_t)B * n->nc * sizeof(float))) != cudaSuccess)
+        return ncuda(n, e, "cudaMalloc(prediction scratch)");
+    n->pcap = B;
+    return LIDAR_OK;
 }
 
 void free_scratch(lidar_tailnet_t *n)
@@ -271,8 +296,7 @@ lidar_status_t lidar_tailnet_create(int32_t n_coarse, uint64_t seed, lidar_tailn
     n->o_f1 = take((size_t)kHid * n->F); n->o_fb1 = take(kHid);
     n->o_f2 = take((size_t)n_coarse * kHid); n->o_fb2 = take(n_coarse);
     n->n_par = o;
-    // He-uniform initialisation of the real (unpadded) weights; the output
-    // layer starts small so that the first prediction is close to the prior
+    // He-uniform initialisation of the real (unpadded) weights
     std::vector<float> h(n->n_par, 0.f);
     Rng r{seed};
     auto init = [&](size_t off, int rows, int cols, int used, double fan_in, double gain) {
@@ -284,7 +308,7 @@ lidar_status_t lidar_tailnet_create(int32_t n_coarse, uint64_t seed, lidar_tailn
     init(n->o_w2, kC, kK2, 306, 306, 1.0);
     init(n->o_w3, kC, kK2, 306, 306, 1.0);
     init(n->o_f1, kHid, n->F, n->F, n->F, 1.0);
-    init(n->o_f2, n_coarse, kHid, kHid, kHid, 0.1);
+    // the output layer starts at zero: the first prediction is the prior
     cudaError_t e;
     if ((e = cudaMalloc(&n->w, n->n_par * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&n->m, n->n_par * sizeof(float))) != cudaSuccess ||
@@ -310,6 +334,7 @@ void lidar_tailnet_destroy(lidar_tailnet_t *n)
 {
     if (!n) return;
     free_scratch(n);
+    free_pred(n);
     cudaFree(n->w); cudaFree(n->m); cudaFree(n->v); cudaFree(n->g); cudaFree(n->wh);
     cudaFree(n->flag); cudaFree(n->loss);
     delete n;
@@ -344,18 +369,34 @@ lidar_status_t lidar_tailnet_predict(lidar_tailnet_t *n, const void *inputs, con
     if (!n) return nfail(nullptr, LIDAR_EINVAL, "network is NULL");
     if (!inputs || !rows || !tail_out || n_beams < 0) return nfail(n, LIDAR_EINVAL, "NULL argument or negative count");
     cudaStream_t s = (cudaStream_t)stream;
-    const int chunk = 8192;
-    lidar_status_t st = ensure_scratch(n, std::min<int>(chunk, std::max(1, n_beams)), false);
+    const int chunk = 65536;
+    lidar_status_t st = ensure_pred(n, std::min<int>(chunk, std::max(1, n_beams)));
     if (st != LIDAR_OK) return st;
+    if (!n->sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     const int rs = n->nc + 4;
+    const __half *wh = n->wh;
+    const float *w = n->w;
     for (int b0 = 0; b0 < n_beams; b0 += chunk) {
         const int B = std::min(chunk, n_beams - b0);
         const __half *x = static_cast<const __half *>(inputs) + (size_t)b0 * kIn;
         const float *r = rows + (size_t)b0 * rs;
         float *o = tail_out + (size_t)b0 * rs;
-        if ((st = forward(n, x, r, B, s)) != LIDAR_OK) return st;
-        // raw predictions s * y_hat into the rows, then clip and copy the bounds
-        gbl::HeadArgs hb{B, n->nc, rs, r, nullptr, n->D, o, nullptr, nullptr, 0.f};
+        // convolutions fused per beam -> f; then the two fully connected layers
+        gbl::ConvArgs ca{B, x, r, n->nc, n->F, wh + n->o_w1, wh + n->o_w2, wh + n->o_w3, w + n->o_b1, w + n->o_b2,
+                         w + n->o_b3, n->pF};
+        NCK(gbl::launch_conv(ca, std::min(B, n->sms), s), "fused convolutions");
+        NCK(gbl::launch_gemm(false, false,
+                             gemm(B, kHid, n->F, n->pF, n->F, wh + n->o_f1, n->F, gbl::kGemmBiasRelu, nullptr, n->pH,
+                                  kHid, w + n->o_fb1), 1, s), "fc1");
+        NCK(gbl::launch_gemm(false, false,
+                             gemm(B, n->nc, kHid, n->pH, kHid, wh + n->o_f2, kHid, gbl::kGemmBias, n->pD, nullptr,
+                                  n->nc, w + n->o_fb2), 1, s), "fc2");
+        // s * y_hat into the rows, then clip to the bound and copy the bounds
+        gbl::HeadArgs hb{B, n->nc, rs, r, nullptr, n->pD, o, nullptr, nullptr, 0.f};
         NCK(gbl::launch_head(hb, s), "head");
         NCK(gbl::launch_finish_rows(r, o, B, n->nc, s), "finish rows");
     }

@@ -67,6 +67,16 @@ struct AdamArgs {
     const int *skip;
 };
 
+struct ConvArgs {
+    int n;                          // beams
+    const __half *x;                // [n][5440][2]
+    const float *rows;              // [n][n_coarse + 4]
+    int n_coarse, F;
+    const __half *w1, *w2, *w3;     // conv weights [32][32], [32][320], [32][320] (parameter layout)
+    const float *b1, *b2, *b3;
+    __half *f;                      // [n][F]: fully connected input rows
+};
+
 // Per-beam scale of the network's input and output: the prior's mass, at
 // least a tenth of the tail bound (0: no tail).
 __host__ __device__ inline float net_scale(const float *row, int n_coarse)
@@ -86,5 +96,7 @@ cudaError_t launch_bias_grad(const __half *dz, int M, int N, float *db, cudaStre
 cudaError_t launch_adam(const AdamArgs &a, cudaStream_t s);
 cudaError_t launch_finite_check(const float *g, size_t n, int *flag, cudaStream_t s);
 cudaError_t launch_to_half(const float *w, __half *wh, size_t n, cudaStream_t s);
+size_t conv_smem_bytes();
+cudaError_t launch_conv(const ConvArgs &a, int grid, cudaStream_t s);
 
 }  // namespace gbl
