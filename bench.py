@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--core-deg", type=float, default=0.3, help="exact core radius of --workload split")
     ap.add_argument("--tail", default="prior", choices=["prior", "net"],
                     help="tail estimate of --workload split: the physics prior or the learned network")
+    ap.add_argument("--size", default="full", choices=["full", "small"],
+                    help="small: a 2048x1024 frame of the wide-tail scene with 100x80 beams (for profiler captures)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
                     help="network weights of --tail net")
     return ap.parse_args()
@@ -65,8 +67,14 @@ WORKLOAD = "frame"
 DEPOSIT = {"atomic": 0, "tc_split": 1, "tc_bf16": 2}
 
 
+SIZE = "full"
+CONV_FLOPS_PER_BEAM = 2 * (1024 * 32 * 18 + 256 * 32 * 306 + 64 * 32 * 306)  # three convolutions
+
+
 def workload():
     from paper_2512_05932_gb300 import scenes
+    if WORKLOAD == "split" and SIZE == "small":
+        return scenes.wide_frame(U=2048, V=1024, n_az=100, n_el=80)
     if WORKLOAD in ("wide", "split"):
         return scenes.wide_frame()
     return scenes.full_frame_boxes()
@@ -177,6 +185,15 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def load_tensor_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    return 1700.0, "fallback"
+
+
 def traffic_for_current_kernel(workload_name):
     """dram bytes per launch of the footprint kernel from the committed ncu
     summary, or None if absent, taken on another workload or on a different
@@ -190,6 +207,18 @@ def traffic_for_current_kernel(workload_name):
     if d.get("kernel_sha256") != sha or not d.get("workload", "").startswith(workload_name):
         return None
     return d.get("bytes_per_launch")
+
+
+def job_rate(local_ms, units_per_rank, steps, world, dist=None, device=None):
+    """Whole-job rate over ranks that each process units_per_rank per step
+    (weak scaling, independent frames): all ranks' units over the slowest
+    rank's time. Returns (units/s, ms per step of the slowest rank)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item()) / steps
+    return world * units_per_rank / (ms * 1e-3), ms
 
 
 # --------------------------------------------------------------------------
@@ -278,12 +307,8 @@ def run_gb300(args, rank, world, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kern = lidar.lidar_profile_read(L.handle)
     lidar.lidar_profile_enable(L.handle, False)
-    t_total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_total, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t_total.item()) / args.steps
     nbeams = len(w.dirs)
-    value = world * nbeams / (ms_per_step * 1e-3)
+    value, ms_per_step = job_rate(sum(step_ms), nbeams, args.steps, world, dist, dev)
 
     # ---- end to end through the host-memory entry point ----
     host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
@@ -407,10 +432,13 @@ def run_split(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     nfb = []
+    if net:
+        net.profile_enable(True)
     with clk:
         for i in range(args.steps):
             nfb.append(step(evs[i]))
         torch.cuda.synchronize(dev)
+    conv = net.profile_read()["conv"] if net else None
     if net:
         feat = [e[0].elapsed_time(e[3]) for e in evs]
         prd = [e[3].elapsed_time(e[1]) for e in evs]
@@ -423,6 +451,20 @@ def run_split(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     alg = algorithmic_bytes(w)
     achieved = alg / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "split step (features + split simulation)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+            "traffic": None, "algorithmic_bytes": alg}
+    if conv and conv[1] > 0:
+        # the fused convolution kernel against the dense FP16 tensor peak (FP16 and BF16 have the same
+        # nominal dense rate; the kernel is timed inside a long step, so the sustained figure)
+        tpk, tkind = load_tensor_peak()
+        flops = CONV_FLOPS_PER_BEAM * nbeams * args.steps / conv[1]
+        conv_ms = conv[0] / conv[1]
+        ach = flops / (conv_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "tailnet_conv_kernel (fused convolutions, FP16 mma.sync)",
+                "achieved": ach, "peak": tpk, "unit": "TFLOP/s", "frac": ach / tpk,
+                "peak_source": f"{tkind} bf16_tflops_sustained (FP16 at the same nominal rate)", "traffic": None,
+                "algorithmic_flops": flops, "avg_launch_ms": conv_ms, "launches_per_step": conv[1] / args.steps}
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         rate, dt, _ = oracle_rate(w, 96, cpu_cores())
@@ -436,10 +478,7 @@ def run_split(args, rank, world, local_rank):
                                                  + ("learned network (FP16)" if net else "physics prior")
                                                  + f" on {nc} coarse bins, exact re-run of beams failing the test",
                                         "l2": "inputs (0.94 GB) and waveforms (3.3 GB) exceed L2"}),
-                "roofline": {"bound": "hbm", "kernel": "split step (features + split simulation)",
-                             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None,
-                             "algorithmic_bytes": alg},
+                "roofline": roof,
                 "stage_ms": {"features": sum(feat) / args.steps, "network": sum(prd) / max(1, len(prd)),
                              "split": sum(spl) / args.steps},
                 "fallback_beams": int(np.median(nfb)), "cpu_baseline": cpu, "e2e": None,
@@ -532,9 +571,10 @@ def run_batch(args, rank, world, local_rank):
 
 
 def main():
-    global WORKLOAD
+    global WORKLOAD, SIZE
     args = parse()
     WORKLOAD = args.workload
+    SIZE = args.size
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

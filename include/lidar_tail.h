@@ -132,8 +132,8 @@ lidar_status_t lidar_tailnet_set_params(lidar_tailnet_t *net, const float *host,
  * ([n][n_coarse + 4]) out: s y clipped to total <= E, the ambient entry and
  * bounds copied from rows, the total in [n_coarse + 3] (the layout
  * lidar_simulate_split takes). Device pointers; asynchronous on `stream`;
- * internal scratch of about 3.4 GB for 8192-beam chunks is allocated on first
- * use. */
+ * internal scratch of about 400 MB for 65536-beam chunks is allocated on first
+ * use. The three convolutions run fused per beam (one launch per chunk). */
 lidar_status_t lidar_tailnet_predict(lidar_tailnet_t *net, const void *inputs, const float *rows, int32_t n_beams,
                                      float *tail_out, void *stream);
 
@@ -156,6 +156,15 @@ lidar_status_t lidar_tailnet_save(const lidar_tailnet_t *net, const char *path, 
 /* Loads a file written by lidar_tailnet_save (a file without state resets
  * the Adam state). Errors: LIDAR_EINVAL (missing, truncated, other shape). */
 lidar_status_t lidar_tailnet_load(lidar_tailnet_t *net, const char *path);
+
+/* Per-stage timing of lidar_tailnet_predict: while enabled, CUDA events are
+ * recorded on the call's stream around the fused convolution launch and
+ * around the dense layers (two GEMMs, output and clipping) of every chunk of
+ * up to 65536 beams. _read synchronises on the last event and returns the
+ * totals (ms) and counts [convolutions, dense layers] since the last read.
+ * Enabling or disabling drops unread records. */
+lidar_status_t lidar_tailnet_profile_enable(lidar_tailnet_t *net, int32_t enable);
+lidar_status_t lidar_tailnet_profile_read(lidar_tailnet_t *net, double total_ms[2], int32_t launches[2]);
 
 /* One frame through the surrogate: lidar_tail_features, lidar_tailnet_predict
  * (or the physics prior when net is NULL) and lidar_simulate_split. Per-beam

@@ -51,6 +51,11 @@ struct lidar_tailnet {
     __half *pF = nullptr, *pH = nullptr;
     float *pD = nullptr;
     int sms = 0;
+    // per-stage timing of predict (lidar_tailnet_profile_enable): events around
+    // the fused convolutions and the dense layers of each chunk
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
     char err[512] = "no error";
 };
 
@@ -69,6 +74,24 @@ lidar_status_t nfail(lidar_tailnet_t *n, lidar_status_t st, const char *fmt, ...
 lidar_status_t ncuda(lidar_tailnet_t *n, cudaError_t e, const char *what)
 {
     return nfail(n, e == cudaErrorMemoryAllocation ? LIDAR_ENOMEM : LIDAR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaEvent_t next_event(lidar_tailnet_t *n)
+{
+    if (!n->prof) return nullptr;
+    if (n->ev_used == n->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        n->ev.push_back(e);
+    }
+    return n->ev[n->ev_used++];
+}
+
+void free_events(lidar_tailnet_t *n)
+{
+    for (cudaEvent_t e : n->ev) cudaEventDestroy(e);
+    n->ev.clear();
+    n->ev_used = 0;
 }
 
 void free_pred(lidar_tailnet_t *n)
@@ -335,6 +358,7 @@ void lidar_tailnet_destroy(lidar_tailnet_t *n)
     if (!n) return;
     free_scratch(n);
     free_pred(n);
+    free_events(n);
     cudaFree(n->w); cudaFree(n->m); cudaFree(n->v); cudaFree(n->g); cudaFree(n->wh);
     cudaFree(n->flag); cudaFree(n->loss);
     delete n;
@@ -388,7 +412,15 @@ lidar_status_t lidar_tailnet_predict(lidar_tailnet_t *n, const void *inputs, con
         // convolutions fused per beam -> f; then the two fully connected layers
         gbl::ConvArgs ca{B, x, r, n->nc, n->F, wh + n->o_w1, wh + n->o_w2, wh + n->o_w3, w + n->o_b1, w + n->o_b2,
                          w + n->o_b3, n->pF};
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (n->prof) {
+            const size_t mark = n->ev_used;
+            e0 = next_event(n); e1 = next_event(n); e2 = next_event(n);
+            if (!e0 || !e1 || !e2) { n->ev_used = mark; e0 = e1 = e2 = nullptr; }
+        }
+        if (e0) cudaEventRecord(e0, s);
         NCK(gbl::launch_conv(ca, std::min(B, n->sms), s), "fused convolutions");
+        if (e1) cudaEventRecord(e1, s);
         NCK(gbl::launch_gemm(false, false,
                              gemm(B, kHid, n->F, n->pF, n->F, wh + n->o_f1, n->F, gbl::kGemmBiasRelu, nullptr, n->pH,
                                   kHid, w + n->o_fb1), 1, s), "fc1");
@@ -399,6 +431,7 @@ lidar_status_t lidar_tailnet_predict(lidar_tailnet_t *n, const void *inputs, con
         gbl::HeadArgs hb{B, n->nc, rs, r, nullptr, n->pD, o, nullptr, nullptr, 0.f};
         NCK(gbl::launch_head(hb, s), "head");
         NCK(gbl::launch_finish_rows(r, o, B, n->nc, s), "finish rows");
+        if (e2) cudaEventRecord(e2, s);
     }
     return LIDAR_OK;
 }
@@ -506,6 +539,32 @@ lidar_status_t lidar_tailnet_load(lidar_tailnet_t *n, const char *path)
     }
     NCK(gbl::launch_to_half(n->w, n->wh, n->n_par, 0), "to half");
     NCK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_tailnet_profile_enable(lidar_tailnet_t *n, int32_t enable)
+{
+    if (!n) return nfail(nullptr, LIDAR_EINVAL, "network is NULL");
+    free_events(n);
+    n->prof = enable != 0;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_tailnet_profile_read(lidar_tailnet_t *n, double total_ms[2], int32_t launches[2])
+{
+    if (!n) return nfail(nullptr, LIDAR_EINVAL, "network is NULL");
+    double t[2] = {0, 0};
+    int32_t c[2] = {0, 0};
+    for (size_t i = 0; i + 3 <= n->ev_used; i += 3) {
+        NCK(cudaEventSynchronize(n->ev[i + 2]), "cudaEventSynchronize");
+        float a = 0, b = 0;
+        NCK(cudaEventElapsedTime(&a, n->ev[i], n->ev[i + 1]), "cudaEventElapsedTime");
+        NCK(cudaEventElapsedTime(&b, n->ev[i + 1], n->ev[i + 2]), "cudaEventElapsedTime");
+        t[0] += a; t[1] += b; c[0] += 1; c[1] += 1;
+    }
+    n->ev_used = 0;
+    if (total_ms) { total_ms[0] = t[0]; total_ms[1] = t[1]; }
+    if (launches) { launches[0] = c[0]; launches[1] = c[1]; }
     return LIDAR_OK;
 }
 

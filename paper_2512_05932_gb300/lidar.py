@@ -81,7 +81,7 @@ TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact
                 "lidar_tailnet_create", "lidar_tailnet_destroy", "lidar_tailnet_last_error", "lidar_tailnet_num_params",
                 "lidar_tailnet_get_params", "lidar_tailnet_set_params", "lidar_tailnet_predict",
                 "lidar_tailnet_train_step", "lidar_tailnet_grads", "lidar_tailnet_save", "lidar_tailnet_load",
-                "lidar_simulate_surrogate")
+                "lidar_simulate_surrogate", "lidar_tailnet_profile_enable", "lidar_tailnet_profile_read")
 KERNELS = ("setup", "footprint_wave")
 TAIL_INPUT_CELLS = 5440
 
@@ -172,6 +172,10 @@ def load(path: str = LIB_PATH):
     lib.lidar_tailnet_save.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
     lib.lidar_tailnet_load.restype = C.c_int
     lib.lidar_tailnet_load.argtypes = [C.c_void_p, C.c_char_p]
+    lib.lidar_tailnet_profile_enable.restype = C.c_int
+    lib.lidar_tailnet_profile_enable.argtypes = [C.c_void_p, C.c_int32]
+    lib.lidar_tailnet_profile_read.restype = C.c_int
+    lib.lidar_tailnet_profile_read.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32)]
     lib.lidar_simulate_surrogate.restype = C.c_int
     lib.lidar_simulate_surrogate.argtypes = [C.c_void_p, C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                              P(lidar_echoes_t), P(C.c_int32), C.c_void_p]
@@ -371,6 +375,15 @@ class TailNet:
         self._check(load().lidar_tailnet_grads(self.handle, inputs.data_ptr(), rows.data_ptr(), target.data_ptr(),
                                                rows.shape[0], g.ctypes.data, C.byref(loss), stream))
         return float(loss.value), g
+
+    def profile_enable(self, enable: bool) -> None:
+        self._check(load().lidar_tailnet_profile_enable(self.handle, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        t = (C.c_double * 2)()
+        n = (C.c_int32 * 2)()
+        self._check(load().lidar_tailnet_profile_read(self.handle, t, n))
+        return {"conv": (t[0], n[0]), "dense": (t[1], n[1])}
 
     def save(self, path: str, with_state: bool = True) -> None:
         self._check(load().lidar_tailnet_save(self.handle, os.fsencode(path), int(bool(with_state))))
