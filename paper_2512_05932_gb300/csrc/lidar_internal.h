@@ -87,7 +87,8 @@ struct FootprintArgs {
     //                  [n_coarse + 2] bound on the ambient estimate's error
     const float *tail_in;    // coarse tail of core-only beams (convolved with tail_box); NULL: none
     const float *tail_box;   // pulse averaged over cf fine bins, B(x) at index x + tb_off,
-                             // x in [-M - 7, M + cf + 6] (zero outside [-M, M + cf - 1])
+                             // x in [-M - 7, M + cf + 6] (zero outside [-M, M + cf - 1]);
+                             // 16-byte aligned base, tb_off a multiple of 4
     int tb_off;
     float *coarse_out;       // coarse histogram and ambient sum of every beam; NULL: none
     int n_coarse, tail_stride;

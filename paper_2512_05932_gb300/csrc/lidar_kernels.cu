@@ -1001,11 +1001,24 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             // first coarse bin reaching output kb: ceil((kb - M - cf + 1) / cf) = floor((kb - M) / cf)
             const int c0 = max(tlo, (kb - M + cf * (M + 1)) / cf - (M + 1));
             const int c1 = min(thi, (kb + 7 + M) / cf);
-            for (int c = c0; c <= c1; ++c) {
-                const float t = __ldg(Tr + c);
-                const float *bx = A.tail_box + A.tb_off + kb - c * cf;
+            if ((cf & 3) == 0) {
+                // kb, c * cf and tb_off are multiples of 4: two 16-byte loads of B per coarse bin
+                for (int c = c0; c <= c1; ++c) {
+                    const float t = __ldg(Tr + c);
+                    const float4 *bx = reinterpret_cast<const float4 *>(A.tail_box + A.tb_off + kb - c * cf);
+                    const float4 u = __ldg(bx), w = __ldg(bx + 1);
+                    acc[0] = fmaf(t, u.x, acc[0]); acc[1] = fmaf(t, u.y, acc[1]);
+                    acc[2] = fmaf(t, u.z, acc[2]); acc[3] = fmaf(t, u.w, acc[3]);
+                    acc[4] = fmaf(t, w.x, acc[4]); acc[5] = fmaf(t, w.y, acc[5]);
+                    acc[6] = fmaf(t, w.z, acc[6]); acc[7] = fmaf(t, w.w, acc[7]);
+                }
+            } else {
+                for (int c = c0; c <= c1; ++c) {
+                    const float t = __ldg(Tr + c);
+                    const float *bx = A.tail_box + A.tb_off + kb - c * cf;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, __ldg(bx + r), acc[r]);
+                    for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, __ldg(bx + r), acc[r]);
+                }
             }
         }
         if (o0 + 8 * lane < nb) {

@@ -242,36 +242,11 @@ struct PrepAcc {
     float eub, ahi, alo, aest;
 };
 
-// One leaf cell of the quadtree: bounds, ambient estimate and prior.
-__device__ __forceinline__ void prep_leaf(const PrepArgs &A, const BeamParam &P, int lvl, int cxw, const CellGeom &g,
-                                          float *hc, PrepAcc &acc)
+// Estimate part of a leaf: the cell's ambient and mass times the mean profile
+// pm over its pixels, the mass spread over the cell's range interval.
+__device__ __forceinline__ void prep_estimate(const PrepArgs &A, int lvl, size_t ci, const float4 &s, float pm,
+                                              float *hc, PrepAcc &acc)
 {
-    const size_t ci = (size_t)(g.v0 >> (2 + lvl)) * A.ncx[lvl] + cxw;
-    const float4 s = A.s[lvl][ci];
-    if (!(s.x > 0.f) && !(s.z > 0.f)) return;
-    const float tmin = fmaxf(0.f, g.th * (1.f - g.rel) - g.rho), tmax = g.th * (1.f + g.rel) + g.rho;
-    if (!(tmax * (1.f + 1e-5f) > A.core) || !(tmin <= A.trunc * (1.f + 1e-5f))) return;
-    const float tb = fmaxf(tmin, A.core * (1.f - 1e-5f));
-    const float pmax = tail_profile(A, tb * tb) * (1.f + 1e-4f);
-    acc.eub += s.x * pmax;
-    acc.ahi += s.z * pmax;
-    if (tmin > A.core * (1.f + 1e-5f) && tmax < A.trunc * (1.f - 1e-5f)) acc.alo += s.z * tail_profile(A, tmax * tmax) * (1.f - 1e-4f);
-    // estimate: the cell's mass spread evenly over its pixels; in cells that
-    // cross the core or truncation radius the profile is taken at every pixel
-    // (zero outside the annulus), elsewhere at the cell centre
-    float pm;
-    if (lvl == 0 && (tmin < A.core || tmax > A.trunc)) {
-        float acc_p = 0.f;
-        for (int dy = 0; dy < g.nv; ++dy)
-            for (int dx = 0; dx < g.nu; ++dx) {
-                float r_;
-                const float th = ang_dist(A, P, (float)(g.u0 + dx), (float)(g.v0 + dy), &r_);
-                if (th > A.core) acc_p += tail_profile(A, th * th);
-            }
-        pm = acc_p / (float)(g.nu * g.nv);
-    } else {
-        pm = (g.th > A.core) ? tail_profile(A, g.th * g.th) : 0.f;
-    }
     if (!(pm > 0.f)) return;
     acc.aest += s.z * pm;
     if (s.x > 0.f) {
@@ -280,6 +255,53 @@ __device__ __forceinline__ void prep_leaf(const PrepArgs &A, const BeamParam &P,
         const float b = fmaf(r.y, A.x_scale, A.x_off + 0.5f) * A.inv_cf;
         spread(hc, A.n_coarse, a, b, s.x * pm);
     }
+}
+
+__device__ __forceinline__ size_t cell_index(const PrepArgs &A, int lvl, int cxw, const CellGeom &g)
+{
+    return (size_t)(g.v0 >> (2 + lvl)) * A.ncx[lvl] + cxw;
+}
+
+// Mean of the annulus profile over the pixel centres of a cell (one thread).
+__device__ __forceinline__ float pixel_mean_profile(const PrepArgs &A, const BeamParam &P, const CellGeom &g)
+{
+    float acc_p = 0.f;
+    for (int dy = 0; dy < g.nv; ++dy)
+        for (int dx = 0; dx < g.nu; ++dx) {
+            float r_;
+            const float th = ang_dist(A, P, (float)(g.u0 + dx), (float)(g.v0 + dy), &r_);
+            if (th > A.core) acc_p += tail_profile(A, th * th);
+        }
+    return acc_p / (float)(g.nu * g.nv);
+}
+
+// One leaf cell of the quadtree: bounds, ambient estimate and prior. The
+// estimate takes the profile at the cell centre, except in 4-pixel cells that
+// cross the core or truncation radius, where it is the mean over the cell's
+// pixels (zero outside the annulus): with defer, such a cell returns true and
+// its estimate is left to the caller (evaluated pixel-parallel by the warp).
+__device__ __forceinline__ bool prep_leaf(const PrepArgs &A, const BeamParam &P, int lvl, int cxw, const CellGeom &g,
+                                          float *hc, PrepAcc &acc, bool defer)
+{
+    const size_t ci = cell_index(A, lvl, cxw, g);
+    const float4 s = A.s[lvl][ci];
+    if (!(s.x > 0.f) && !(s.z > 0.f)) return false;
+    const float tmin = fmaxf(0.f, g.th * (1.f - g.rel) - g.rho), tmax = g.th * (1.f + g.rel) + g.rho;
+    if (!(tmax * (1.f + 1e-5f) > A.core) || !(tmin <= A.trunc * (1.f + 1e-5f))) return false;
+    const float tb = fmaxf(tmin, A.core * (1.f - 1e-5f));
+    const float pmax = tail_profile(A, tb * tb) * (1.f + 1e-4f);
+    acc.eub += s.x * pmax;
+    acc.ahi += s.z * pmax;
+    if (tmin > A.core * (1.f + 1e-5f) && tmax < A.trunc * (1.f - 1e-5f)) acc.alo += s.z * tail_profile(A, tmax * tmax) * (1.f - 1e-4f);
+    float pm;
+    if (lvl == 0 && (tmin < A.core || tmax > A.trunc)) {
+        if (defer) return true;
+        pm = pixel_mean_profile(A, P, g);
+    } else {
+        pm = (g.th > A.core) ? tail_profile(A, g.th * g.th) : 0.f;
+    }
+    prep_estimate(A, lvl, ci, s, pm, hc, acc);
+    return false;
 }
 
 __global__ void __launch_bounds__(kPrepThreads) tail_prep_kernel(PrepArgs A)
@@ -324,7 +346,7 @@ __global__ void __launch_bounds__(kPrepThreads) tail_prep_kernel(PrepArgs A)
                 continue;
             }
         }
-        prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc);
+        prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc, false);
     }
     __syncwarp();
     const int n3 = min(n3s[warp], kPrepList);
@@ -343,16 +365,55 @@ __global__ void __launch_bounds__(kPrepThreads) tail_prep_kernel(PrepArgs A)
                 continue;
             }
         }
-        prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc);
+        prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc, false);
     }
     __syncwarp();
     const int n2 = min(n2s[warp], kPrepList);
+    // 4-pixel cells; those crossing the core or truncation radius are listed
+    // (in l3, free now) and their pixel-level estimate done below
+    if (lane == 0) n3s[warp] = 0;
+    __syncwarp();
     for (int i = lane; i < n2; i += 32) {
         const int lvl = 0;
         const int cy = l2[i] >> 16, cx = (int)(short)(l2[i] & 0xFFFF);
         CellGeom g;
         if (!cell_geom(A, P, lvl, cx, cy, g)) continue;
-        prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc);
+        if (prep_leaf(A, P, lvl, wrap_cell(A, lvl, cx), g, hc, acc, true)) {
+            const int k = atomicAdd(n3s + warp, 1);
+            if (k < kPrepList) {
+                l3[k] = l2[i];
+            } else {
+                const size_t ci = cell_index(A, lvl, wrap_cell(A, lvl, cx), g);
+                prep_estimate(A, lvl, ci, A.s[lvl][ci], pixel_mean_profile(A, P, g), hc, acc);
+            }
+        }
+    }
+    __syncwarp();
+    // pixel-level estimate of the listed cells: half-warp per cell, one lane per pixel
+    const int ns = min(n3s[warp], kPrepList);
+    for (int base = 0; base < 16 * ns; base += 32) {
+        const int i = base + lane, cell = i >> 4, pix = i & 15;
+        float p = 0.f;
+        CellGeom g;
+        int cx = 0;
+        bool ok = false;
+        if (cell < ns) {
+            const int cy = l3[cell] >> 16;
+            cx = (int)(short)(l3[cell] & 0xFFFF);
+            ok = cell_geom(A, P, 0, cx, cy, g);
+            if (ok && (pix & 3) < g.nu && (pix >> 2) < g.nv) {
+                float r_;
+                const float th = ang_dist(A, P, (float)(g.u0 + (pix & 3)), (float)(g.v0 + (pix >> 2)), &r_);
+                if (th > A.core) p = tail_profile(A, th * th);
+            }
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (ok && pix == 0) {
+            const int cxw = wrap_cell(A, 0, cx);
+            const size_t ci = cell_index(A, 0, cxw, g);
+            prep_estimate(A, 0, ci, A.s[0][ci], p / (float)(g.nu * g.nv), hc, acc);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

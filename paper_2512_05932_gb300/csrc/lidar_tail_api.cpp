@@ -27,6 +27,8 @@ struct TailState {
     BeamParam *d_fb_beams = nullptr;
     float *d_box = nullptr;         // pulse averaged over the fine bins of a coarse bin (FootprintArgs::tail_box)
     int box_off = 0;
+    int G_fb = 2;                   // beams per CTA of the exact re-run: small groups, since the re-run
+    size_t smem_fb = 0;             // beams are scattered (large union boxes for large groups)
     float4 *mip_s[kMipLevels] = {};
     float2 *mip_r[kMipLevels] = {};
     size_t mip_cap[kMipLevels] = {};
@@ -118,9 +120,11 @@ gbl::FootprintArgs frame_args(lidar_t *l, const lidar_gbuffer_t *g)
     return fa;
 }
 
-lidar_status_t launch_fp(lidar_t *l, const gbl::FootprintArgs &fa, cudaStream_t s)
+lidar_status_t launch_fp(lidar_t *l, const gbl::FootprintArgs &fa, cudaStream_t s, bool rerun = false)
 {
-    cudaError_t e = gbl::launch_footprint(l->kind, l->G, false, l->threads, l->smem, fa, s);
+    const int G = rerun ? l->tail->G_fb : l->G;
+    const size_t smem = rerun ? l->tail->smem_fb : l->smem;
+    cudaError_t e = gbl::launch_footprint(l->kind, G, false, l->threads, smem, fa, s);
     if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     return LIDAR_OK;
 }
@@ -163,12 +167,17 @@ lidar_status_t lidar_tail_configure(lidar_t *l, double core_deg, int32_t n_coars
     t->d1 = (float)(d1 * up); t->d2 = (float)(d2 * up); t->dd = (float)(dd * up);
     // B(x) = (1/cf) sum_{j < cf} p(x - j), x in [-M - 7, M + cf + 6]
     const int cf = l->n_bins / n_coarse;
-    t->box_off = M + 7;
-    std::vector<float> box(2 * M + cf + 14, 0.f);
+    t->box_off = (M + 7 + 3) & ~3;  // multiple of 4: aligned 16-byte loads in the kernel
+    std::vector<float> box(((t->box_off + M + cf + 7) + 3) & ~3, 0.f);
     for (int x = -M - 7; x <= M + cf + 6; ++x) {
         double acc = 0;
         for (int j = 0; j < cf; ++j) acc += p(x - j);
         box[x + t->box_off] = (float)(acc / cf);
+    }
+    t->smem_fb = gbl::footprint_smem_bytes(t->G_fb, model_args(l));
+    if ((e = gbl::prepare_footprint(l->kind, t->G_fb, false, t->smem_fb)) != cudaSuccess) {
+        tail_free(l);
+        return cuda_fail(l, e, "cudaFuncSetAttribute");
     }
     std::vector<uint8_t> ones(l->n_beams, 1);
     if ((e = cudaMalloc(&t->d_core, l->n_beams)) != cudaSuccess ||
@@ -327,7 +336,7 @@ lidar_status_t lidar_simulate_split(lidar_t *l, const lidar_gbuffer_t *g, const 
     fb.n_beams = nfb;
     fb.out_ids = t->d_fb + 1;
     fb.wave = wave; fb.echoes = echoes->echoes; fb.counts = echoes->counts;
-    return launch_fp(l, fb, s);
+    return launch_fp(l, fb, s, true);
 }
 
 lidar_status_t lidar_simulate_surrogate(lidar_t *l, lidar_tailnet_t *net, const lidar_gbuffer_t *g,
