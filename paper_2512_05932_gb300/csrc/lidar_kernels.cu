@@ -311,7 +311,7 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     L.taps_off = M + 8;
     L.taps_len = 2 * M + 17;
     size_t off = (size_t)G * L.HB * 4;
-    L.off_taps = off; off += (size_t)L.taps_len * 4;
+    L.off_taps = off; off += (size_t)(skew_pos(L.taps_len) + 1) * 4;  // stored at skew_pos(index)
     L.off_amb = off; off += (size_t)G * 4;
     L.off_nrm = off; off += (size_t)G * 4;
     L.off_supp = off; off += (size_t)G * 8;
@@ -674,7 +674,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     for (int i = tid; i < G * Ly.HB; i += blockDim.x) hbuf[i] = 0.f;
     for (int i = tid; i < Ly.taps_len; i += blockDim.x) {
         int m = i - Ly.taps_off;
-        taps[i] = (m >= -M && m <= M) ? A.taps_pad[A.tp_off + m] : 0.f;
+        taps[skew_pos(i)] = (m >= -M && m <= M) ? A.taps_pad[A.tp_off + m] : 0.f;
     }
     if (tid < G) {
         amb_s[tid] = 0.f;
@@ -972,8 +972,11 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         float acc[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) acc[r] = ambv;
-        int m_lo = max(-M, o0 - hi), m_hi = min(M, o0 + kBlk - 1 - lo);
         const int kb = min(o0 + 8 * lane, nb - 8);  // lanes past the end compute a copy, not stored
+        // taps that connect this lane's 8 outputs with the histogram's support
+        // (the rest multiply zeros); lanes then read the same histogram bin
+        // and taps 8 apart, which the skewed tap layout keeps in distinct banks
+        int m_lo = max(-M, kb - hi), m_hi = min(M, kb + 7 - lo);
         if (hi >= 0 && m_lo <= m_hi) {
             m_lo = (m_lo >> 3) << 3;  // floor to a multiple of 8
             const float *hb = hj;
@@ -985,7 +988,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 for (int i = 0; i < 8; ++i) {
                     const int m = m0 + i;
                     win[(8 - i) & 7] = hb[skew_pos(kb - m + pad)];
-                    const float t = taps[Ly.taps_off + m];
+                    const float t = taps[skew_pos(Ly.taps_off + m)];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) acc[r] = fmaf(t, win[(r - i) & 7], acc[r]);
                 }
