@@ -297,7 +297,7 @@ struct Layout {
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_nrm, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
+    size_t off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
 };
 
 
@@ -314,6 +314,7 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     L.off_taps = off; off += (size_t)(skew_pos(L.taps_len) + 1) * 4;  // stored at skew_pos(index)
     L.off_amb = off; off += (size_t)G * 4;
     L.off_nrm = off; off += (size_t)G * 4;
+    L.off_tmass = off; off += (size_t)G * 4;
     L.off_supp = off; off += (size_t)G * 8;
     L.off_tsupp = off; off += (size_t)G * 8;
     off = (off + 15) & ~(size_t)15;
@@ -659,6 +660,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
     int *tsupp = reinterpret_cast<int *>(smem_raw + Ly.off_tsupp);  // coarse support of an added tail
     float *nrm2_s = reinterpret_cast<float *>(smem_raw + Ly.off_nrm);
+    float *tmass_s = reinterpret_cast<float *>(smem_raw + Ly.off_tmass);  // mass of an added tail
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
     float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
     float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
@@ -918,14 +920,19 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             if (A.tail_in && bp[jj].pad0) {
                 // added tail of a core-only beam: its coarse support and ambient sum
                 // (the coarse histogram itself enters in the convolution phase)
-                for (int c = lane; c < A.n_coarse; c += 32)
-                    if (A.tail_in[row + c] != 0.f) { tlo = min(tlo, c); thi = max(thi, c); }
+                float tm = 0.f;
+                for (int c = lane; c < A.n_coarse; c += 32) {
+                    const float v = A.tail_in[row + c];
+                    if (v != 0.f) { tlo = min(tlo, c); thi = max(thi, c); }
+                    tm += v;
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     tlo = min(tlo, __shfl_xor_sync(0xffffffffu, tlo, o));
                     thi = max(thi, __shfl_xor_sync(0xffffffffu, thi, o));
+                    tm += __shfl_xor_sync(0xffffffffu, tm, o);
                 }
-                if (lane == 0) amb_s[jj] += A.tail_in[row + A.n_coarse];
+                if (lane == 0) { amb_s[jj] += A.tail_in[row + A.n_coarse]; tmass_s[jj] = tm; }
             }
             if (A.coarse_out) {
                 float tot = 0.f;
@@ -1059,12 +1066,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         if (ambv > T) { kbeg = 0; kend = nb - 1; }
         else if (hi < 0) { kbeg = 1; kend = 0; }
         else { kbeg = max(0, lo - M - 1); kend = min(nb - 1, hi + M + 1); }
-        if (tsupp[2 * jj + 1] >= 0 && !(ambv > T)) {
-            const int cf = nb / A.n_coarse;
-            const int tb = max(0, tsupp[2 * jj] * cf - M - 1), te = min(nb - 1, (tsupp[2 * jj + 1] + 1) * cf + M);
-            if (kbeg > kend) { kbeg = tb; kend = te; }
-            else { kbeg = min(kbeg, tb); kend = max(kend, te); }
-        }
         // Acceptance test of a core-only beam whose tail was predicted: the
         // exact tail and the prediction are both non-negative with mass at
         // most Eub, so the difference moves any bin by at most eps and bin
@@ -1084,6 +1085,18 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             gfail = !(l2err <= A.g_l2 * sqrtf(nrm2_s[jj]));
             if (ambv <= T) gfail |= !(T - ambv > g_eps);  // bins outside the scan
             gfail |= !(isfinite(g_eub) && isfinite(g_eps));
+        }
+        // An added tail widens the scan to its own support, unless it is too
+        // weak to matter there: away from the core's support the waveform is at
+        // most ambv + (tail mass) max(p), and if that stays below T - eps
+        // neither this waveform nor the exact one (within eps of it) can have a
+        // bin at or above T there.
+        if (tsupp[2 * jj + 1] >= 0 && !(ambv > T) &&
+            !(gated && ambv + 1.01f * tmass_s[jj] * A.g_pmax < T - g_eps)) {
+            const int cf = nb / A.n_coarse;
+            const int tb = max(0, tsupp[2 * jj] * cf - M - 1), te = min(nb - 1, (tsupp[2 * jj + 1] + 1) * cf + M);
+            if (kbeg > kend) { kbeg = tb; kend = te; }
+            else { kbeg = min(kbeg, tb); kend = max(kend, te); }
         }
         int count = 0;
         bool open = false;
@@ -1283,10 +1296,12 @@ size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
 
 // Instantiated configurations: profile kind x beams per CTA x deposit form.
-// Shared-memory atomics: G in {2, 4, 8, 16}; tensor cores: G in {4, 8}.
-#define GBL_FOR_EACH(X)                                                                              \
-    X(0, 2, false) X(0, 4, false) X(0, 8, false) X(0, 16, false) X(1, 2, false) X(1, 4, false)      \
-    X(1, 8, false) X(1, 16, false) X(0, 4, true) X(0, 8, true) X(1, 4, true) X(1, 8, true)
+// Shared-memory atomics: G in {1, 2, 4, 8, 16} (1: scattered beams, e.g. the
+// exact re-run of the tail split); tensor cores: G in {4, 8}.
+#define GBL_FOR_EACH(X)                                                                                \
+    X(0, 1, false) X(0, 2, false) X(0, 4, false) X(0, 8, false) X(0, 16, false) X(1, 1, false)        \
+    X(1, 2, false) X(1, 4, false) X(1, 8, false) X(1, 16, false) X(0, 4, true) X(0, 8, true)          \
+    X(1, 4, true) X(1, 8, true)
 
 cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem)
 {

@@ -27,8 +27,10 @@ struct TailState {
     BeamParam *d_fb_beams = nullptr;
     float *d_box = nullptr;         // pulse averaged over the fine bins of a coarse bin (FootprintArgs::tail_box)
     int box_off = 0;
-    int G_fb = 2;                   // beams per CTA of the exact re-run: small groups, since the re-run
-    size_t smem_fb = 0;             // beams are scattered (large union boxes for large groups)
+    int G_core = 4;                 // beams per CTA of the core pass (the sensor's)
+    size_t smem_core = 0;
+    int G_fb = 1;                   // beams per CTA of the exact re-run: one, since the re-run beams are
+    size_t smem_fb = 0;             // scattered (a CTA walks the union of its beams' pixel boxes)
     float4 *mip_s[kMipLevels] = {};
     float2 *mip_r[kMipLevels] = {};
     size_t mip_cap[kMipLevels] = {};
@@ -122,8 +124,8 @@ gbl::FootprintArgs frame_args(lidar_t *l, const lidar_gbuffer_t *g)
 
 lidar_status_t launch_fp(lidar_t *l, const gbl::FootprintArgs &fa, cudaStream_t s, bool rerun = false)
 {
-    const int G = rerun ? l->tail->G_fb : l->G;
-    const size_t smem = rerun ? l->tail->smem_fb : l->smem;
+    const int G = rerun ? l->tail->G_fb : l->tail->G_core;
+    const size_t smem = rerun ? l->tail->smem_fb : l->tail->smem_core;
     cudaError_t e = gbl::launch_footprint(l->kind, G, false, l->threads, smem, fa, s);
     if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     return LIDAR_OK;
@@ -174,8 +176,11 @@ lidar_status_t lidar_tail_configure(lidar_t *l, double core_deg, int32_t n_coars
         for (int j = 0; j < cf; ++j) acc += p(x - j);
         box[x + t->box_off] = (float)(acc / cf);
     }
+    t->G_core = l->G;
     t->smem_fb = gbl::footprint_smem_bytes(t->G_fb, model_args(l));
-    if ((e = gbl::prepare_footprint(l->kind, t->G_fb, false, t->smem_fb)) != cudaSuccess) {
+    t->smem_core = gbl::footprint_smem_bytes(t->G_core, model_args(l));
+    if ((e = gbl::prepare_footprint(l->kind, t->G_fb, false, t->smem_fb)) != cudaSuccess ||
+        (e = gbl::prepare_footprint(l->kind, t->G_core, false, t->smem_core)) != cudaSuccess) {
         tail_free(l);
         return cuda_fail(l, e, "cudaFuncSetAttribute");
     }
