@@ -555,3 +555,63 @@ void orc_offsets(const float *R, const float *dir, const double *dirs3, int n, d
     orc_beam_frame(R, dir, &f);
     for (int i = 0; i < n; ++i) front[i] = orc_local_offset(&f, dirs3 + 3 * (long)i, &u[i], &v[i]);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 2 (range stacking), nearest slice above threshold                    */
+/* ------------------------------------------------------------------------ */
+
+/* Per-pixel inputs of range stacking: intensity I = the pixel's received
+ * power (rho_hat times its solid angle, 0 without a hit) and range index
+ * floor(range / dr) (-1 without a hit). */
+void orc_stack_inputs(const orc_gbuffer *g, double dr, double *I, int32_t *rbar)
+{
+    for (int v = 0; v < g->V; ++v)
+        for (int u = 0; u < g->U; ++u) {
+            long i = (long)v * g->U + u;
+            double w, t0, t1, a;
+            int hit = orc_pixel(g, u, v, &w, &t0, &t1, &a);
+            I[i] = hit ? w : 0.0;
+            rbar[i] = hit ? (int32_t)floor(g->range[i] / dr) : -1;
+        }
+}
+
+/* Alg. 2: for s = s_max down to 1, the slice image (I where rbar == s, else
+ * 0) is convolved with the centred kernel K[kh][kw] (zero outside the image:
+ * out[v][u] = sum_{i,j} K[m + i][n + j] in[v - i][u - j], m = kh/2, n = kw/2),
+ * and every pixel whose convolved value is >= thr takes s and that value.
+ * Initial values: S = s_max, X = 0. Slices without a pixel are skipped (their
+ * convolution is zero, below thr > 0). */
+void orc_range_stack(int U, int V, const double *I, const int32_t *rbar, int kh, int kw, const double *K,
+                     double thr, int s_max, int32_t *S, double *X)
+{
+    const int m = kh / 2, n = kw / 2;
+    long np = (long)U * V;
+    double *slice = malloc(np * sizeof(double));
+    for (long i = 0; i < np; ++i) { S[i] = s_max; X[i] = 0.0; }
+    for (int s = s_max; s >= 1; --s) {
+        int any = 0;
+        for (long i = 0; i < np; ++i) {
+            slice[i] = rbar[i] == s ? I[i] : 0.0;
+            if (rbar[i] == s) any = 1;
+        }
+        if (!any) continue;
+        for (int v = 0; v < V; ++v)
+            for (int u = 0; u < U; ++u) {
+                double acc = 0.0;
+                for (int i = -m; i <= m; ++i) {
+                    int vv = v - i;
+                    if (vv < 0 || vv >= V) continue;
+                    for (int j = -n; j <= n; ++j) {
+                        int uu = u - j;
+                        if (uu < 0 || uu >= U) continue;
+                        acc += K[(long)(m + i) * kw + (n + j)] * slice[(long)vv * U + uu];
+                    }
+                }
+                if (acc >= thr) {
+                    S[(long)v * U + u] = s;
+                    X[(long)v * U + u] = acc;
+                }
+            }
+    }
+    free(slice);
+}

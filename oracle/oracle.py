@@ -99,6 +99,8 @@ def lib():
         _lib.orc_pixels.argtypes = [C.POINTER(_GBuffer), p, p, p, p, p]
         _lib.orc_offsets.restype = None
         _lib.orc_offsets.argtypes = [p, p, p, i, p, p, p]
+        _lib.orc_stack_inputs.argtypes = [C.POINTER(_GBuffer), d, p, p]
+        _lib.orc_range_stack.argtypes = [i, i, p, p, i, i, p, d, i, p, p]
         _lib.orc_pixel.restype = i
     return _lib
 
@@ -270,3 +272,26 @@ def simulate(gb, dirs, profile, pu, cal, pose=None, beams=None, nthreads=1, max_
 def simulate_workload(wl, beams=None, nthreads=1, max_out=16):
     return simulate(wl.gbuffer, wl.dirs, wl.profile, wl.pulse, wl.calib, wl.pose, beams, nthreads,
                     max_out)
+
+
+def stack_inputs(gb, dr):
+    """Per-pixel intensity and range index of Alg. 2 (range stacking)."""
+    keep = []
+    g = _gbuffer(gb, keep)
+    I = np.zeros((gb.V, gb.U))
+    rbar = np.zeros((gb.V, gb.U), np.int32)
+    lib().orc_stack_inputs(C.byref(g), float(dr), I.ctypes.data, rbar.ctypes.data)
+    return I, rbar
+
+
+def range_stack(I, rbar, kernel, threshold, s_max):
+    """Alg. 2: nearest slice index and intensity per pixel (FP64)."""
+    I = np.ascontiguousarray(I, np.float64)
+    rbar = np.ascontiguousarray(rbar, np.int32)
+    K = np.ascontiguousarray(kernel, np.float64)
+    V, U = I.shape
+    S = np.zeros((V, U), np.int32)
+    X = np.zeros((V, U))
+    lib().orc_range_stack(U, V, I.ctypes.data, rbar.ctypes.data, K.shape[0], K.shape[1], K.ctypes.data,
+                          float(threshold), int(s_max), S.ctypes.data, X.ctypes.data)
+    return S, X

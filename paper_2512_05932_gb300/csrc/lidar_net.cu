@@ -409,11 +409,13 @@ cudaError_t launch_to_half(const float *w, __half *wh, size_t n, cudaStream_t s)
 // Fused inference of the three convolutions (persistent; one beam at a time
 // per CTA, 8 warps). Shared memory holds the FP16 conv weights (re-laid out
 // so that every 16-column k-step is aligned), the beam's input pyramid
-// (double-buffered with cp.async) and the activations: a1 and a2 split by
+// (double-buffered with cp.async, levels 0-2 in zero-bordered planes so that
+// window reads need no bounds tests) and the activations: a1 and a2 split by
 // pixel parity into four sub-images with an 80-byte pixel pitch, so that the
 // stride-2 window rows of the next layer are contiguous and ldmatrix reads
-// them without bank conflicts. Writes the fully connected layer's input row
-// f = [a3, L3, prior / s] per beam.
+// them without bank conflicts. Every warp keeps its output tiles for the whole
+// launch, so the shared-memory addresses of its A fragments are computed once.
+// Writes the fully connected layer's input row f = [a3, L3, prior / s].
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -422,17 +424,21 @@ constexpr int kCP = 40;                        // activation pixel pitch (halves
 constexpr int kW1P = 40, kW23P = 328;           // weight row pitches (halves)
 constexpr int kInHalves = 2 * 5440;             // one beam's input
 constexpr int kL1Off = 2 * 4096, kL2Off = kL1Off + 2 * 1024, kL3Off = kL2Off + 2 * 256;
+// zero-bordered input planes: S + 2 rows of S + 8 pixels (4 left, 4 right), 2 halves per pixel
+constexpr int kP0W = 72, kP1W = 40, kP2W = 24;
+constexpr int kP0 = 66 * kP0W * 2, kP1 = 34 * kP1W * 2, kP2 = 18 * kP2W * 2, kP3 = 128;
+constexpr int kXB = kP0 + kP1 + kP2 + kP3;     // halves per input buffer
 
 struct ConvSmem {
     __half w1[32 * kW1P];
     __half w2[32 * kW23P];
     __half w3[32 * kW23P];
     float bias[96];
-    __half x[2][kInHalves];
+    __half x[2][kXB];
     __half a1[4 * 256 * kCP];
     __half a2[4 * 64 * kCP];
     __half a3[64 * 32];
-    __half zero[16];
+    __half zero[48];
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
@@ -443,26 +449,40 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// A fragment (rows g and g + 8 of a 16-row tile, k-step of 16) of the
-// 2-channel pyramid part of a convolution's K: column tap * 2 + c, taps
-// 0..7 in chunk 0 and tap 8 in chunk 1. lv: the level [S][S][2]; (oy, ox)
-// of the two rows; chunk 0 or 1.
-__device__ __forceinline__ void pyr_frag(uint32_t (&a)[4], const __half *lv, int S, int oy0, int ox0, int oy1,
-                                         int ox1, int chunk, int t)
+__device__ __forceinline__ void ldsm_x4_addr(uint32_t (&r)[4], uint32_t a)
 {
-    auto pair = [&](int oy, int ox, int tap) -> uint32_t {
-        const int iy = 2 * oy + tap / 3 - 1, ix = 2 * ox + tap % 3 - 1;
-        if (tap > 8 || iy < 0 || iy >= S || ix < 0 || ix >= S) return 0u;
-        return *reinterpret_cast<const uint32_t *>(lv + 2 * (iy * S + ix));
-    };
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ uint32_t lds32(const __half *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// Halves offset of tap (ky, kx) = (tap / 3, tap % 3) in a zero-bordered plane of width W.
+__device__ __forceinline__ int tap_off(int tap, int W) { return 2 * ((tap / 3) * W + tap % 3); }
+
+// A fragment of the 2-channel pyramid part of K (column tap * 2 + c; taps
+// 0..7 in chunk 0, tap 8 in chunk 1) for rows at plane offsets r0 and r1 (the
+// window origin of each row's output pixel); t = lane % 4.
+template <int W>
+__device__ __forceinline__ void pyr_frag2(uint32_t (&a)[4], const __half *pl, int r0, int r1, int chunk, int t)
+{
     if (chunk == 0) {
-        a[0] = pair(oy0, ox0, t); a[1] = pair(oy1, ox1, t);
-        a[2] = pair(oy0, ox0, t + 4); a[3] = pair(oy1, ox1, t + 4);
+        const int o0 = tap_off(t, W), o1 = tap_off(t + 4, W);
+        a[0] = lds32(pl + r0 + o0); a[1] = lds32(pl + r1 + o0);
+        a[2] = lds32(pl + r0 + o1); a[3] = lds32(pl + r1 + o1);
     } else {
-        a[0] = pair(oy0, ox0, t == 0 ? 8 : 99); a[1] = pair(oy1, ox1, t == 0 ? 8 : 99);
+        const int o8 = tap_off(8, W);
+        a[0] = t == 0 ? lds32(pl + r0 + o8) : 0u;
+        a[1] = t == 0 ? lds32(pl + r1 + o8) : 0u;
         a[2] = 0u; a[3] = 0u;
     }
 }
+
+// Window origin (halves) of output pixel (oy, ox) in a zero-bordered plane of
+// width W: input pixel (2 oy - 1, 2 ox - 1) at padded row 2 oy, column 2 ox + 3.
+template <int W>
+__device__ __forceinline__ int win_origin(int oy, int ox) { return 2 * ((2 * oy) * W + 2 * ox + 3); }
 
 // Stores bias + ReLU of a 16 x 32 accumulator tile (rows g, g + 8) as FP16
 // pairs at dst(row) + channel.
@@ -501,13 +521,66 @@ __global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
         S.w3[n * kW23P + k] = src >= 0 ? A.w3[n * 320 + src] : __float2half(0.f);
     }
     for (int i = tid; i < 96; i += 256) S.bias[i] = i < 32 ? A.b1[i] : (i < 64 ? A.b2[i - 32] : A.b3[i - 64]);
-    if (tid < 16) S.zero[tid] = __float2half(0.f);
+    if (tid < 48) S.zero[tid] = __float2half(0.f);
+    // zero borders of both input buffers (cp.async writes the interiors only)
+    for (int i = tid; i < 2 * kXB / 8; i += 256) reinterpret_cast<uint4 *>(S.x)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
 
     auto prefetch = [&](int b, int buf) {
         const __half *src = A.x + (size_t)b * kInHalves;
-        for (int i = tid; i < kInHalves / 8; i += 256) cp_async16(S.x[buf] + 8 * i, src + 8 * i);
+        __half *X = S.x[buf];
+        // L0: 64 rows of 256 bytes; L1: 32 rows of 128; L2: 16 rows of 64; L3: 256 bytes
+        for (int i = tid; i < 64 * 16 + 32 * 8 + 16 * 4 + 16; i += 256) {
+            const __half *s;
+            __half *d;
+            if (i < 1024) {
+                const int r = i >> 4, c = i & 15;
+                s = src + r * 128 + c * 8;
+                d = X + ((r + 1) * kP0W + 4) * 2 + c * 8;
+            } else if (i < 1024 + 256) {
+                const int j = i - 1024, r = j >> 3, c = j & 7;
+                s = src + kL1Off + r * 64 + c * 8;
+                d = X + kP0 + ((r + 1) * kP1W + 4) * 2 + c * 8;
+            } else if (i < 1024 + 256 + 64) {
+                const int j = i - 1280, r = j >> 2, c = j & 3;
+                s = src + kL2Off + r * 32 + c * 8;
+                d = X + kP0 + kP1 + ((r + 1) * kP2W + 4) * 2 + c * 8;
+            } else {
+                const int j = i - 1344;
+                s = src + kL3Off + j * 8;
+                d = X + kP0 + kP1 + kP2 + j * 8;
+            }
+            cp_async16(d, s);
+        }
         cp_async_commit();
     };
+
+    // per-warp A-fragment addresses of the activation part of conv2 (output
+    // rows oy = warp, warp + 8) and conv3 (rows 2 (warp / 2), + 1), one per
+    // tap: the window row of this lane's ldmatrix row, or the zero row
+    uint32_t ad2[2][9], ad3[9];
+    {
+        const uint32_t zero = (uint32_t)__cvta_generic_to_shared(S.zero);
+        const uint32_t a1s = (uint32_t)__cvta_generic_to_shared(S.a1), a2s = (uint32_t)__cvta_generic_to_shared(S.a2);
+        const int koff = (q >> 1) * 8;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3, sub = ((ky + 1) & 1) * 2 + ((kx + 1) & 1);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int oy = warp + 8 * mi, ox = (q & 1) * 8 + r8;
+                const int sy = ky == 0 ? oy - 1 : oy, sx = kx == 0 ? ox - 1 : ox;
+                ad2[mi][tap] = (sy < 0 || sx < 0) ? zero : a1s + 2u * (uint32_t)((sub * 256 + sy * 16 + sx) * kCP + koff);
+            }
+            const int oy = 2 * (warp >> 1) + (q & 1), ox = r8;
+            const int sy = ky == 0 ? oy - 1 : oy, sx = kx == 0 ? ox - 1 : ox;
+            ad3[tap] = (sy < 0 || sx < 0) ? zero : a2s + 2u * (uint32_t)((sub * 64 + sy * 8 + sx) * kCP + koff);
+        }
+    }
+    const uint32_t w2s = (uint32_t)__cvta_generic_to_shared(S.w2), w3s = (uint32_t)__cvta_generic_to_shared(S.w3);
+    const uint32_t bw2 = w2s + 2u * (uint32_t)(((q >> 1) * 8 + r8) * kW23P + (q & 1) * 8);
+    const uint32_t bw3 = w3s + 2u * (uint32_t)((((warp & 1) * 16) + (q >> 1) * 8 + r8) * kW23P + (q & 1) * 8);
+
     int buf = 0;
     if ((int)blockIdx.x < A.n) prefetch(blockIdx.x, 0);
 
@@ -525,13 +598,15 @@ __global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
 #pragma unroll
                 for (int nj = 0; nj < 2; ++nj)
                     ldsm_x4(bw[ks][nj], S.w1 + (nj * 16 + (q >> 1) * 8 + r8) * kW1P + ks * 16 + (q & 1) * 8);
+#pragma unroll 2
             for (int mt = warp; mt < 64; mt += 8) {
                 const int oy = mt >> 1, ox0 = (mt & 1) * 16;
+                const int r0 = win_origin<kP0W>(oy, ox0 + g), r1 = r0 + 32;  // ox + 8 -> 16 pixels right
                 float acc[4][4] = {};
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     uint32_t a[4];
-                    pyr_frag(a, X, 64, oy, ox0 + g, oy, ox0 + g + 8, ks, t);
+                    pyr_frag2<kP0W>(a, X, r0, r1, ks, t);
 #pragma unroll
                     for (int ni = 0; ni < 4; ++ni)
                         mma_f16(acc[ni], a, bw[ks][ni >> 1][(ni & 1) * 2], bw[ks][ni >> 1][(ni & 1) * 2 + 1]);
@@ -547,27 +622,21 @@ __global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
         // ---- conv2: [a1, L1] -> 16^2 x 32; warp w takes output rows w, w + 8
         {
             float acc[2][4][4] = {};
+            const __half *L1 = X + kP0;
+#pragma unroll
             for (int ks = 0; ks < 20; ++ks) {
                 uint32_t bw[2][4];
-#pragma unroll
-                for (int nj = 0; nj < 2; ++nj)
-                    ldsm_x4(bw[nj], S.w2 + (nj * 16 + (q >> 1) * 8 + r8) * kW23P + ks * 16 + (q & 1) * 8);
+                ldsm_x4_addr(bw[0], bw2 + 2u * (uint32_t)(ks * 16));
+                ldsm_x4_addr(bw[1], bw2 + 2u * (uint32_t)(16 * kW23P + ks * 16));
 #pragma unroll
                 for (int mi = 0; mi < 2; ++mi) {
-                    const int oy = warp + 8 * mi;
                     uint32_t a[4];
                     if (ks < 18) {
-                        const int tap = ks >> 1, c0 = (ks & 1) * 16;
-                        const int ky = tap / 3, kx = tap % 3;
-                        const int sy = ky == 0 ? oy - 1 : oy;
-                        const int ox = (q & 1) * 8 + r8;
-                        const int sx = kx == 0 ? ox - 1 : ox;
-                        const int sub = ((ky + 1) & 1) * 2 + ((kx + 1) & 1);
-                        const __half *p = (sy < 0 || sx < 0) ? S.zero
-                                                             : S.a1 + (sub * 256 + sy * 16 + sx) * kCP + c0 + (q >> 1) * 8;
-                        ldsm_x4(a, p);
+                        ldsm_x4_addr(a, ad2[mi][ks >> 1] + 2u * (uint32_t)((ks & 1) * 16));
                     } else {
-                        pyr_frag(a, X + kL1Off, 32, oy, g, oy, g + 8, ks - 18, t);
+                        const int oy = warp + 8 * mi;
+                        const int r0 = win_origin<kP1W>(oy, g);
+                        pyr_frag2<kP1W>(a, L1, r0, r0 + 32, ks - 18, t);
                     }
 #pragma unroll
                     for (int ni = 0; ni < 4; ++ni)
@@ -588,22 +657,18 @@ __global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
         // 2 mt, 2 mt + 1), n-tiles 2 (w % 2) .. + 1
         {
             const int mt = warp >> 1, nh = warp & 1;
+            const __half *L2 = X + kP0 + kP1;
             float acc[2][4] = {};
+#pragma unroll
             for (int ks = 0; ks < 20; ++ks) {
                 uint32_t bw[4];
-                ldsm_x4(bw, S.w3 + (nh * 16 + (q >> 1) * 8 + r8) * kW23P + ks * 16 + (q & 1) * 8);
+                ldsm_x4_addr(bw, bw3 + 2u * (uint32_t)(ks * 16));
                 uint32_t a[4];
                 if (ks < 18) {
-                    const int tap = ks >> 1, c0 = (ks & 1) * 16;
-                    const int ky = tap / 3, kx = tap % 3;
-                    const int oy = 2 * mt + (q & 1), ox = r8;
-                    const int sy = ky == 0 ? oy - 1 : oy, sx = kx == 0 ? ox - 1 : ox;
-                    const int sub = ((ky + 1) & 1) * 2 + ((kx + 1) & 1);
-                    const __half *p = (sy < 0 || sx < 0) ? S.zero
-                                                         : S.a2 + (sub * 64 + sy * 8 + sx) * kCP + c0 + (q >> 1) * 8;
-                    ldsm_x4(a, p);
+                    ldsm_x4_addr(a, ad3[ks >> 1] + 2u * (uint32_t)((ks & 1) * 16));
                 } else {
-                    pyr_frag(a, X + kL2Off, 16, 2 * mt, g, 2 * mt + 1, g, ks - 18, t);
+                    const int r0 = win_origin<kP2W>(2 * mt, g), r1 = win_origin<kP2W>(2 * mt + 1, g);
+                    pyr_frag2<kP2W>(a, L2, r0, r1, ks - 18, t);
                 }
 #pragma unroll
                 for (int ni = 0; ni < 2; ++ni) mma_f16(acc[ni], a, bw[(ni & 1) * 2], bw[(ni & 1) * 2 + 1]);
@@ -627,7 +692,7 @@ __global__ void __launch_bounds__(256, 1) tailnet_conv_kernel(ConvArgs A)
             for (int i = tid; i < 2048 / 8; i += 256)
                 reinterpret_cast<uint4 *>(f)[i] = reinterpret_cast<const uint4 *>(S.a3)[i];
             for (int i = tid; i < 128 / 8; i += 256)
-                reinterpret_cast<uint4 *>(f + 2048)[i] = reinterpret_cast<const uint4 *>(X + kL3Off)[i];
+                reinterpret_cast<uint4 *>(f + 2048)[i] = reinterpret_cast<const uint4 *>(X + kP0 + kP1 + kP2)[i];
             const float *row = A.rows + (size_t)b * (A.n_coarse + 4);
             const float sc = net_scale(row, A.n_coarse);
             for (int c = tid; c < A.n_coarse; c += 256) f[2176 + c] = __float2half_rn(sc > 0.f ? row[c] / sc : 0.f);

@@ -1,0 +1,371 @@
+// Range stacking (Alg. 2) on sm_103a: include/lidar_stack.h.
+//
+//   stack_inputs_kernel  per pixel: intensity I = rho_hat * d omega (FP32,
+//                        as the beam model's per-pixel prepass computes it)
+//                        and the range index floor(R / dr) (FP64 division,
+//                        so that slice boundaries match the definition), or
+//                        0 ("no slice") outside 1..s_max.
+//   stack_tile_kernel    one CTA per 32 x 8 output tile: the kernel and the
+//                        tile's input region (tile + kernel halo) are staged
+//                        in shared memory; each thread walks its pixel's
+//                        stencil in the same order as its warp (the kernel
+//                        weight is a broadcast), keeping the 24 nearest slices
+//                        it meets with their sums; the nearest one at or above
+//                        the threshold is the answer. If none is and more
+//                        slices were present, the walk repeats above them.
+//                        Slices too weak to reach the threshold anywhere in
+//                        the tile are dropped first.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <stdint.h>
+#include <vector>
+
+#include "lidar_stack.h"
+
+namespace {
+
+constexpr int kTW = 32, kTH = 8;  // output tile (one thread per output pixel)
+constexpr int kSlots = 24;
+constexpr int kMaxK = 129;
+constexpr int kSpan = 4096;       // slice range of a tile's region for which weak slices are dropped
+constexpr int kDense = 4;         // at most this many remaining slices: one dense pass per slice
+
+struct StackArgs {
+    int U, V;
+    float az0, el0, daz, del, sv;
+    const float *range, *nx, *ny, *nz, *rho, *retro;
+    double dr;
+    int s_max;
+    float *I;           // [V][U]
+    uint16_t *S;        // [V][U], 0 = no slice
+    const float *K;     // [kh][kw]
+    int kh, kw;
+    float thr, kmax;    // threshold, largest kernel weight
+    int32_t *out_slice;
+    float *out_val;
+};
+
+__global__ void __launch_bounds__(256) stack_inputs_kernel(StackArgs A)
+{
+    const long n = (long)A.U * A.V;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+        const int v = (int)(idx / A.U), u = (int)(idx - (long)v * A.U);
+        float w = 0.f;
+        int s = 0;
+        const float rr = A.range[idx];
+        if (isfinite(rr) && rr > 0.f) {
+            const float az = A.az0 + ((float)u + 0.5f) * A.daz;
+            const float el = A.el0 + ((float)v + 0.5f) * A.del;
+            float sa, ca, se, ce;
+            sincosf(az, &sa, &ca);
+            sincosf(el, &se, &ce);
+            const float domega = 2.f * A.daz * ce * A.sv;
+            const float dn = ce * (ca * A.nx[idx] + sa * A.ny[idx]) + se * A.nz[idx];
+            const float beta = A.rho[idx] * (1.f / 3.14159265358979f) + A.retro[idx];
+            w = beta * fabsf(dn) / (rr * rr) * domega;
+            const double q = floor((double)rr / A.dr);
+            if (q >= 1.0 && q <= (double)A.s_max) s = (int)q;
+        }
+        A.I[idx] = w;
+        A.S[idx] = (uint16_t)s;
+    }
+}
+
+__global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int kh = A.kh, kw = A.kw, m = kh / 2, n = kw / 2;
+    const int RH = kTH + kh - 1, RW = kTW + kw - 1;
+    float *Ks = reinterpret_cast<float *>(smem);
+    float *RI = Ks + kh * kw;
+    uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RW);
+    const int tid = threadIdx.x, tx = tid % kTW, ty = tid / kTW;
+    const int u0 = blockIdx.x * kTW, v0 = blockIdx.y * kTH;
+    for (int i = tid; i < kh * kw; i += blockDim.x) Ks[i] = A.K[i];
+    // region rows v0 - m .. v0 + kTH - 1 + m, columns u0 - n .. u0 + kTW - 1 + n
+    for (int i = tid; i < RH * RW; i += blockDim.x) {
+        const int ry = i / RW, rx = i - ry * RW;
+        const int v = v0 - m + ry, u = u0 - n + rx;
+        float w = 0.f;
+        uint16_t s = 0;
+        if (v >= 0 && v < A.V && u >= 0 && u < A.U) {
+            const long idx = (long)v * A.U + u;
+            w = A.I[idx];
+            s = A.S[idx];
+        }
+        RI[i] = w;
+        RS[i] = s;
+    }
+    __syncthreads();
+
+    // Slice skipping: a slice whose whole intensity in the region, times the
+    // largest kernel weight, stays below the threshold cannot reach it at any
+    // output of the tile; its pixels are dropped (when the region's slices span
+    // at most kSpan indices, so that a shared-memory histogram holds them).
+    // When at most kDense slices remain, each is convolved densely in turn
+    // (nearest first) instead of the slot walk.
+    __shared__ int dense_n;
+    __shared__ int dense_s[kDense];
+    {
+        __shared__ int s_lo, s_hi;
+        __shared__ float hist[kSpan];
+        if (tid == 0) { s_lo = INT_MAX; s_hi = 0; dense_n = -1; }
+        __syncthreads();
+        int lo_ = INT_MAX, hi_ = 0;
+        for (int i = tid; i < RH * RW; i += blockDim.x)
+            if (RS[i]) { lo_ = min(lo_, (int)RS[i]); hi_ = max(hi_, (int)RS[i]); }
+        atomicMin(&s_lo, lo_);
+        atomicMax(&s_hi, hi_);
+        __syncthreads();
+        const int slo = s_lo, shi = s_hi;
+        if (shi >= slo && shi - slo < kSpan) {
+            for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
+            __syncthreads();
+            for (int i = tid; i < RH * RW; i += blockDim.x)
+                if (RS[i]) atomicAdd(&hist[RS[i] - slo], RI[i]);
+            __syncthreads();
+            const float cut = A.thr * (1.f - 1e-5f);
+            for (int i = tid; i < RH * RW; i += blockDim.x)
+                if (RS[i] && hist[RS[i] - slo] * A.kmax < cut) RS[i] = 0;
+            __syncthreads();
+            // the remaining slices in ascending order (one warp), if few
+            if (tid < 32) {
+                int cnt = 0;
+                for (int b0 = 0; b0 <= shi - slo && cnt <= kDense; b0 += 32) {
+                    const int bin = b0 + tid;
+                    const bool keep = bin <= shi - slo && hist[bin] > 0.f && hist[bin] * A.kmax >= cut;
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    const int pos = cnt + __popc(bal & ((1u << tid) - 1u));
+                    if (keep && pos < kDense) dense_s[pos] = slo + bin;
+                    cnt += __popc(bal);
+                }
+                if (tid == 0) dense_n = cnt <= kDense ? cnt : -1;
+            }
+        }
+        __syncthreads();
+    }
+
+    const int u = u0 + tx, v = v0 + ty;
+    bool done = !(u < A.U && v < A.V);
+    int lo = 0;  // slices <= lo are known to stay below the threshold
+    int outS = A.s_max;
+    float outX = 0.f;
+    // region coordinates of input (v - a + m, u - b + n): (ty + 2m - a, tx + 2n - b)
+    const int base = (ty + 2 * m) * RW + (tx + 2 * n);
+    if (dense_n >= 0) {
+        for (int k = 0; k < dense_n && !done; ++k) {
+            const int s = dense_s[k];
+            float acc = 0.f;
+            for (int a = 0; a < kh; ++a) {
+                const int rb = base - a * RW;
+                const float *krow = Ks + a * kw;
+                for (int b = 0; b < kw; ++b) {
+                    const float w = RS[rb - b] == s ? RI[rb - b] : 0.f;
+                    acc = fmaf(w, krow[b], acc);
+                }
+            }
+            if (acc >= A.thr) { outS = s; outX = acc; done = true; }
+        }
+        done = true;
+    }
+    while (__syncthreads_or(!done)) {
+        if (done) continue;
+        int sl[kSlots];
+        float sum[kSlots];
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) { sl[k] = INT_MAX; sum[k] = 0.f; }
+        bool over = false;
+        // Adds (s, w) to the slots: keeps the kSlots nearest slices; the
+        // farthest is replaced when a nearer one arrives (an empty slot is
+        // INT_MAX). A slice that has to leave can never come back in this
+        // pass, since the farthest kept slice only moves nearer.
+        auto add = [&](int s, float w) {
+            bool found = false;
+            int imax = 0, smax = sl[0];
+#pragma unroll
+            for (int k = 0; k < kSlots; ++k) {
+                if (sl[k] == s) { sum[k] += w; found = true; }
+                if (sl[k] > smax) { smax = sl[k]; imax = k; }
+            }
+            if (!found) {
+                if (s < smax) {
+                    if (smax != INT_MAX) over = true;
+#pragma unroll
+                    for (int k = 0; k < kSlots; ++k)
+                        if (k == imax) { sl[k] = s; sum[k] = w; }
+                } else {
+                    over = true;
+                }
+            }
+        };
+        // neighbouring stencil pixels mostly share a slice (a surface seen
+        // along a row): their products are summed in a run first
+        int run_s = 0;
+        float run_w = 0.f;
+        for (int a = 0; a < kh; ++a) {
+            const int rb = base - a * RW;
+            const float *krow = Ks + a * kw;
+            for (int b = 0; b < kw; ++b) {
+                const int s = RS[rb - b];
+                if (s <= lo) continue;
+                const float w = RI[rb - b] * krow[b];
+                if (s == run_s) { run_w += w; continue; }
+                if (run_s) add(run_s, run_w);
+                run_s = s;
+                run_w = w;
+            }
+        }
+        if (run_s) add(run_s, run_w);
+        int best = INT_MAX, kmax = 0;
+        float bx = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+            if (sl[k] != INT_MAX && sum[k] >= A.thr && sl[k] < best) { best = sl[k]; bx = sum[k]; }
+            if (sl[k] != INT_MAX) kmax = max(kmax, sl[k]);
+        }
+        if (best != INT_MAX) { outS = best; outX = bx; done = true; }
+        else if (!over) done = true;
+        else lo = kmax;
+    }
+    if (u < A.U && v < A.V) {
+        const long idx = (long)v * A.U + u;
+        A.out_slice[idx] = outS;
+        A.out_val[idx] = outX;
+    }
+}
+
+thread_local char g_stack_err[512] = "no error";
+
+}  // namespace
+
+struct lidar_stack {
+    int kh = 0, kw = 0, s_max = 0;
+    double dr = 0, thr = 0;
+    float kmax = 0.f;
+    float *d_K = nullptr;
+    float *d_I = nullptr;
+    uint16_t *d_S = nullptr;
+    size_t cap = 0;
+    char err[512] = "no error";
+};
+
+namespace {
+
+lidar_status_t sfail(lidar_stack_t *h, lidar_status_t st, const char *fmt, ...)
+{
+    char *buf = h ? h->err : g_stack_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lidar_status_t scuda(lidar_stack_t *h, cudaError_t e, const char *what)
+{
+    return sfail(h, e == cudaErrorMemoryAllocation ? LIDAR_ENOMEM : LIDAR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t tile_smem(int kh, int kw)
+{
+    const size_t RH = kTH + kh - 1, RW = kTW + kw - 1;
+    return (size_t)kh * kw * 4 + RH * RW * 4 + RH * RW * 2;
+}
+
+}  // namespace
+
+extern "C" {
+
+lidar_status_t lidar_stack_create(const lidar_stack_params_t *p, lidar_stack_t **out)
+{
+    if (!out) return sfail(nullptr, LIDAR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p || !p->kernel) return sfail(nullptr, LIDAR_EINVAL, "params or kernel is NULL");
+    if (p->kh < 1 || p->kw < 1 || p->kh > kMaxK || p->kw > kMaxK || !(p->kh & 1) || !(p->kw & 1))
+        return sfail(nullptr, LIDAR_EINVAL, "kernel sizes must be odd and in [1, %d]", kMaxK);
+    if (!(std::isfinite(p->threshold) && p->threshold > 0)) return sfail(nullptr, LIDAR_EINVAL, "threshold must be > 0");
+    if (!(std::isfinite(p->dr) && p->dr > 0)) return sfail(nullptr, LIDAR_EINVAL, "dr must be > 0");
+    if (!std::isfinite(p->r_max)) return sfail(nullptr, LIDAR_EINVAL, "r_max must be finite");
+    const double sm = std::floor(p->r_max / p->dr);
+    if (!(sm >= 1 && sm <= 65535)) return sfail(nullptr, LIDAR_EINVAL, "floor(r_max / dr) must be in [1, 65535]");
+    for (int i = 0; i < p->kh * p->kw; ++i)
+        if (!(std::isfinite(p->kernel[i]) && p->kernel[i] >= 0.f))
+            return sfail(nullptr, LIDAR_EINVAL, "kernel[%d] is negative or not finite", i);
+    // dynamic shared memory next to the kernel's 16 KB histogram (227 KB per block)
+    if (tile_smem(p->kh, p->kw) > 210 * 1024) return sfail(nullptr, LIDAR_EINVAL, "kernel too large");
+    lidar_stack_t *h = new (std::nothrow) lidar_stack();
+    if (!h) return sfail(nullptr, LIDAR_ENOMEM, "host allocation failed");
+    h->kh = p->kh; h->kw = p->kw; h->s_max = (int)sm; h->dr = p->dr; h->thr = p->threshold;
+    for (int i = 0; i < p->kh * p->kw; ++i) h->kmax = std::max(h->kmax, p->kernel[i]);
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_K, (size_t)p->kh * p->kw * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_K, p->kernel, (size_t)p->kh * p->kw * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(stack_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tile_smem(p->kh, p->kw))) != cudaSuccess) {
+        lidar_status_t st = scuda(nullptr, e, "range stacking set-up");
+        lidar_stack_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_range_stack(lidar_stack_t *h, const lidar_gbuffer_t *g, int32_t *out_slice, float *out_intensity,
+                                 void *stream)
+{
+    if (!h) return sfail(nullptr, LIDAR_EINVAL, "handle is NULL");
+    if (!g || !out_slice || !out_intensity) return sfail(h, LIDAR_EINVAL, "gbuffer or output pointer is NULL");
+    if (g->U < 1 || g->V < 1 || (long long)g->U * g->V > (1LL << 30))
+        return sfail(h, LIDAR_EINVAL, "gbuffer size must be 1..2^30 pixels");
+    if (!(std::isfinite(g->daz) && g->daz > 0 && std::isfinite(g->del) && g->del > 0))
+        return sfail(h, LIDAR_EINVAL, "gbuffer daz, del must be > 0");
+    if (!g->range || !g->nx || !g->ny || !g->nz || !g->rho_d || !g->retro)
+        return sfail(h, LIDAR_EINVAL, "gbuffer plane pointer is NULL");
+    const size_t np = (size_t)g->U * g->V;
+    cudaError_t e;
+    if (np > h->cap) {
+        cudaFree(h->d_I);
+        cudaFree(h->d_S);
+        h->d_I = nullptr; h->d_S = nullptr; h->cap = 0;
+        if ((e = cudaMalloc(&h->d_I, np * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_S, np * sizeof(uint16_t))) != cudaSuccess)
+            return scuda(h, e, "cudaMalloc(range stacking scratch)");
+        h->cap = np;
+    }
+    StackArgs a{};
+    a.U = g->U; a.V = g->V;
+    a.az0 = (float)g->az0; a.el0 = (float)g->el0; a.daz = (float)g->daz; a.del = (float)g->del;
+    a.sv = (float)std::sin(0.5 * g->del);
+    a.range = g->range; a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.rho = g->rho_d; a.retro = g->retro;
+    a.dr = h->dr; a.s_max = h->s_max;
+    a.I = h->d_I; a.S = h->d_S; a.K = h->d_K; a.kh = h->kh; a.kw = h->kw; a.thr = (float)h->thr;
+    a.kmax = h->kmax;
+    a.out_slice = out_slice; a.out_val = out_intensity;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = (int)std::min<size_t>((np + 255) / 256, 152 * 16);
+    stack_inputs_kernel<<<grid, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking input kernel launch");
+    dim3 tg((g->U + kTW - 1) / kTW, (g->V + kTH - 1) / kTH);
+    stack_tile_kernel<<<tg, kTW * kTH, tile_smem(h->kh, h->kw), s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking tile kernel launch");
+    return LIDAR_OK;
+}
+
+const char *lidar_stack_last_error(const lidar_stack_t *h) { return h ? h->err : g_stack_err; }
+
+void lidar_stack_destroy(lidar_stack_t *h)
+{
+    if (!h) return;
+    cudaFree(h->d_K);
+    cudaFree(h->d_I);
+    cudaFree(h->d_S);
+    delete h;
+}
+
+}  // extern "C"

@@ -62,6 +62,11 @@ class lidar_echoes_t(C.Structure):
     _fields_ = [("echoes", C.c_void_p), ("counts", C.c_void_p)]
 
 
+class lidar_stack_params_t(C.Structure):
+    _fields_ = [("kh", C.c_int32), ("kw", C.c_int32), ("kernel", C.POINTER(C.c_float)), ("threshold", C.c_double),
+                ("dr", C.c_double), ("r_max", C.c_double)]
+
+
 class lidar_frame_t(C.Structure):
     _fields_ = [("sensor", C.c_void_p), ("gbuffer", lidar_gbuffer_t), ("pose", lidar_pose_t),
                 ("out_waveforms", C.c_void_p), ("out_echoes", lidar_echoes_t)]
@@ -82,6 +87,8 @@ TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact
                 "lidar_tailnet_get_params", "lidar_tailnet_set_params", "lidar_tailnet_predict",
                 "lidar_tailnet_train_step", "lidar_tailnet_grads", "lidar_tailnet_save", "lidar_tailnet_load",
                 "lidar_simulate_surrogate", "lidar_tailnet_profile_enable", "lidar_tailnet_profile_read")
+# include/lidar_stack.h
+STACK_SYMBOLS = ("lidar_stack_create", "lidar_range_stack", "lidar_stack_last_error", "lidar_stack_destroy")
 KERNELS = ("setup", "footprint_wave")
 TAIL_INPUT_CELLS = 5440
 
@@ -176,6 +183,14 @@ def load(path: str = LIB_PATH):
     lib.lidar_tailnet_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_tailnet_profile_read.restype = C.c_int
     lib.lidar_tailnet_profile_read.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32)]
+    lib.lidar_stack_create.restype = C.c_int
+    lib.lidar_stack_create.argtypes = [P(lidar_stack_params_t), P(C.c_void_p)]
+    lib.lidar_range_stack.restype = C.c_int
+    lib.lidar_range_stack.argtypes = [C.c_void_p, P(lidar_gbuffer_t), C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.lidar_stack_last_error.restype = C.c_char_p
+    lib.lidar_stack_last_error.argtypes = [C.c_void_p]
+    lib.lidar_stack_destroy.restype = None
+    lib.lidar_stack_destroy.argtypes = [C.c_void_p]
     lib.lidar_simulate_surrogate.restype = C.c_int
     lib.lidar_simulate_surrogate.argtypes = [C.c_void_p, C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                              P(lidar_echoes_t), P(C.c_int32), C.c_void_p]
@@ -394,6 +409,39 @@ class TailNet:
     def close(self):
         if self.handle:
             load().lidar_tailnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RangeStack:
+    """Range stacking (include/lidar_stack.h): nearest slice above threshold per pixel."""
+
+    def __init__(self, kernel, threshold: float, dr: float, r_max: float):
+        k = np.ascontiguousarray(kernel, np.float32)
+        self._k = k
+        p = lidar_stack_params_t(k.shape[0], k.shape[1], k.ctypes.data_as(C.POINTER(C.c_float)), float(threshold),
+                                 float(dr), float(r_max))
+        h = C.c_void_p()
+        lib = load()
+        st = lib.lidar_stack_create(C.byref(p), C.byref(h))
+        if st != 0:
+            raise LidarError(st, lib.lidar_stack_last_error(None).decode())
+        self.handle = h.value
+        self.s_max = int(np.floor(r_max / dr))
+
+    def run(self, gbuffer: lidar_gbuffer_t, out_slice: int, out_intensity: int, stream: int = 0) -> None:
+        st = load().lidar_range_stack(self.handle, C.byref(gbuffer), out_slice, out_intensity, stream)
+        if st != 0:
+            raise LidarError(st, load().lidar_stack_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            load().lidar_stack_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -34,6 +34,7 @@ def declared_functions(header=None):
 def test_header_declares_binding_symbols():
     assert declared_functions("lidar.h") == sorted(lidar.SYMBOLS)
     assert declared_functions("lidar_tail.h") == sorted(lidar.TAIL_SYMBOLS)
+    assert declared_functions("lidar_stack.h") == sorted(lidar.STACK_SYMBOLS)
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -121,3 +122,23 @@ def test_new_entry_points_reject_null(lib):
 def test_frame_struct_layout(lib):
     # lidar_frame_t: sensor pointer, gbuffer, pose, waveforms pointer, echoes
     assert C.sizeof(lidar.lidar_frame_t) == 8 + C.sizeof(lidar.lidar_gbuffer_t) + 36 + 4 + 8 + 16
+
+
+@pytest.mark.parametrize("kh,kw,thr,dr,rmax,match", [
+    (4, 5, 1.0, 0.1, 10.0, "odd"),
+    (131, 5, 1.0, 0.1, 10.0, "odd"),
+    (3, 3, 0.0, 0.1, 10.0, "threshold"),
+    (3, 3, 1.0, -0.1, 10.0, "dr"),
+    (3, 3, 1.0, 0.1, 0.05, "r_max / dr"),
+    (3, 3, 1.0, 1e-6, 1.0, "r_max / dr"),
+])
+def test_range_stack_rejects_bad_parameters(lib, kh, kw, thr, dr, rmax, match):
+    with pytest.raises(lidar.LidarError, match=match):
+        lidar.RangeStack(np.ones((kh, kw), np.float32), thr, dr, rmax)
+
+
+def test_range_stack_rejects_negative_kernel(lib):
+    k = np.ones((3, 3), np.float32)
+    k[1, 1] = -1
+    with pytest.raises(lidar.LidarError, match="negative"):
+        lidar.RangeStack(k, 1.0, 0.1, 10.0)

@@ -1,0 +1,113 @@
+"""Range stacking (include/lidar_stack.h, Alg. 2) against the FP64 oracle.
+
+Bar: slice indices bit-exact, except at pixels whose oracle value lies within
+1e-5 of the threshold (FP32 sums may land on either side), where the GPU's
+value must itself be within that band; intensities within 1e-5 relative."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_05932_gb300 import lidar
+from paper_2512_05932_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    O.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def run_gpu(gb, kernel, thr, dr, r_max):
+    st = lidar.RangeStack(kernel, thr, dr, r_max)
+    planes = lidar.gbuffer_to_device(gb)
+    g = lidar.make_gbuffer(gb, [p.data_ptr() for p in planes])
+    s_out = torch.full((gb.V, gb.U), -7, dtype=torch.int32, device="cuda")
+    x_out = torch.full((gb.V, gb.U), float("nan"), dtype=torch.float32, device="cuda")
+    st.run(g, s_out.data_ptr(), x_out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    st.close()
+    return s_out.cpu().numpy(), x_out.cpu().numpy().astype(np.float64), st.s_max
+
+
+def check(gb, kernel, thr, dr, r_max, band=1e-5):
+    S_g, X_g, s_max = run_gpu(gb, kernel, thr, dr, r_max)
+    I, rb = O.stack_inputs(gb, dr)
+    S_o, X_o = O.range_stack(I, rb, np.asarray(kernel, np.float64), thr, s_max)
+    # the oracle's per-slice values near the threshold are ambiguous for FP32 sums
+    amb = np.zeros_like(S_o, bool)
+    for s in np.unique(rb[(rb >= 1) & (rb <= s_max)]):
+        from scipy.signal import convolve2d
+        conv = convolve2d(np.where(rb == s, I, 0.0), np.asarray(kernel, np.float64), mode="same")
+        amb |= np.abs(conv - thr) <= band * thr
+    sure = ~amb
+    assert (S_g[sure] == S_o[sure]).all(), np.argwhere((S_g != S_o) & sure)[:5]
+    both = sure & (X_o > 0)
+    np.testing.assert_allclose(X_g[both], X_o[both], rtol=band)
+    assert (X_g[sure & (X_o == 0)] == 0).all()
+    assert (S_g >= 1).all() and (S_g <= s_max).all()
+    return dict(pixels=S_o.size, echoes=int((X_o > 0).sum()), ambiguous=int(amb.sum()))
+
+
+def profile_kernel(half, pitch_deg, sigma_deg=0.05, tail_amp=1e-4):
+    o = (np.arange(2 * half + 1) - half) * pitch_deg
+    th = np.hypot(o[:, None], o[None, :])
+    k = np.exp(-0.5 * (th / sigma_deg) ** 2) + tail_amp * np.minimum(1.0, (np.maximum(th, 1e-9) / 0.05) ** -3)
+    return (k / k.sum()).astype(np.float32)
+
+
+def test_plane_and_retro_patch():
+    w = S.small_plane_retro()
+    st = check(w.gbuffer, profile_kernel(10, 0.02), thr=5e-8, dr=0.05, r_max=30.0)
+    assert st["echoes"] > 1000
+
+
+def test_ragged_asymmetric_kernel():
+    w = S.tiny_case()
+    g = np.random.default_rng(3)
+    k = g.uniform(0, 1, (5, 9)).astype(np.float32)
+    I, _ = O.stack_inputs(w.gbuffer, 0.01)
+    check(w.gbuffer, k, thr=float(np.median(I[I > 0])) * 3, dr=0.01, r_max=20.0)
+
+
+def test_many_slices_per_stencil():
+    """Ground at grazing angles puts dozens of slices under one stencil: the
+    24-slot passes must still find the nearest slice above the threshold."""
+    w = S.full_frame_boxes(U=128, V=64, n_boxes=12, rows=2, cols=10)
+    I, rb = O.stack_inputs(w.gbuffer, 0.02)
+    k = np.ones((15, 15), np.float32)
+    thr = float(np.quantile(I[I > 0], 0.9)) * 3
+    st = check(w.gbuffer, k, thr=thr, dr=0.02, r_max=200.0)
+    assert st["echoes"] > 0
+
+
+def test_far_slice_behind_many_weak_near_slices():
+    U = V = 24
+    gb = S.GBuffer(U, V, -U * 0.02 * DEG / 2, -V * 0.02 * DEG / 2, 0.02 * DEG, 0.02 * DEG,
+                   *[np.zeros((V, U), np.float32) for _ in range(7)])
+    gb.range[:] = np.inf
+    gb.nx[:] = -1.0
+    # 40 weak pixels at distinct near slices around the centre (more than the
+    # 24 slices one pass keeps), one strong far pixel at the centre
+    pos = [(v, u) for v in range(9, 16) for u in range(9, 16) if (v, u) != (12, 12)][:40]
+    for i, (v, u) in enumerate(pos):
+        gb.range[v, u] = 1.0 + 0.1 * i
+        gb.rho_d[v, u] = 0.01
+    gb.range[12, 12] = 5.0
+    gb.retro[12, 12] = 100.0
+    k = np.ones((7, 7), np.float32)
+    I, rb = O.stack_inputs(gb, 0.1)
+    thr = float(I[12, 12]) * 0.5
+    S_g, X_g, s_max = run_gpu(gb, k, thr, 0.1, 10.0)
+    S_o, X_o = O.range_stack(I, rb, k.astype(np.float64), thr, s_max)
+    assert (S_o[12, 12] == rb[12, 12]) and len(np.unique(rb[rb > 0])) > 24
+    np.testing.assert_array_equal(S_g, S_o)
+    np.testing.assert_allclose(X_g, X_o, rtol=1e-6)

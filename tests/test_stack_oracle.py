@@ -1,0 +1,77 @@
+"""Pins of the FP64 statement of Alg. 2 (range stacking; oracle/lidar_oracle.c
+orc_range_stack) against SciPy's 2-D convolution, closed forms for single
+pixels, the nearest-slice rule and the per-pixel inputs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_05932_gb300 import scenes as S
+
+signal = pytest.importorskip("scipy.signal")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    O.build()
+
+
+def test_single_pixel_reproduces_the_kernel():
+    I = np.zeros((9, 11))
+    I[4, 5] = 2.0
+    rb = np.full((9, 11), -1, np.int32)
+    rb[4, 5] = 3
+    K = np.arange(15, dtype=float).reshape(3, 5) + 1
+    S_, X = O.range_stack(I, rb, K, 6.0, 10)
+    expect = np.zeros((9, 11))
+    expect[3:6, 3:8] = 2 * K                      # impulse response = the kernel
+    above = expect >= 6.0                          # ">=": the value 6 itself counts
+    assert above.sum() == 13
+    np.testing.assert_array_equal(S_, np.where(above, 3, 10))
+    np.testing.assert_allclose(X, np.where(above, expect, 0.0), rtol=0, atol=0)
+
+
+def test_nearest_slice_wins_where_it_reaches_the_threshold():
+    I = np.zeros((7, 20))
+    rb = np.full((7, 20), -1, np.int32)
+    I[3, 6], rb[3, 6] = 1.0, 8      # far surface
+    I[3, 9], rb[3, 9] = 1.0, 2      # near surface, 3 px to the right
+    K = np.ones((3, 7))             # reaches +-3 columns
+    S_, X = O.range_stack(I, rb, K, 0.5, 12)
+    # columns 6..12 are within reach of the near pixel -> slice 2
+    assert (S_[2:5, 6:13] == 2).all() and (X[2:5, 6:13] == 1.0).all()
+    # columns 3..5 only see the far pixel -> slice 8
+    assert (S_[2:5, 3:6] == 8).all()
+    # nothing else
+    assert (S_[:, :3] == 12).all() and (S_[:, 13:] == 12).all() and (X[0] == 0).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_matches_scipy_convolution_per_slice(seed):
+    g = np.random.default_rng(seed)
+    V, U, s_max = 13, 17, 6
+    I = g.uniform(0, 1, (V, U))
+    rb = g.integers(-1, s_max + 2, (V, U)).astype(np.int32)  # includes slices 0 and > s_max (never used)
+    K = g.uniform(0, 1, (5, 3))
+    thr = 1.2
+    S_, X = O.range_stack(I, rb, K, thr, s_max)
+    S_ref = np.full((V, U), s_max, np.int32)
+    X_ref = np.zeros((V, U))
+    for s in range(s_max, 0, -1):
+        conv = signal.convolve2d(np.where(rb == s, I, 0.0), K, mode="same")
+        hit = conv >= thr
+        S_ref[hit] = s
+        X_ref[hit] = conv[hit]
+    np.testing.assert_array_equal(S_, S_ref)
+    np.testing.assert_allclose(X, X_ref, rtol=1e-12, atol=1e-15)
+
+
+def test_inputs_are_pixel_power_and_floor_range():
+    w = S.tiny_case()
+    dr = 0.05
+    I, rb = O.stack_inputs(w.gbuffer, dr)
+    px = O.pixels(w.gbuffer)
+    hit = px["hit"].astype(bool)
+    np.testing.assert_allclose(I[hit], px["w"][hit], rtol=0)
+    assert (I[~hit] == 0).all() and (rb[~hit] == -1).all()
+    r = w.gbuffer.range.astype(np.float64)
+    np.testing.assert_array_equal(rb[hit], np.floor(r[hit] / dr).astype(np.int32))
