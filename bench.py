@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--core-deg", type=float, default=0.3, help="exact core radius of --workload split")
     ap.add_argument("--tail", default="prior", choices=["prior", "net"],
                     help="tail estimate of --workload split: the physics prior or the learned network")
+    ap.add_argument("--dense", default="tcgen05", choices=["tcgen05", "mma_sync"],
+                    help="kernel of the network's dense layers (--tail net)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: a 2048x1024 frame of the wide-tail scene with 100x80 beams (for profiler captures)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
@@ -338,8 +340,6 @@ def run_gb300(args, rank, world, local_rank):
     names = lidar.KERNELS
     tot = {k: kern[k][0] for k in names}
     dom = max(names, key=lambda k: tot[k])
-    if args.deposit != "atomic":
-        pass
     launches = kern[dom][1]
     avg_ms = tot[dom] / max(1, launches)
     peak, peak_kind = load_peaks()
@@ -401,6 +401,7 @@ def run_split(args, rank, world, local_rank):
     if args.tail == "net":
         net = lidar.TailNet(nc)
         net.load(args.weights)
+        net.set_dense(net.DENSE_TCGEN05 if args.dense == "tcgen05" else net.DENSE_MMA_SYNC)
         inputs = torch.empty((L.n_beams, lidar.TAIL_INPUT_CELLS, 2), dtype=torch.float16, device=dev)
         pred = torch.zeros_like(rows)
 
@@ -438,7 +439,11 @@ def run_split(args, rank, world, local_rank):
         for i in range(args.steps):
             nfb.append(step(evs[i]))
         torch.cuda.synchronize(dev)
-    conv = net.profile_read()["conv"] if net else None
+    stages = net.profile_read() if net else {}
+    if net:
+        net.sync(s)
+    conv = stages.get("conv")
+    dense = stages.get("dense")
     if net:
         feat = [e[0].elapsed_time(e[3]) for e in evs]
         prd = [e[3].elapsed_time(e[1]) for e in evs]
@@ -479,18 +484,34 @@ def run_split(args, rank, world, local_rank):
                                                  + f" on {nc} coarse bins, exact re-run of beams failing the test",
                                         "l2": "inputs (0.94 GB) and waveforms (3.3 GB) exceed L2"}),
                 "roofline": roof,
+                "dense_layers": dense_summary(dense, nbeams, nc, args) if net else None,
                 "stage_ms": {"features": sum(feat) / args.steps, "network": sum(prd) / max(1, len(prd)),
                              "split": sum(spl) / args.steps},
                 "fallback_beams": int(np.median(nfb)), "cpu_baseline": cpu, "e2e": None,
-                # features: setup + 4 cell-sum levels + prep; network: 11 per 8192-beam chunk;
+                # features: setup + 4 cell-sum levels + prep; network: 5 per 65536-beam chunk
+                # (fused convolutions, two dense layers, output, clipping);
                 # split: setup + footprint + compaction (+ setup + footprint of the re-run)
-                "gpu_launches": int(args.steps * (6 + (11 * -(-nbeams // 8192) if net else 0) + 3
+                "gpu_launches": int(args.steps * (6 + (5 * -(-nbeams // 65536) if net else 0) + 3
                                                   + (2 if np.median(nfb) > 0 else 0))),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if net:
         net.close()
     L.close()
+
+
+def dense_summary(dense, nbeams, nc, args):
+    """The network's dense layers per step: kernel, time and tensor throughput
+    (2 (F 256 + 256 nc) FLOP per beam, F = 2176 + nc; the timed span also holds
+    the output and clipping launches)."""
+    if not dense or dense[1] == 0:
+        return None
+    tpk, tkind = load_tensor_peak()
+    flops = 2.0 * ((2176 + nc) * 256 + 256 * nc) * nbeams
+    ms = dense[0] / args.steps
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"kernel": args.dense, "ms_per_step": ms, "tflops": ach, "peak": tpk, "frac": ach / tpk,
+            "peak_source": f"{tkind} bf16_tflops_sustained (FP16 at the same nominal rate)"}
 
 
 def stack_workload():

@@ -166,6 +166,27 @@ lidar_status_t lidar_tailnet_load(lidar_tailnet_t *net, const char *path);
 lidar_status_t lidar_tailnet_profile_enable(lidar_tailnet_t *net, int32_t enable);
 lidar_status_t lidar_tailnet_profile_read(lidar_tailnet_t *net, double total_ms[2], int32_t launches[2]);
 
+/* Which kernel runs the network's forward GEMMs: the three convolutions
+ * of training (as im2col GEMMs) and both dense layers of training and
+ * prediction. The fused convolutions of prediction and all gradient GEMMs
+ * use the mma.sync kernels in either mode.
+ *   LIDAR_DENSE_TCGEN05   (default) 5th-generation tensor cores: 256-row
+ *                         tiles, FP16 operands copied by TMA into swizzled
+ *                         shared memory, FP32 accumulators in tensor memory;
+ *                         used when the output width is a multiple of 16 up
+ *                         to 256, else the mma.sync kernel runs.
+ *   LIDAR_DENSE_MMA_SYNC  64 x 64 tiles of mma.sync m16n8k16 (FP32 accumulators
+ *                         in registers).
+ * Both accumulate in FP32; results differ by rounding order only. */
+enum { LIDAR_DENSE_TCGEN05 = 0, LIDAR_DENSE_MMA_SYNC = 1 };
+lidar_status_t lidar_tailnet_set_dense(lidar_tailnet_t *net, int32_t mode);
+
+/* Synchronises `stream` and reports errors of the network's asynchronous
+ * work since the last check: LIDAR_ECUDA for a CUDA error, LIDAR_ETIMEOUT if a
+ * bounded wait of the tensor-core GEMM gave up (its outputs are then
+ * undefined). Clears the recorded timeout. */
+lidar_status_t lidar_tailnet_sync(lidar_tailnet_t *net, void *stream);
+
 /* One frame through the surrogate: lidar_tail_features, lidar_tailnet_predict
  * (or the physics prior when net is NULL) and lidar_simulate_split. Per-beam
  * scratch (about 22 KB per beam for the network input) is allocated on first

@@ -40,6 +40,8 @@ struct lidar_tailnet {
     __half *wh = nullptr;
     int *flag = nullptr;
     float *loss = nullptr;
+    int *uerr = nullptr;          // error word of the tcgen05 GEMM (bounded waits)
+    int dense_mode = LIDAR_DENSE_TCGEN05;
     int64_t step = 0;
     // scratch for `cap` beams
     int cap = 0;
@@ -169,6 +171,19 @@ gbl::GemmArgs gemm(int M, int N, int K, const __half *A, int lda, const __half *
     return g;
 }
 
+// Forward GEMM with bias (+ ReLU), non-transposed operands: the tcgen05
+// kernel when the network uses it and the shape allows (N a multiple of 16 up
+// to 256), else the mma.sync kernel.
+cudaError_t dense(lidar_tailnet_t *n, const gbl::GemmArgs &g, cudaStream_t s)
+{
+    if (n->dense_mode == LIDAR_DENSE_TCGEN05) {
+        gbl::UmmaArgs u{g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.bias, g.mode == gbl::kGemmBiasRelu ? 1 : 0,
+                        g.Ch, g.mode == gbl::kGemmBias ? g.C : nullptr, g.ldc, n->uerr};
+        if (gbl::umma_gemm_supported(u)) return gbl::launch_umma_gemm(u, s);
+    }
+    return gbl::launch_gemm(false, false, g, 1, s);
+}
+
 // Weight-gradient GEMM (reduction over the batch rows) split over K with FP32 atomics.
 cudaError_t gemm_splitk(bool ta, bool tb, gbl::GemmArgs g, cudaStream_t s)
 {
@@ -192,30 +207,30 @@ lidar_status_t forward(lidar_tailnet_t *n, const __half *x, const float *rows, i
     // conv1: 64^2 x 2 -> 32^2 x 32
     ia = gbl::Im2colArgs{B, 64, 64, 32, 32, 0, kK1, nullptr, x, kIn, 0, n->X1};
     NCK(gbl::launch_im2col(ia, s), "im2col");
-    NCK(gbl::launch_gemm(false, false,
+    NCK(dense(n,
                          gemm(B * 1024, kC, kK1, n->X1, kK1, wh + n->o_w1, kK1, gbl::kGemmBiasRelu, nullptr, n->A1, kC,
-                              w + n->o_b1), 1, s), "conv1");
+                              w + n->o_b1), s), "conv1");
     // conv2: [a1, L1] 32^2 x 34 -> 16^2 x 32
     ia = gbl::Im2colArgs{B, 32, 32, 16, 16, kC, kK2, n->A1, x, kIn, kOffL1, n->X2};
     NCK(gbl::launch_im2col(ia, s), "im2col");
-    NCK(gbl::launch_gemm(false, false,
+    NCK(dense(n,
                          gemm(B * 256, kC, kK2, n->X2, kK2, wh + n->o_w2, kK2, gbl::kGemmBiasRelu, nullptr, n->A2, kC,
-                              w + n->o_b2), 1, s), "conv2");
+                              w + n->o_b2), s), "conv2");
     // conv3: [a2, L2] 16^2 x 34 -> 8^2 x 32
     ia = gbl::Im2colArgs{B, 16, 16, 8, 8, kC, kK2, n->A2, x, kIn, kOffL2, n->X3};
     NCK(gbl::launch_im2col(ia, s), "im2col");
-    NCK(gbl::launch_gemm(false, false,
+    NCK(dense(n,
                          gemm(B * 64, kC, kK2, n->X3, kK2, wh + n->o_w3, kK2, gbl::kGemmBiasRelu, nullptr, n->A3, kC,
-                              w + n->o_b3), 1, s), "conv3");
+                              w + n->o_b3), s), "conv3");
     // f = [a3, L3, prior / s]; h = relu(W1 f + b1); d = W2 h + b2
     gbl::FlattenArgs fa{B, n->F, kNA, kNL, n->nc, n->nc + 4, n->A3, x, kIn, kOffL3, rows, n->Fm};
     NCK(gbl::launch_flatten(fa, s), "flatten");
-    NCK(gbl::launch_gemm(false, false,
+    NCK(dense(n,
                          gemm(B, kHid, n->F, n->Fm, n->F, wh + n->o_f1, n->F, gbl::kGemmBiasRelu, nullptr, n->H, kHid,
-                              w + n->o_fb1), 1, s), "fc1");
-    NCK(gbl::launch_gemm(false, false,
+                              w + n->o_fb1), s), "fc1");
+    NCK(dense(n,
                          gemm(B, n->nc, kHid, n->H, kHid, wh + n->o_f2, kHid, gbl::kGemmBias, n->D, nullptr, n->nc,
-                              w + n->o_fb2), 1, s), "fc2");
+                              w + n->o_fb2), s), "fc2");
     return LIDAR_OK;
 }
 
@@ -284,6 +299,18 @@ lidar_status_t loss_grad(lidar_tailnet_t *n, const void *inputs, const float *ro
     return LIDAR_OK;
 }
 
+// Reads and clears the tcgen05 GEMM's error word (synchronous copy).
+lidar_status_t check_timeout(lidar_tailnet_t *n)
+{
+    int h = 0;
+    NCK(cudaMemcpy(&h, n->uerr, sizeof(int), cudaMemcpyDeviceToHost), "error word download");
+    if (h) {
+        NCK(cudaMemset(n->uerr, 0, sizeof(int)), "cudaMemset");
+        return nfail(n, LIDAR_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up; outputs are undefined");
+    }
+    return LIDAR_OK;
+}
+
 // splitmix64 -> uniform in [-1, 1)
 struct Rng {
     uint64_t s;
@@ -340,6 +367,8 @@ lidar_status_t lidar_tailnet_create(int32_t n_coarse, uint64_t seed, lidar_tailn
         (e = cudaMalloc(&n->wh, n->n_par * sizeof(__half))) != cudaSuccess ||
         (e = cudaMalloc(&n->flag, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&n->loss, sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&n->uerr, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(n->uerr, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMemcpy(n->w, h.data(), n->n_par * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(n->m, 0, n->n_par * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(n->v, 0, n->n_par * sizeof(float))) != cudaSuccess ||
@@ -360,11 +389,28 @@ void lidar_tailnet_destroy(lidar_tailnet_t *n)
     free_pred(n);
     free_events(n);
     cudaFree(n->w); cudaFree(n->m); cudaFree(n->v); cudaFree(n->g); cudaFree(n->wh);
-    cudaFree(n->flag); cudaFree(n->loss);
+    cudaFree(n->flag); cudaFree(n->loss); cudaFree(n->uerr);
     delete n;
 }
 
 const char *lidar_tailnet_last_error(const lidar_tailnet_t *n) { return n ? n->err : g_net_err; }
+
+lidar_status_t lidar_tailnet_set_dense(lidar_tailnet_t *n, int32_t mode)
+{
+    if (!n) return nfail(nullptr, LIDAR_EINVAL, "network is NULL");
+    if (mode != LIDAR_DENSE_TCGEN05 && mode != LIDAR_DENSE_MMA_SYNC)
+        return nfail(n, LIDAR_EINVAL, "dense mode must be LIDAR_DENSE_TCGEN05 or LIDAR_DENSE_MMA_SYNC");
+    n->dense_mode = mode;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_tailnet_sync(lidar_tailnet_t *n, void *stream)
+{
+    if (!n) return nfail(nullptr, LIDAR_EINVAL, "network is NULL");
+    NCK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    NCK(cudaGetLastError(), "asynchronous error");
+    return check_timeout(n);
+}
 
 int64_t lidar_tailnet_num_params(const lidar_tailnet_t *n) { return n ? (int64_t)n->n_par : 0; }
 
@@ -421,12 +467,12 @@ lidar_status_t lidar_tailnet_predict(lidar_tailnet_t *n, const void *inputs, con
         if (e0) cudaEventRecord(e0, s);
         NCK(gbl::launch_conv(ca, std::min(B, n->sms), s), "fused convolutions");
         if (e1) cudaEventRecord(e1, s);
-        NCK(gbl::launch_gemm(false, false,
+        NCK(dense(n,
                              gemm(B, kHid, n->F, n->pF, n->F, wh + n->o_f1, n->F, gbl::kGemmBiasRelu, nullptr, n->pH,
-                                  kHid, w + n->o_fb1), 1, s), "fc1");
-        NCK(gbl::launch_gemm(false, false,
+                                  kHid, w + n->o_fb1), s), "fc1");
+        NCK(dense(n,
                              gemm(B, n->nc, kHid, n->pH, kHid, wh + n->o_f2, kHid, gbl::kGemmBias, n->pD, nullptr,
-                                  n->nc, w + n->o_fb2), 1, s), "fc2");
+                                  n->nc, w + n->o_fb2), s), "fc2");
         // s * y_hat into the rows, then clip to the bound and copy the bounds
         gbl::HeadArgs hb{B, n->nc, rs, r, nullptr, n->pD, o, nullptr, nullptr, 0.f};
         NCK(gbl::launch_head(hb, s), "head");
@@ -450,7 +496,7 @@ lidar_status_t lidar_tailnet_grads(lidar_tailnet_t *n, const void *inputs, const
         for (size_t i = 0; i < n->n_par; ++i) grads_host[i] /= kLossScale;
     }
     if (loss_host) NCK(cudaMemcpy(loss_host, n->loss, sizeof(float), cudaMemcpyDeviceToHost), "loss download");
-    return LIDAR_OK;
+    return check_timeout(n);
 }
 
 lidar_status_t lidar_tailnet_train_step(lidar_tailnet_t *n, const void *inputs, const float *rows,
@@ -474,6 +520,7 @@ lidar_status_t lidar_tailnet_train_step(lidar_tailnet_t *n, const void *inputs, 
     if (loss_host) {
         NCK(cudaMemcpyAsync(loss_host, n->loss, sizeof(float), cudaMemcpyDeviceToHost, s), "loss download");
         NCK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        return check_timeout(n);
     }
     return LIDAR_OK;
 }

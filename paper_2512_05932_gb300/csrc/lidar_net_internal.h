@@ -85,7 +85,28 @@ __host__ __device__ inline float net_scale(const float *row, int n_coarse)
     return m > 0.1f * e ? m : 0.1f * e;
 }
 
+// Forward GEMM on tcgen05 (lidar_umma.cu): C[m][n] = sum_k A[m][k] B[n][k]
+// + bias[n] (ReLU if relu), written as FP16 (Ch) and/or FP32 (C), row
+// stride ldc. N in 16..256 (multiple of 16), K and the leading dimensions
+// multiples of 8, A and B 16-byte aligned. A bounded wait that gives up sets
+// *err to 1 (err may be NULL).
+struct UmmaArgs {
+    int M, N, K;
+    const __half *A;
+    int lda;
+    const __half *B;
+    int ldb;
+    const float *bias;
+    int relu;
+    __half *Ch;
+    float *C;
+    int ldc;
+    int *err;
+};
+
 cudaError_t launch_gemm(bool ta, bool tb, const GemmArgs &g, int splits, cudaStream_t s);
+bool umma_gemm_supported(const UmmaArgs &g);
+cudaError_t launch_umma_gemm(const UmmaArgs &g, cudaStream_t s);
 cudaError_t launch_im2col(const Im2colArgs &a, cudaStream_t s);
 cudaError_t launch_col2im(const Col2imArgs &a, cudaStream_t s);
 cudaError_t launch_flatten(const FlattenArgs &a, cudaStream_t s);

@@ -370,7 +370,10 @@ lidar_status_t lidar_simulate_surrogate(lidar_t *l, lidar_tailnet_t *net, const 
             return fail(l, st, "tail network: %s", lidar_tailnet_last_error(net));
         tail = t->d_pred;
     }
-    return lidar_simulate_split(l, g, pose, tail, wave, echoes, n_fallback, stream);
+    if ((st = lidar_simulate_split(l, g, pose, tail, wave, echoes, n_fallback, stream)) != LIDAR_OK) return st;
+    if (net && (st = lidar_tailnet_sync(net, stream)) != LIDAR_OK)
+        return fail(l, st, "tail network: %s", lidar_tailnet_last_error(net));
+    return LIDAR_OK;
 }
 
 }  // extern "C"

@@ -86,7 +86,8 @@ TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact
                 "lidar_tailnet_create", "lidar_tailnet_destroy", "lidar_tailnet_last_error", "lidar_tailnet_num_params",
                 "lidar_tailnet_get_params", "lidar_tailnet_set_params", "lidar_tailnet_predict",
                 "lidar_tailnet_train_step", "lidar_tailnet_grads", "lidar_tailnet_save", "lidar_tailnet_load",
-                "lidar_simulate_surrogate", "lidar_tailnet_profile_enable", "lidar_tailnet_profile_read")
+                "lidar_simulate_surrogate", "lidar_tailnet_profile_enable", "lidar_tailnet_profile_read",
+                "lidar_tailnet_set_dense", "lidar_tailnet_sync")
 # include/lidar_stack.h
 STACK_SYMBOLS = ("lidar_stack_create", "lidar_range_stack", "lidar_stack_last_error", "lidar_stack_destroy")
 KERNELS = ("setup", "footprint_wave")
@@ -183,6 +184,10 @@ def load(path: str = LIB_PATH):
     lib.lidar_tailnet_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_tailnet_profile_read.restype = C.c_int
     lib.lidar_tailnet_profile_read.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32)]
+    lib.lidar_tailnet_set_dense.restype = C.c_int
+    lib.lidar_tailnet_set_dense.argtypes = [C.c_void_p, C.c_int32]
+    lib.lidar_tailnet_sync.restype = C.c_int
+    lib.lidar_tailnet_sync.argtypes = [C.c_void_p, C.c_void_p]
     lib.lidar_stack_create.restype = C.c_int
     lib.lidar_stack_create.argtypes = [P(lidar_stack_params_t), P(C.c_void_p)]
     lib.lidar_range_stack.restype = C.c_int
@@ -390,6 +395,17 @@ class TailNet:
         self._check(load().lidar_tailnet_grads(self.handle, inputs.data_ptr(), rows.data_ptr(), target.data_ptr(),
                                                rows.shape[0], g.ctypes.data, C.byref(loss), stream))
         return float(loss.value), g
+
+    DENSE_TCGEN05 = 0
+    DENSE_MMA_SYNC = 1
+
+    def set_dense(self, mode: int) -> None:
+        """Kernel of the forward GEMMs: DENSE_TCGEN05 (default) or DENSE_MMA_SYNC."""
+        self._check(load().lidar_tailnet_set_dense(self.handle, int(mode)))
+
+    def sync(self, stream: int = 0) -> None:
+        """Synchronises `stream`; raises on an asynchronous error or a GEMM wait that gave up."""
+        self._check(load().lidar_tailnet_sync(self.handle, stream))
 
     def profile_enable(self, enable: bool) -> None:
         self._check(load().lidar_tailnet_profile_enable(self.handle, int(bool(enable))))

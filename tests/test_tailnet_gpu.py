@@ -59,6 +59,16 @@ def randomize(net, seed):
     net.set_params(TN.pack(P, net.n_coarse).astype(np.float32))
 
 
+def clip_to_bound(tail, rows, nc):
+    """A prediction whose mass exceeds the row's bound E is scaled down to E
+    (the documented output of lidar_tailnet_predict); a random network with
+    many coarse bins often predicts more than E."""
+    E = np.asarray(rows, np.float64)[:, nc + 1]
+    m = tail.sum(axis=1)
+    f = np.where(m > E, E / np.where(m > 0, m, 1), 1.0)
+    return tail * f[:, None]
+
+
 def test_predict_matches_fp64_network():
     net = lidar.TailNet(NC, seed=7)
     randomize(net, 7)
@@ -76,6 +86,35 @@ def test_predict_matches_fp64_network():
     net.close()
 
 
+DENSE = {"tcgen05": lidar.TailNet.DENSE_TCGEN05, "mma_sync": lidar.TailNet.DENSE_MMA_SYNC}
+
+
+@pytest.mark.parametrize("dense", sorted(DENSE))
+@pytest.mark.parametrize("nc,B", [(256, 300), (64, 161), (40, 130)])
+def test_predict_many_beams_matches_fp64_network(nc, B, dense):
+    """More beams than one persistent pass of the fused convolutions covers,
+    several row tiles of the dense layers with a ragged last tile, in both
+    GEMM modes (40 bins: the output layer is not a multiple of 16 wide, so it
+    runs on mma.sync in either mode)."""
+    net = lidar.TailNet(nc, seed=13)
+    net.set_dense(DENSE[dense])
+    randomize(net, 13)
+    x, rows, _ = random_batch(6, B, nc=nc)
+    out = torch.zeros((B, nc + 4), dtype=torch.float32, device="cuda")
+    net.predict(dev(x), dev(rows), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref, _ = TN.forward(net.get_params().astype(np.float64), x.astype(np.float64), rows, nc)
+    ref = clip_to_bound(ref, rows, nc)
+    err = np.abs(got[:, :nc] - ref) / np.abs(ref).max(axis=1, keepdims=True)
+    bad = np.argwhere(err.max(axis=1) > 2e-2).ravel()
+    assert err.max() <= 2e-2, (err.max(), bad[:20], len(bad))
+    np.testing.assert_allclose(got[:, nc + 3], got[:, :nc].sum(1), rtol=1e-5)
+    assert (got[:, nc + 3] <= rows[:, nc + 1] * (1 + 1e-6)).all()
+    net.sync()
+    net.close()
+
+
 def test_predict_clips_to_the_bound():
     net = lidar.TailNet(NC, seed=8)
     randomize(net, 8)
@@ -88,8 +127,10 @@ def test_predict_clips_to_the_bound():
     net.close()
 
 
-def test_gradient_matches_fp64_backprop():
+@pytest.mark.parametrize("dense", sorted(DENSE))
+def test_gradient_matches_fp64_backprop(dense):
     net = lidar.TailNet(NC, seed=9)
+    net.set_dense(DENSE[dense])
     randomize(net, 9)
     x, rows, target = random_batch(3, 8)
     loss, g = net.grads(dev(x), dev(rows), dev(target))
@@ -142,6 +183,13 @@ def test_training_reduces_the_loss_and_checkpoints_resume(tmp_path):
     np.testing.assert_array_equal(other.get_params(), net.get_params())
     net.close()
     other.close()
+
+
+def test_dense_mode_rejects_unknown_values():
+    net = lidar.TailNet(NC, seed=1)
+    with pytest.raises(lidar.LidarError, match="dense mode"):
+        net.set_dense(7)
+    net.close()
 
 
 def test_load_rejects_other_shapes_and_garbage(tmp_path):
