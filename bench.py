@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LiDAR beams/s (waveform+echoes) at <=1e-3 rel err vs FP64 oracle; % HBM roofline"
+METRIC_ECHO = "LiDAR beams/s (echoes only, no waveform output) at <=1e-3 rel err vs FP64 oracle; % HBM roofline"
 UNIT = "beams/s"
 L2_BYTES = 129 * 1024 * 1024
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "footprint_wave_boxes2048x1024.traffic.json")
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--echo-only", action="store_true",
+                    help="frame workload through lidar_simulate_echoes (echoes and counts, no waveform output)")
     ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
     ap.add_argument("--deposit", default="atomic", choices=["atomic", "tc_split", "tc_bf16"],
                     help="deposit form of the footprint kernel (lidar_set_deposit)")
@@ -98,12 +101,13 @@ def config_of(w, extra=None):
     return c
 
 
-def algorithmic_bytes(w):
+def algorithmic_bytes(w, echo_only=False):
     """HBM bytes one frame must move: the G-buffer read once (7 fp32 planes)
-    plus the waveforms, echoes and echo counts written once."""
+    plus the waveforms (unless echo-only), echoes and echo counts written once."""
     gb = w.gbuffer
     nb = len(w.dirs)
-    return gb.U * gb.V * 7 * 4 + nb * (w.pulse["n_bins"] * 4 + w.calib["max_echoes"] * 32 + 4)
+    wave = 0 if echo_only else w.pulse["n_bins"] * 4
+    return gb.U * gb.V * 7 * 4 + nb * (wave + w.calib["max_echoes"] * 32 + 4)
 
 
 def cpu_cores():
@@ -275,8 +279,17 @@ def run_gb300(args, rank, world, local_rank):
     lidar.lidar_set_deposit(L.handle, DEPOSIT[args.deposit])
     planes = lidar.gbuffer_to_device(w.gbuffer, dev)
     outs = L.alloc_outputs(dev)
+    if args.echo_only:
+        outs = (None, outs[1], outs[2])  # no waveform buffer at all
+        torch.cuda.empty_cache()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    def frame():
+        if args.echo_only:
+            L.simulate_echoes(w.gbuffer, planes, w.pose, (outs[1], outs[2]), stream)
+        else:
+            L.simulate(w.gbuffer, planes, w.pose, outs, stream)
 
     clk = ClockSampler(local_rank).__enter__()
     # warm-up: at least W steps and at least 1.5 s, so that the clock sampler
@@ -284,7 +297,7 @@ def run_gb300(args, rank, world, local_rank):
     t_w = time.perf_counter()
     n_w = 0
     while n_w < args.warmup or time.perf_counter() - t_w < 1.5:
-        L.simulate(w.gbuffer, planes, w.pose, outs, stream)
+        frame()
         n_w += 1
         if n_w % 16 == 0:
             torch.cuda.synchronize(dev)
@@ -301,7 +314,7 @@ def run_gb300(args, rank, world, local_rank):
         for i in range(args.steps):
             flush.fill_(float(i))
             starts[i].record(stream)
-            L.simulate(w.gbuffer, planes, w.pose, outs, stream)
+            frame()
             ends[i].record(stream)
         torch.cuda.synchronize(dev)
         if dist:
@@ -314,16 +327,30 @@ def run_gb300(args, rank, world, local_rank):
 
     # ---- end to end through the host-memory entry point ----
     host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
-    host_out = (torch.empty((nbeams, L.n_bins), dtype=torch.float32, pin_memory=True),
+    host_out = (torch.empty((nbeams, L.n_bins), dtype=torch.float32, pin_memory=True) if not args.echo_only else
+                torch.empty((0,), dtype=torch.float32),
                 torch.empty((nbeams, L.max_echoes, 8), dtype=torch.int32, pin_memory=True),
                 torch.empty((nbeams,), dtype=torch.int32, pin_memory=True))
+
+    def frame_host():
+        if args.echo_only:
+            # pinned G-buffer up, echo-only call, echoes and counts down
+            for d, h in zip(planes, host_planes):
+                d.copy_(h, non_blocking=True)
+            L.simulate_echoes(w.gbuffer, planes, w.pose, (outs[1], outs[2]), stream)
+            host_out[1].copy_(outs[1], non_blocking=True)
+            host_out[2].copy_(outs[2], non_blocking=True)
+            stream.synchronize()
+        else:
+            L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+
     for _ in range(2):
-        L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+        frame_host()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+        frame_host()
     e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
@@ -343,7 +370,7 @@ def run_gb300(args, rank, world, local_rank):
     launches = kern[dom][1]
     avg_ms = tot[dom] / max(1, launches)
     peak, peak_kind = load_peaks()
-    alg = algorithmic_bytes(w)
+    alg = algorithmic_bytes(w, args.echo_only)
     achieved = alg / (avg_ms * 1e-3) / 1e9
     pix_samples = None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -358,11 +385,14 @@ def run_gb300(args, rank, world, local_rank):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_beams} evenly spaced beams of the frame, all pixels each ({dt:.1f} s wall)"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.deposit == "tc_bf16" else "f32", "data": "synthetic",
-            "config": config_of(w, {"l2": "flushed between timed steps (258 MB write)",
-                                    "parallelism": f"replicas x{world}", "deposit": args.deposit}),
+    extra = {"l2": "flushed between timed steps (258 MB write)", "parallelism": f"replicas x{world}",
+             "deposit": args.deposit}
+    if args.echo_only:
+        extra["output"] = "echoes and counts only (lidar_simulate_echoes)"
+    line = {"metric": METRIC_ECHO if args.echo_only else METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.deposit == "tc_bf16" else "f32",
+            "data": "synthetic", "config": config_of(w, extra),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),

@@ -51,7 +51,7 @@ typedef enum {
     LIDAR_EINVAL = 1,   /* invalid argument (message says which) */
     LIDAR_ENOMEM = 2,   /* host or device allocation failed */
     LIDAR_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
-    LIDAR_ETIMEOUT = 4, /* reserved: a bounded device wait gave up */
+    LIDAR_ETIMEOUT = 4, /* a bounded device wait gave up (reported at the next sync) */
     LIDAR_ENUMERIC = 5  /* calibration fit or normalisation failed */
 } lidar_status_t;
 
@@ -192,6 +192,28 @@ lidar_status_t lidar_create(const lidar_profile_t *profile, const lidar_pattern_
 lidar_status_t lidar_simulate(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                               float *out_waveforms, lidar_echoes_t *out_echoes, void *stream);
 
+/* Echo-only simulation: what a sensor reports (its echoes, Sec. II-C: echo
+ * range, EPW and intensity per return), without the waveforms. Same
+ * computation and results as lidar_simulate (echoes and counts are
+ * bit-identical); the difference is where each beam's waveform goes between
+ * the pulse convolution and the echo scan. Each CTA of the footprint kernel
+ * claims a slot of a library-owned pool sized for the CTAs the GPU holds at
+ * once (SMs x resident CTAs x beams per CTA x n_bins floats, about 20 MB for
+ * a 2048-bin sensor on 152 SMs), writes its beams' waveforms there, scans
+ * them and frees the slot; the pool stays in L2, so the waveform bytes (4
+ * n_bins per beam, most of lidar_simulate's output) never reach HBM and no
+ * [n_beams][n_bins] buffer is needed.
+ *   - The first call (and the first after lidar_set_deposit changes the beams
+ *     per CTA) allocates the pool with cudaMalloc, synchronising the device.
+ *   - Calls on several streams may overlap: slots are claimed atomically and
+ *     the pool holds one for every CTA the GPU can run at once.
+ *   - A slot claim that gives up (bounded; not expected, see above) leaves
+ *     that CTA's beams unwritten and is reported by lidar_sync as
+ *     LIDAR_ETIMEOUT.
+ * out_echoes and errors as for lidar_simulate. */
+lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
+                                     lidar_echoes_t *out_echoes, void *stream);
+
 /* Same computation from host memory: the G-buffer plane pointers in `gbuffer`
  * are HOST pointers, and the outputs are host arrays (waveforms
  * [n_beams][n_bins], echoes [n_beams][max_echoes], counts [n_beams]). The
@@ -260,7 +282,8 @@ lidar_status_t lidar_autotune_batch(lidar_t *executor, const lidar_frame_t *fram
 /* Current batch tuning: beams per CTA and resident CTAs per SM. */
 lidar_status_t lidar_batch_config(const lidar_t *executor, int32_t *beams_per_cta, int32_t *ctas_per_sm);
 
-/* Synchronises `stream` and reports any asynchronous CUDA error as LIDAR_ECUDA. */
+/* Synchronises `stream` and reports any asynchronous CUDA error as LIDAR_ECUDA,
+ * and a slot claim of lidar_simulate_echoes that gave up as LIDAR_ETIMEOUT. */
 lidar_status_t lidar_sync(lidar_t *lidar, void *stream);
 
 /* Queries: number of beams, bins, echoes per beam, the profile normaliser Z

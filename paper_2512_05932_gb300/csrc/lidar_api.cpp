@@ -342,6 +342,9 @@ void free_all(lidar_t *l)
     cudaFree(l->d_wave);
     cudaFree(l->d_echo);
     cudaFree(l->d_counts);
+    cudaFree(l->d_slot_pool);
+    cudaFree(l->d_slot_busy);
+    cudaFree(l->d_err);
     tail_free(l);
 }
 
@@ -396,9 +399,46 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     return fa;
 }
 
+// Waveform pool of the echo-only path: a slot of G rows for every CTA of the
+// footprint kernel that the GPU can hold at once (grown with cudaMalloc).
+lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = gbl::footprint_occupancy(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, &per_sm)) != cudaSuccess)
+        return cuda_fail(l, e, "footprint occupancy");
+    const int n = sms * std::max(1, per_sm);
+    const size_t need = (size_t)n * G * l->n_bins;
+    if (n <= l->n_slots && need <= l->slot_floats && need / n == (size_t)G * l->n_bins) return LIDAR_OK;
+    cudaFree(l->d_slot_pool);
+    cudaFree(l->d_slot_busy);
+    l->d_slot_pool = nullptr;
+    l->d_slot_busy = nullptr;
+    l->n_slots = 0;
+    l->slot_floats = 0;
+    if ((e = cudaMalloc(&l->d_slot_pool, need * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&l->d_slot_busy, (size_t)n * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(l->d_slot_busy, 0, (size_t)n * sizeof(int))) != cudaSuccess ||
+        (!l->d_err && (e = cudaMalloc(&l->d_err, sizeof(int))) != cudaSuccess) ||
+        (e = cudaMemset(l->d_err, 0, sizeof(int))) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cuda_fail(l, e, "cudaMalloc(echo-only waveform pool)");
+    l->n_slots = n;
+    l->slot_floats = need;
+    return LIDAR_OK;
+}
+
+// Enqueues the setup and footprint kernels of one frame; wave == NULL
+// selects the echo-only form (waveforms in the pooled slots).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
                        int32_t *counts, cudaStream_t s)
 {
+    const bool tc = l->deposit != 0;
+    if (!wave) {
+        lidar_status_t st0 = ensure_slots(l, tc ? l->G_tc : l->G, tc);
+        if (st0 != LIDAR_OK) return st0;
+    }
     size_t pixels = (size_t)g->U * g->V;
     lidar_status_t st = ensure_scratch(l, pixels);
     if (st != LIDAR_OK) return st;
@@ -421,7 +461,12 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     fa.beams = l->d_beams;
     fa.n_beams = l->n_beams;
     fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
-    const bool tc = l->deposit != 0;
+    if (!wave) {
+        fa.slot_pool = l->d_slot_pool;
+        fa.slot_busy = l->d_slot_busy;
+        fa.n_slots = l->n_slots;
+        fa.err = l->d_err;
+    }
     e = gbl::launch_footprint(l->kind, tc ? l->G_tc : l->G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
     if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     if (ev2) cudaEventRecord(ev2, s);
@@ -787,6 +832,18 @@ lidar_status_t lidar_simulate(lidar_t *l, const lidar_gbuffer_t *g, const lidar_
     return enqueue(l, g, R, wave, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
+lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose,
+                                     lidar_echoes_t *echoes, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    lidar_status_t st = check_gbuffer(l, g);
+    if (st != LIDAR_OK) return st;
+    double R[9];
+    if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
+    if (!echoes || !echoes->echoes || !echoes->counts) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
+}
+
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
                                    lidar_echo_t *echoes, int32_t *counts, void *stream)
 {
@@ -944,6 +1001,16 @@ lidar_status_t lidar_sync(lidar_t *l, void *stream)
     if (e != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(l, e, "asynchronous error");
+    if (l && l->d_err) {
+        int h = 0;
+        if ((e = cudaMemcpy(&h, l->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(l, e, "error word download");
+        if (h) {
+            cudaMemset(l->d_err, 0, sizeof(int));
+            return fail(l, LIDAR_ETIMEOUT, "echo-only simulation: a CTA found no free waveform slot; its beams' "
+                                           "echoes were not written");
+        }
+    }
     return LIDAR_OK;
 }
 

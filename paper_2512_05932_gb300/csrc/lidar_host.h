@@ -51,6 +51,13 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
+    // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
+    // slot_floats / n_slots floats, their busy flags, and an error word
+    float *d_slot_pool = nullptr;
+    int *d_slot_busy = nullptr;
+    int *d_err = nullptr;
+    int n_slots = 0;
+    size_t slot_floats = 0;
     // sensor-model fingerprint (batch compatibility) and table hash
     uint64_t model_hash = 0;
     // batched execution

@@ -104,9 +104,18 @@ struct FootprintArgs {
     float c0, c1, c2;
     float rA, rB;          // range of bin-centre coordinate x: rA + x * rB
     // outputs
-    float *wave;
+    float *wave;             // beam b's waveform at wave + (b - wave_row0) * n_bins
     lidar_echo_t *echoes;
     int32_t *counts;
+    int wave_row0;
+    // echo-only simulation: each CTA keeps its beams' waveforms in a slot of
+    // slot_pool (G * n_bins floats) that it claims from slot_busy (0 free,
+    // 1 held) and frees at exit; n_slots >= the CTAs the GPU holds at once.
+    // NULL: waveforms are outputs in `wave`.
+    float *slot_pool;
+    int *slot_busy;
+    int n_slots;
+    int *err;                // set to 1 if a slot claim gives up
 };
 
 // Per-frame fields of the batched footprint kernel.
@@ -129,6 +138,7 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s);
 size_t footprint_smem_bytes(int G, const FootprintArgs &a);
 int footprint_pad(int M);
 cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem);
+cudaError_t footprint_occupancy(int kind, int G, bool tc, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem, const FootprintArgs &a,
                              cudaStream_t s);
 cudaError_t launch_setup_batch(const SetupArgs *frames, const int *pix_blk, const int *beam_blk, int n_frames,

@@ -1033,7 +1033,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         }
         if (o0 + 8 * lane < nb) {
             const size_t orow = A.out_ids ? (size_t)A.out_ids[b0 + jj] : (size_t)(b0 + jj);
-            float4 *dst = reinterpret_cast<float4 *>(A.wave + orow * nb + o0 + 8 * lane);
+            float4 *dst = reinterpret_cast<float4 *>(A.wave + (orow - (size_t)A.wave_row0) * nb + o0 + 8 * lane);
             dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
         }
@@ -1057,7 +1057,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     // run, so the scan covers [lo - M - 1, hi + M + 1]. Loads run one chunk ahead.
     for (int jj = warp; jj < gcount; jj += nwarps) {
         const int beam = A.out_ids ? A.out_ids[b0 + jj] : b0 + jj;
-        const float *xw = A.wave + (size_t)beam * nb;
+        const float *xw = A.wave + (size_t)(beam - A.wave_row0) * nb;
         lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
         const float T = A.T;
         const float ambv = amb_s[jj] * A.s_amb;
@@ -1255,11 +1255,51 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
 }
 
+// Claims a free slot of the echo-only waveform pool, starting at `start`
+// (slot = CTA index modulo the pool: usually free, as the CTA that used it
+// last has finished). Bounded: -1 after 1024 passes over the pool.
+__device__ int claim_slot(int *busy, int n, int start)
+{
+    for (int pass = 0; pass < 1024; ++pass) {
+        for (int i = 0; i < n; ++i) {
+            const int s = (start + i) % n;
+            if (atomicCAS(busy + s, 0, 1) == 0) {
+                __threadfence();
+                return s;
+            }
+        }
+        __nanosleep(1000);
+    }
+    return -1;
+}
+
 template <int KIND, int G, bool TC>
 __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_wave_kernel(FootprintArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (!A.slot_pool) {
+        footprint_group<KIND, G, TC>(A, blockIdx.x, smem_raw);
+        return;
+    }
+    // Echo-only: the group's waveforms go to a pooled slot (G rows) instead of
+    // the caller's memory. The pool holds a slot for every CTA the GPU can
+    // keep resident, so a claim finds one on its first pass.
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) s_slot = claim_slot(A.slot_busy, A.n_slots, (int)(blockIdx.x % (unsigned)A.n_slots));
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot < 0) {
+        if (threadIdx.x == 0) atomicExch(A.err, 1);
+        return;
+    }
+    A.wave = A.slot_pool + (size_t)slot * G * A.n_bins;
+    A.wave_row0 = blockIdx.x * G;
     footprint_group<KIND, G, TC>(A, blockIdx.x, smem_raw);
+    __syncthreads();  // every read of the slot (echo scan) is done
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(A.slot_busy + slot, 0);
+    }
 }
 
 // Batched form: a persistent grid whose CTAs take (frame, group) items, in the
@@ -1309,6 +1349,17 @@ cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem)
     if (kind == K && G == GG && tc == T)                                                                      \
         return cudaFuncSetAttribute(footprint_wave_kernel<K, GG, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)smem);
+    GBL_FOR_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t footprint_occupancy(int kind, int G, bool tc, int threads, size_t smem, int *blocks_per_sm)
+{
+#define GBL_CASE(K, GG, T)                                                                                       \
+    if (kind == K && G == GG && tc == T)                                                                         \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, footprint_wave_kernel<K, GG, T>, threads, \
+                                                             smem);
     GBL_FOR_EACH(GBL_CASE)
 #undef GBL_CASE
     return cudaErrorInvalidValue;

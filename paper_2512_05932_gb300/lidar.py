@@ -77,7 +77,8 @@ ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), 
 assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 
 # exported symbols (every function declared in include/lidar.h)
-SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_host", "lidar_simulate_noalloc", "lidar_sync",
+SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_simulate_host", "lidar_simulate_noalloc",
+           "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
@@ -117,6 +118,9 @@ def load(path: str = LIB_PATH):
     lib.lidar_simulate.restype = C.c_int
     lib.lidar_simulate.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                    P(lidar_echoes_t), C.c_void_p]
+    lib.lidar_simulate_echoes.restype = C.c_int
+    lib.lidar_simulate_echoes.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), P(lidar_echoes_t),
+                                          C.c_void_p]
     lib.lidar_simulate_host.restype = C.c_int
     lib.lidar_simulate_host.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
@@ -291,6 +295,13 @@ def lidar_simulate(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_wav
                    out_echoes: int, out_counts: int, stream: int = 0) -> None:
     e = lidar_echoes_t(out_echoes, out_counts)
     st = load().lidar_simulate(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
+    _check(st, handle)
+
+
+def lidar_simulate_echoes(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_echoes: int, out_counts: int,
+                          stream: int = 0) -> None:
+    e = lidar_echoes_t(out_echoes, out_counts)
+    st = load().lidar_simulate_echoes(handle, C.byref(gbuffer), C.byref(pose), C.byref(e), stream)
     _check(st, handle)
 
 
@@ -575,6 +586,21 @@ class Lidar:
         lidar_simulate(self.handle, g, make_pose(np.eye(3) if pose is None else pose), wave.data_ptr(),
                        echoes.data_ptr(), counts.data_ptr(), s)
         return wave, echoes, counts
+
+    def simulate_echoes(self, geom, planes, pose=None, outputs=None, stream=None):
+        """Echo-only form (lidar_simulate_echoes): returns (echoes, counts)."""
+        import torch
+        echoes, counts = outputs if outputs is not None else self._alloc_echoes(planes[0].device)
+        g = make_gbuffer(geom, [p.data_ptr() for p in planes])
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        lidar_simulate_echoes(self.handle, g, make_pose(np.eye(3) if pose is None else pose), echoes.data_ptr(),
+                              counts.data_ptr(), s)
+        return echoes, counts
+
+    def _alloc_echoes(self, device):
+        import torch
+        return (torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, device=device),
+                torch.empty((self.n_beams,), dtype=torch.int32, device=device))
 
     def simulate_host(self, geom, host_planes, pose=None, outputs=None, stream=None):
         """Host-memory entry point: planes and outputs are (pinned) CPU tensors."""

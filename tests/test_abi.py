@@ -117,6 +117,8 @@ def test_new_entry_points_reject_null(lib):
     g = lidar.lidar_gbuffer_t()
     with pytest.raises(lidar.LidarError):
         lidar.lidar_simulate_noalloc(None, g, lidar.make_pose(np.eye(3)), 0, 0, 0, 0)
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_simulate_echoes(None, g, lidar.make_pose(np.eye(3)), 0, 0, 0)
 
 
 def test_frame_struct_layout(lib):
