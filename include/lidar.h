@@ -69,8 +69,22 @@ typedef enum {
  *                         column i <-> u), node (i, j) at
  *                         u = (i - (w-1)/2) pitch, v = (j - (h-1)/2) pitch,
  *                         extended by one ring of zeros (P falls linearly to 0
- *                         one pitch beyond the edge nodes). Values >= 0. */
-typedef enum { LIDAR_PROFILE_RADIAL = 0, LIDAR_PROFILE_TABLE = 1 } lidar_profile_kind_t;
+ *                         one pitch beyond the edge nodes). Values >= 0.
+ *   LIDAR_PROFILE_SEPARABLE: P(u, v) = H(u) V(v), a separable kernel (the
+ *                         measured collector sensitivity of Sec. III-C is a
+ *                         product of a horizontal and a vertical profile).
+ *                         table holds H (table_w nodes along u) followed by V
+ *                         (table_h nodes along v), nodes placed as for TABLE;
+ *                         each is interpolated linearly and falls to 0 one
+ *                         pitch beyond its end nodes. This is exactly the
+ *                         TABLE profile of the outer product V[j] H[i], but
+ *                         stored and evaluated as two 1-D tables (w + h
+ *                         values instead of w h), which stay in the L1 cache. */
+typedef enum {
+    LIDAR_PROFILE_RADIAL = 0,
+    LIDAR_PROFILE_TABLE = 1,
+    LIDAR_PROFILE_SEPARABLE = 2
+} lidar_profile_kind_t;
 
 typedef struct {
     int32_t kind;          /* lidar_profile_kind_t */
@@ -79,10 +93,11 @@ typedef struct {
     double tail_core_deg;
     double tail_pow;
     double trunc_deg;      /* RADIAL support radius, (0, 10] degrees */
-    int32_t table_w;       /* TABLE: 2..4096 */
-    int32_t table_h;       /* TABLE: 2..4096 */
-    double pitch_deg;      /* TABLE node spacing; half-diagonal of the support <= 10 deg */
-    const float *table;    /* TABLE: host pointer, [table_h][table_w], copied at create */
+    int32_t table_w;       /* TABLE, SEPARABLE: 2..4096 */
+    int32_t table_h;       /* TABLE, SEPARABLE: 2..4096 */
+    double pitch_deg;      /* node spacing; half-diagonal of the support <= 10 deg */
+    const float *table;    /* host pointer, copied at create: TABLE [table_h][table_w];
+                              SEPARABLE H[table_w] then V[table_h] */
 } lidar_profile_t;
 
 /* Beam set B with centre directions Psi_b (Sec. II-A), sensor frame.
@@ -194,9 +209,10 @@ lidar_status_t lidar_simulate(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, co
 
 /* Echo-only simulation: what a sensor reports (its echoes, Sec. II-C: echo
  * range, EPW and intensity per return), without the waveforms. Same
- * computation and results as lidar_simulate (echoes and counts are
- * bit-identical); the difference is where each beam's waveform goes between
- * the pulse convolution and the echo scan. Each CTA of the footprint kernel
+ * computation and results as lidar_simulate (up to the order of the FP32
+ * deposit additions, which varies from run to run in both); the difference
+ * is where each beam's waveform goes between the pulse convolution and the
+ * echo scan. Each CTA of the footprint kernel
  * claims a slot of a library-owned pool sized for the CTAs the GPU holds at
  * once (SMs x resident CTAs x beams per CTA x n_bins floats, about 20 MB for
  * a 2048-bin sensor on 152 SMs), writes its beams' waveforms there, scans
