@@ -63,6 +63,9 @@ def parse():
                     help="kernel of the network's dense layers (--tail net)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: a 2048x1024 frame of the wide-tail scene with 100x80 beams (for profiler captures)")
+    ap.add_argument("--profile", default="table", choices=["table", "separable"],
+                    help="frame workload: the 401x401 table, or the separable profile H(u) V(v) of its "
+                         "centre row and column (two 401-node tables)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
                     help="network weights of --tail net")
     return ap.parse_args()
@@ -73,6 +76,7 @@ DEPOSIT = {"atomic": 0, "tc_split": 1, "tc_bf16": 2}
 
 
 SIZE = "full"
+PROFILE = "table"
 CONV_FLOPS_PER_BEAM = 2 * (1024 * 32 * 18 + 256 * 32 * 306 + 64 * 32 * 306)  # three convolutions
 
 
@@ -82,6 +86,14 @@ def workload():
         return scenes.wide_frame(U=2048, V=1024, n_az=100, n_el=80)
     if WORKLOAD in ("wide", "split"):
         return scenes.wide_frame()
+    if PROFILE == "separable":
+        w = scenes.full_frame_boxes()
+        t = np.asarray(w.profile["table"], np.float64)
+        c = t.shape[0] // 2
+        w.profile = scenes.separable_profile(t[c, :] / np.sqrt(t[c, c]), t[:, c] / np.sqrt(t[c, c]),
+                                             w.profile["pitch_deg"])
+        w.name = w.name.replace("table401", "separable401")
+        return w
     return scenes.full_frame_boxes()
 
 
@@ -94,7 +106,8 @@ def config_of(w, extra=None):
              "max_echoes": int(w.calib["max_echoes"]), "seed": 5}
     else:
         c = {"workload": w.name, "gbuffer": f"{gb.U}x{gb.V}", "fov_deg": "120x30", "beams": int(len(w.dirs)),
-             "pattern": "linescan 16x1600", "profile": "table 401x401 @0.01deg", "n_bins": int(w.pulse["n_bins"]),
+             "pattern": "linescan 16x1600", "profile": ("separable 401+401 @0.01deg (centre row x column of the table)" if PROFILE == "separable"
+                         else "table 401x401 @0.01deg"), "n_bins": int(w.pulse["n_bins"]),
              "dt_ns": w.pulse["dt_s"] * 1e9, "max_echoes": int(w.calib["max_echoes"]), "seed": 2}
     if extra:
         c.update(extra)
@@ -712,10 +725,11 @@ def run_batch(args, rank, world, local_rank):
 
 
 def main():
-    global WORKLOAD, SIZE
+    global WORKLOAD, SIZE, PROFILE
     args = parse()
     WORKLOAD = args.workload
     SIZE = args.size
+    PROFILE = args.profile
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -42,11 +42,12 @@ enum { ORC_CLIPPED_START = 1u, ORC_CLIPPED_END = 2u, ORC_NEAR_THRESHOLD = 4u,
        ORC_PEAK_AMBIGUOUS = 8u };
 
 typedef struct {
-    int32_t kind; /* 0 radial analytic, 1 table */
+    int32_t kind; /* 0 radial analytic, 1 table, 2 separable H(u) V(v) */
     double sigma_deg, tail_amp, tail_core_deg, tail_pow, trunc_deg;
     int32_t tw, th;
     double pitch_deg;
-    const float *table; /* [th][tw], row j <-> v, column i <-> u */
+    const float *table; /* kind 1: [th][tw], row j <-> v, column i <-> u;
+                           kind 2: H[tw] (nodes along u) then V[th] (nodes along v) */
 } orc_profile;
 
 typedef struct {
@@ -75,6 +76,17 @@ typedef struct {
 /* Profile kappa*eta (Eq. centered kernel; Sec. III combined kernel)         */
 /* ------------------------------------------------------------------------ */
 
+/* Linear interpolation of n nodes t[0..n) at fractional index f, zero
+ * beyond the end nodes (the value falls to 0 one node spacing outside). */
+static double orc_lerp_nodes(const float *t, long n, double f)
+{
+    double f0 = floor(f), a = f - f0, val = 0.0;
+    long i = (long)f0;
+    if (i >= 0 && i < n) val += (1.0 - a) * (double)t[i];
+    if (i + 1 >= 0 && i + 1 < n) val += a * (double)t[i + 1];
+    return val;
+}
+
 /* Unnormalised profile value at local offset (u, v) in degrees. */
 double orc_profile_raw(const orc_profile *p, double u, double v)
 {
@@ -85,6 +97,12 @@ double orc_profile_raw(const orc_profile *p, double u, double v)
         double t = 1.0;
         if (th > p->tail_core_deg) t = pow(th / p->tail_core_deg, -p->tail_pow);
         return g + p->tail_amp * t;
+    }
+    if (p->kind == 2) {
+        /* separable kernel (Sec. III-C: horizontal times vertical profile) */
+        double fi = u / p->pitch_deg + 0.5 * (p->tw - 1);
+        double fj = v / p->pitch_deg + 0.5 * (p->th - 1);
+        return orc_lerp_nodes(p->table, p->tw, fi) * orc_lerp_nodes(p->table + p->tw, p->th, fj);
     }
     /* bilinear interpolation of the table extended by zeros beyond its edge */
     double fi = u / p->pitch_deg + 0.5 * (p->tw - 1);

@@ -115,6 +115,14 @@ def _profile(prof, keep):
     if s.kind == 0:
         for k in ("sigma_deg", "tail_amp", "tail_core_deg", "tail_pow", "trunc_deg"):
             setattr(s, k, float(prof[k]))
+    elif s.kind == 2:
+        h = np.ascontiguousarray(prof["h"], dtype=np.float32)
+        v = np.ascontiguousarray(prof["v"], dtype=np.float32)
+        t = np.ascontiguousarray(np.concatenate([h, v]), dtype=np.float32)
+        keep.append(t)
+        s.tw, s.th = len(h), len(v)
+        s.pitch_deg = float(prof["pitch_deg"])
+        s.table = _fptr(t)
     else:
         t = np.ascontiguousarray(prof["table"], dtype=np.float32)
         keep.append(t)

@@ -204,7 +204,7 @@ lidar_status_t check_create(const lidar_profile_t *p, const lidar_pattern_t *pat
             return fail(nullptr, LIDAR_EINVAL, "profile.tail_pow must be >= 0");
         if (!finite_pos(p->trunc_deg) || p->trunc_deg > kMaxSupportDeg)
             return fail(nullptr, LIDAR_EINVAL, "profile.trunc_deg must be in (0, 10]");
-    } else if (p->kind == LIDAR_PROFILE_TABLE) {
+    } else if (p->kind == LIDAR_PROFILE_TABLE || p->kind == LIDAR_PROFILE_SEPARABLE) {
         if (p->table_w < 2 || p->table_h < 2 || p->table_w > 4096 || p->table_h > 4096)
             return fail(nullptr, LIDAR_EINVAL, "profile table size must be 2..4096 per side");
         if (!p->table) return fail(nullptr, LIDAR_EINVAL, "profile.table is NULL");
@@ -212,7 +212,9 @@ lidar_status_t check_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         double hu = (0.5 * (p->table_w - 1) + 1) * p->pitch_deg, hv = (0.5 * (p->table_h - 1) + 1) * p->pitch_deg;
         if (std::sqrt(hu * hu + hv * hv) > kMaxSupportDeg)
             return fail(nullptr, LIDAR_EINVAL, "profile table support exceeds 10 degrees");
-        for (long i = 0; i < (long)p->table_w * p->table_h; ++i)
+        const long nv = p->kind == LIDAR_PROFILE_SEPARABLE ? (long)p->table_w + p->table_h
+                                                           : (long)p->table_w * p->table_h;
+        for (long i = 0; i < nv; ++i)
             if (!(std::isfinite(p->table[i]) && p->table[i] >= 0.f))
                 return fail(nullptr, LIDAR_EINVAL, "profile.table[%ld] is negative or not finite", i);
     } else {
@@ -335,6 +337,7 @@ void free_all(lidar_t *l)
     free_events(l);
     cudaFree(l->d_dirs);
     cudaFree(l->d_quads);
+    cudaFree(l->d_pairs);
     cudaFree(l->d_taps);
     cudaFree(l->d_beams);
     cudaFree(l->d_rec);
@@ -387,6 +390,9 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
     fa.invZ = (float)(1.0 / l->Z);
     fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
+    fa.sep = l->separable ? 1 : 0;
+    fa.hpairs = l->d_pairs;
+    fa.vpairs = l->d_pairs ? l->d_pairs + l->qw : nullptr;
     fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
     fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
     fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
@@ -666,7 +672,8 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     lidar_t *l = new (std::nothrow) lidar();
     if (!l) return fail(nullptr, LIDAR_ENOMEM, "host allocation failed");
     l->n_beams = pat->n_beams;
-    l->kind = p->kind;
+    l->kind = p->kind == LIDAR_PROFILE_SEPARABLE ? LIDAR_PROFILE_TABLE : p->kind;
+    l->separable = p->kind == LIDAR_PROFILE_SEPARABLE;
     l->n_bins = pu->n_bins;
     l->dt = pu->dt_s;
     l->t0 = pu->t0_s;
@@ -676,6 +683,7 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
 
     // profile normalisation and device form
     std::vector<float4> quads;
+    std::vector<float2> pairs;
     if (p->kind == LIDAR_PROFILE_RADIAL) {
         l->Z = radial_norm(p);
         double s = p->sigma_deg * kDeg, tc = p->tail_core_deg * kDeg, tr = p->trunc_deg * kDeg;
@@ -690,16 +698,26 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         std::vector<double> padded((size_t)pw * ph, 0.0);
         for (int j = 0; j < p->table_h; ++j)
             for (int i = 0; i < p->table_w; ++i)
-                padded[(size_t)(j + 1) * pw + i + 1] = p->table[(size_t)j * p->table_w + i];
+                padded[(size_t)(j + 1) * pw + i + 1] =
+                    l->separable ? (double)p->table[p->table_w + j] * p->table[i] : p->table[(size_t)j * p->table_w + i];
         l->Z = table_norm(p, padded, pw, ph);
         l->qw = p->table_w + 1;
         l->qh = p->table_h + 1;
-        quads.resize((size_t)l->qw * l->qh);
-        for (int j = 0; j < l->qh; ++j)
-            for (int i = 0; i < l->qw; ++i) {
-                auto at = [&](int ii, int jj) { return (float)(padded[(size_t)jj * pw + ii] / l->Z); };
-                quads[(size_t)j * l->qw + i] = make_float4(at(i, j), at(i + 1, j), at(i, j + 1), at(i + 1, j + 1));
-            }
+        if (l->separable) {
+            // zero-padded H (divided by Z) and V as pairs of consecutive nodes
+            auto hz = [&](int i) { return (i < 1 || i > p->table_w) ? 0.0 : p->table[i - 1] / l->Z; };
+            auto vz = [&](int j) { return (j < 1 || j > p->table_h) ? 0.0 : (double)p->table[p->table_w + j - 1]; };
+            for (int i = 0; i < l->qw; ++i) pairs.push_back(make_float2((float)hz(i), (float)hz(i + 1)));
+            for (int j = 0; j < l->qh; ++j) pairs.push_back(make_float2((float)vz(j), (float)vz(j + 1)));
+        } else {
+            quads.resize((size_t)l->qw * l->qh);
+            for (int j = 0; j < l->qh; ++j)
+                for (int i = 0; i < l->qw; ++i) {
+                    auto at = [&](int ii, int jj) { return (float)(padded[(size_t)jj * pw + ii] / l->Z); };
+                    quads[(size_t)j * l->qw + i] =
+                        make_float4(at(i, j), at(i + 1, j), at(i, j + 1), at(i + 1, j + 1));
+                }
+        }
         l->tk = (float)(1.0 / (p->pitch_deg * kDeg));
         l->tcu = (float)(0.5 * (p->table_w - 1) + 1.0);
         l->tcv = (float)(0.5 * (p->table_h - 1) + 1.0);
@@ -742,11 +760,12 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         };
         double md[12] = {l->Z, l->dt, l->t0, l->T, l->s_amb, l->coef[0], l->coef[1], l->coef[2],
                          (double)l->kg, (double)l->trunc2, (double)l->tail_amp, (double)l->tail_hp};
-        int32_t mi[6] = {l->kind, l->n_bins, l->M, l->max_echoes, l->qw, l->qh};
+        int32_t mi[7] = {l->kind, l->n_bins, l->M, l->max_echoes, l->qw, l->qh, l->separable ? 1 : 0};
         mix(md, sizeof md);
         mix(mi, sizeof mi);
-        if (p->kind == LIDAR_PROFILE_TABLE) {
-            mix(p->table, (size_t)p->table_w * p->table_h * sizeof(float));
+        if (p->kind == LIDAR_PROFILE_TABLE || p->kind == LIDAR_PROFILE_SEPARABLE) {
+            mix(p->table, (p->kind == LIDAR_PROFILE_SEPARABLE ? (size_t)p->table_w + p->table_h
+                                                              : (size_t)p->table_w * p->table_h) * sizeof(float));
             mix(&p->pitch_deg, sizeof p->pitch_deg);
         } else {
             double pr[5] = {p->sigma_deg, p->tail_amp, p->tail_core_deg, p->tail_pow, p->trunc_deg};
@@ -813,6 +832,15 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
             free_all(l);
             delete l;
             return cuda_fail(nullptr, e, "profile table upload");
+        }
+    }
+    if (!pairs.empty()) {
+        if ((e = cudaMalloc(&l->d_pairs, pairs.size() * sizeof(float2))) != cudaSuccess ||
+            (e = cudaMemcpy(l->d_pairs, pairs.data(), pairs.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+            free_all(l);
+            delete l;
+            return cuda_fail(nullptr, e, "separable profile upload");
         }
     }
     *out = l;

@@ -15,7 +15,8 @@ struct TailState;
 struct lidar {
     // sensor
     int32_t n_beams = 0;
-    int32_t kind = 0;
+    int32_t kind = 0;          // kernel form: RADIAL or TABLE (a separable profile runs as TABLE)
+    bool separable = false;    // LIDAR_PROFILE_SEPARABLE: pairs of H and V instead of quads
     double Z = 0.0;
     double support_rad = 0.0;
     // radial profile
@@ -41,6 +42,7 @@ struct lidar {
     // device memory owned by the library
     float *d_dirs = nullptr;
     float4 *d_quads = nullptr;
+    float2 *d_pairs = nullptr;  // separable: qw H pairs, then qh V pairs
     float *d_taps = nullptr;
     gbl::BeamParam *d_beams = nullptr;
     float4 *d_rec = nullptr;

@@ -71,6 +71,9 @@ struct FootprintArgs {
     float invZ;
     const float4 *quads;   // (h+1) rows of (w+1) corner quads, already divided by Z (table)
     int qw, qh;
+    int sep;               // separable table: P = H(u) V(v) instead of the quads
+    const float2 *hpairs;  // [qw]: (H[i], H[i+1]) of the zero-padded H, divided by Z
+    const float2 *vpairs;  // [qh]: (V[j], V[j+1]) of the zero-padded V
     float tk, tcu, tcv;    // table coordinate = offset_rad * tk + tc{u,v}
     // pulse and bins
     int n_bins, nch, M, R;

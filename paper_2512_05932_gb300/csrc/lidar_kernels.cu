@@ -342,9 +342,9 @@ __device__ __forceinline__ float ex2_approx(float x)
 }
 
 struct ProfFetch {
-    float4 q;      // table: the 4 corner values; radial: q.x = weight
+    float4 q;      // table: the 4 corner values; separable: H pair, V pair; radial: q.x = weight
     float fx, fy;
-    bool ok;
+    bool ok, sep;
 };
 
 template <int KIND>
@@ -379,7 +379,15 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
         r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
         r.fx = fu - iu;
         r.fy = fv - iv;
-        r.q = r.ok ? __ldg(A.quads + (size_t)j * A.qw + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.sep = A.sep != 0;
+        if (!r.ok) {
+            r.q = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (r.sep) {
+            const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
+            r.q = make_float4(h.x, h.y, v.x, v.y);
+        } else {
+            r.q = __ldg(A.quads + (size_t)j * A.qw + i);
+        }
     }
     return r;
 }
@@ -405,6 +413,7 @@ __device__ __forceinline__ float profile_finish(const ProfFetch &r)
 {
     if (!r.ok) return 0.f;
     if (KIND == LIDAR_PROFILE_RADIAL) return r.q.x;
+    if (r.sep) return fmaf(r.fx, r.q.y - r.q.x, r.q.x) * fmaf(r.fy, r.q.w - r.q.z, r.q.z);
     float top = fmaf(r.fx, r.q.y - r.q.x, r.q.x);
     float bot = fmaf(r.fx, r.q.w - r.q.z, r.q.z);
     return fmaf(r.fy, bot - top, top);

@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblidar_gb300.so")
 
 LIDAR_OK, LIDAR_EINVAL, LIDAR_ENOMEM, LIDAR_ECUDA, LIDAR_ETIMEOUT, LIDAR_ENUMERIC = range(6)
-LIDAR_PROFILE_RADIAL, LIDAR_PROFILE_TABLE = 0, 1
+LIDAR_PROFILE_RADIAL, LIDAR_PROFILE_TABLE, LIDAR_PROFILE_SEPARABLE = 0, 1, 2
 ECHO_CLIPPED_START, ECHO_CLIPPED_END, ECHO_NEAR_THRESHOLD = 1, 2, 4
 
 
@@ -218,6 +218,14 @@ def make_profile(prof: dict, keep: list) -> lidar_profile_t:
     if p.kind == LIDAR_PROFILE_RADIAL:
         for k in ("sigma_deg", "tail_amp", "tail_core_deg", "tail_pow", "trunc_deg"):
             setattr(p, k, float(prof[k]))
+    elif p.kind == LIDAR_PROFILE_SEPARABLE:
+        h = np.ascontiguousarray(prof["h"], dtype=np.float32)
+        v = np.ascontiguousarray(prof["v"], dtype=np.float32)
+        t = np.ascontiguousarray(np.concatenate([h, v]), dtype=np.float32)
+        keep.append(t)
+        p.table_w, p.table_h = len(h), len(v)
+        p.pitch_deg = float(prof["pitch_deg"])
+        p.table = t.ctypes.data_as(C.POINTER(C.c_float))
     else:
         t = np.ascontiguousarray(prof["table"], dtype=np.float32)
         keep.append(t)

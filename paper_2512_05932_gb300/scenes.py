@@ -304,6 +304,23 @@ def table_profile(table, pitch_deg):
     return dict(kind=1, table=table, table_w=table.shape[1], table_h=table.shape[0], pitch_deg=pitch_deg)
 
 
+def separable_profile(h, v, pitch_deg):
+    """P(u, v) = H(u) V(v): nodes of H along u and of V along v, centred, at pitch_deg."""
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    return dict(kind=2, h=h, v=v, pitch_deg=pitch_deg)
+
+
+def separable_gauss_tail(n_u, n_v, pitch_deg, sigma_u, sigma_v, tail_amp=0.0, tail_core=0.05, tail_pow=3.0):
+    """1-D profiles exp(-x^2 / 2 s^2) + tail_amp min(1, (|x| / core)^-pow) on
+    n nodes at pitch_deg along u and v (an anisotropic separable beam)."""
+    def prof(n, s):
+        x = (np.arange(n) - 0.5 * (n - 1)) * pitch_deg
+        ax = np.maximum(np.abs(x), 1e-12)
+        return np.exp(-0.5 * (x / s) ** 2) + tail_amp * np.minimum(1.0, (ax / tail_core) ** -tail_pow)
+    return separable_profile(prof(n_u, sigma_u), prof(n_v, sigma_v), pitch_deg)
+
+
 def pulse(n_bins=1024, dt_s=0.1e-9, t0_s=0.0, fwhm_s=4e-9, trunc_sigmas=6.0):
     return dict(n_bins=n_bins, dt_s=dt_s, t0_s=t0_s, fwhm_s=fwhm_s, trunc_sigmas=trunc_sigmas)
 

@@ -88,6 +88,36 @@ def test_table_norm_closed_form(orc):
         assert Z == pytest.approx(2 * math.pi * su * sv * DEG * DEG, rel=2e-6)
 
 
+def test_separable_profile_is_the_outer_product_table(orc):
+    # H(u) V(v) with 1-D linear interpolation must equal the bilinear table of
+    # the outer product V[j] H[i] everywhere (nodes, cell interiors, the zero
+    # ring and beyond), and integrate to the same Z
+    g = np.random.default_rng(11)
+    h = g.uniform(0.1, 2.0, 7).astype(np.float32)
+    v = g.uniform(0.1, 2.0, 5).astype(np.float32)
+    sep = S.separable_profile(h, v, 0.1)
+    tab = S.table_profile(np.outer(v.astype(np.float64), h.astype(np.float64)), 0.1)
+    for j in range(5):
+        for i in range(7):
+            u_, v_ = (i - 3) * 0.1, (j - 2) * 0.1
+            assert orc.profile_raw(sep, u_, v_)[0] == pytest.approx(float(h[i]) * float(v[j]), rel=1e-12)
+    uu = g.uniform(-0.5, 0.5, 200)
+    vv = g.uniform(-0.4, 0.4, 200)
+    np.testing.assert_allclose(orc.profile_raw(sep, uu, vv), orc.profile_raw(tab, uu, vv), rtol=1e-6, atol=1e-12)
+    assert orc.profile_raw(sep, 0.41, 0.0)[0] == 0.0 and orc.profile_raw(sep, 0.0, 0.31)[0] == 0.0
+    # u runs along H, v along V: swapping the tables must change the value
+    assert orc.profile_raw(sep, 0.3, 0.0)[0] != pytest.approx(orc.profile_raw(
+        S.separable_profile(v, h, 0.1), 0.3, 0.0)[0], rel=1e-3)
+    assert orc.profile_norm(sep) == pytest.approx(orc.profile_norm(tab), rel=1e-6)
+
+
+def test_separable_gauss_norm_closed_form(orc):
+    # a product of sampled 1-D Gaussians integrates to 2 pi su sv (small angles)
+    for su, sv in ((0.05, 0.05), (0.05, 0.1)):
+        prof = S.separable_gauss_tail(121, 161, 0.01, su, sv)
+        assert orc.profile_norm(prof) == pytest.approx(2 * math.pi * su * sv * DEG * DEG, rel=2e-6)
+
+
 # --------------------------------------------------------------------------
 # beam frame and local offsets
 # --------------------------------------------------------------------------
@@ -440,6 +470,24 @@ def test_anisotropic_table_axes_and_roll(orc):
     roll = S.pose_ypr(0.0, 0.0, math.pi / 2)
     ra2 = orc.simulate(gba, S._dirs_from_angles([0.0], [x0 * DEG]), prof, PU1, CAL1, pose=roll)
     # the sensor-frame elevation offset becomes a G-buffer azimuth offset
+    assert _split(ra2) == pytest.approx(Phi(x0, sv), abs=2e-3)
+
+
+def test_anisotropic_separable_axes_and_roll(orc):
+    # the separable form of the same anisotropic Gaussian: sigma_u along
+    # azimuth, sigma_v along elevation, swapped by a 90 deg roll
+    su, sv = 0.05, 0.1
+    prof = S.separable_gauss_tail(81, 161, 0.01, su, sv)
+    x0 = 0.04
+    gba = _edge_scene(x_edge_az=0.0)
+    gbe = _edge_scene(el_edge=0.0)
+    Phi = lambda x, s: 0.5 * (1 + special.erf(x / (s * math.sqrt(2))))
+    ra = orc.simulate(gba, S._dirs_from_angles([-x0 * DEG], [0.0]), prof, PU1, CAL1)
+    re = orc.simulate(gbe, S._dirs_from_angles([0.0], [-x0 * DEG]), prof, PU1, CAL1)
+    assert _split(ra) == pytest.approx(Phi(x0, su), abs=2e-3)
+    assert _split(re) == pytest.approx(Phi(x0, sv), abs=2e-3)
+    roll = S.pose_ypr(0.0, 0.0, math.pi / 2)
+    ra2 = orc.simulate(gba, S._dirs_from_angles([0.0], [x0 * DEG]), prof, PU1, CAL1, pose=roll)
     assert _split(ra2) == pytest.approx(Phi(x0, sv), abs=2e-3)
 
 

@@ -34,8 +34,9 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def run_gpu(w, host=False):
+def run_gpu(w, host=False, deposit=0):
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    lidar.lidar_set_deposit(L.handle, deposit)
     if host:
         planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
         wave, ech, cnt = L.simulate_host(w.gbuffer, planes, w.pose)
@@ -96,8 +97,8 @@ def compare(ref, wave, ech, cnt, beams, T, max_echoes, pulse=None, tol_l2=1e-3):
     return stats
 
 
-def check_workload(w, beams=None, host=False, max_ambiguous_frac=0.02):
-    L, wave, ech, cnt = run_gpu(w, host)
+def check_workload(w, beams=None, host=False, max_ambiguous_frac=0.02, deposit=0):
+    L, wave, ech, cnt = run_gpu(w, host, deposit)
     if beams is None:
         beams = np.arange(len(w.dirs), dtype=np.int32)
     ref = O.simulate_workload(w, beams=beams, nthreads=NTHREADS, max_out=8)
@@ -141,6 +142,32 @@ def test_table_profile_anisotropic_with_roll():
     w.profile = S.table_profile(S.elliptic_gauss_table(41, 81, 0.01, 0.05, 0.1), 0.01)
     w.pose = S.pose_ypr(0.001, 0.002, 0.6)
     check_workload(w, beams=np.arange(0, 512, 3, dtype=np.int32))
+
+
+@pytest.mark.parametrize("deposit", [0, 1])
+def test_separable_profile_anisotropic_with_roll_and_tail(deposit):
+    """Separable profile H(u) V(v) (two 1-D tables, sigma 0.05 / 0.1 deg with a
+    power-law tail on each axis) under a rolled pose, in the atomic and the
+    tensor-core deposit forms."""
+    w = S.small_plane_retro()
+    w.profile = S.separable_gauss_tail(61, 101, 0.01, 0.05, 0.1, tail_amp=1e-3)
+    w.pose = S.pose_ypr(0.001, 0.002, 0.6)
+    st = check_workload(w, beams=np.arange(0, 512, 3, dtype=np.int32), deposit=deposit)
+    assert st["echoes"] > 100
+
+
+def test_separable_equals_outer_product_table_on_gpu():
+    """The separable kernel path and the table path on the outer-product
+    table give the same waveforms up to FP32 rounding."""
+    w = S.small_plane_retro()
+    prof = S.separable_gauss_tail(41, 81, 0.01, 0.05, 0.1, tail_amp=1e-3)
+    w.profile = prof
+    _, wave_s, _, cnt_s = run_gpu(w)
+    w.profile = S.table_profile(np.outer(prof["v"].astype(np.float64), prof["h"].astype(np.float64)), 0.01)
+    _, wave_t, _, cnt_t = run_gpu(w)
+    rel = np.linalg.norm(wave_s - wave_t, axis=1) / np.maximum(np.linalg.norm(wave_t, axis=1), 1e-30)
+    assert rel.max() <= 1e-5, rel.max()
+    assert (cnt_s == cnt_t).mean() >= 0.99
 
 
 def test_ragged_beam_count_and_min_bins():
