@@ -63,6 +63,9 @@ def parse():
                     help="kernel of the network's dense layers (--tail net)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: a 2048x1024 frame of the wide-tail scene with 100x80 beams (for profiler captures)")
+    ap.add_argument("--stack-kernel", default="general", choices=["general", "separable"],
+                    help="stack workload: the 69x69 kernel, or the separable kernel of its centre column x row "
+                         "(row and column passes)")
     ap.add_argument("--profile", default="table", choices=["table", "separable"],
                     help="frame workload: the 401x401 table, or the separable profile H(u) V(v) of its "
                          "centre row and column (two 401-node tables)")
@@ -587,7 +590,12 @@ def run_stack(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w, k, dr, rmax, thr = stack_workload()
     gb = w.gbuffer
-    st = lidar.RangeStack(k, thr, dr, rmax)
+    sep = None
+    if args.stack_kernel == "separable":
+        c = k.shape[0] // 2
+        sep = ((k[:, c] / np.sqrt(k[c, c])).astype(np.float32), (k[c, :] / np.sqrt(k[c, c])).astype(np.float32))
+        k = np.outer(sep[0].astype(np.float64), sep[1].astype(np.float64)).astype(np.float32)
+    st = lidar.RangeStack(None if sep else k, thr, dr, rmax, separable=sep)
     planes = lidar.gbuffer_to_device(gb, dev)
     g = lidar.make_gbuffer(gb, [p.data_ptr() for p in planes])
     s_out = torch.empty((gb.V, gb.U), dtype=torch.int32, device=dev)
@@ -635,8 +643,10 @@ def run_stack(args, rank, world, local_rank):
                 "value": world * npx / (ms * 1e-3), "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"boxes_{gb.U}x{gb.V}_stack_kernel69_1200slices", "gbuffer": f"{gb.U}x{gb.V}",
-                           "kernel": "69x69 px (table profile sampled at the pixel pitch)", "dr_m": dr,
+                "config": {"workload": f"boxes_{gb.U}x{gb.V}_stack_kernel69_1200slices"
+                                       + ("_separable" if sep else ""), "gbuffer": f"{gb.U}x{gb.V}",
+                           "kernel": ("69+69 px separable (centre column x row of the 69x69 kernel)" if sep else
+                                      "69x69 px (table profile sampled at the pixel pitch)"), "dr_m": dr,
                            "r_max_m": rmax, "slices": int(math.floor(rmax / dr)), "threshold": thr,
                            "echo_pixels": echoes, "l2": "flushed between timed steps (258 MB write)"},
                 "roofline": {"bound": "hbm", "kernel": "range stacking step", "achieved": achieved, "peak": peak,

@@ -43,6 +43,27 @@ typedef struct {
  * LIDAR_ENOMEM, LIDAR_ECUDA. */
 lidar_status_t lidar_stack_create(const lidar_stack_params_t *p, lidar_stack_t **out);
 
+/* A separable kernel K[a][b] = col[a] row[b] (Sec. III-C: the measured
+ * collector profile is a product of a vertical and a horizontal profile;
+ * Alg. 2's convolution then splits into a row pass and a column pass).
+ * Same definition and results as lidar_stack_create with that K (up to FP32
+ * summation order); the GPU convolves each slice present in a 32x32-pixel
+ * output tile with the row vector along every row of the tile's region, then
+ * with the column vector, nearest slice first, so an output costs kh + kw
+ * multiply-adds per slice instead of kh kw. Slices too weak to reach the
+ * threshold anywhere in the tile are skipped as in the general form. */
+typedef struct {
+    int32_t kh, kw;       /* odd, 1..129 */
+    const float *col;     /* host, [kh] (vertical, along v), finite and >= 0; copied at create */
+    const float *row;     /* host, [kw] (horizontal, along u), finite and >= 0; copied at create */
+    double threshold;     /* > 0 */
+    double dr;            /* range resolution (m), > 0 */
+    double r_max;         /* maximum range (m); 1 <= floor(r_max / dr) <= 65535 */
+} lidar_stack_sep_params_t;
+
+/* As lidar_stack_create, for K = col row^T. Errors as lidar_stack_create. */
+lidar_status_t lidar_stack_create_separable(const lidar_stack_sep_params_t *p, lidar_stack_t **out);
+
 /* One frame: g as for lidar_simulate (device planes, not modified);
  * out_slice ([V][U] int32) and out_intensity ([V][U] float) are device
  * buffers owned by the caller. Per-pixel scratch (6 bytes per pixel) is

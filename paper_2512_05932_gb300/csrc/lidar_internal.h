@@ -107,10 +107,9 @@ struct FootprintArgs {
     float c0, c1, c2;
     float rA, rB;          // range of bin-centre coordinate x: rA + x * rB
     // outputs
-    float *wave;             // beam b's waveform at wave + (b - wave_row0) * n_bins
+    float *wave;             // [n_beams][n_bins] (unless slot_pool is set)
     lidar_echo_t *echoes;
     int32_t *counts;
-    int wave_row0;
     // echo-only simulation: each CTA keeps its beams' waveforms in a slot of
     // slot_pool (G * n_bins floats) that it claims from slot_busy (0 free,
     // 1 held) and frees at exit; n_slots >= the CTAs the GPU holds at once.

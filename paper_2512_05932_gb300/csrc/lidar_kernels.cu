@@ -344,8 +344,13 @@ __device__ __forceinline__ float ex2_approx(float x)
 struct ProfFetch {
     float4 q;      // table: the 4 corner values; separable: H pair, V pair; radial: q.x = weight
     float fx, fy;
-    bool ok, sep;
+    bool ok;
 };
+
+// Echo-only form: the waveform-pool slot of this CTA (written by
+// footprint_wave_kernel when FootprintArgs::slot_pool is set, read by the
+// pulse convolution and the echo scan).
+__shared__ int s_wave_slot;
 
 template <int KIND>
 __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float x, float y, bool act,
@@ -379,10 +384,9 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
         r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
         r.fx = fu - iu;
         r.fy = fv - iv;
-        r.sep = A.sep != 0;
         if (!r.ok) {
             r.q = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else if (r.sep) {
+        } else if (A.sep) {
             const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
             r.q = make_float4(h.x, h.y, v.x, v.y);
         } else {
@@ -409,11 +413,11 @@ __device__ __forceinline__ void wide_flush(float *hj, uint32_t key, float a0, fl
 }
 
 template <int KIND>
-__device__ __forceinline__ float profile_finish(const ProfFetch &r)
+__device__ __forceinline__ float profile_finish(const FootprintArgs &A, const ProfFetch &r)
 {
     if (!r.ok) return 0.f;
     if (KIND == LIDAR_PROFILE_RADIAL) return r.q.x;
-    if (r.sep) return fmaf(r.fx, r.q.y - r.q.x, r.q.x) * fmaf(r.fy, r.q.w - r.q.z, r.q.z);
+    if (A.sep) return fmaf(r.fx, r.q.y - r.q.x, r.q.x) * fmaf(r.fy, r.q.w - r.q.z, r.q.z);
     float top = fmaf(r.fx, r.q.y - r.q.x, r.q.x);
     float bot = fmaf(r.fx, r.q.w - r.q.z, r.q.z);
     return fmaf(r.fy, bot - top, top);
@@ -593,7 +597,7 @@ __device__ __forceinline__ float phase1_tc(const FootprintArgs &A, const Layout 
                     const bool front = act && fmaf(-Kc, tt.y, cdEl) > 0.f;
                     float x = fmaf(ax, tt.x, fmaf(bx, tt.y, cx));
                     float y = fmaf(ay, tt.x, fmaf(by, tt.y, cy));
-                    Pw[u] = profile_finish<KIND>(profile_fetch<KIND>(A, x, y, front));
+                    Pw[u] = profile_finish<KIND>(A, profile_fetch<KIND>(A, x, y, front));
                     amb_acc = fmaf(Pw[u], a, amb_acc);
                 }
 #pragma unroll
@@ -850,7 +854,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 for (int u = 0; u < 2; ++u) {
                     uint32_t kab = __float_as_uint(r0[u].x);
                     float a = r0[u].y;
-                    float Pw = profile_finish<KIND>(pf[u]);
+                    float Pw = profile_finish<KIND>(A, pf[u]);
                     if (!(Pw > 0.f)) continue;
                     amb_acc = fmaf(Pw, a, amb_acc);
                     if (kab == kNoDeposit) continue;
@@ -1042,7 +1046,8 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         }
         if (o0 + 8 * lane < nb) {
             const size_t orow = A.out_ids ? (size_t)A.out_ids[b0 + jj] : (size_t)(b0 + jj);
-            float4 *dst = reinterpret_cast<float4 *>(A.wave + (orow - (size_t)A.wave_row0) * nb + o0 + 8 * lane);
+            float *wrow = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * G + jj) * nb : A.wave + orow * nb;
+            float4 *dst = reinterpret_cast<float4 *>(wrow + o0 + 8 * lane);
             dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
         }
@@ -1066,7 +1071,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     // run, so the scan covers [lo - M - 1, hi + M + 1]. Loads run one chunk ahead.
     for (int jj = warp; jj < gcount; jj += nwarps) {
         const int beam = A.out_ids ? A.out_ids[b0 + jj] : b0 + jj;
-        const float *xw = A.wave + (size_t)(beam - A.wave_row0) * nb;
+        const float *xw = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * G + jj) * nb : A.wave + (size_t)beam * nb;
         lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
         const float T = A.T;
         const float ambv = amb_s[jj] * A.s_amb;
@@ -1286,28 +1291,24 @@ template <int KIND, int G, bool TC>
 __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_wave_kernel(FootprintArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (!A.slot_pool) {
-        footprint_group<KIND, G, TC>(A, blockIdx.x, smem_raw);
-        return;
-    }
     // Echo-only: the group's waveforms go to a pooled slot (G rows) instead of
     // the caller's memory. The pool holds a slot for every CTA the GPU can
     // keep resident, so a claim finds one on its first pass.
-    __shared__ int s_slot;
-    if (threadIdx.x == 0) s_slot = claim_slot(A.slot_busy, A.n_slots, (int)(blockIdx.x % (unsigned)A.n_slots));
-    __syncthreads();
-    const int slot = s_slot;
-    if (slot < 0) {
-        if (threadIdx.x == 0) atomicExch(A.err, 1);
-        return;
+    if (A.slot_pool) {
+        if (threadIdx.x == 0) s_wave_slot = claim_slot(A.slot_busy, A.n_slots, (int)(blockIdx.x % (unsigned)A.n_slots));
+        __syncthreads();
+        if (s_wave_slot < 0) {
+            if (threadIdx.x == 0) atomicExch(A.err, 1);
+            return;
+        }
     }
-    A.wave = A.slot_pool + (size_t)slot * G * A.n_bins;
-    A.wave_row0 = blockIdx.x * G;
     footprint_group<KIND, G, TC>(A, blockIdx.x, smem_raw);
-    __syncthreads();  // every read of the slot (echo scan) is done
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(A.slot_busy + slot, 0);
+    if (A.slot_pool) {
+        __syncthreads();  // every read of the slot (echo scan) is done
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(A.slot_busy + s_wave_slot, 0);
+        }
     }
 }
 

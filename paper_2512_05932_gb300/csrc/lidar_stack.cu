@@ -45,6 +45,7 @@ struct StackArgs {
     float *I;           // [V][U]
     uint16_t *S;        // [V][U], 0 = no slice
     const float *K;     // [kh][kw]
+    const float *Kc, *Kr;  // separable form: K[a][b] = Kc[a] Kr[b]
     int kh, kw;
     float thr, kmax;    // threshold, largest kernel weight
     int32_t *out_slice;
@@ -240,6 +241,164 @@ __global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Separable kernel K[a][b] = col[a] row[b] (lidar_stack_create_separable).
+// One CTA of 256 threads per 32 x 32 output tile; region = tile + halo as in
+// stack_tile_kernel. The slices present in the region (and strong enough to
+// reach the threshold somewhere in the tile) are taken nearest first; per
+// slice s a row pass writes R[ry][x] = sum_b row[b] I_s(ry, x - b + 2n) for
+// every region row ry and output column x, and a column pass gives
+// out(y, x) = sum_a col[a] R[y - a + 2m][x], where I_s is I on the pixels of
+// slice s and 0 elsewhere; an output takes the first slice that reaches the
+// threshold. Cost per output and slice O(kh + kw) instead of O(kh kw).
+// ---------------------------------------------------------------------------
+
+constexpr int kSW = 32, kSH = 32;   // output tile of the separable kernel
+constexpr int kList = 64;           // slices listed per round
+
+__global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int kh = A.kh, kw = A.kw, m = kh / 2, n = kw / 2;
+    const int RH = kSH + kh - 1, RW = kSW + kw - 1;
+    float *Kc = reinterpret_cast<float *>(smem);        // col[kh]
+    float *Kr = Kc + kh;                                 // row[kw]
+    float *Rb = Kr + kw;                                 // R[RH][kSW]
+    float *RI = Rb + RH * kSW;                           // region intensity [RH][RW]
+    uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RW);  // region slice
+    __shared__ float hist[kSpan];
+    __shared__ int lst[kList];
+    __shared__ int s_lo, s_hi, s_cnt, s_min;
+    const int tid = threadIdx.x, tx = tid % kSW, tyb = tid / kSW;  // rows tyb + 8 i
+    const int u0 = blockIdx.x * kSW, v0 = blockIdx.y * kSH;
+    for (int i = tid; i < kh; i += blockDim.x) Kc[i] = A.Kc[i];
+    for (int i = tid; i < kw; i += blockDim.x) Kr[i] = A.Kr[i];
+    for (int i = tid; i < RH * RW; i += blockDim.x) {
+        const int ry = i / RW, rx = i - ry * RW;
+        const int v = v0 - m + ry, u = u0 - n + rx;
+        float w = 0.f;
+        uint16_t s = 0;
+        if (v >= 0 && v < A.V && u >= 0 && u < A.U) {
+            const long idx = (long)v * A.U + u;
+            w = A.I[idx];
+            s = A.S[idx];
+        }
+        RI[i] = w;
+        RS[i] = s;
+    }
+    if (tid == 0) { s_lo = INT_MAX; s_hi = 0; }
+    __syncthreads();
+    {
+        int lo_ = INT_MAX, hi_ = 0;
+        for (int i = tid; i < RH * RW; i += blockDim.x)
+            if (RS[i]) { lo_ = min(lo_, (int)RS[i]); hi_ = max(hi_, (int)RS[i]); }
+        atomicMin(&s_lo, lo_);
+        atomicMax(&s_hi, hi_);
+    }
+    __syncthreads();
+    const int slo = s_lo, shi = s_hi;
+    const bool use_hist = shi >= slo && shi - slo < kSpan;
+    const float cut = A.thr * (1.f - 1e-5f);
+    if (use_hist) {
+        for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
+        __syncthreads();
+        for (int i = tid; i < RH * RW; i += blockDim.x)
+            if (RS[i]) atomicAdd(&hist[RS[i] - slo], RI[i]);
+        __syncthreads();
+    }
+    // per region row: range of the slices on it (rows without slice s skip the row pass)
+    int *rmin = reinterpret_cast<int *>(RS + ((RH * RW + 1) & ~1));
+    int *rmax = rmin + RH;
+    for (int ry = tid; ry < RH; ry += blockDim.x) {
+        int a = INT_MAX, b = 0;
+        for (int rx = 0; rx < RW; ++rx) {
+            const int s = RS[ry * RW + rx];
+            if (s) { a = min(a, s); b = max(b, s); }
+        }
+        rmin[ry] = a;
+        rmax[ry] = b;
+    }
+    __syncthreads();
+
+    int outS[4];
+    float outX[4];
+    int done = 0;  // bit i: output row tyb + 8 i has its answer (or is outside the image)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        outS[i] = A.s_max;
+        outX[i] = 0.f;
+        if (!(u0 + tx < A.U && v0 + tyb + 8 * i < A.V)) done |= 1 << i;
+    }
+    int lo = 0;  // slices <= lo have been processed
+    bool finished = __syncthreads_and(done == 0xF) != 0;
+    while (!finished) {
+        // the next (up to kList) slices above lo, nearest first
+        if (tid == 0) { s_cnt = 0; s_min = INT_MAX; }
+        __syncthreads();
+        if (use_hist) {
+            if (tid < 32) {
+                int cnt = 0;
+                for (int b0 = max(0, lo + 1 - slo); b0 <= shi - slo && cnt < kList; b0 += 32) {
+                    const int bin = b0 + tid;
+                    const bool keep = bin <= shi - slo && hist[bin] > 0.f && hist[bin] * A.kmax >= cut;
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    const int pos = cnt + __popc(bal & ((1u << tid) - 1u));
+                    if (keep && pos < kList) lst[pos] = slo + bin;
+                    cnt += __popc(bal);
+                }
+                if (tid == 0) s_cnt = min(cnt, kList);
+            }
+        } else {
+            int mn = INT_MAX;
+            for (int i = tid; i < RH * RW; i += blockDim.x)
+                if (RS[i] > lo) mn = min(mn, (int)RS[i]);
+            atomicMin(&s_min, mn);
+            __syncthreads();
+            if (tid == 0 && s_min != INT_MAX) { lst[0] = s_min; s_cnt = 1; }
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        if (cnt == 0) break;
+        for (int k = 0; k < cnt && !finished; ++k) {
+            const int s = lst[k];
+            // row pass over every region row: output column tx
+            for (int ry = tyb; ry < RH; ry += 8) {
+                float acc = 0.f;
+                if (s >= rmin[ry] && s <= rmax[ry]) {
+                    const int rb = ry * RW + tx + 2 * n;  // tap b reads region column tx + 2n - b
+                    for (int b = 0; b < kw; ++b) {
+                        const int ri = rb - b;
+                        acc = fmaf(RS[ri] == s ? RI[ri] : 0.f, Kr[b], acc);
+                    }
+                }
+                Rb[ry * kSW + tx] = acc;
+            }
+            __syncthreads();
+            // column pass and the threshold test
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if ((done >> i) & 1) continue;
+                const int y = tyb + 8 * i;
+                float acc = 0.f;
+                for (int a = 0; a < kh; ++a) acc = fmaf(Rb[(y - a + 2 * m) * kSW + tx], Kc[a], acc);
+                if (acc >= A.thr) { outS[i] = s; outX[i] = acc; done |= 1 << i; }
+            }
+            finished = __syncthreads_and(done == 0xF) != 0;  // also: Rb is free again
+        }
+        lo = lst[cnt - 1];
+        __syncthreads();  // every thread has read lst before the next round overwrites it
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int u = u0 + tx, v = v0 + tyb + 8 * i;
+        if (u < A.U && v < A.V) {
+            const long idx = (long)v * A.U + u;
+            A.out_slice[idx] = outS[i];
+            A.out_val[idx] = outX[i];
+        }
+    }
+}
+
 thread_local char g_stack_err[512] = "no error";
 
 }  // namespace
@@ -248,7 +407,8 @@ struct lidar_stack {
     int kh = 0, kw = 0, s_max = 0;
     double dr = 0, thr = 0;
     float kmax = 0.f;
-    float *d_K = nullptr;
+    bool sep = false;           // separable kernel: row/column passes
+    float *d_K = nullptr;       // [kh][kw], or col[kh] then row[kw] when sep
     float *d_I = nullptr;
     uint16_t *d_S = nullptr;
     size_t cap = 0;
@@ -276,6 +436,26 @@ size_t tile_smem(int kh, int kw)
 {
     const size_t RH = kTH + kh - 1, RW = kTW + kw - 1;
     return (size_t)kh * kw * 4 + RH * RW * 4 + RH * RW * 2;
+}
+
+// dynamic shared memory of stack_sep_kernel: col, row, R, region (float +
+// uint16, padded to 4 bytes), per-row slice range
+size_t sep_smem(int kh, int kw)
+{
+    const size_t RH = kSH + kh - 1, RW = kSW + kw - 1;
+    return (size_t)(kh + kw) * 4 + RH * kSW * 4 + RH * RW * 4 + ((RH * RW + 1) & ~(size_t)1) * 2 + 2 * RH * 4;
+}
+
+lidar_status_t check_common(int kh, int kw, double thr, double dr, double r_max, double *sm)
+{
+    if (kh < 1 || kw < 1 || kh > kMaxK || kw > kMaxK || !(kh & 1) || !(kw & 1))
+        return sfail(nullptr, LIDAR_EINVAL, "kernel sizes must be odd and in [1, %d]", kMaxK);
+    if (!(std::isfinite(thr) && thr > 0)) return sfail(nullptr, LIDAR_EINVAL, "threshold must be > 0");
+    if (!(std::isfinite(dr) && dr > 0)) return sfail(nullptr, LIDAR_EINVAL, "dr must be > 0");
+    if (!std::isfinite(r_max)) return sfail(nullptr, LIDAR_EINVAL, "r_max must be finite");
+    *sm = std::floor(r_max / dr);
+    if (!(*sm >= 1 && *sm <= 65535)) return sfail(nullptr, LIDAR_EINVAL, "floor(r_max / dr) must be in [1, 65535]");
+    return LIDAR_OK;
 }
 
 }  // namespace
@@ -345,15 +525,61 @@ lidar_status_t lidar_range_stack(lidar_stack_t *h, const lidar_gbuffer_t *g, int
     a.range = g->range; a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.rho = g->rho_d; a.retro = g->retro;
     a.dr = h->dr; a.s_max = h->s_max;
     a.I = h->d_I; a.S = h->d_S; a.K = h->d_K; a.kh = h->kh; a.kw = h->kw; a.thr = (float)h->thr;
+    if (h->sep) { a.Kc = h->d_K; a.Kr = h->d_K + h->kh; }
     a.kmax = h->kmax;
     a.out_slice = out_slice; a.out_val = out_intensity;
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = (int)std::min<size_t>((np + 255) / 256, 152 * 16);
     stack_inputs_kernel<<<grid, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking input kernel launch");
+    if (h->sep) {
+        dim3 sg((g->U + kSW - 1) / kSW, (g->V + kSH - 1) / kSH);
+        stack_sep_kernel<<<sg, 256, sep_smem(h->kh, h->kw), s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking separable kernel launch");
+        return LIDAR_OK;
+    }
     dim3 tg((g->U + kTW - 1) / kTW, (g->V + kTH - 1) / kTH);
     stack_tile_kernel<<<tg, kTW * kTH, tile_smem(h->kh, h->kw), s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking tile kernel launch");
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_stack_create_separable(const lidar_stack_sep_params_t *p, lidar_stack_t **out)
+{
+    if (!out) return sfail(nullptr, LIDAR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p || !p->col || !p->row) return sfail(nullptr, LIDAR_EINVAL, "params, col or row is NULL");
+    double sm = 0;
+    lidar_status_t st = check_common(p->kh, p->kw, p->threshold, p->dr, p->r_max, &sm);
+    if (st != LIDAR_OK) return st;
+    float cmax = 0.f, rmax = 0.f;
+    for (int i = 0; i < p->kh; ++i) {
+        if (!(std::isfinite(p->col[i]) && p->col[i] >= 0.f))
+            return sfail(nullptr, LIDAR_EINVAL, "col[%d] is negative or not finite", i);
+        cmax = std::max(cmax, p->col[i]);
+    }
+    for (int i = 0; i < p->kw; ++i) {
+        if (!(std::isfinite(p->row[i]) && p->row[i] >= 0.f))
+            return sfail(nullptr, LIDAR_EINVAL, "row[%d] is negative or not finite", i);
+        rmax = std::max(rmax, p->row[i]);
+    }
+    lidar_stack_t *h = new (std::nothrow) lidar_stack();
+    if (!h) return sfail(nullptr, LIDAR_ENOMEM, "host allocation failed");
+    h->kh = p->kh; h->kw = p->kw; h->s_max = (int)sm; h->dr = p->dr; h->thr = p->threshold;
+    h->sep = true;
+    h->kmax = (float)((double)cmax * rmax);
+    std::vector<float> k(p->col, p->col + p->kh);
+    k.insert(k.end(), p->row, p->row + p->kw);
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_K, k.size() * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_K, k.data(), k.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(stack_sep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sep_smem(p->kh, p->kw))) != cudaSuccess) {
+        st = scuda(nullptr, e, "range stacking set-up");
+        lidar_stack_destroy(h);
+        return st;
+    }
+    *out = h;
     return LIDAR_OK;
 }
 

@@ -67,6 +67,11 @@ class lidar_stack_params_t(C.Structure):
                 ("dr", C.c_double), ("r_max", C.c_double)]
 
 
+class lidar_stack_sep_params_t(C.Structure):
+    _fields_ = [("kh", C.c_int32), ("kw", C.c_int32), ("col", C.POINTER(C.c_float)), ("row", C.POINTER(C.c_float)),
+                ("threshold", C.c_double), ("dr", C.c_double), ("r_max", C.c_double)]
+
+
 class lidar_frame_t(C.Structure):
     _fields_ = [("sensor", C.c_void_p), ("gbuffer", lidar_gbuffer_t), ("pose", lidar_pose_t),
                 ("out_waveforms", C.c_void_p), ("out_echoes", lidar_echoes_t)]
@@ -90,7 +95,8 @@ TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact
                 "lidar_simulate_surrogate", "lidar_tailnet_profile_enable", "lidar_tailnet_profile_read",
                 "lidar_tailnet_set_dense", "lidar_tailnet_sync")
 # include/lidar_stack.h
-STACK_SYMBOLS = ("lidar_stack_create", "lidar_range_stack", "lidar_stack_last_error", "lidar_stack_destroy")
+STACK_SYMBOLS = ("lidar_stack_create", "lidar_stack_create_separable", "lidar_range_stack", "lidar_stack_last_error",
+                 "lidar_stack_destroy")
 KERNELS = ("setup", "footprint_wave")
 TAIL_INPUT_CELLS = 5440
 
@@ -194,6 +200,8 @@ def load(path: str = LIB_PATH):
     lib.lidar_tailnet_sync.argtypes = [C.c_void_p, C.c_void_p]
     lib.lidar_stack_create.restype = C.c_int
     lib.lidar_stack_create.argtypes = [P(lidar_stack_params_t), P(C.c_void_p)]
+    lib.lidar_stack_create_separable.restype = C.c_int
+    lib.lidar_stack_create_separable.argtypes = [P(lidar_stack_sep_params_t), P(C.c_void_p)]
     lib.lidar_range_stack.restype = C.c_int
     lib.lidar_range_stack.argtypes = [C.c_void_p, P(lidar_gbuffer_t), C.c_void_p, C.c_void_p, C.c_void_p]
     lib.lidar_stack_last_error.restype = C.c_char_p
@@ -456,14 +464,25 @@ class TailNet:
 class RangeStack:
     """Range stacking (include/lidar_stack.h): nearest slice above threshold per pixel."""
 
-    def __init__(self, kernel, threshold: float, dr: float, r_max: float):
-        k = np.ascontiguousarray(kernel, np.float32)
-        self._k = k
-        p = lidar_stack_params_t(k.shape[0], k.shape[1], k.ctypes.data_as(C.POINTER(C.c_float)), float(threshold),
-                                 float(dr), float(r_max))
+    def __init__(self, kernel, threshold: float, dr: float, r_max: float, separable=None):
+        """kernel: [kh][kw] array, or None with separable = (col[kh], row[kw])
+        for K = col row^T (lidar_stack_create_separable)."""
         h = C.c_void_p()
         lib = load()
-        st = lib.lidar_stack_create(C.byref(p), C.byref(h))
+        if separable is not None:
+            col = np.ascontiguousarray(separable[0], np.float32)
+            row = np.ascontiguousarray(separable[1], np.float32)
+            self._k = (col, row)
+            p = lidar_stack_sep_params_t(len(col), len(row), col.ctypes.data_as(C.POINTER(C.c_float)),
+                                         row.ctypes.data_as(C.POINTER(C.c_float)), float(threshold), float(dr),
+                                         float(r_max))
+            st = lib.lidar_stack_create_separable(C.byref(p), C.byref(h))
+        else:
+            k = np.ascontiguousarray(kernel, np.float32)
+            self._k = k
+            p = lidar_stack_params_t(k.shape[0], k.shape[1], k.ctypes.data_as(C.POINTER(C.c_float)),
+                                     float(threshold), float(dr), float(r_max))
+            st = lib.lidar_stack_create(C.byref(p), C.byref(h))
         if st != 0:
             raise LidarError(st, lib.lidar_stack_last_error(None).decode())
         self.handle = h.value

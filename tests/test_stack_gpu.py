@@ -26,8 +26,8 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def run_gpu(gb, kernel, thr, dr, r_max):
-    st = lidar.RangeStack(kernel, thr, dr, r_max)
+def run_gpu(gb, kernel, thr, dr, r_max, separable=None):
+    st = lidar.RangeStack(kernel, thr, dr, r_max, separable=separable)
     planes = lidar.gbuffer_to_device(gb)
     g = lidar.make_gbuffer(gb, [p.data_ptr() for p in planes])
     s_out = torch.full((gb.V, gb.U), -7, dtype=torch.int32, device="cuda")
@@ -38,8 +38,11 @@ def run_gpu(gb, kernel, thr, dr, r_max):
     return s_out.cpu().numpy(), x_out.cpu().numpy().astype(np.float64), st.s_max
 
 
-def check(gb, kernel, thr, dr, r_max, band=1e-5):
-    S_g, X_g, s_max = run_gpu(gb, kernel, thr, dr, r_max)
+def check(gb, kernel, thr, dr, r_max, band=1e-5, separable=None):
+    if separable is not None:  # the oracle convolves with K = col row^T (FP64)
+        kernel = np.outer(np.asarray(separable[0], np.float32).astype(np.float64),
+                          np.asarray(separable[1], np.float32).astype(np.float64))
+    S_g, X_g, s_max = run_gpu(gb, kernel, thr, dr, r_max, separable)
     I, rb = O.stack_inputs(gb, dr)
     S_o, X_o = O.range_stack(I, rb, np.asarray(kernel, np.float64), thr, s_max)
     # the oracle's per-slice values near the threshold are ambiguous for FP32 sums
@@ -111,3 +114,81 @@ def test_far_slice_behind_many_weak_near_slices():
     assert (S_o[12, 12] == rb[12, 12]) and len(np.unique(rb[rb > 0])) > 24
     np.testing.assert_array_equal(S_g, S_o)
     np.testing.assert_allclose(X_g, X_o, rtol=1e-6)
+
+
+# --------------------------------------------------------------------------
+# separable kernels (lidar_stack_create_separable): row and column passes
+
+
+def gauss_tail_1d(half, pitch_deg, sigma_deg, tail_amp=1e-4):
+    o = (np.arange(2 * half + 1) - half) * pitch_deg
+    k = np.exp(-0.5 * (o / sigma_deg) ** 2) + tail_amp * np.minimum(1.0, (np.maximum(np.abs(o), 1e-9) / 0.05) ** -3)
+    return (k / k.sum()).astype(np.float32)
+
+
+def test_separable_plane_and_retro_patch():
+    w = S.small_plane_retro()
+    col, row = gauss_tail_1d(10, 0.02, 0.05), gauss_tail_1d(14, 0.02, 0.08)
+    st = check(w.gbuffer, None, thr=5e-8, dr=0.05, r_max=30.0, separable=(col, row))
+    assert st["echoes"] > 1000
+
+
+def test_separable_ragged_asymmetric():
+    w = S.tiny_case()
+    g = np.random.default_rng(4)
+    col, row = g.uniform(0, 1, 5).astype(np.float32), g.uniform(0, 1, 9).astype(np.float32)
+    I, _ = O.stack_inputs(w.gbuffer, 0.01)
+    check(w.gbuffer, None, thr=float(np.median(I[I > 0])) * 3, dr=0.01, r_max=20.0, separable=(col, row))
+
+
+def test_separable_many_slices_per_tile():
+    """Grazing ground: many slices per 32x32 tile (more than one 64-slice list)."""
+    w = S.full_frame_boxes(U=128, V=64, n_boxes=12, rows=2, cols=10)
+    I, rb = O.stack_inputs(w.gbuffer, 0.02)
+    ones = np.ones(15, np.float32)
+    thr = float(np.quantile(I[I > 0], 0.9)) * 3
+    st = check(w.gbuffer, None, thr=thr, dr=0.02, r_max=200.0, separable=(ones, ones))
+    assert st["echoes"] > 0
+
+
+def test_separable_far_slice_behind_many_weak_near_slices():
+    U = V = 24
+    gb = S.GBuffer(U, V, -U * 0.02 * DEG / 2, -V * 0.02 * DEG / 2, 0.02 * DEG, 0.02 * DEG,
+                   *[np.zeros((V, U), np.float32) for _ in range(7)])
+    gb.range[:] = np.inf
+    gb.nx[:] = -1.0
+    pos = [(v, u) for v in range(9, 16) for u in range(9, 16) if (v, u) != (12, 12)][:40]
+    for i, (v, u) in enumerate(pos):
+        gb.range[v, u] = 1.0 + 0.1 * i
+        gb.rho_d[v, u] = 0.01
+    gb.range[12, 12] = 5.0
+    gb.retro[12, 12] = 100.0
+    ones = np.ones(7, np.float32)
+    I, rb = O.stack_inputs(gb, 0.1)
+    thr = float(I[12, 12]) * 0.5
+    S_g, X_g, s_max = run_gpu(gb, None, thr, 0.1, 10.0, separable=(ones, ones))
+    S_o, X_o = O.range_stack(I, rb, np.ones((7, 7)), thr, s_max)
+    assert (S_o[12, 12] == rb[12, 12]) and len(np.unique(rb[rb > 0])) > 24
+    np.testing.assert_array_equal(S_g, S_o)
+    np.testing.assert_allclose(X_g, X_o, rtol=1e-6)
+
+
+def test_separable_matches_general_form_on_gpu():
+    """The same K through both entry points: equal slices wherever the value
+    is not within FP32 noise of the threshold."""
+    w = S.small_plane_retro()
+    col, row = gauss_tail_1d(10, 0.02, 0.05), gauss_tail_1d(10, 0.02, 0.05)
+    K = np.outer(col.astype(np.float64), row.astype(np.float64)).astype(np.float32)
+    S1, X1, _ = run_gpu(w.gbuffer, K, 5e-8, 0.05, 30.0)
+    S2, X2, _ = run_gpu(w.gbuffer, None, 5e-8, 0.05, 30.0, separable=(col, row))
+    near = (np.abs(X1 - 5e-8) <= 1e-4 * 5e-8) | (np.abs(X2 - 5e-8) <= 1e-4 * 5e-8)
+    assert (S1[~near] == S2[~near]).all()
+    both = ~near & (X1 > 0)
+    np.testing.assert_allclose(X2[both], X1[both], rtol=1e-5)
+
+
+def test_separable_rejects_bad_parameters():
+    with pytest.raises(lidar.LidarError, match="odd"):
+        lidar.RangeStack(None, 1.0, 0.1, 10.0, separable=(np.ones(4), np.ones(5)))
+    with pytest.raises(lidar.LidarError, match="row"):
+        lidar.RangeStack(None, 1.0, 0.1, 10.0, separable=(np.ones(5), -np.ones(5)))
