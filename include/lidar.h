@@ -150,6 +150,25 @@ typedef struct {
     const float *range, *nx, *ny, *nz, *rho_d, *retro, *ambient;
 } lidar_gbuffer_t;
 
+/* Pinhole G-buffer: a rasterised rendering (Sec. II-D, rasterization), which
+ * follows a pinhole projection rather than the spherical grid of
+ * lidar_gbuffer_t (Sec. II-C remarks that the beam kernels are then
+ * inhomogeneous). Pixel (i, j), 0 <= i < W, 0 <= j < H, has its centre at
+ * image coordinates X = (i + 1/2 - cx) / fx, Y = (j + 1/2 - cy) / fy and
+ * looks along the camera-frame direction (X, Y, 1); R (row-major 3x3) maps
+ * camera-frame vectors to the sensor frame (its columns are the image x axis,
+ * the image y axis and the optical axis). Planes are float32 [H][W], device
+ * memory, with the meanings of lidar_gbuffer_t; normals in the sensor frame.
+ * With depth_is_z != 0 the range plane holds z-buffer depth along the
+ * optical axis (the distance along the pixel-centre ray is z |(X, Y, 1)|). */
+typedef struct {
+    int32_t W, H;
+    double fx, fy, cx, cy;       /* pixels; fx, fy > 0 */
+    double R[9];                 /* camera -> sensor frame, orthonormal (1e-3) */
+    int32_t depth_is_z;
+    const float *range, *nx, *ny, *nz, *rho_d, *retro, *ambient;
+} lidar_pinhole_t;
+
 /* Sensor pose: rotation R (row-major 3x3) taking sensor-frame vectors into the
  * G-buffer frame (a beam axis is R dir). Orthonormal with det +1 (1e-3). */
 typedef struct {
@@ -196,6 +215,23 @@ typedef struct lidar lidar_t;
 lidar_status_t lidar_create(const lidar_profile_t *profile, const lidar_pattern_t *pattern,
                             const lidar_pulse_t *pulse, const lidar_calib_t *calib, lidar_t **out);
 
+/* Reprojects a pinhole G-buffer onto the spherical grid of dst (Sec. II-C:
+ * reprojection of the rendered images is one of the ways to use pinhole
+ * renderings), so that lidar_simulate* can run on it. For each dst pixel with
+ * centre direction v (sensor frame): v is projected through the pinhole; the
+ * src pixel whose cell contains the projection (none if it falls outside the
+ * image or behind the camera) gives the normal, reflectance, retro gain and
+ * ambient radiance, and its range r along its own centre direction p is
+ * extrapolated along the surface to v with the normal correction of
+ * Sec. II-D: r_corr = (p . n) / (v . n) r (kept uncorrected where v . n is
+ * below 1e-3 in magnitude or of the other sign than p . n). Pixels without a
+ * source get range +inf and zeros. Geometry in FP64.
+ * src: pinhole planes (device, read); dst: the target grid (U, V, az0, el0,
+ * daz, del as for lidar_simulate) with caller-owned device planes, all seven
+ * written. Allocates nothing; asynchronous on `stream`.
+ * Errors: LIDAR_EINVAL (sizes, intrinsics, rotation, NULL planes), LIDAR_ECUDA. */
+lidar_status_t lidar_reproject_pinhole(const lidar_pinhole_t *src, const lidar_gbuffer_t *dst, void *stream);
+
 /* Simulates all beams for one G-buffer and pose, enqueued on `stream`
  * (a cudaStream_t; NULL = legacy default stream). Asynchronous: returns after
  * enqueueing; results are ready when the stream reaches this point.
@@ -213,16 +249,17 @@ lidar_status_t lidar_simulate(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, co
  * deposit additions, which varies from run to run in both); the difference
  * is where each beam's waveform goes between the pulse convolution and the
  * echo scan. Each CTA of the footprint kernel
- * claims a slot of a library-owned pool sized for the CTAs the GPU holds at
- * once (SMs x resident CTAs x beams per CTA x n_bins floats, about 20 MB for
- * a 2048-bin sensor on 152 SMs), writes its beams' waveforms there, scans
- * them and frees the slot; the pool stays in L2, so the waveform bytes (4
- * n_bins per beam, most of lidar_simulate's output) never reach HBM and no
- * [n_beams][n_bins] buffer is needed.
+ * claims a slot of a library-owned pool that has, for every SM id below 256,
+ * one slot per CTA an SM can hold (beams per CTA x n_bins floats each: 33.5 MB
+ * for a 2048-bin sensor at 8 beams and 2 CTAs per SM, of which the slots of
+ * the enabled SMs, about 20 MB on 152 SMs, are used), writes its beams'
+ * waveforms there, scans them and frees the slot; the slots in use stay in
+ * L2, so the waveform bytes (4 n_bins per beam, most of lidar_simulate's
+ * output) do not reach HBM and no [n_beams][n_bins] buffer is needed.
  *   - The first call (and the first after lidar_set_deposit changes the beams
  *     per CTA) allocates the pool with cudaMalloc, synchronising the device.
- *   - Calls on several streams may overlap: slots are claimed atomically and
- *     the pool holds one for every CTA the GPU can run at once.
+ *   - Calls on several streams may overlap: slots are claimed atomically; a
+ *     CTA whose SM's slots are all held takes any free slot of the pool.
  *   - A slot claim that gives up (bounded; not expected, see above) leaves
  *     that CTA's beams unwritten and is reported by lidar_sync as
  *     LIDAR_ETIMEOUT.

@@ -12,7 +12,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblidar_gb300.so")
 SOURCES = ["lidar_api.cpp", "lidar_kernels.cu", "lidar_noalloc.cu", "lidar_tail.cu", "lidar_tail_api.cpp", "lidar_net.cu",
-           "lidar_net_api.cpp", "lidar_stack.cu", "lidar_umma.cu"]
+           "lidar_net_api.cpp", "lidar_stack.cu", "lidar_umma.cu",
+           "lidar_pinhole.cu"]
 HEADERS = [os.path.join(INCLUDE, "lidar.h"), os.path.join(INCLUDE, "lidar_tail.h"), os.path.join(INCLUDE, "lidar_stack.h"), os.path.join(CSRC, "lidar_internal.h"),
            os.path.join(CSRC, "lidar_host.h"), os.path.join(CSRC, "lidar_tail_internal.h"),
            os.path.join(CSRC, "lidar_net_internal.h")]

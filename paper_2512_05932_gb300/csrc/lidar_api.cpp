@@ -390,7 +390,6 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
     fa.invZ = (float)(1.0 / l->Z);
     fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
-    fa.sep = l->separable ? 1 : 0;
     fa.hpairs = l->d_pairs;
     fa.vpairs = l->d_pairs ? l->d_pairs + l->qw : nullptr;
     fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
@@ -405,8 +404,13 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     return fa;
 }
 
+// SM ids covered by per-SM slots of the echo-only pool (ids of enabled SMs
+// need not be contiguous; a CTA on a higher id takes any free slot).
+constexpr int kSlotSms = 256;
+
 // Waveform pool of the echo-only path: a slot of G rows for every CTA of the
-// footprint kernel that the GPU can hold at once (grown with cudaMalloc).
+// footprint kernel that an SM can hold at once, for SM ids 0..kSlotSms-1
+// (grown with cudaMalloc).
 lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
 {
     int dev = 0, sms = 0, per_sm = 0;
@@ -415,9 +419,11 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = gbl::footprint_occupancy(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, &per_sm)) != cudaSuccess)
         return cuda_fail(l, e, "footprint occupancy");
-    const int n = sms * std::max(1, per_sm);
+    (void)sms;
+    per_sm = std::max(1, per_sm);
+    const int n = kSlotSms * per_sm;
     const size_t need = (size_t)n * G * l->n_bins;
-    if (n <= l->n_slots && need <= l->slot_floats && need / n == (size_t)G * l->n_bins) return LIDAR_OK;
+    if (n == l->n_slots && per_sm == l->slots_per_sm && need == l->slot_floats) return LIDAR_OK;
     cudaFree(l->d_slot_pool);
     cudaFree(l->d_slot_busy);
     l->d_slot_pool = nullptr;
@@ -431,6 +437,7 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
         (e = cudaMemset(l->d_err, 0, sizeof(int))) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
         return cuda_fail(l, e, "cudaMalloc(echo-only waveform pool)");
     l->n_slots = n;
+    l->slots_per_sm = per_sm;
     l->slot_floats = need;
     return LIDAR_OK;
 }
@@ -471,6 +478,8 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.slot_pool = l->d_slot_pool;
         fa.slot_busy = l->d_slot_busy;
         fa.n_slots = l->n_slots;
+        fa.slot_sms = kSlotSms;
+        fa.slots_per_sm = l->slots_per_sm;
         fa.err = l->d_err;
     }
     e = gbl::launch_footprint(l->kind, tc ? l->G_tc : l->G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
@@ -672,7 +681,7 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     lidar_t *l = new (std::nothrow) lidar();
     if (!l) return fail(nullptr, LIDAR_ENOMEM, "host allocation failed");
     l->n_beams = pat->n_beams;
-    l->kind = p->kind == LIDAR_PROFILE_SEPARABLE ? LIDAR_PROFILE_TABLE : p->kind;
+    l->kind = p->kind;
     l->separable = p->kind == LIDAR_PROFILE_SEPARABLE;
     l->n_bins = pu->n_bins;
     l->dt = pu->dt_s;

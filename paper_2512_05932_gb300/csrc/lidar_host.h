@@ -15,7 +15,7 @@ struct TailState;
 struct lidar {
     // sensor
     int32_t n_beams = 0;
-    int32_t kind = 0;          // kernel form: RADIAL or TABLE (a separable profile runs as TABLE)
+    int32_t kind = 0;          // lidar_profile_kind_t (the footprint kernel's KIND)
     bool separable = false;    // LIDAR_PROFILE_SEPARABLE: pairs of H and V instead of quads
     double Z = 0.0;
     double support_rad = 0.0;
@@ -58,7 +58,7 @@ struct lidar {
     float *d_slot_pool = nullptr;
     int *d_slot_busy = nullptr;
     int *d_err = nullptr;
-    int n_slots = 0;
+    int n_slots = 0, slots_per_sm = 0;
     size_t slot_floats = 0;
     // sensor-model fingerprint (batch compatibility) and table hash
     uint64_t model_hash = 0;

@@ -71,7 +71,7 @@ struct FootprintArgs {
     float invZ;
     const float4 *quads;   // (h+1) rows of (w+1) corner quads, already divided by Z (table)
     int qw, qh;
-    int sep;               // separable table: P = H(u) V(v) instead of the quads
+    // separable profile P = H(u) V(v) (kind LIDAR_PROFILE_SEPARABLE):
     const float2 *hpairs;  // [qw]: (H[i], H[i+1]) of the zero-padded H, divided by Z
     const float2 *vpairs;  // [qh]: (V[j], V[j+1]) of the zero-padded V
     float tk, tcu, tcv;    // table coordinate = offset_rad * tk + tc{u,v}
@@ -116,7 +116,8 @@ struct FootprintArgs {
     // NULL: waveforms are outputs in `wave`.
     float *slot_pool;
     int *slot_busy;
-    int n_slots;
+    int n_slots;             // slot_sms * slots_per_sm
+    int slot_sms, slots_per_sm;
     int *err;                // set to 1 if a slot claim gives up
 };
 

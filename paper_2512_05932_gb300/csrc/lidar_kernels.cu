@@ -386,7 +386,7 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
         r.fy = fv - iv;
         if (!r.ok) {
             r.q = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else if (A.sep) {
+        } else if (KIND == LIDAR_PROFILE_SEPARABLE) {
             const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
             r.q = make_float4(h.x, h.y, v.x, v.y);
         } else {
@@ -417,7 +417,7 @@ __device__ __forceinline__ float profile_finish(const FootprintArgs &A, const Pr
 {
     if (!r.ok) return 0.f;
     if (KIND == LIDAR_PROFILE_RADIAL) return r.q.x;
-    if (A.sep) return fmaf(r.fx, r.q.y - r.q.x, r.q.x) * fmaf(r.fy, r.q.w - r.q.z, r.q.z);
+    if (KIND == LIDAR_PROFILE_SEPARABLE) return fmaf(r.fx, r.q.y - r.q.x, r.q.x) * fmaf(r.fy, r.q.w - r.q.z, r.q.z);
     float top = fmaf(r.fx, r.q.y - r.q.x, r.q.x);
     float bot = fmaf(r.fx, r.q.w - r.q.z, r.q.z);
     return fmaf(r.fy, bot - top, top);
@@ -1269,11 +1269,25 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
 }
 
-// Claims a free slot of the echo-only waveform pool, starting at `start`
-// (slot = CTA index modulo the pool: usually free, as the CTA that used it
-// last has finished). Bounded: -1 after 1024 passes over the pool.
-__device__ int claim_slot(int *busy, int n, int start)
+// Claims a free slot of the echo-only waveform pool. The pool has
+// slots_per_sm slots for each SM id below slot_sms; a CTA first tries the
+// slots of its own SM, of which at most slots_per_sm - 1 are held by the
+// other CTAs resident there, then (another kernel sharing the pool, an SM id
+// beyond slot_sms) scans the whole pool. Bounded: -1 after 1024 passes.
+__device__ int claim_slot(int *busy, int n, int slot_sms, int per_sm)
 {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    if ((int)smid < slot_sms) {
+        for (int k = 0; k < per_sm; ++k) {
+            const int s = (int)smid * per_sm + k;
+            if (atomicCAS(busy + s, 0, 1) == 0) {
+                __threadfence();
+                return s;
+            }
+        }
+    }
+    const int start = (int)(blockIdx.x % (unsigned)n);
     for (int pass = 0; pass < 1024; ++pass) {
         for (int i = 0; i < n; ++i) {
             const int s = (start + i) % n;
@@ -1292,10 +1306,9 @@ __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_wave_kernel(Footpri
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // Echo-only: the group's waveforms go to a pooled slot (G rows) instead of
-    // the caller's memory. The pool holds a slot for every CTA the GPU can
-    // keep resident, so a claim finds one on its first pass.
+    // the caller's memory, one of its own SM's slots in the common case.
     if (A.slot_pool) {
-        if (threadIdx.x == 0) s_wave_slot = claim_slot(A.slot_busy, A.n_slots, (int)(blockIdx.x % (unsigned)A.n_slots));
+        if (threadIdx.x == 0) s_wave_slot = claim_slot(A.slot_busy, A.n_slots, A.slot_sms, A.slots_per_sm);
         __syncthreads();
         if (s_wave_slot < 0) {
             if (threadIdx.x == 0) atomicExch(A.err, 1);
@@ -1345,13 +1358,15 @@ size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 
 int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
 
-// Instantiated configurations: profile kind x beams per CTA x deposit form.
-// Shared-memory atomics: G in {1, 2, 4, 8, 16} (1: scattered beams, e.g. the
-// exact re-run of the tail split); tensor cores: G in {4, 8}.
+// Instantiated configurations: profile kind (radial, table, separable) x
+// beams per CTA x deposit form. Shared-memory atomics: G in {1, 2, 4, 8, 16}
+// (1: scattered beams, e.g. the exact re-run of the tail split); tensor
+// cores: G in {4, 8}.
 #define GBL_FOR_EACH(X)                                                                                \
     X(0, 1, false) X(0, 2, false) X(0, 4, false) X(0, 8, false) X(0, 16, false) X(1, 1, false)        \
     X(1, 2, false) X(1, 4, false) X(1, 8, false) X(1, 16, false) X(0, 4, true) X(0, 8, true)          \
-    X(1, 4, true) X(1, 8, true)
+    X(1, 4, true) X(1, 8, true) X(2, 1, false) X(2, 2, false) X(2, 4, false) X(2, 8, false)           \
+    X(2, 16, false) X(2, 4, true) X(2, 8, true)
 
 cudaError_t prepare_footprint(int kind, int G, bool tc, size_t smem)
 {

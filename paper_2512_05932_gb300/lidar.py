@@ -67,6 +67,13 @@ class lidar_stack_params_t(C.Structure):
                 ("dr", C.c_double), ("r_max", C.c_double)]
 
 
+class lidar_pinhole_t(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double), ("R", C.c_double * 9), ("depth_is_z", C.c_int32),
+                ("range", C.c_void_p), ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p),
+                ("rho_d", C.c_void_p), ("retro", C.c_void_p), ("ambient", C.c_void_p)]
+
+
 class lidar_stack_sep_params_t(C.Structure):
     _fields_ = [("kh", C.c_int32), ("kw", C.c_int32), ("col", C.POINTER(C.c_float)), ("row", C.POINTER(C.c_float)),
                 ("threshold", C.c_double), ("dr", C.c_double), ("r_max", C.c_double)]
@@ -82,7 +89,7 @@ ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), 
 assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 
 # exported symbols (every function declared in include/lidar.h)
-SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_simulate_host", "lidar_simulate_noalloc",
+SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_reproject_pinhole", "lidar_simulate_host", "lidar_simulate_noalloc",
            "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
@@ -124,6 +131,8 @@ def load(path: str = LIB_PATH):
     lib.lidar_simulate.restype = C.c_int
     lib.lidar_simulate.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                    P(lidar_echoes_t), C.c_void_p]
+    lib.lidar_reproject_pinhole.restype = C.c_int
+    lib.lidar_reproject_pinhole.argtypes = [P(lidar_pinhole_t), P(lidar_gbuffer_t), C.c_void_p]
     lib.lidar_simulate_echoes.restype = C.c_int
     lib.lidar_simulate_echoes.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), P(lidar_echoes_t),
                                           C.c_void_p]
@@ -312,6 +321,23 @@ def lidar_simulate(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_wav
     e = lidar_echoes_t(out_echoes, out_counts)
     st = load().lidar_simulate(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, C.byref(e), stream)
     _check(st, handle)
+
+
+def make_pinhole(ph, ptrs) -> lidar_pinhole_t:
+    """lidar_pinhole_t of a scenes.PinholeGBuffer with device plane pointers
+    (range, nx, ny, nz, rho_d, retro, ambient)."""
+    s = lidar_pinhole_t()
+    s.W, s.H = int(ph.W), int(ph.H)
+    s.fx, s.fy, s.cx, s.cy = float(ph.fx), float(ph.fy), float(ph.cx), float(ph.cy)
+    for i, x in enumerate(np.asarray(ph.R, np.float64).ravel()):
+        s.R[i] = float(x)
+    s.depth_is_z = int(bool(ph.depth_is_z))
+    s.range, s.nx, s.ny, s.nz, s.rho_d, s.retro, s.ambient = [int(p) for p in ptrs]
+    return s
+
+
+def lidar_reproject_pinhole(src: lidar_pinhole_t, dst: lidar_gbuffer_t, stream: int = 0) -> None:
+    _check(load().lidar_reproject_pinhole(C.byref(src), C.byref(dst), stream), None)
 
 
 def lidar_simulate_echoes(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, out_echoes: int, out_counts: int,

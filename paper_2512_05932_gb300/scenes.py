@@ -207,6 +207,114 @@ def raycast(scene: Scene, U, V, az0, el0, daz, dele) -> GBuffer:
     return gb
 
 
+@dataclass
+class PinholeGBuffer:
+    """A pinhole rendering (include/lidar.h lidar_pinhole_t): pixel (i, j) looks
+    along camera-frame (X, Y, 1), X = (i + 1/2 - cx) / fx, Y = (j + 1/2 - cy) / fy;
+    R maps camera-frame vectors to the sensor frame. Planes [H, W] float32 as for
+    GBuffer (range along the pixel-centre ray, or z depth if depth_is_z)."""
+    W: int
+    H: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    R: np.ndarray
+    depth_is_z: bool
+    range: np.ndarray
+    nx: np.ndarray
+    ny: np.ndarray
+    nz: np.ndarray
+    rho_d: np.ndarray
+    retro: np.ndarray
+    ambient: np.ndarray
+
+    def planes(self):
+        return [getattr(self, p) for p in GBuffer.PLANES]
+
+    def pixel_dirs(self) -> np.ndarray:
+        """Unit sensor-frame directions of the pixel centres, float64 [H, W, 3]."""
+        X = (np.arange(self.W) + 0.5 - self.cx) / self.fx
+        Y = (np.arange(self.H) + 0.5 - self.cy) / self.fy
+        c = np.stack(np.broadcast_arrays(X[None, :], Y[:, None], np.ones((self.H, 1))), axis=-1)
+        c = c / np.linalg.norm(c, axis=-1, keepdims=True)
+        return c @ np.asarray(self.R, np.float64).T
+
+
+def camera_looking_along(yaw, pitch):
+    """Camera -> sensor rotation of a camera whose optical axis points at
+    (azimuth yaw, elevation pitch), image x to the right (decreasing azimuth)
+    and image y down."""
+    ca, sa, ce, se = math.cos(yaw), math.sin(yaw), math.cos(pitch), math.sin(pitch)
+    z = np.array([ce * ca, ce * sa, se])
+    x = np.array([sa, -ca, 0.0])
+    y = np.cross(z, x)
+    return np.stack([x, y, z], axis=1)
+
+
+def raycast_pinhole(scene: Scene, W, H, fx, fy, cx, cy, R, depth_is_z=False) -> PinholeGBuffer:
+    """Nearest-hit ray cast of the scene through the pinhole pixel centres."""
+    ph = PinholeGBuffer(W, H, fx, fy, cx, cy, np.asarray(R, np.float64), bool(depth_is_z), *[None] * 7)
+    dirs = ph.pixel_dirs()
+    P = _empty_planes(H, W)
+    for pl in scene.planes:
+        t = _hit_plane(dirs, pl.n, pl.d)
+        rho = np.full(t.shape, pl.rho_d)
+        retro = np.full(t.shape, pl.retro)
+        if pl.decal is not None:
+            dq = dirs * np.where(np.isfinite(t), t, 0.0)[..., None] - pl.decal.c
+            inside = (np.abs(dq @ pl.decal.e1) <= pl.decal.h1) & (np.abs(dq @ pl.decal.e2) <= pl.decal.h2)
+            inside &= np.isfinite(t)
+            rho = np.where(inside, pl.decal.rho_d, rho)
+            retro = np.where(inside, pl.decal.retro, retro)
+        better = t < P["range"]
+        for key, val in (("range", t), ("nx", pl.n[0]), ("ny", pl.n[1]), ("nz", pl.n[2]), ("rho_d", rho),
+                         ("retro", retro)):
+            P[key] = np.where(better, val, P[key])
+    for r in scene.rects:
+        n = r.n
+        t = _hit_plane(dirs, n, float(n @ r.c))
+        dq = dirs * np.where(np.isfinite(t), t, 0.0)[..., None] - r.c
+        inside = (np.abs(dq @ r.e1) <= r.h1) & (np.abs(dq @ r.e2) <= r.h2) & np.isfinite(t)
+        t = np.where(inside, t, np.inf)
+        better = t < P["range"]
+        for key, val in (("range", t), ("nx", n[0]), ("ny", n[1]), ("nz", n[2]), ("rho_d", r.rho_d),
+                         ("retro", r.retro)):
+            P[key] = np.where(better, val, P[key])
+    hit = np.isfinite(P["range"])
+    if scene.ambient == "uniform":
+        P["ambient"][:] = scene.ambient_level
+    elif scene.ambient == "sun":
+        P["ambient"] = np.where(hit, scene.ambient_level * P["rho_d"] / math.pi * np.maximum(0.0, P["nz"]), 0.0)
+    for k in ("nx", "ny", "nz", "rho_d", "retro"):
+        P[k] = np.where(hit, P[k], 0.0)
+    if depth_is_z:
+        # z depth = distance times the cosine to the optical axis
+        cz = dirs @ np.asarray(R, np.float64)[:, 2]
+        P["range"] = np.where(hit, P["range"] * cz, P["range"])
+    for k in GBuffer.PLANES:
+        setattr(ph, k, np.ascontiguousarray(P[k], dtype=np.float32))
+    return ph
+
+
+def pinhole_plane_retro(seed: int = 6, W: int = 320, H: int = 240, f: float = 2000.0, depth_is_z=False):
+    """The plane + retro patch scene rendered through a pinhole looking 0.5 deg
+    off the plane's normal (a 9.2 x 6.9 deg field of view), and the spherical
+    target grid (0.02 deg pitch) that covers it with a margin."""
+    g = rng(seed)
+    jit = g.uniform(-1e-3, 1e-3, size=2)
+    decal = Rect(np.array([10.0, jit[0], jit[1]]), np.array([0.0, 1.0, 0.0]),
+                 np.array([0.0, 0.0, 1.0]), 0.25, 0.25, rho_d=0.5, retro=100.0)
+    scene = Scene(planes=[Plane(np.array([1.0, 0.0, 0.0]), 10.0, 0.5, 0.0, decal)],
+                  ambient="uniform", ambient_level=0.01)
+    R = camera_looking_along(0.5 * DEG, 0.2 * DEG)
+    ph = raycast_pinhole(scene, W, H, f, f, W / 2.0, H / 2.0, R, depth_is_z)
+    pitch = 0.02 * DEG
+    U, V = 384, 256
+    grid = GBuffer(U, V, 0.5 * DEG - U * pitch / 2, 0.2 * DEG - V * pitch / 2, pitch, pitch, *[None] * 7)
+    return ph, grid
+
+
 def box_rects(center, half, yaw, rho_d, retro_faces) -> list:
     """The six faces of a box with vertical axis, as outward-facing rectangles."""
     cy, sy = math.cos(yaw), math.sin(yaw)
