@@ -216,10 +216,10 @@ def load_tensor_peak():
     return 1700.0, "fallback"
 
 
-def traffic_for_current_kernel(workload_name):
-    """dram bytes per launch of the footprint kernel from the committed ncu
-    summary, or None if absent, taken on another workload or on a different
-    kernel source."""
+def profile_for_current_kernel(workload_name):
+    """The committed ncu figures of the footprint kernel (dram bytes and
+    executed warp instructions per launch), or None if absent, taken on
+    another workload or on a different kernel source."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
@@ -228,7 +228,27 @@ def traffic_for_current_kernel(workload_name):
         sha = hashlib.sha256(f.read()).hexdigest()
     if d.get("kernel_sha256") != sha or not d.get("workload", "").startswith(workload_name):
         return None
-    return d.get("bytes_per_launch")
+    return d
+
+
+def traffic_for_current_kernel(workload_name):
+    """dram bytes per launch of the footprint kernel (see profile_for_current_kernel)."""
+    d = profile_for_current_kernel(workload_name)
+    return d.get("bytes_per_launch") if d else None
+
+
+def issue_roofline(workload_name, avg_ms, sm_mhz, n_sm):
+    """Issue rate of the footprint kernel: warp instructions per launch (ncu,
+    same kernel source) over the live launch time, against one instruction
+    per clock on each of the 4 schedulers of every SM at the sampled clock."""
+    d = profile_for_current_kernel(workload_name)
+    if not d or not d.get("inst_executed") or not sm_mhz:
+        return None
+    ach = d["inst_executed"] / (avg_ms * 1e-3)
+    peak = n_sm * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp instructions/s", "frac": ach / peak,
+            "instructions_per_launch": d["inst_executed"],
+            "peak_source": f"{n_sm} SMs x 4 schedulers x {sm_mhz:.0f} MHz (sampled SM clock)"}
 
 
 def job_rate(local_ms, units_per_rank, steps, world, dist=None, device=None):
@@ -388,11 +408,15 @@ def run_gb300(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     alg = algorithmic_bytes(w, args.echo_only)
     achieved = alg / (avg_ms * 1e-3) / 1e9
-    pix_samples = None
+    # the committed counters belong to the plain frame's kernel launch only
+    prof_key = w.name + ("_echo_only" if args.echo_only else "")
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-            "traffic": traffic_for_current_kernel(w.name), "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
+            "traffic": traffic_for_current_kernel(prof_key), "algorithmic_bytes": alg, "avg_launch_ms": avg_ms,
             "kernel_share": {k: tot[k] / sum(tot.values()) for k in names}}
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof["issue"] = issue_roofline(prof_key, avg_ms, clocks.get("sm_mhz"), n_sm) if dom == "footprint_wave" else None
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -412,7 +436,7 @@ def run_gb300(args, rank, world, local_rank):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "kernel_ms": {k: tot[k] / max(1, kern[k][1]) for k in names}}
     print(json.dumps(line), flush=True)
     L.close()
