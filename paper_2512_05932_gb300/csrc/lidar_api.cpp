@@ -378,6 +378,8 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
     sa.az0d = g->az0; sa.el0d = g->el0; sa.dazd = g->daz; sa.deld = g->del;
     sa.panorama = is_panorama(g) ? 1 : 0;
     sa.support_rad = l->support_rad;
+    sa.sup_u = l->sup_u;
+    sa.sup_v = l->sup_v;
     sa.beams = beams;
     sa.bin_records = l->deposit != 0 ? 1 : 0;
     return sa;
@@ -732,6 +734,8 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         l->tcv = (float)(0.5 * (p->table_h - 1) + 1.0);
         double hu = (0.5 * (p->table_w - 1) + 1) * p->pitch_deg, hv = (0.5 * (p->table_h - 1) + 1) * p->pitch_deg;
         l->support_rad = std::sqrt(hu * hu + hv * hv) * kDeg;
+        l->sup_u = hu * kDeg;
+        l->sup_v = hv * kDeg;
     }
     if (!(std::isfinite(l->Z) && l->Z > 0)) {
         double Z = l->Z;

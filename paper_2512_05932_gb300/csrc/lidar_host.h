@@ -19,6 +19,7 @@ struct lidar {
     bool separable = false;    // LIDAR_PROFILE_SEPARABLE: pairs of H and V instead of quads
     double Z = 0.0;
     double support_rad = 0.0;
+    double sup_u = 0.0, sup_v = 0.0;  // rectangular support (rad) of a table / separable profile
     // radial profile
     float kg = 0.f, trunc2 = 0.f, tail_amp = 0.f, tc2_inv = 0.f, tail_hp = 0.f;
     // table profile

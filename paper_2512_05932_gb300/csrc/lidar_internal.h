@@ -55,6 +55,7 @@ struct SetupArgs {
     double az0d, el0d, dazd, deld;
     int panorama;
     double support_rad;
+    double sup_u, sup_v;     // half-widths (rad) of a table / separable profile's rectangle (0: radial)
     BeamParam *beams;
 };
 

@@ -197,12 +197,34 @@ __device__ void setup_beam(const SetupArgs &A, int b)
     double th = core ? A.core_rad : A.support_rad;
     long r0 = (long)ceil((el_b - th - A.el0d) / A.deld - 0.5) - 1;
     long r1 = (long)floor((el_b + th - A.el0d) / A.deld - 0.5) + 1;
+    // A table or separable profile is zero outside the rectangle |u| <= hu,
+    // |v| <= hv, where every direction d has |d.E1| <= hu and |d.E2| <= hv
+    // (d.E1 = sin(theta) cos(phi) <= u): with d = cos(theta) a + (d.E1) E1 +
+    // (d.E2) E2 and theta <= th, its height d_z and its east component
+    // d.g1 = cos(el) sin(az - az_b) are bounded by the same sums, which gives
+    // a box of about half the circle's when the rectangle is a square.
+    double dl_rect = -1.0;
+    if (!core && A.sup_u > 0.0) {
+        const double E2[3] = {a[1] * E1[2] - a[2] * E1[1], a[2] * E1[0] - a[0] * E1[2], a[0] * E1[1] - a[1] * E1[0]};
+        const double zc = a[2] * cos(th);
+        const double zs = A.sup_u * fabs(E1[2]) + A.sup_v * fabs(E2[2]);
+        const double el_lo = asin(fmax(-1.0, fmin(a[2], zc) - zs));
+        const double el_hi = asin(fmin(1.0, fmax(a[2], zc) + zs));
+        const long q0 = (long)ceil((el_lo - A.el0d) / A.deld - 0.5) - 1;
+        const long q1 = (long)floor((el_hi - A.el0d) / A.deld - 0.5) + 1;
+        if (q0 > r0) r0 = q0;
+        if (q1 < r1) r1 = q1;
+        const double S = A.sup_u * fabs(E1[0] * g1[0] + E1[1] * g1[1]) + A.sup_v * fabs(E2[0] * g1[0] + E2[1] * g1[1]);
+        const double cmin = fmin(cos(el_lo), cos(el_hi));
+        if (cmin > 0.0 && S < cmin) dl_rect = asin(S / cmin);
+    }
     if (r0 < 0) r0 = 0;
     if (r1 > A.V - 1) r1 = A.V - 1;
     long c0, c1;
     bool full = fabs(el_b) + th >= 0.5 * CUDART_PI - 1e-9;
     if (!full) {
         double dl = asin(fmin(1.0, sin(th) / ceb));
+        if (dl_rect >= 0.0 && dl_rect < dl) dl = dl_rect;
         c0 = (long)ceil((az_b - dl - A.az0d) / A.dazd - 0.5) - 1;
         c1 = (long)floor((az_b + dl - A.az0d) / A.dazd - 0.5) + 1;
         if (A.panorama && c1 - c0 + 1 >= A.U) full = true;
