@@ -380,6 +380,7 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
     sa.support_rad = l->support_rad;
     sa.sup_u = l->sup_u;
     sa.sup_v = l->sup_v;
+    sa.cos_sup = std::cos(l->support_rad);
     sa.beams = beams;
     sa.bin_records = l->deposit != 0 ? 1 : 0;
     return sa;

@@ -56,6 +56,7 @@ struct SetupArgs {
     int panorama;
     double support_rad;
     double sup_u, sup_v;     // half-widths (rad) of a table / separable profile's rectangle (0: radial)
+    double cos_sup;          // cos(support_rad)
     BeamParam *beams;
 };
 

@@ -202,21 +202,27 @@ __device__ void setup_beam(const SetupArgs &A, int b)
     // (d.E1 = sin(theta) cos(phi) <= u): with d = cos(theta) a + (d.E1) E1 +
     // (d.E2) E2 and theta <= th, its height d_z and its east component
     // d.g1 = cos(el) sin(az - az_b) are bounded by the same sums, which gives
-    // a box of about half the circle's when the rectangle is a square.
+    // a box of about half the circle's when the rectangle is a square. FP32
+    // suffices: its errors (~1e-7 rad) are far below the one-pixel margin the
+    // box keeps on each side.
     double dl_rect = -1.0;
     if (!core && A.sup_u > 0.0) {
-        const double E2[3] = {a[1] * E1[2] - a[2] * E1[1], a[2] * E1[0] - a[0] * E1[2], a[0] * E1[1] - a[1] * E1[0]};
-        const double zc = a[2] * cos(th);
-        const double zs = A.sup_u * fabs(E1[2]) + A.sup_v * fabs(E2[2]);
-        const double el_lo = asin(fmax(-1.0, fmin(a[2], zc) - zs));
-        const double el_hi = asin(fmin(1.0, fmax(a[2], zc) + zs));
-        const long q0 = (long)ceil((el_lo - A.el0d) / A.deld - 0.5) - 1;
-        const long q1 = (long)floor((el_hi - A.el0d) / A.deld - 0.5) + 1;
+        const float ax = (float)a[0], ay = (float)a[1], az = (float)a[2];
+        const float e1x = (float)E1[0], e1y = (float)E1[1], e1z = (float)E1[2];
+        const float e2x = ay * e1z - az * e1y, e2y = az * e1x - ax * e1z, e2z = ax * e1y - ay * e1x;
+        const float su = (float)A.sup_u, sv = (float)A.sup_v;
+        const float zc = az * (float)A.cos_sup;
+        const float zs = su * fabsf(e1z) + sv * fabsf(e2z);
+        const float el_lo = asinf(fmaxf(-1.f, fminf(az, zc) - zs));
+        const float el_hi = asinf(fminf(1.f, fmaxf(az, zc) + zs));
+        const long q0 = (long)ceil(((double)el_lo - A.el0d) / A.deld - 0.5) - 1;
+        const long q1 = (long)floor(((double)el_hi - A.el0d) / A.deld - 0.5) + 1;
         if (q0 > r0) r0 = q0;
         if (q1 < r1) r1 = q1;
-        const double S = A.sup_u * fabs(E1[0] * g1[0] + E1[1] * g1[1]) + A.sup_v * fabs(E2[0] * g1[0] + E2[1] * g1[1]);
-        const double cmin = fmin(cos(el_lo), cos(el_hi));
-        if (cmin > 0.0 && S < cmin) dl_rect = asin(S / cmin);
+        const float g1x = (float)g1[0], g1y = (float)g1[1];
+        const float S = su * fabsf(e1x * g1x + e1y * g1y) + sv * fabsf(e2x * g1x + e2y * g1y);
+        const float cmin = fminf(cosf(el_lo), cosf(el_hi));
+        if (cmin > 0.f && S < cmin) dl_rect = (double)asinf(S / cmin);
     }
     if (r0 < 0) r0 = 0;
     if (r1 > A.V - 1) r1 = A.V - 1;
