@@ -839,28 +839,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 float dEl = ((float)(row - P.ri) - P.rf) * A.del;
                 sincosf(dEl, &sdEl, &cdEl);
             }
-            if (KIND == LIDAR_PROFILE_RADIAL && my_lo <= my_hi) {
-                // A radial profile is zero beyond theta = th: on this row the
-                // support is the chord |dAz| <= 2 asin(sqrt(nu / 2)), nu =
-                // (cos dEl - cos th) / (cos el cos el_b), with the numerator in
-                // product form (no cancellation at the circle's top and bottom)
-                // and th widened by a pixel so that the bound stays conservative.
-                const float th = sqrtf(t2max) + fmaxf(A.daz, A.del);
-                const float dEl = ((float)(row - P.ri) - P.rf) * A.del;
-                const float num = 2.f * sinf(0.5f * (th + dEl)) * sinf(0.5f * (th - dEl));
-                const float den = cosEl * P.cos_elb;
-                if (num <= 0.f) {
-                    my_lo = 1; my_hi = 0;
-                } else if (den > 0.f) {
-                    const float h = 0.5f * num / den;
-                    if (h < 1.f) {
-                        const float wc = 2.f * asinf(sqrtf(h)) / A.daz;
-                        const float ua = (float)P.ci + P.cf;
-                        my_lo = max(my_lo, (int)ceilf(ua - wc) - 1);
-                        my_hi = min(my_hi, (int)floorf(ua + wc) + 1);
-                    }
-                }
-            }
             float Kv = P.sin_elb * cosEl;
             float Kc = P.cos_elb * cosEl;
             // x = cg xg + sg yg, y = cg yg - sg xg with xg = cosEl sD and
