@@ -271,8 +271,10 @@ lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuf
  * are HOST pointers, and the outputs are host arrays (waveforms
  * [n_beams][n_bins], echoes [n_beams][max_echoes], counts [n_beams]). The
  * library copies the inputs to device buffers it owns, simulates, copies the
- * results back and synchronises `stream` before returning. Page-locked host
- * memory gives asynchronous, full-bandwidth copies. */
+ * results back and synchronises `stream` before returning. A frame of at
+ * least 1216 beam groups is simulated in 4 launches, and the results of each
+ * are copied back on a library-owned stream while the next one runs.
+ * Page-locked host memory gives asynchronous, full-bandwidth copies. */
 lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);

@@ -348,6 +348,9 @@ void free_all(lidar_t *l)
     cudaFree(l->d_slot_pool);
     cudaFree(l->d_slot_busy);
     cudaFree(l->d_err);
+    if (l->copy_stream) cudaStreamDestroy(l->copy_stream);
+    for (cudaEvent_t &ev : l->chunk_ev)
+        if (ev) cudaEventDestroy(ev);
     tail_free(l);
 }
 
@@ -446,9 +449,14 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
 }
 
 // Enqueues the setup and footprint kernels of one frame; wave == NULL
-// selects the echo-only form (waveforms in the pooled slots).
+// selects the echo-only form (waveforms in the pooled slots). With n_chunks
+// > 1 the footprint kernel is launched once per range of whole beam groups,
+// chunk i covering beams [bounds[i], bounds[i + 1]), and chunk_done[i] is
+// recorded on `s` after it (so that its outputs can be copied while the next
+// chunk runs).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
-                       int32_t *counts, cudaStream_t s)
+                       int32_t *counts, cudaStream_t s, int n_chunks = 1, const int *bounds = nullptr,
+                       cudaEvent_t *chunk_done = nullptr)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -485,8 +493,26 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.slots_per_sm = l->slots_per_sm;
         fa.err = l->d_err;
     }
-    e = gbl::launch_footprint(l->kind, tc ? l->G_tc : l->G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
-    if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
+    const int G = tc ? l->G_tc : l->G;
+    if (n_chunks <= 1) {
+        e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
+        if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
+    } else {
+        for (int i = 0; i < n_chunks; ++i) {
+            const int b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
+            gbl::FootprintArgs fc = fa;
+            fc.beams = l->d_beams + b0;
+            fc.n_beams = nb;
+            fc.wave = wave + (size_t)b0 * l->n_bins;
+            fc.echoes = echoes + (size_t)b0 * l->max_echoes;
+            fc.counts = counts + b0;
+            if (nb > 0) {
+                e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, s);
+                if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
+            }
+            if ((e = cudaEventRecord(chunk_done[i], s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+        }
+    }
     if (ev2) cudaEventRecord(ev2, s);
     return LIDAR_OK;
 }
@@ -922,15 +948,38 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     }
     dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
     dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
-    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s)) != LIDAR_OK) return st;
-    if ((e = cudaMemcpyAsync(wave, l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost,
-                             s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
-                             cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess)
-        return cuda_fail(l, e, "result download");
+    // A frame with many beam groups is simulated in kHostChunks launches whose
+    // results are copied back on a second stream while the next one runs.
+    const int G = l->deposit != 0 ? l->G_tc : l->G;
+    const int ng = (l->n_beams + G - 1) / G;
+    const int K = ng >= 8 * 152 ? kHostChunks : 1;
+    int bounds[kHostChunks + 1];
+    for (int i = 0; i <= K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * i / K) * G);
+    if (K > 1) {
+        if (!l->copy_stream &&
+            (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamCreate(result copies)");
+        for (int i = 0; i < kHostChunks; ++i)
+            if (!l->chunk_ev[i] && (e = cudaEventCreateWithFlags(&l->chunk_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaEventCreate(result copies)");
+    }
+    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K, bounds, l->chunk_ev)) != LIDAR_OK) return st;
+    for (int i = 0; i < K; ++i) {
+        const size_t b0 = (size_t)bounds[i], nb = (size_t)(bounds[i + 1] - bounds[i]);
+        cudaStream_t cs = K > 1 ? l->copy_stream : s;
+        if (K > 1 && (e = cudaStreamWaitEvent(cs, l->chunk_ev[i], 0)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamWaitEvent");
+        if ((e = cudaMemcpyAsync(wave + b0 * l->n_bins, l->d_wave + b0 * l->n_bins, nb * l->n_bins * sizeof(float),
+                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(echoes + b0 * l->max_echoes, l->d_echo + b0 * l->max_echoes,
+                                 nb * l->max_echoes * sizeof(lidar_echo_t), cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(counts + b0, l->d_counts + b0, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, cs)) !=
+                cudaSuccess)
+            return cuda_fail(l, e, "result download");
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+    if (K > 1 && (e = cudaStreamSynchronize(l->copy_stream)) != cudaSuccess)
+        return cuda_fail(l, e, "cudaStreamSynchronize(result copies)");
     return LIDAR_OK;
 }
 

@@ -54,6 +54,10 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
+    // lidar_simulate_host: results of finished beam chunks are copied back on
+    // copy_stream while later chunks run (chunk_ev[i]: chunk i finished)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
@@ -92,6 +96,7 @@ constexpr double kC = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kDeg = kPi / 180.0;
 constexpr double kMaxSupportDeg = 10.0;
+constexpr int kHostChunks = 4;  // footprint launches per frame of lidar_simulate_host (large frames)
 
 lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...);
 lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what);
