@@ -393,6 +393,7 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
 gbl::FootprintArgs model_args(const lidar_t *l)
 {
     gbl::FootprintArgs fa{};
+    fa.kind_radial = l->kind == LIDAR_PROFILE_RADIAL ? 1 : 0;
     fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
     fa.invZ = (float)(1.0 / l->Z);
     fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;

@@ -325,11 +325,12 @@ struct Layout {
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
+    size_t off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_chord, off_ctr,
+        off_bp, total;
 };
 
 
-__host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
+__host__ __device__ inline Layout make_layout(int G, int n_bins, int M, bool chord = false)
 {
     Layout L;
     L.pad = 32 * ((M + 16 + 31) / 32);
@@ -349,6 +350,7 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
     L.off_tab = off; off += (size_t)G * kTC * sizeof(float2);
     L.off_rtab = off; off += (size_t)G * kRT * sizeof(float2);
     L.off_ctab = off; off += (size_t)kRT * sizeof(float);
+    L.off_chord = off; off += chord ? (size_t)G * kRT * sizeof(float) : 0;  // radial profiles only
     L.off_ctr = off; off += 16;
     off = (off + 15) & ~(size_t)15;
     L.off_bp = off; off += (size_t)G * sizeof(BeamParam);
@@ -693,7 +695,7 @@ template <int KIND, int G, bool TC>
 __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
 {
     const int nb = A.n_bins, M = A.M;
-    const Layout Ly = make_layout(G, nb, M);
+    const Layout Ly = make_layout(G, nb, M, KIND == LIDAR_PROFILE_RADIAL);
     const int pad = Ly.pad;
     float *hbuf = reinterpret_cast<float *>(smem_raw);
     float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
@@ -705,6 +707,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
     float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
     float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
+    float *chord = reinterpret_cast<float *>(smem_raw + Ly.off_chord);  // radial: per-(beam, row) half-width
     int *uctr = reinterpret_cast<int *>(smem_raw + Ly.off_ctr);
     BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
 
@@ -759,7 +762,23 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             float sv, cv;
             sincosf(dEl, &sv, &cv);
             rtab[jj * kRT + rr] = make_float2(sv, cv);
-            if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
+            const float ce = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
+            if (jj == 0) ctab[rr] = ce;
+            if (KIND == LIDAR_PROFILE_RADIAL) {
+                // A radial profile is zero beyond theta = th: on this row the
+                // support is the chord |dAz| <= 2 asin(sqrt(nu / 2)), nu =
+                // (cos dEl - cos th) / (cos el cos el_b), with the numerator in
+                // product form (no cancellation at the circle's top and bottom)
+                // and th widened by a pixel so that the bound stays conservative.
+                // Stored as the half-width in columns; -1: no pixel; 1e30: any.
+                const float th = sqrtf(Q.pad0 ? A.core2 : A.trunc2) + fmaxf(A.daz, A.del);
+                const float num = 2.f * sinf(0.5f * (th + dEl)) * sinf(0.5f * (th - dEl));
+                const float den = ce * Q.cos_elb;
+                float wc = 1e30f;
+                if (num <= 0.f) wc = -1.f;
+                else if (den > 0.f && 0.5f * num < den) wc = 2.f * asinf(sqrtf(0.5f * num / den)) / A.daz;
+                chord[jj * kRT + rr] = wc;
+            }
         }
     }
 
@@ -834,6 +853,16 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             if (use_rtab) {
                 const float2 rt = rtab[j * kRT + (row - R0)];
                 sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
+                if (KIND == LIDAR_PROFILE_RADIAL && my_lo <= my_hi) {
+                    const float wc = chord[j * kRT + (row - R0)];
+                    if (wc < 0.f) {
+                        my_lo = 1; my_hi = 0;
+                    } else if (wc < 1e29f) {
+                        const float ua = (float)P.ci + P.cf;
+                        my_lo = max(my_lo, (int)ceilf(ua - wc) - 1);
+                        my_hi = min(my_hi, (int)floorf(ua + wc) + 1);
+                    }
+                }
             } else {
                 cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
                 float dEl = ((float)(row - P.ri) - P.rf) * A.del;
@@ -1381,7 +1410,7 @@ __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_batch_kernel(Footpr
 
 size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 {
-    return make_layout(G, a.n_bins, a.M).total;
+    return make_layout(G, a.n_bins, a.M, a.kind_radial != 0).total;
 }
 
 int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
