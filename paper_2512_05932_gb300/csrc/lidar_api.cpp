@@ -825,6 +825,7 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     gbl::FootprintArgs probe{};
     probe.n_bins = l->n_bins;
     probe.M = l->M;
+    probe.kind_radial = l->kind == LIDAR_PROFILE_RADIAL ? 1 : 0;  // the layout depends on it
     // prefer the largest group that still lets two CTAs share an SM, then
     // the largest group that fits at all
     int chosen = 0;

@@ -1447,9 +1447,17 @@ cudaError_t footprint_occupancy(int kind, int G, bool tc, int threads, size_t sm
     return cudaErrorInvalidValue;
 }
 
+// The shared-memory layout a kernel instantiation uses (radial profiles add
+// the chord table): a launch with less dynamic shared memory is refused.
+bool smem_covers_layout(int kind, int G, size_t smem, const FootprintArgs &a)
+{
+    return smem >= make_layout(G, a.n_bins, a.M, kind == LIDAR_PROFILE_RADIAL).total;
+}
+
 cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem, const FootprintArgs &a,
                              cudaStream_t s)
 {
+    if (!smem_covers_layout(kind, G, smem, a)) return cudaErrorInvalidValue;
     int groups = (a.n_beams + G - 1) / G;
 #define GBL_CASE(K, GG, T)                                               \
     if (kind == K && G == GG && tc == T) {                               \
@@ -1476,6 +1484,7 @@ cudaError_t launch_footprint_batch(int kind, int G, bool tc, int threads, int gr
                                    const FootprintArgs &base, const FrameDesc *frames, const int2 *items,
                                    int n_items, int *counter, cudaStream_t s)
 {
+    if (!smem_covers_layout(kind, G, smem, base)) return cudaErrorInvalidValue;
 #define GBL_CASE(K, GG, T)                                                                                     \
     if (kind == K && G == GG && tc == T) {                                                                     \
         footprint_batch_kernel<K, GG, T><<<grid, threads, smem, s>>>(base, frames, items, n_items, counter); \
