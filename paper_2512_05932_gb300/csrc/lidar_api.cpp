@@ -393,7 +393,6 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
 gbl::FootprintArgs model_args(const lidar_t *l)
 {
     gbl::FootprintArgs fa{};
-    fa.kind_radial = l->kind == LIDAR_PROFILE_RADIAL ? 1 : 0;
     fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
     fa.invZ = (float)(1.0 / l->Z);
     fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
@@ -825,7 +824,6 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     gbl::FootprintArgs probe{};
     probe.n_bins = l->n_bins;
     probe.M = l->M;
-    probe.kind_radial = l->kind == LIDAR_PROFILE_RADIAL ? 1 : 0;  // the layout depends on it
     // prefer the largest group that still lets two CTAs share an SM, then
     // the largest group that fits at all
     int chosen = 0;

@@ -67,7 +67,6 @@ struct FootprintArgs {
     const BeamParam *beams;
     int n_beams;
     // profile
-    int kind_radial;   // radial profile (shared-memory layout: per-row chord table)
     float kg;          // -log2(e) / (2 sigma^2), rad^-2 (radial)
     float trunc2;      // support radius^2, rad^2 (radial)
     float tail_amp, tc2_inv, tail_hp;  // radial tail: amp * min(1, (t2 * tc2_inv)^hp)

@@ -325,12 +325,11 @@ struct Layout {
     int HB;        // floats per beam buffer (odd)
     int taps_off;  // tap m lives at index taps_off + m
     int taps_len;
-    size_t off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_chord, off_ctr,
-        off_bp, total;
+    size_t off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_rtab, off_ctab, off_ctr, off_bp, total;
 };
 
 
-__host__ __device__ inline Layout make_layout(int G, int n_bins, int M, bool chord = false)
+__host__ __device__ inline Layout make_layout(int G, int n_bins, int M)
 {
     Layout L;
     L.pad = 32 * ((M + 16 + 31) / 32);
@@ -350,7 +349,6 @@ __host__ __device__ inline Layout make_layout(int G, int n_bins, int M, bool cho
     L.off_tab = off; off += (size_t)G * kTC * sizeof(float2);
     L.off_rtab = off; off += (size_t)G * kRT * sizeof(float2);
     L.off_ctab = off; off += (size_t)kRT * sizeof(float);
-    L.off_chord = off; off += chord ? (size_t)G * kRT * sizeof(float) : 0;  // radial profiles only
     L.off_ctr = off; off += 16;
     off = (off + 15) & ~(size_t)15;
     L.off_bp = off; off += (size_t)G * sizeof(BeamParam);
@@ -695,7 +693,7 @@ template <int KIND, int G, bool TC>
 __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
 {
     const int nb = A.n_bins, M = A.M;
-    const Layout Ly = make_layout(G, nb, M, KIND == LIDAR_PROFILE_RADIAL);
+    const Layout Ly = make_layout(G, nb, M);
     const int pad = Ly.pad;
     float *hbuf = reinterpret_cast<float *>(smem_raw);
     float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
@@ -707,7 +705,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
     float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
     float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
-    float *chord = reinterpret_cast<float *>(smem_raw + Ly.off_chord);  // radial: per-(beam, row) half-width
     int *uctr = reinterpret_cast<int *>(smem_raw + Ly.off_ctr);
     BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
 
@@ -762,23 +759,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             float sv, cv;
             sincosf(dEl, &sv, &cv);
             rtab[jj * kRT + rr] = make_float2(sv, cv);
-            const float ce = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
-            if (jj == 0) ctab[rr] = ce;
-            if (KIND == LIDAR_PROFILE_RADIAL) {
-                // A radial profile is zero beyond theta = th: on this row the
-                // support is the chord |dAz| <= 2 asin(sqrt(nu / 2)), nu =
-                // (cos dEl - cos th) / (cos el cos el_b), with the numerator in
-                // product form (no cancellation at the circle's top and bottom)
-                // and th widened by a pixel so that the bound stays conservative.
-                // Stored as the half-width in columns; -1: no pixel; 1e30: any.
-                const float th = sqrtf(Q.pad0 ? A.core2 : A.trunc2) + fmaxf(A.daz, A.del);
-                const float num = 2.f * sinf(0.5f * (th + dEl)) * sinf(0.5f * (th - dEl));
-                const float den = ce * Q.cos_elb;
-                float wc = 1e30f;
-                if (num <= 0.f) wc = -1.f;
-                else if (den > 0.f && 0.5f * num < den) wc = 2.f * asinf(sqrtf(0.5f * num / den)) / A.daz;
-                chord[jj * kRT + rr] = wc;
-            }
+            if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
         }
     }
 
@@ -853,16 +834,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             if (use_rtab) {
                 const float2 rt = rtab[j * kRT + (row - R0)];
                 sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
-                if (KIND == LIDAR_PROFILE_RADIAL && my_lo <= my_hi) {
-                    const float wc = chord[j * kRT + (row - R0)];
-                    if (wc < 0.f) {
-                        my_lo = 1; my_hi = 0;
-                    } else if (wc < 1e29f) {
-                        const float ua = (float)P.ci + P.cf;
-                        my_lo = max(my_lo, (int)ceilf(ua - wc) - 1);
-                        my_hi = min(my_hi, (int)floorf(ua + wc) + 1);
-                    }
-                }
             } else {
                 cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
                 float dEl = ((float)(row - P.ri) - P.rf) * A.del;
@@ -1410,7 +1381,7 @@ __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_batch_kernel(Footpr
 
 size_t footprint_smem_bytes(int G, const FootprintArgs &a)
 {
-    return make_layout(G, a.n_bins, a.M, a.kind_radial != 0).total;
+    return make_layout(G, a.n_bins, a.M).total;
 }
 
 int footprint_pad(int M) { return make_layout(1, 32, M).pad; }
@@ -1447,17 +1418,17 @@ cudaError_t footprint_occupancy(int kind, int G, bool tc, int threads, size_t sm
     return cudaErrorInvalidValue;
 }
 
-// The shared-memory layout a kernel instantiation uses (radial profiles add
-// the chord table): a launch with less dynamic shared memory is refused.
-bool smem_covers_layout(int kind, int G, size_t smem, const FootprintArgs &a)
+// The shared-memory layout a kernel instantiation uses: a launch with less
+// dynamic shared memory is refused.
+bool smem_covers_layout(int G, size_t smem, const FootprintArgs &a)
 {
-    return smem >= make_layout(G, a.n_bins, a.M, kind == LIDAR_PROFILE_RADIAL).total;
+    return smem >= make_layout(G, a.n_bins, a.M).total;
 }
 
 cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem, const FootprintArgs &a,
                              cudaStream_t s)
 {
-    if (!smem_covers_layout(kind, G, smem, a)) return cudaErrorInvalidValue;
+    if (!smem_covers_layout(G, smem, a)) return cudaErrorInvalidValue;
     int groups = (a.n_beams + G - 1) / G;
 #define GBL_CASE(K, GG, T)                                               \
     if (kind == K && G == GG && tc == T) {                               \
@@ -1484,7 +1455,7 @@ cudaError_t launch_footprint_batch(int kind, int G, bool tc, int threads, int gr
                                    const FootprintArgs &base, const FrameDesc *frames, const int2 *items,
                                    int n_items, int *counter, cudaStream_t s)
 {
-    if (!smem_covers_layout(kind, G, smem, base)) return cudaErrorInvalidValue;
+    if (!smem_covers_layout(G, smem, base)) return cudaErrorInvalidValue;
 #define GBL_CASE(K, GG, T)                                                                                     \
     if (kind == K && G == GG && tc == T) {                                                                     \
         footprint_batch_kernel<K, GG, T><<<grid, threads, smem, s>>>(base, frames, items, n_items, counter); \
