@@ -1,5 +1,5 @@
 // Internal types of the tail network kernels (lidar_net.cu) and their host
-// driver (lidar_net_api.cpp). Not part of the public ABI.
+// side (lidar_net_api.cpp). Not part of the public ABI.
 #pragma once
 
 #include <cuda_fp16.h>
