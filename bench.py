@@ -237,6 +237,54 @@ def traffic_for_current_kernel(workload_name):
     return d.get("bytes_per_launch") if d else None
 
 
+def support_pixels_per_beam(w, n_sample=384):
+    """Mean number of pixel-samples per beam, (beam, pixel) pairs inside the
+    profile's truncated support and the G-buffer, over n_sample evenly spaced
+    beams: pixel-centre offsets in each beam's azimuthal-equidistant frame
+    (FP64), against the radial truncation or the table's rectangle."""
+    gb, prof = w.gbuffer, w.profile
+    deg = math.pi / 180
+    if prof["kind"] == 0:
+        lim = ("circle", prof["trunc_deg"] * deg)
+    else:
+        nu, nv = ((prof["table"].shape[1], prof["table"].shape[0]) if prof["kind"] == 1
+                  else (len(prof["h"]), len(prof["v"])))
+        lim = ("rect", (0.5 * (nu - 1) + 1) * prof["pitch_deg"] * deg, (0.5 * (nv - 1) + 1) * prof["pitch_deg"] * deg)
+    R = np.asarray(w.pose, np.float64)
+    rad = lim[1] if lim[0] == "circle" else math.hypot(lim[1], lim[2])
+    beams = np.linspace(0, len(w.dirs) - 1, min(n_sample, len(w.dirs))).astype(int)
+    counts = []
+    for b in beams:
+        d = np.asarray(w.dirs[b], np.float64)
+        d /= np.linalg.norm(d)
+        e1 = np.array([-d[1], d[0], 0.0])
+        e1 = e1 / np.linalg.norm(e1) if np.linalg.norm(e1) > 1e-12 else np.array([0.0, 1.0, 0.0])
+        a, E1 = R @ d, R @ e1
+        E2 = np.cross(a, E1)
+        el_b, az_b = math.asin(max(-1.0, min(1.0, a[2]))), math.atan2(a[1], a[0])
+        v0 = max(0, int((el_b - rad - gb.el0) / gb.dele) - 1)
+        v1 = min(gb.V, int((el_b + rad - gb.el0) / gb.dele) + 2)
+        dl = math.asin(min(1.0, math.sin(rad) / max(1e-9, math.cos(el_b) - math.sin(rad))))
+        u0 = max(0, int((az_b - dl - gb.az0) / gb.daz) - 1)
+        u1 = min(gb.U, int((az_b + dl - gb.az0) / gb.daz) + 2)
+        if v0 >= v1 or u0 >= u1:
+            counts.append(0)
+            continue
+        el = gb.el0 + (np.arange(v0, v1) + 0.5) * gb.dele
+        az = gb.az0 + (np.arange(u0, u1) + 0.5) * gb.daz
+        ce = np.cos(el)[:, None]
+        D = np.stack(np.broadcast_arrays(ce * np.cos(az)[None, :], ce * np.sin(az)[None, :], np.sin(el)[:, None]), -1)
+        c = np.clip(D @ a, -1.0, 1.0)
+        th = np.arccos(c)
+        if lim[0] == "circle":
+            inside = (th <= lim[1]) & (c > 0)
+        else:
+            f = np.where(th > 1e-12, th / np.maximum(np.sin(th), 1e-300), 1.0)
+            inside = (np.abs((D @ E1) * f) <= lim[1]) & (np.abs((D @ E2) * f) <= lim[2]) & (c > 0)
+        counts.append(int(inside.sum()))
+    return float(np.mean(counts)), len(beams)
+
+
 def issue_roofline(workload_name, avg_ms, sm_mhz, n_sm):
     """Issue rate of the footprint kernel: warp instructions per launch (ncu,
     same kernel source) over the live launch time, against one instruction
@@ -418,6 +466,11 @@ def run_gb300(args, rank, world, local_rank):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     roof["issue"] = issue_roofline(prof_key, avg_ms, clocks.get("sm_mhz"), n_sm) if dom == "footprint_wave" else None
 
+    per_beam, n_samp = support_pixels_per_beam(w)
+    pixel_samples = {"per_s": value * per_beam, "per_beam_mean": per_beam,
+                     "sample": f"{n_samp} evenly spaced beams: (beam, pixel) pairs inside the profile's "
+                               "truncated support and the G-buffer"}
+
     cpu = None
     if not args.no_cpu_baseline:
         cores = cpu_cores()
@@ -433,7 +486,7 @@ def run_gb300(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.deposit == "tc_bf16" else "f32",
             "data": "synthetic", "config": config_of(w, extra),
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "pixel_samples": pixel_samples,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),
             "clocks": clocks,
