@@ -271,16 +271,32 @@ def raycast_pinhole(scene: Scene, W, H, fx, fy, cx, cy, R, depth_is_z=False) -> 
         for key, val in (("range", t), ("nx", pl.n[0]), ("ny", pl.n[1]), ("nz", pl.n[2]), ("rho_d", rho),
                          ("retro", retro)):
             P[key] = np.where(better, val, P[key])
+    Rm = np.asarray(R, np.float64)
     for r in scene.rects:
+        # the pixels the rectangle can cover: its projected corners' box (+2 px),
+        # or the whole image if a corner lies behind the camera
+        corners = [r.c + sa * r.h1 * r.e1 + sb * r.h2 * r.e2 for sa in (-1, 1) for sb in (-1, 1)]
+        cam = np.array(corners) @ Rm  # camera-frame coordinates
+        if (cam[:, 2] > 1e-6).all():
+            pxs = cx + fx * cam[:, 0] / cam[:, 2]
+            pys = cy + fy * cam[:, 1] / cam[:, 2]
+            i0, i1 = max(0, int(math.floor(pxs.min())) - 2), min(W, int(math.ceil(pxs.max())) + 3)
+            j0, j1 = max(0, int(math.floor(pys.min())) - 2), min(H, int(math.ceil(pys.max())) + 3)
+            if i0 >= i1 or j0 >= j1:
+                continue
+        else:
+            i0, i1, j0, j1 = 0, W, 0, H
+        sl = (slice(j0, j1), slice(i0, i1))
+        d = dirs[sl]
         n = r.n
-        t = _hit_plane(dirs, n, float(n @ r.c))
-        dq = dirs * np.where(np.isfinite(t), t, 0.0)[..., None] - r.c
+        t = _hit_plane(d, n, float(n @ r.c))
+        dq = d * np.where(np.isfinite(t), t, 0.0)[..., None] - r.c
         inside = (np.abs(dq @ r.e1) <= r.h1) & (np.abs(dq @ r.e2) <= r.h2) & np.isfinite(t)
         t = np.where(inside, t, np.inf)
-        better = t < P["range"]
+        better = t < P["range"][sl]
         for key, val in (("range", t), ("nx", n[0]), ("ny", n[1]), ("nz", n[2]), ("rho_d", r.rho_d),
                          ("retro", r.retro)):
-            P[key] = np.where(better, val, P[key])
+            P[key][sl] = np.where(better, val, P[key][sl])
     hit = np.isfinite(P["range"])
     if scene.ambient == "uniform":
         P["ambient"][:] = scene.ambient_level
@@ -313,6 +329,41 @@ def pinhole_plane_retro(seed: int = 6, W: int = 320, H: int = 240, f: float = 20
     U, V = 384, 256
     grid = GBuffer(U, V, 0.5 * DEG - U * pitch / 2, 0.2 * DEG - V * pitch / 2, pitch, pitch, *[None] * 7)
     return ph, grid
+
+
+def pinhole_boxes_frame(seed: int = 7, W: int = 2048, H: int = 1024, U: int = 2048, V: int = 1024,
+                        n_boxes: int = 40, rows: int = 16, cols: int = 1600):
+    """A rasterised frame: the full frame's scene family (ground 2 m below the
+    sensor, boxes at 5-150 m, log-uniform reflectance, 5 % retro faces, sun
+    ambient) within +-28 deg of azimuth, rendered through a W x H pinhole with
+    a 60 deg horizontal field of view (square pixels) looking along +x; the
+    spherical target grid U x V spans +-29 x +-14 deg (inside the pinhole's
+    view). Sensor: 16 x 1600 line scan over 56 x 26 deg, the 401 x 401 table
+    profile, 2048 bins of 0.1 ns. Returns (PinholeGBuffer, target GBuffer
+    geometry, Workload whose gbuffer is the target geometry)."""
+    g = rng(seed)
+    h_sensor = 2.0
+    planes = [Plane(np.array([0.0, 0.0, 1.0]), -h_sensor, 0.2, 0.0)]
+    rects = []
+    for _ in range(n_boxes):
+        rng_m = g.uniform(5.0, 150.0)
+        az = g.uniform(-28 * DEG, 28 * DEG)
+        half = g.uniform(0.25, 2.5, size=3)
+        yaw = g.uniform(-math.pi, math.pi)
+        rho = math.exp(g.uniform(math.log(0.05), math.log(0.9)))
+        retro = np.where(g.uniform(size=6) < 0.05, 100.0, 0.0)
+        dist = max(rng_m, float(np.linalg.norm(half)) + 1.5)
+        c = np.array([dist * math.cos(az), dist * math.sin(az), -h_sensor + half[2]])
+        rects += box_rects(c, half, yaw, rho, retro)
+    scene = Scene(planes=planes, rects=rects, ambient="sun", ambient_level=1e3)
+    f = W / 2 / math.tan(30 * DEG)
+    ph = raycast_pinhole(scene, W, H, f, f, W / 2.0, H / 2.0, camera_looking_along(0.0, 0.0))
+    daz, dele = 58 * DEG / U, 28 * DEG / V
+    grid = GBuffer(U, V, -29 * DEG, -14 * DEG, daz, dele, *[None] * 7)
+    dirs = linescan_pattern(rows, cols, 56 * DEG, 26 * DEG)
+    wl = Workload(f"pinhole{W}x{H}_to_{U}x{V}_boxes_linescan{rows}x{cols}_table401_2048bins", grid, dirs,
+                  table_profile(three_gauss_tail_table(), 0.01), pulse(2048, 0.1e-9), calib(2e-7, 1e-9, 3, True))
+    return ph, grid, wl
 
 
 def box_rects(center, half, yaw, rho_d, retro_faces) -> list:
