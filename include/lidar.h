@@ -225,7 +225,9 @@ lidar_status_t lidar_create(const lidar_profile_t *profile, const lidar_pattern_
  * extrapolated along the surface to v with the normal correction of
  * Sec. II-D: r_corr = (p . n) / (v . n) r (kept uncorrected where v . n is
  * below 1e-3 in magnitude or of the other sign than p . n). Pixels without a
- * source get range +inf and zeros. Geometry in FP64.
+ * source get range +inf and zeros. The projection and the cell choice are
+ * FP64; the range correction forms p - v and v . n in FP64 and the small
+ * remaining term in FP32 (relative error of the range about 1e-7).
  * src: pinhole planes (device, read); dst: the target grid (U, V, az0, el0,
  * daz, del as for lidar_simulate) with caller-owned device planes, all seven
  * written. Allocates nothing; asynchronous on `stream`.

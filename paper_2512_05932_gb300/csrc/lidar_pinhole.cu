@@ -5,11 +5,13 @@
 // r_corr = (p . n) / (v . n) r, which avoids interpolating ranges between
 // pixels (that would create ghost points between objects).
 //
-// One thread per target pixel, grid-stride. The geometry (direction,
-// projection, cell choice, correction) is FP64 so that the cell a direction
-// falls in is decided as an FP64 reference decides it; the planes are read
-// and written as FP32. A streaming kernel: 7 x 4 bytes written per target
-// pixel and at most 7 x 4 bytes gathered from the source.
+// One thread per target pixel, 32 x 8 pixels per CTA. The projection and the
+// choice of the source cell are FP64, so that the cell a direction falls in is
+// decided as an FP64 reference decides it; the FP64 sines and cosines are
+// taken once per tile column and row (shared memory); the range correction
+// forms p - v and v.n in FP64 and the rest in FP32 (its result is an FP32
+// range). A streaming kernel: 7 x 4 bytes written
+// per target pixel and at most 7 x 4 bytes gathered from the source.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,55 +36,80 @@ struct ReprojArgs {
     float *d_range, *d_nx, *d_ny, *d_nz, *d_rho, *d_retro, *d_amb;
 };
 
-__global__ void __launch_bounds__(256) reproject_kernel(ReprojArgs A)
+constexpr int kRW = 32, kRH = 8;  // target tile per CTA (one thread per pixel)
+
+__global__ void __launch_bounds__(kRW * kRH) reproject_kernel(ReprojArgs A)
 {
-    const long n = (long)A.U * A.V;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-        const int v = (int)(idx / A.U), u = (int)(idx - (long)v * A.U);
-        double sa, ca, se, ce;
-        sincos(A.az0 + (u + 0.5) * A.daz, &sa, &ca);
-        sincos(A.el0 + (v + 0.5) * A.del, &se, &ce);
-        const double d[3] = {ce * ca, ce * sa, se};  // target direction, sensor frame
-        // camera frame: c = R^T d
-        const double c0 = A.R[0] * d[0] + A.R[3] * d[1] + A.R[6] * d[2];
-        const double c1 = A.R[1] * d[0] + A.R[4] * d[1] + A.R[7] * d[2];
-        const double c2 = A.R[2] * d[0] + A.R[5] * d[1] + A.R[8] * d[2];
-        float o_range = INFINITY, o_nx = 0.f, o_ny = 0.f, o_nz = 0.f, o_rho = 0.f, o_retro = 0.f, o_amb = 0.f;
-        if (c2 > 0.0) {
-            const double px = A.cx + A.fx * (c0 / c2), py = A.cy + A.fy * (c1 / c2);
-            const double fi = floor(px), fj = floor(py);
-            if (fi >= 0.0 && fi < (double)A.W && fj >= 0.0 && fj < (double)A.H) {
-                const long s = (long)fj * A.W + (long)fi;
-                const double nx = A.s_nx[s], ny = A.s_ny[s], nz = A.s_nz[s];
-                o_nx = (float)nx; o_ny = (float)ny; o_nz = (float)nz;
-                o_rho = A.s_rho[s]; o_retro = A.s_retro[s]; o_amb = A.s_amb[s];
-                const double r = A.s_range[s];
-                if (isfinite(r) && r > 0.0) {
-                    // source pixel-centre direction p (sensor frame)
-                    const double X = (fi + 0.5 - A.cx) / A.fx, Y = (fj + 0.5 - A.cy) / A.fy;
-                    const double inv = 1.0 / sqrt(X * X + Y * Y + 1.0);
-                    const double p0 = (A.R[0] * X + A.R[1] * Y + A.R[2]) * inv;
-                    const double p1 = (A.R[3] * X + A.R[4] * Y + A.R[5]) * inv;
-                    const double p2 = (A.R[6] * X + A.R[7] * Y + A.R[8]) * inv;
-                    const double rp = A.depth_is_z ? r / inv : r;  // distance along p
-                    const double pn = p0 * nx + p1 * ny + p2 * nz;
-                    const double vn = d[0] * nx + d[1] * ny + d[2] * nz;
-                    double rc = rp;
-                    if (fabs(vn) >= 1e-3 && vn * pn > 0.0) rc = pn / vn * rp;
-                    o_range = (float)rc;
-                } else {
-                    o_range = (float)r;  // no hit (kept as given)
-                }
+    // Per tile: for each column the FP64 azimuth terms and for each row the
+    // elevation terms of c = R^T v, v = (cos el cos az, cos el sin az, sin el):
+    // c_k = cos(el) (cos(az) R[0][k] + sin(az) R[1][k]) + sin(el) R[2][k].
+    __shared__ double colA[kRW][3];
+    __shared__ double rowB[kRH][4];  // cos el, sin(el) R[2][k]
+    const int tx = threadIdx.x % kRW, ty = threadIdx.x / kRW;
+    const int u0 = blockIdx.x * kRW, v0 = blockIdx.y * kRH;
+    if (threadIdx.x < kRW) {
+        double sa, ca;
+        sincos(A.az0 + (u0 + threadIdx.x + 0.5) * A.daz, &sa, &ca);
+        for (int k = 0; k < 3; ++k) colA[threadIdx.x][k] = ca * A.R[k] + sa * A.R[3 + k];
+    } else if (threadIdx.x < kRW + kRH) {
+        const int r = threadIdx.x - kRW;
+        double se, ce;
+        sincos(A.el0 + (v0 + r + 0.5) * A.del, &se, &ce);
+        rowB[r][0] = ce;
+        for (int k = 0; k < 3; ++k) rowB[r][1 + k] = se * A.R[6 + k];
+    }
+    __syncthreads();
+    const int u = u0 + tx, v = v0 + ty;
+    if (u >= A.U || v >= A.V) return;
+    const long idx = (long)v * A.U + u;
+    const double ce = rowB[ty][0];
+    const double c0 = ce * colA[tx][0] + rowB[ty][1];
+    const double c1 = ce * colA[tx][1] + rowB[ty][2];
+    const double c2 = ce * colA[tx][2] + rowB[ty][3];
+    float o_range = INFINITY, o_nx = 0.f, o_ny = 0.f, o_nz = 0.f, o_rho = 0.f, o_retro = 0.f, o_amb = 0.f;
+    if (c2 > 0.0) {
+        // the source cell: FP64, as an FP64 reference decides it
+        const double inv = 1.0 / c2;
+        const double fi = floor(A.cx + A.fx * (c0 * inv)), fj = floor(A.cy + A.fy * (c1 * inv));
+        if (fi >= 0.0 && fi < (double)A.W && fj >= 0.0 && fj < (double)A.H) {
+            const int i = (int)fi, j = (int)fj;
+            const long s = (long)j * A.W + i;
+            const float nx = A.s_nx[s], ny = A.s_ny[s], nz = A.s_nz[s];
+            o_nx = nx; o_ny = ny; o_nz = nz;
+            o_rho = A.s_rho[s]; o_retro = A.s_retro[s]; o_amb = A.s_amb[s];
+            const float r = A.s_range[s];
+            if (isfinite(r) && r > 0.f) {
+                // r_corr = (p.n)/(v.n) r = r (1 + ((p - v).n) / (v.n)): the
+                // correction term is small, so it is exact enough in FP32 once
+                // p - v (pixel-sized) is formed in FP64 in the camera frame,
+                // where v = c and p = (X, Y, 1) / |(X, Y, 1)|
+                const double X = (i + 0.5 - A.cx) / A.fx, Y = (j + 0.5 - A.cy) / A.fy;
+                const double ip = rsqrt(fma(X, X, fma(Y, Y, 1.0)));
+                const float e0 = (float)(X * ip - c0), e1 = (float)(Y * ip - c1), e2 = (float)(ip - c2);
+                // normal in the camera frame, R^T n, and v.n in FP64: v.n may be
+                // small (grazing incidence), where FP32 would lose its digits
+                const double m0 = A.R[0] * nx + A.R[3] * ny + A.R[6] * nz;
+                const double m1 = A.R[1] * nx + A.R[4] * ny + A.R[7] * nz;
+                const double m2 = A.R[2] * nx + A.R[5] * ny + A.R[8] * nz;
+                const float vn = (float)(c0 * m0 + c1 * m1 + c2 * m2);
+                const float dn = e0 * (float)m0 + e1 * (float)m1 + e2 * (float)m2;
+                const float pn = vn + dn;
+                const float rp = A.depth_is_z ? r / (float)ip : r;
+                float rc = rp;
+                if (fabsf(vn) >= 1e-3f && vn * pn > 0.f) rc = fmaf(rp, dn / vn, rp);
+                o_range = rc;
+            } else {
+                o_range = r;  // no hit (kept as given)
             }
         }
-        A.d_range[idx] = o_range;
-        A.d_nx[idx] = o_nx;
-        A.d_ny[idx] = o_ny;
-        A.d_nz[idx] = o_nz;
-        A.d_rho[idx] = o_rho;
-        A.d_retro[idx] = o_retro;
-        A.d_amb[idx] = o_amb;
     }
+    A.d_range[idx] = o_range;
+    A.d_nx[idx] = o_nx;
+    A.d_ny[idx] = o_ny;
+    A.d_nz[idx] = o_nz;
+    A.d_rho[idx] = o_rho;
+    A.d_retro[idx] = o_retro;
+    A.d_amb[idx] = o_amb;
 }
 
 }  // namespace
@@ -127,9 +154,8 @@ extern "C" lidar_status_t lidar_reproject_pinhole(const lidar_pinhole_t *src, co
     a.d_ny = const_cast<float *>(dst->ny); a.d_nz = const_cast<float *>(dst->nz);
     a.d_rho = const_cast<float *>(dst->rho_d); a.d_retro = const_cast<float *>(dst->retro);
     a.d_amb = const_cast<float *>(dst->ambient);
-    const long n = (long)dst->U * dst->V;
-    const int grid = (int)std::min<long>((n + 255) / 256, 152L * 16);
-    reproject_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    const dim3 grid((dst->U + kRW - 1) / kRW, (dst->V + kRH - 1) / kRH);
+    reproject_kernel<<<grid, kRW * kRH, 0, (cudaStream_t)stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gblh::cuda_fail(nullptr, e, "reprojection kernel launch");
     return LIDAR_OK;
