@@ -251,34 +251,82 @@ __global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
 // out(y, x) = sum_a col[a] R[y - a + 2m][x], where I_s is I on the pixels of
 // slice s and 0 elsewhere; an output takes the first slice that reaches the
 // threshold. Cost per output and slice O(kh + kw) instead of O(kh kw).
+//
+// Both passes are register-blocked: a thread makes 4 adjacent outputs (4
+// columns of one region row in the row pass, 4 rows of one column in the
+// column pass) from a window read in chunks of 4 elements. Output o and window
+// element q of chunk c meet at tap 2h + o - 4c - q (h = half the kernel
+// length), so a chunk touches 7 consecutive taps; the taps sit in a zero-padded
+// copy whose padding makes every chunk's 8-tap slice 16-byte aligned, and
+// consecutive chunks share 4 of them. Per chunk: one 16-byte load of
+// intensities (+ 8 bytes of slice ids) or 4 loads of row sums, one 16-byte
+// load of taps, 16 FMAs.
 // ---------------------------------------------------------------------------
 
 constexpr int kSW = 32, kSH = 32;   // output tile of the separable kernel
 constexpr int kList = 64;           // slices listed per round
 
+struct SepLayout {
+    int nCr, nCc;     // window chunks of the row and the column pass
+    int pr, pc;       // zero taps in front of row[] and col[]
+    int Lr, Lc;       // padded tap array lengths (multiples of 4)
+    int RH, RW, RWp;  // region rows, columns, padded row stride (multiple of 4)
+    int RHb;          // rows of the row-pass result (the column pass reads past RH)
+};
+
+__host__ __device__ inline SepLayout sep_layout(int kh, int kw)
+{
+    SepLayout L;
+    L.nCr = (kw + 6) >> 2;  // ceil((kw + 3) / 4): 4 outputs need kw + 3 window elements
+    L.nCc = (kh + 6) >> 2;
+    L.pr = ((kw - 1) & 3) ? 5 : 3;  // pad + (kw - 1) - 3 = 0 mod 4
+    L.pc = ((kh - 1) & 3) ? 5 : 3;
+    L.Lr = (L.pr + kw + 4 + 3) & ~3;
+    L.Lc = (L.pc + kh + 4 + 3) & ~3;
+    L.RH = kSH + kh - 1;
+    L.RW = kSW + kw - 1;
+    L.RWp = kSW + 4 * L.nCr;
+    L.RHb = kSH + 4 * L.nCc;
+    return L;
+}
+
+// acc[o] += sum_q w[q] k[3 + o - q], k = (lo, hi) the chunk's 8 taps
+__device__ __forceinline__ void chunk_fma(float acc[4], const float w[4], float4 lo, float4 hi)
+{
+    const float k[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[o] = fmaf(w[q], k[3 + o - q], acc[o]);
+}
+
 __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int kh = A.kh, kw = A.kw, m = kh / 2, n = kw / 2;
-    const int RH = kSH + kh - 1, RW = kSW + kw - 1;
-    float *Kc = reinterpret_cast<float *>(smem);        // col[kh]
-    float *Kr = Kc + kh;                                 // row[kw]
-    float *Rb = Kr + kw;                                 // R[RH][kSW]
-    float *RI = Rb + RH * kSW;                           // region intensity [RH][RW]
-    uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RW);  // region slice
+    const SepLayout L = sep_layout(kh, kw);
+    const int RH = L.RH, RW = L.RW, RWp = L.RWp;
+    float *Kc = reinterpret_cast<float *>(smem);   // [Lc]: col[a] at pc + a, zeros elsewhere
+    float *Kr = Kc + L.Lc;                          // [Lr]: row[b] at pr + b
+    float *Rb = Kr + L.Lr;                          // row-pass result [RHb][kSW]
+    float *RI = Rb + L.RHb * kSW;                   // region intensity [RH][RWp]
+    uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RWp);  // region slice [RH][RWp]
+    int *rmin = reinterpret_cast<int *>(RS + RH * RWp);          // per region row: slice range
+    int *rmax = rmin + RH;
     __shared__ float hist[kSpan];
     __shared__ int lst[kList];
     __shared__ int s_lo, s_hi, s_cnt, s_min;
-    const int tid = threadIdx.x, tx = tid % kSW, tyb = tid / kSW;  // rows tyb + 8 i
+    const int tid = threadIdx.x;
     const int u0 = blockIdx.x * kSW, v0 = blockIdx.y * kSH;
-    for (int i = tid; i < kh; i += blockDim.x) Kc[i] = A.Kc[i];
-    for (int i = tid; i < kw; i += blockDim.x) Kr[i] = A.Kr[i];
-    for (int i = tid; i < RH * RW; i += blockDim.x) {
-        const int ry = i / RW, rx = i - ry * RW;
+    for (int i = tid; i < L.Lc; i += blockDim.x) Kc[i] = (i >= L.pc && i < L.pc + kh) ? A.Kc[i - L.pc] : 0.f;
+    for (int i = tid; i < L.Lr; i += blockDim.x) Kr[i] = (i >= L.pr && i < L.pr + kw) ? A.Kr[i - L.pr] : 0.f;
+    for (int i = RH * kSW + tid; i < L.RHb * kSW; i += blockDim.x) Rb[i] = 0.f;  // never written again
+    for (int i = tid; i < RH * RWp; i += blockDim.x) {
+        const int ry = i / RWp, rx = i - ry * RWp;
         const int v = v0 - m + ry, u = u0 - n + rx;
         float w = 0.f;
         uint16_t s = 0;
-        if (v >= 0 && v < A.V && u >= 0 && u < A.U) {
+        if (rx < RW && v >= 0 && v < A.V && u >= 0 && u < A.U) {
             const long idx = (long)v * A.U + u;
             w = A.I[idx];
             s = A.S[idx];
@@ -290,7 +338,7 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     __syncthreads();
     {
         int lo_ = INT_MAX, hi_ = 0;
-        for (int i = tid; i < RH * RW; i += blockDim.x)
+        for (int i = tid; i < RH * RWp; i += blockDim.x)
             if (RS[i]) { lo_ = min(lo_, (int)RS[i]); hi_ = max(hi_, (int)RS[i]); }
         atomicMin(&s_lo, lo_);
         atomicMax(&s_hi, hi_);
@@ -302,17 +350,15 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     if (use_hist) {
         for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
         __syncthreads();
-        for (int i = tid; i < RH * RW; i += blockDim.x)
+        for (int i = tid; i < RH * RWp; i += blockDim.x)
             if (RS[i]) atomicAdd(&hist[RS[i] - slo], RI[i]);
         __syncthreads();
     }
     // per region row: range of the slices on it (rows without slice s skip the row pass)
-    int *rmin = reinterpret_cast<int *>(RS + ((RH * RW + 1) & ~1));
-    int *rmax = rmin + RH;
     for (int ry = tid; ry < RH; ry += blockDim.x) {
         int a = INT_MAX, b = 0;
         for (int rx = 0; rx < RW; ++rx) {
-            const int s = RS[ry * RW + rx];
+            const int s = RS[ry * RWp + rx];
             if (s) { a = min(a, s); b = max(b, s); }
         }
         rmin[ry] = a;
@@ -320,15 +366,19 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     }
     __syncthreads();
 
+    // column pass: this thread's outputs are rows 4 g + o of column tx
+    const int tx = tid % kSW, g = tid / kSW;
     int outS[4];
     float outX[4];
-    int done = 0;  // bit i: output row tyb + 8 i has its answer (or is outside the image)
+    int done = 0;  // bit o: output row 4 g + o has its answer (or is outside the image)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        outS[i] = A.s_max;
-        outX[i] = 0.f;
-        if (!(u0 + tx < A.U && v0 + tyb + 8 * i < A.V)) done |= 1 << i;
+    for (int o = 0; o < 4; ++o) {
+        outS[o] = A.s_max;
+        outX[o] = 0.f;
+        if (!(u0 + tx < A.U && v0 + 4 * g + o < A.V)) done |= 1 << o;
     }
+    const float4 *Kr4 = reinterpret_cast<const float4 *>(Kr + L.pr + 2 * n - 3);  // taps of chunk 0
+    const float4 *Kc4 = reinterpret_cast<const float4 *>(Kc + L.pc + 2 * m - 3);
     int lo = 0;  // slices <= lo have been processed
     bool finished = __syncthreads_and(done == 0xF) != 0;
     while (!finished) {
@@ -350,7 +400,7 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
             }
         } else {
             int mn = INT_MAX;
-            for (int i = tid; i < RH * RW; i += blockDim.x)
+            for (int i = tid; i < RH * RWp; i += blockDim.x)
                 if (RS[i] > lo) mn = min(mn, (int)RS[i]);
             atomicMin(&s_min, mn);
             __syncthreads();
@@ -361,27 +411,44 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
         if (cnt == 0) break;
         for (int k = 0; k < cnt && !finished; ++k) {
             const int s = lst[k];
-            // row pass over every region row: output column tx
-            for (int ry = tyb; ry < RH; ry += 8) {
-                float acc = 0.f;
+            // row pass: item = (region row ry, column group cg of 4 outputs);
+            // the 8 items of a row are adjacent threads (one 128-byte row of
+            // 16-byte loads per quarter warp)
+            for (int it = tid; it < RH * (kSW / 4); it += blockDim.x) {
+                const int ry = it >> 3, cg = it & 7;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 if (s >= rmin[ry] && s <= rmax[ry]) {
-                    const int rb = ry * RW + tx + 2 * n;  // tap b reads region column tx + 2n - b
-                    for (int b = 0; b < kw; ++b) {
-                        const int ri = rb - b;
-                        acc = fmaf(RS[ri] == s ? RI[ri] : 0.f, Kr[b], acc);
+                    const float4 *wI = reinterpret_cast<const float4 *>(RI + ry * RWp + 4 * cg);
+                    const uint2 *wS = reinterpret_cast<const uint2 *>(RS + ry * RWp + 4 * cg);
+                    float4 hi = Kr4[1];
+                    for (int c = 0; c < L.nCr; ++c) {
+                        const float4 x = wI[c];
+                        const uint2 t = wS[c];
+                        const float w[4] = {(int)(t.x & 0xFFFFu) == s ? x.x : 0.f, (int)(t.x >> 16) == s ? x.y : 0.f,
+                                            (int)(t.y & 0xFFFFu) == s ? x.z : 0.f, (int)(t.y >> 16) == s ? x.w : 0.f};
+                        const float4 lo4 = Kr4[-c];
+                        chunk_fma(acc, w, lo4, hi);
+                        hi = lo4;
                     }
                 }
-                Rb[ry * kSW + tx] = acc;
+                reinterpret_cast<float4 *>(Rb + ry * kSW)[cg] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             }
             __syncthreads();
             // column pass and the threshold test
+            if (done != 0xF) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                const float *col = Rb + 4 * g * kSW + tx;
+                float4 hi = Kc4[1];
+                for (int c = 0; c < L.nCc; ++c) {
+                    const float *r = col + 4 * c * kSW;
+                    const float w[4] = {r[0], r[kSW], r[2 * kSW], r[3 * kSW]};
+                    const float4 lo4 = Kc4[-c];
+                    chunk_fma(acc, w, lo4, hi);
+                    hi = lo4;
+                }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if ((done >> i) & 1) continue;
-                const int y = tyb + 8 * i;
-                float acc = 0.f;
-                for (int a = 0; a < kh; ++a) acc = fmaf(Rb[(y - a + 2 * m) * kSW + tx], Kc[a], acc);
-                if (acc >= A.thr) { outS[i] = s; outX[i] = acc; done |= 1 << i; }
+                for (int o = 0; o < 4; ++o)
+                    if (!((done >> o) & 1) && acc[o] >= A.thr) { outS[o] = s; outX[o] = acc[o]; done |= 1 << o; }
             }
             finished = __syncthreads_and(done == 0xF) != 0;  // also: Rb is free again
         }
@@ -389,12 +456,12 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
         __syncthreads();  // every thread has read lst before the next round overwrites it
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int u = u0 + tx, v = v0 + tyb + 8 * i;
+    for (int o = 0; o < 4; ++o) {
+        const int u = u0 + tx, v = v0 + 4 * g + o;
         if (u < A.U && v < A.V) {
             const long idx = (long)v * A.U + u;
-            A.out_slice[idx] = outS[i];
-            A.out_val[idx] = outX[i];
+            A.out_slice[idx] = outS[o];
+            A.out_val[idx] = outX[o];
         }
     }
 }
@@ -438,12 +505,12 @@ size_t tile_smem(int kh, int kw)
     return (size_t)kh * kw * 4 + RH * RW * 4 + RH * RW * 2;
 }
 
-// dynamic shared memory of stack_sep_kernel: col, row, R, region (float +
-// uint16, padded to 4 bytes), per-row slice range
+// dynamic shared memory of stack_sep_kernel: padded taps, row-pass result,
+// region (float + uint16), per-row slice range
 size_t sep_smem(int kh, int kw)
 {
-    const size_t RH = kSH + kh - 1, RW = kSW + kw - 1;
-    return (size_t)(kh + kw) * 4 + RH * kSW * 4 + RH * RW * 4 + ((RH * RW + 1) & ~(size_t)1) * 2 + 2 * RH * 4;
+    const SepLayout L = sep_layout(kh, kw);
+    return (size_t)(L.Lc + L.Lr) * 4 + (size_t)L.RHb * kSW * 4 + (size_t)L.RH * L.RWp * 6 + (size_t)L.RH * 8;
 }
 
 lidar_status_t check_common(int kh, int kw, double thr, double dr, double r_max, double *sm)

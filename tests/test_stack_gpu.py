@@ -141,6 +141,18 @@ def test_separable_ragged_asymmetric():
     check(w.gbuffer, None, thr=float(np.median(I[I > 0])) * 3, dr=0.01, r_max=20.0, separable=(col, row))
 
 
+@pytest.mark.parametrize("kh,kw", [(1, 3), (3, 1), (129, 127), (7, 69)])
+def test_separable_kernel_length_edges(kh, kw):
+    """A single row or column, the largest kernel, and pads of both parities
+    (the passes read the taps from zero-padded copies in 4-tap chunks)."""
+    w = S.tiny_case()
+    g = np.random.default_rng(kh * 1000 + kw)
+    col, row = g.uniform(0.1, 1, kh).astype(np.float32), g.uniform(0.1, 1, kw).astype(np.float32)
+    I, _ = O.stack_inputs(w.gbuffer, 0.01)
+    st = check(w.gbuffer, None, thr=float(np.median(I[I > 0])) * 2, dr=0.01, r_max=20.0, separable=(col, row))
+    assert st["echoes"] > 0
+
+
 def test_separable_many_slices_per_tile():
     """Grazing ground: many slices per 32x32 tile (more than one 64-slice list)."""
     w = S.full_frame_boxes(U=128, V=64, n_boxes=12, rows=2, cols=10)
