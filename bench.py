@@ -37,6 +37,8 @@ UNIT = "beams/s"
 L2_BYTES = 129 * 1024 * 1024
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "footprint_wave_boxes2048x1024.traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2512_05932_gb300", "csrc", "lidar_kernels.cu")
+STACK_SEP_COUNTERS = os.path.join(ROOT, "profiles", "stack_sep_boxes4096x1024.counters.json")
+STACK_SRC = os.path.join(ROOT, "paper_2512_05932_gb300", "csrc", "lidar_stack.cu")
 
 
 def parse():
@@ -216,19 +218,24 @@ def load_tensor_peak():
     return 1700.0, "fallback"
 
 
-def profile_for_current_kernel(workload_name):
-    """The committed ncu figures of the footprint kernel (dram bytes and
-    executed warp instructions per launch), or None if absent, taken on
-    another workload or on a different kernel source."""
-    if not os.path.exists(TRAFFIC_FILE):
+def committed_counters(path, src, workload_name):
+    """Committed ncu figures of one kernel (dram bytes and executed warp
+    instructions per launch), or None if absent, taken on another workload or
+    on a different kernel source than the one in the tree."""
+    if not os.path.exists(path):
         return None
-    with open(TRAFFIC_FILE) as f:
+    with open(path) as f:
         d = json.load(f)
-    with open(KERNEL_SRC, "rb") as f:
+    with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     if d.get("kernel_sha256") != sha or not d.get("workload", "").startswith(workload_name):
         return None
     return d
+
+
+def profile_for_current_kernel(workload_name):
+    """The committed ncu figures of the footprint kernel (see committed_counters)."""
+    return committed_counters(TRAFFIC_FILE, KERNEL_SRC, workload_name)
 
 
 def traffic_for_current_kernel(workload_name):
@@ -285,11 +292,12 @@ def support_pixels_per_beam(w, n_sample=384):
     return float(np.mean(counts)), len(beams)
 
 
-def issue_roofline(workload_name, avg_ms, sm_mhz, n_sm):
-    """Issue rate of the footprint kernel: warp instructions per launch (ncu,
-    same kernel source) over the live launch time, against one instruction
-    per clock on each of the 4 schedulers of every SM at the sampled clock."""
-    d = profile_for_current_kernel(workload_name)
+def issue_roofline(workload_name, avg_ms, sm_mhz, n_sm, counters=None):
+    """Issue rate of a kernel (the footprint kernel unless counters are
+    given): warp instructions per launch (ncu, same kernel source) over the
+    live launch time, against one instruction per clock on each of the 4
+    schedulers of every SM at the sampled clock."""
+    d = counters if counters is not None else profile_for_current_kernel(workload_name)
     if not d or not d.get("inst_executed") or not sm_mhz:
         return None
     ach = d["inst_executed"] / (avg_ms * 1e-3)
@@ -672,6 +680,7 @@ def run_pinhole(args, rank, world, local_rank):
             torch.cuda.synchronize(dev)
     torch.cuda.synchronize(dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    lidar.lidar_profile_enable(L.handle, True)
     with clk:
         for i in range(args.steps):
             flush.fill_(float(i))
@@ -683,6 +692,10 @@ def run_pinhole(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
     rep = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
     sim = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    kern = lidar.lidar_profile_read(L.handle)
+    lidar.lidar_profile_enable(L.handle, False)
+    kernel_ms = {k: kern[k][0] / max(1, kern[k][1]) for k in lidar.KERNELS if kern[k][1]}
+    kernel_ms["reproject"] = rep
     nbeams = len(w.dirs)
     value, ms = job_rate((rep + sim) * args.steps, nbeams, args.steps, world, None, dev)
     # e2e: pinned pinhole planes up, reprojection + simulation, waveforms, echoes and counts down
@@ -707,10 +720,22 @@ def run_pinhole(args, rank, world, local_rank):
     npx = grid.U * grid.V
     rep_bytes = npx * 7 * 4 * 2  # each target pixel: 7 planes gathered from the source, 7 written
     alg = npx * 7 * 4 * 2 + nbeams * (w.pulse["n_bins"] * 4 + w.calib["max_echoes"] * 32 + 4)
-    roof = {"bound": "hbm", "kernel": "reproject_kernel (pinhole -> spherical grid)", "achieved": rep_bytes / (rep * 1e-3) / 1e9,
-            "peak": peak, "unit": "GB/s", "frac": rep_bytes / (rep * 1e-3) / 1e9 / peak,
-            "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None, "algorithmic_bytes": rep_bytes,
-            "avg_launch_ms": rep, "step_algorithmic_bytes": alg}
+    rep_roof = {"bound": "hbm", "kernel": "reproject_kernel (pinhole -> spherical grid)",
+                "achieved": rep_bytes / (rep * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": rep_bytes / (rep * 1e-3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "algorithmic_bytes": rep_bytes, "avg_launch_ms": rep,
+                "note": "FP64-pipe bound (projection and cell choice in FP64)"}
+    # the dominant kernel of the step (the footprint kernel of the beam model)
+    dom = max(kernel_ms, key=kernel_ms.get)
+    if dom == "reproject":
+        roof = dict(rep_roof, traffic=None)
+    else:
+        fb = algorithmic_bytes(w, False)
+        ach = fb / (kernel_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None, "algorithmic_bytes": fb,
+                "avg_launch_ms": kernel_ms[dom], "step_algorithmic_bytes": alg,
+                "note": "issue-bound like the frame workload's footprint kernel", "reproject": rep_roof}
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         from oracle import oracle as O
@@ -732,7 +757,8 @@ def run_pinhole(args, rank, world, local_rank):
                            "gbuffer": f"{grid.U}x{grid.V} spherical grid (58 x 28 deg)", "beams": nbeams,
                            "pattern": "linescan 16x1600", "profile": "table 401x401 @0.01deg", "n_bins": 2048,
                            "l2": "flushed between timed steps (258 MB write)"},
-                "roofline": roof, "stage_ms": {"reproject": rep, "simulate": sim}, "cpu_baseline": cpu,
+                "roofline": roof, "stage_ms": {"reproject": rep, "simulate": sim}, "kernel_ms": kernel_ms,
+                "cpu_baseline": cpu,
                 "e2e": {"value": e2e, "unit": UNIT,
                         "h2d_bytes_per_step": sum(p.numel() * 4 for p in host_src),
                         "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in host_out)},
@@ -803,6 +829,26 @@ def run_stack(args, rank, world, local_rank):
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
     npx = gb.U * gb.V
     echoes = int((x_out > 0).sum().item())
+    # e2e: pinned G-buffer planes up, stacking, slice indices and intensities down
+    host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in gb.planes()]
+    host_s = torch.empty(s_out.shape, dtype=s_out.dtype, pin_memory=True)
+    host_x = torch.empty(x_out.shape, dtype=x_out.dtype, pin_memory=True)
+
+    def step_host():
+        for d_, h_ in zip(planes, host_planes):
+            d_.copy_(h_, non_blocking=True)
+        st.run(g, s_out.data_ptr(), x_out.data_ptr(), stream.cuda_stream)
+        host_s.copy_(s_out, non_blocking=True)
+        host_x.copy_(x_out, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        step_host()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    e2e = world * npx * args.steps / (time.perf_counter() - t0)
+    clocks = clk.summary()
     peak, peak_kind = load_peaks()
     alg = npx * 28 + npx * 8  # planes read once, slice index and intensity written once
     achieved = alg / (ms * 1e-3) / 1e9
@@ -820,6 +866,18 @@ def run_stack(args, rank, world, local_rank):
         dt = time.perf_counter() - t
         cpu = {"value": sub.U * sub.V / dt, "unit": "pixels/s", "cores": 1, "kind": "oracle",
                "sample": f"{sub.U}x{sub.V} window of the frame, one thread ({dt:.1f} s wall)"}
+    roof = {"bound": "hbm", "kernel": "range stacking step", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+            "traffic": None, "algorithmic_bytes": alg}
+    if sep:
+        # the separable kernel is bound by instruction issue (ncu counters of
+        # the same source, step time: the per-pixel input kernel adds ~4 %)
+        cnt = committed_counters(STACK_SEP_COUNTERS, STACK_SRC, "boxes_4096x1024_stack_kernel69_1200slices_separable")
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        roof["issue"] = issue_roofline(None, ms, clocks.get("sm_mhz"), n_sm, counters=cnt or {})
+        if roof["issue"]:
+            roof["issue"]["kernel"] = "stack_sep_kernel (time: whole step)"
+        roof["traffic"] = cnt.get("bytes_per_launch") if cnt else None
     if rank == 0:
         line = {"metric": "range stacking: pixel-centred beams/s (nearest slice above threshold, Alg. 2)",
                 "value": world * npx / (ms * 1e-3), "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
@@ -831,10 +889,11 @@ def run_stack(args, rank, world, local_rank):
                                       "69x69 px (table profile sampled at the pixel pitch)"), "dr_m": dr,
                            "r_max_m": rmax, "slices": int(math.floor(rmax / dr)), "threshold": thr,
                            "echo_pixels": echoes, "l2": "flushed between timed steps (258 MB write)"},
-                "roofline": {"bound": "hbm", "kernel": "range stacking step", "achieved": achieved, "peak": peak,
-                             "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                             "traffic": None, "algorithmic_bytes": alg},
-                "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(args.steps * 2), "clocks": clk.summary()}
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e, "unit": "pixels/s", "h2d_bytes_per_step": sum(p.numel() * 4 for p in host_planes),
+                        "d2h_bytes_per_step": host_s.numel() * 4 + host_x.numel() * 4},
+                "gpu_launches": int(args.steps * 2), "clocks": clocks}
         print(json.dumps(line), flush=True)
     st.close()
 
