@@ -37,13 +37,14 @@ __device__ __forceinline__ float hatf(float x) { return fmaxf(0.f, 1.f - fabsf(x
 // one unused slot after every 32, so that lanes 8 bins apart hit distinct banks.
 __host__ __device__ __forceinline__ int skew_pos(int x) { return x + (x >> 5); }
 
-// Mean of hat(x - k) over [X0, X1] (bin-centre units): the interval is cut at
-// the kinks k-1, k, k+1; on each piece the hat is linear, so the piece's
-// contribution is its length times the hat at its midpoint.
-__device__ float mean_hat(float X0, float X1, float k)
+// Integral of hat(x - k) over [X0, X1] (bin-centre units; the mean times
+// X1 - X0): the interval is cut at the kinks k-1, k, k+1; on each piece the
+// hat is linear, so the piece's contribution is its length times the hat at
+// its midpoint. The caller divides by X1 - X0 once for all bins (a point
+// interval, X1 = X0, gives the hat at X0 and no division).
+__device__ float int_hat(float X0, float X1, float k)
 {
-    float W = X1 - X0;
-    if (!(W > 0.f)) return hatf(X0 - k);
+    if (!(X1 - X0 > 0.f)) return hatf(X0 - k);
     float lo = X0, acc = 0.f;
 #pragma unroll
     for (int c = -1; c <= 1; ++c) {
@@ -54,7 +55,7 @@ __device__ float mean_hat(float X0, float X1, float k)
         }
     }
     acc += (X1 - lo) * hatf(0.5f * (lo + X1) - k);
-    return acc / W;
+    return acc;
 }
 
 __device__ void setup_pixel(const SetupArgs &A, int idx)
@@ -83,7 +84,10 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
         // corner rays (r_c = r * (d.n) / (d_c.n)), normal facing the sensor
         float sgn = dn > 0.f ? -1.f : 1.f;
         float mup = fmaxf(-sgn * dn, kMuMin);
-        float rmin = rr, rmax = rr;
+        // r_c = (r mup) / mu_c is decreasing in mu_c > 0, and so is its
+        // correctly rounded quotient: the extremes over the corners come from
+        // the extreme denominators (two divisions instead of four)
+        float mu_lo = INFINITY, mu_hi = 0.f;
 #pragma unroll
         for (int cj = -1; cj <= 1; cj += 2)
 #pragma unroll
@@ -93,24 +97,28 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
                 float cec = ce * A.cv - (float)cj * se * A.sv;
                 float sec = se * A.cv + (float)cj * ce * A.sv;
                 float dcn = cec * (cac * nx + sac * ny) + sec * nz;
-                float rc = rr * mup / fmaxf(-sgn * dcn, kMuMin);
-                rmin = fminf(rmin, rc);
-                rmax = fmaxf(rmax, rc);
+                const float mu = fmaxf(-sgn * dcn, kMuMin);
+                mu_lo = fminf(mu_lo, mu);
+                mu_hi = fmaxf(mu_hi, mu);
             }
+        const float rm = rr * mup;
+        float rmin = fminf(rr, rm / mu_hi), rmax = fmaxf(rr, rm / mu_lo);
         float X0 = rmin * A.x_scale + A.x_off;
         float X1 = rmax * A.x_scale + A.x_off;
         const float nb = (float)A.n_bins;
         float f = floorf(X0);
         // the hat functions of bins 0..n-1 cover (-1, n): anything else is dropped
         if (w > 0.f && X1 > -1.f && X0 < nb) {
+            // w times the mean of a hat over [X0, X1] = (w / (X1 - X0)) times its integral
+            const float ww = X1 - X0 > 0.f ? w / (X1 - X0) : w;
             if (X1 <= f + 3.f) {
                 // narrow: at most 4 bins f..f+3 touched; the record holds their
                 // positions in the footprint kernel's skewed histogram buffer
                 if (f >= -3.f) {
-                    h0 = w * mean_hat(X0, X1, f);
-                    h1 = w * mean_hat(X0, X1, f + 1.f);
-                    h2 = w * mean_hat(X0, X1, f + 2.f);
-                    h3 = w * mean_hat(X0, X1, f + 3.f);
+                    h0 = ww * int_hat(X0, X1, f);
+                    h1 = ww * int_hat(X0, X1, f + 1.f);
+                    h2 = ww * int_hat(X0, X1, f + 2.f);
+                    h3 = ww * int_hat(X0, X1, f + 3.f);
                     if (A.bin_records) {
                         // tensor-core deposit: the bin index itself
                         kab = (uint32_t)((int)f + kBinBias) | (0xFFFFu << 16);
@@ -125,11 +133,11 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
                 // wide (X1 - X0 > 2): partial bins f, f+1 and g, g+1, every bin
                 // in between fully covered with weight w / (X1 - X0)
                 float g = floorf(X1);
-                h0 = w * mean_hat(X0, X1, f);
-                h1 = w * mean_hat(X0, X1, f + 1.f);
-                h2 = w * mean_hat(X0, X1, g);
-                h3 = w * mean_hat(X0, X1, g + 1.f);
-                cr = w / (X1 - X0);
+                h0 = ww * int_hat(X0, X1, f);
+                h1 = ww * int_hat(X0, X1, f + 1.f);
+                h2 = ww * int_hat(X0, X1, g);
+                h3 = ww * int_hat(X0, X1, g + 1.f);
+                cr = ww;
                 // bins far outside the window: zero weight, parked next to it
                 // (the run between them keeps its extent)
                 if (f < -4.f) { f = -4.f; h0 = 0.f; h1 = 0.f; }
@@ -880,12 +888,12 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    uint32_t kab = __float_as_uint(r0[u].x);
-                    float a = r0[u].y;
-                    float Pw = profile_finish<KIND>(A, pf[u]);
-                    if (!(Pw > 0.f)) continue;
-                    amb_acc = fmaf(Pw, a, amb_acc);
-                    if (kab == kNoDeposit) continue;
+                    const uint32_t kab = __float_as_uint(r0[u].x);
+                    // Pw = 0 for an inactive sample or outside the support:
+                    // the ambient term adds nothing then
+                    const float Pw = profile_finish<KIND>(A, pf[u]);
+                    amb_acc = fmaf(Pw, r0[u].y, amb_acc);
+                    if (!(Pw > 0.f) || kab == kNoDeposit) continue;
                     // second half of the record (same 32-byte sector as the first)
                     const float4 r1u = __ldg(recrow + 2 * cws[u] + 1);
                     uint32_t kq = __float_as_uint(r1u.x);
