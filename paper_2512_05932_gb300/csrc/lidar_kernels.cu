@@ -426,7 +426,7 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
             const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
             r.q = make_float4(h.x, h.y, v.x, v.y);
         } else {
-            r.q = __ldg(A.quads + (size_t)j * A.qw + i);
+            r.q = __ldg(A.quads + (j * A.qw + i));  // at most 4097 x 4097 quads
         }
     }
     return r;
@@ -607,7 +607,12 @@ __device__ __forceinline__ float phase1_tc(const FootprintArgs &A, const Layout 
                     const int c = ct + 2 * t + (u & 1) + 8 * (u >> 1);
                     const bool inrow = c <= c_hi;  // pixel of this unit (for every beam)
                     int cw = c;
-                    if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    if (A.panorama) {
+                        // the group's columns lie within about one period of [0, U)
+                        if (cw < 0) cw += A.U;
+                        else if (cw >= A.U) cw -= A.U;
+                        if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    }
                     cw = inrow ? cw : 0;
                     float4 r0 = __ldg(recrow + 2 * cw);
                     float4 r1 = __ldg(recrow + 2 * cw + 1);
@@ -867,7 +872,12 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                     const int c = c2 + u * CQ;
                     act[u] = c >= my_lo && c <= my_hi;
                     int cw = c;
-                    if (A.panorama) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    if (A.panorama) {
+                        // the group's columns lie within about one period of [0, U)
+                        if (cw < 0) cw += A.U;
+                        else if (cw >= A.U) cw -= A.U;
+                        if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    }
                     cw = act[u] ? cw : 0;
                     cws[u] = cw;
                     r0[u] = __ldg(recrow + 2 * cw);
