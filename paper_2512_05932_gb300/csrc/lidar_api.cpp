@@ -8,6 +8,7 @@
 #include <string>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -456,7 +457,7 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
 // chunk runs).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
                        int32_t *counts, cudaStream_t s, int n_chunks = 1, const int *bounds = nullptr,
-                       cudaEvent_t *chunk_done = nullptr)
+                       cudaEvent_t *chunk_done = nullptr, float *wave_mirror = nullptr)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -492,6 +493,7 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.slot_sms = kSlotSms;
         fa.slots_per_sm = l->slots_per_sm;
         fa.err = l->d_err;
+        fa.wave_mirror = wave_mirror;
     }
     const int G = tc ? l->G_tc : l->G;
     if (n_chunks <= 1) {
@@ -912,6 +914,38 @@ lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const
     return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
+// Device address of pinned host memory mapped into the device's address space
+// (cudaHostAlloc, or cudaHostRegister with mapping), 16-byte aligned; null for
+// anything else (pageable or device memory).
+static void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not known to CUDA: pageable memory
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15)) return nullptr;
+    return a.devicePointer;
+}
+
+// Waits for the stream and turns a slot-claim timeout of the echo-only form
+// into LIDAR_ETIMEOUT.
+static lidar_status_t sync_checked(lidar_t *l, cudaStream_t s)
+{
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+    if (l->d_err) {
+        int h = 0;
+        if ((e = cudaMemcpy(&h, l->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(l, e, "error word download");
+        if (h) {
+            cudaMemset(l->d_err, 0, sizeof(int));
+            return fail(l, LIDAR_ETIMEOUT, "a CTA found no free waveform slot; its beams' results were not written");
+        }
+    }
+    return LIDAR_OK;
+}
+
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
                                    lidar_echo_t *echoes, int32_t *counts, void *stream)
 {
@@ -948,6 +982,17 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     }
     dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
     dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
+    // Outputs in pinned, device-mapped host memory: the kernels write them
+    // there directly (the echo-only form, which keeps each waveform in an
+    // L2-sized slot for its echo scan, also stores the row to the caller's
+    // buffer), so no staging buffer or copy is needed.
+    float *wave_m = static_cast<float *>(mapped_host(wave));
+    lidar_echo_t *echo_m = static_cast<lidar_echo_t *>(mapped_host(echoes));
+    int32_t *count_m = static_cast<int32_t *>(mapped_host(counts));
+    if (wave_m && echo_m && count_m) {
+        if ((st = enqueue(l, &dg, R, nullptr, echo_m, count_m, s, 1, nullptr, nullptr, wave_m)) != LIDAR_OK) return st;
+        return sync_checked(l, s);
+    }
     // A frame with many beam groups is simulated in kHostChunks launches whose
     // results are copied back on a second stream while the next one runs.
     const int G = l->deposit != 0 ? l->G_tc : l->G;

@@ -38,8 +38,15 @@ def run_gpu(w, host=False, deposit=0):
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
     lidar.lidar_set_deposit(L.handle, deposit)
     if host:
+        # pinned outputs: the kernels write them directly; pageable outputs:
+        # device staging buffers and chunked copies
         planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
-        wave, ech, cnt = L.simulate_host(w.gbuffer, planes, w.pose)
+        outs = None
+        if host == "pageable":
+            outs = (torch.empty((L.n_beams, L.n_bins), dtype=torch.float32),
+                    torch.empty((L.n_beams, L.max_echoes, 8), dtype=torch.int32),
+                    torch.empty((L.n_beams,), dtype=torch.int32))
+        wave, ech, cnt = L.simulate_host(w.gbuffer, planes, w.pose, outs)
     else:
         planes = lidar.gbuffer_to_device(w.gbuffer)
         wave, ech, cnt = L.simulate(w.gbuffer, planes, w.pose)
@@ -123,8 +130,9 @@ def test_tiny_ragged_rolled_pose():
     check_workload(S.tiny_case())
 
 
-def test_tiny_host_entry_point():
-    check_workload(S.tiny_case(), host=True)
+@pytest.mark.parametrize("host", ["pinned", "pageable"])
+def test_tiny_host_entry_point(host):
+    check_workload(S.tiny_case(), host=host)
 
 
 def test_full_frame_sampled_beams():
@@ -137,14 +145,16 @@ def test_full_frame_sampled_beams():
     assert st["echoes"] > 0
 
 
-def test_full_frame_host_entry_point_matches_device_entry_point():
-    """The host-memory entry point splits a large frame into several launches
-    whose results are copied back while the next runs: same waveforms (up to
-    the FP32 order of the deposits), echoes and counts as the device entry
-    point on the same frame."""
+@pytest.mark.parametrize("host", ["pinned", "pageable"])
+def test_full_frame_host_entry_point_matches_device_entry_point(host):
+    """The host-memory entry point, writing pinned outputs directly from the
+    kernels or (pageable outputs) splitting a large frame into several
+    launches whose results are copied back while the next runs: same
+    waveforms (up to the FP32 order of the deposits), echoes and counts as the
+    device entry point on the same frame."""
     w = S.full_frame_boxes()
     _, wave_d, ech_d, cnt_d = run_gpu(w)
-    _, wave_h, ech_h, cnt_h = run_gpu(w, host=True)
+    _, wave_h, ech_h, cnt_h = run_gpu(w, host=host)
     rel = np.linalg.norm(wave_h - wave_d, axis=1) / np.maximum(np.linalg.norm(wave_d, axis=1), 1e-30)
     assert rel.max() <= 1e-5, rel.max()
     assert (cnt_h == cnt_d).mean() >= 0.999
