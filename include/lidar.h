@@ -272,20 +272,13 @@ lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuf
 /* Same computation from host memory: the G-buffer plane pointers in `gbuffer`
  * are HOST pointers, and the outputs are host arrays (waveforms
  * [n_beams][n_bins], echoes [n_beams][max_echoes], counts [n_beams]). The
- * library copies the inputs to device buffers it owns, simulates and
- * synchronises `stream` before returning.
- *   - If all three outputs are page-locked host memory mapped into the
- *     device's address space (cudaHostAlloc, or cudaHostRegister with
- *     mapping; 16-byte aligned), the kernels write them directly: the
- *     echo-only form of lidar_simulate_echoes runs, and each waveform row is
- *     stored once to `wave` as well as to the L2-resident slot its echo scan
- *     reads. No output staging buffer or copy. The buffers must hold the sizes
- *     above (the kernels write through them as they would through device
- *     pointers). A slot-claim timeout returns LIDAR_ETIMEOUT.
- *   - Otherwise the results go through device staging buffers: a frame of at
- *     least 1216 beam groups is simulated in 4 launches, and the results of
- *     each are copied back on a library-owned stream while the next one runs.
- * Page-locked inputs give asynchronous, full-bandwidth copies. */
+ * library copies the inputs to device buffers it owns, simulates, copies the
+ * results back and synchronises `stream` before returning. A frame of at
+ * least 1216 beam groups is simulated in 8 launches that alternate between
+ * `stream` and a library-owned stream (so that one launch's CTAs fill the SMs
+ * the previous one is leaving), and the results of each are copied back on a
+ * third, library-owned stream while later ones run. Page-locked host memory
+ * gives asynchronous, full-bandwidth copies. */
 lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);

@@ -8,7 +8,6 @@
 #include <string>
 #include <cmath>
 #include <cstdarg>
-#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -350,8 +349,11 @@ void free_all(lidar_t *l)
     cudaFree(l->d_slot_busy);
     cudaFree(l->d_err);
     if (l->copy_stream) cudaStreamDestroy(l->copy_stream);
+    if (l->aux_stream) cudaStreamDestroy(l->aux_stream);
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
+    if (l->setup_ev) cudaEventDestroy(l->setup_ev);
+    if (l->join_ev) cudaEventDestroy(l->join_ev);
     tail_free(l);
 }
 
@@ -457,7 +459,7 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
 // chunk runs).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
                        int32_t *counts, cudaStream_t s, int n_chunks = 1, const int *bounds = nullptr,
-                       cudaEvent_t *chunk_done = nullptr, float *wave_mirror = nullptr)
+                       cudaEvent_t *chunk_done = nullptr, cudaStream_t aux_stream = nullptr)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -493,15 +495,20 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.slot_sms = kSlotSms;
         fa.slots_per_sm = l->slots_per_sm;
         fa.err = l->d_err;
-        fa.wave_mirror = wave_mirror;
     }
     const int G = tc ? l->G_tc : l->G;
     if (n_chunks <= 1) {
         e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
         if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     } else {
+        // odd chunks on aux (after the setup), even ones on s; s joins aux at the end
+        cudaStream_t aux = aux_stream ? aux_stream : s;
+        if (aux != s && ((e = cudaEventRecord(l->setup_ev, s)) != cudaSuccess ||
+                         (e = cudaStreamWaitEvent(aux, l->setup_ev, 0)) != cudaSuccess))
+            return cuda_fail(l, e, "chunk stream set-up");
         for (int i = 0; i < n_chunks; ++i) {
             const int b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
+            cudaStream_t cs = (i & 1) ? aux : s;
             gbl::FootprintArgs fc = fa;
             fc.beams = l->d_beams + b0;
             fc.n_beams = nb;
@@ -509,11 +516,14 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
             fc.echoes = echoes + (size_t)b0 * l->max_echoes;
             fc.counts = counts + b0;
             if (nb > 0) {
-                e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, s);
+                e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs);
                 if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
             }
-            if ((e = cudaEventRecord(chunk_done[i], s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+            if ((e = cudaEventRecord(chunk_done[i], cs)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
         }
+        if (aux != s && ((e = cudaEventRecord(l->join_ev, aux)) != cudaSuccess ||
+                         (e = cudaStreamWaitEvent(s, l->join_ev, 0)) != cudaSuccess))
+            return cuda_fail(l, e, "chunk stream join");
     }
     if (ev2) cudaEventRecord(ev2, s);
     return LIDAR_OK;
@@ -914,38 +924,6 @@ lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const
     return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
-// Device address of pinned host memory mapped into the device's address space
-// (cudaHostAlloc, or cudaHostRegister with mapping), 16-byte aligned; null for
-// anything else (pageable or device memory).
-static void *mapped_host(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();  // not known to CUDA: pageable memory
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15)) return nullptr;
-    return a.devicePointer;
-}
-
-// Waits for the stream and turns a slot-claim timeout of the echo-only form
-// into LIDAR_ETIMEOUT.
-static lidar_status_t sync_checked(lidar_t *l, cudaStream_t s)
-{
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
-    if (l->d_err) {
-        int h = 0;
-        if ((e = cudaMemcpy(&h, l->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_fail(l, e, "error word download");
-        if (h) {
-            cudaMemset(l->d_err, 0, sizeof(int));
-            return fail(l, LIDAR_ETIMEOUT, "a CTA found no free waveform slot; its beams' results were not written");
-        }
-    }
-    return LIDAR_OK;
-}
-
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
                                    lidar_echo_t *echoes, int32_t *counts, void *stream)
 {
@@ -982,33 +960,29 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     }
     dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
     dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
-    // Outputs in pinned, device-mapped host memory: the kernels write them
-    // there directly (the echo-only form, which keeps each waveform in an
-    // L2-sized slot for its echo scan, also stores the row to the caller's
-    // buffer), so no staging buffer or copy is needed.
-    float *wave_m = static_cast<float *>(mapped_host(wave));
-    lidar_echo_t *echo_m = static_cast<lidar_echo_t *>(mapped_host(echoes));
-    int32_t *count_m = static_cast<int32_t *>(mapped_host(counts));
-    if (wave_m && echo_m && count_m) {
-        if ((st = enqueue(l, &dg, R, nullptr, echo_m, count_m, s, 1, nullptr, nullptr, wave_m)) != LIDAR_OK) return st;
-        return sync_checked(l, s);
-    }
-    // A frame with many beam groups is simulated in kHostChunks launches whose
-    // results are copied back on a second stream while the next one runs.
+    // A frame with many beam groups is simulated in kHostChunks launches,
+    // alternating between two streams, whose results are copied back on a
+    // third stream while later ones run.
     const int G = l->deposit != 0 ? l->G_tc : l->G;
     const int ng = (l->n_beams + G - 1) / G;
     const int K = ng >= 8 * 152 ? kHostChunks : 1;
     int bounds[kHostChunks + 1];
     for (int i = 0; i <= K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * i / K) * G);
     if (K > 1) {
-        if (!l->copy_stream &&
-            (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(l, e, "cudaStreamCreate(result copies)");
+        if ((!l->copy_stream &&
+             (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) ||
+            (!l->aux_stream && (e = cudaStreamCreateWithFlags(&l->aux_stream, cudaStreamNonBlocking)) != cudaSuccess))
+            return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
         for (int i = 0; i < kHostChunks; ++i)
             if (!l->chunk_ev[i] && (e = cudaEventCreateWithFlags(&l->chunk_ev[i], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventCreate(result copies)");
+        if ((!l->setup_ev && (e = cudaEventCreateWithFlags(&l->setup_ev, cudaEventDisableTiming)) != cudaSuccess) ||
+            (!l->join_ev && (e = cudaEventCreateWithFlags(&l->join_ev, cudaEventDisableTiming)) != cudaSuccess))
+            return cuda_fail(l, e, "cudaEventCreate(chunk streams)");
     }
-    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K, bounds, l->chunk_ev)) != LIDAR_OK) return st;
+    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K, bounds, l->chunk_ev,
+                      K > 1 ? l->aux_stream : nullptr)) != LIDAR_OK)
+        return st;
     for (int i = 0; i < K; ++i) {
         const size_t b0 = (size_t)bounds[i], nb = (size_t)(bounds[i + 1] - bounds[i]);
         cudaStream_t cs = K > 1 ? l->copy_stream : s;

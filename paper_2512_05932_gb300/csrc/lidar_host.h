@@ -54,10 +54,14 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
-    // lidar_simulate_host: results of finished beam chunks are copied back on
-    // copy_stream while later chunks run (chunk_ev[i]: chunk i finished)
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // lidar_simulate_host: beam chunks alternate between the caller's stream
+    // and aux_stream (so one chunk's CTAs fill the SMs the previous one is
+    // leaving); the results of finished chunks are copied back on copy_stream
+    // while later chunks run (chunk_ev[i]: chunk i finished; setup_ev: the
+    // per-pixel setup done; join_ev: aux_stream's last chunk done)
+    cudaStream_t copy_stream = nullptr, aux_stream = nullptr;
+    cudaEvent_t chunk_ev[8] = {};
+    cudaEvent_t setup_ev = nullptr, join_ev = nullptr;
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
@@ -96,7 +100,8 @@ constexpr double kC = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kDeg = kPi / 180.0;
 constexpr double kMaxSupportDeg = 10.0;
-constexpr int kHostChunks = 4;  // footprint launches per frame of lidar_simulate_host (large frames)
+constexpr int kHostChunks = 8;  // footprint launches per frame of lidar_simulate_host (large frames)
+static_assert(kHostChunks == sizeof(lidar::chunk_ev) / sizeof(cudaEvent_t), "one event per chunk");
 
 lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...);
 lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what);

@@ -117,7 +117,6 @@ struct FootprintArgs {
     // 1 held) and frees at exit; n_slots >= the CTAs the GPU holds at once.
     // NULL: waveforms are outputs in `wave`.
     float *slot_pool;
-    float *wave_mirror;    // echo-only form: every waveform row also stored here (device-accessible host memory), or null
     int *slot_busy;
     int n_slots;             // slot_sms * slots_per_sm
     int slot_sms, slots_per_sm;

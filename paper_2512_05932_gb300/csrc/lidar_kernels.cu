@@ -1096,13 +1096,6 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             float4 *dst = reinterpret_cast<float4 *>(wrow + o0 + 8 * lane);
             dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            if (A.wave_mirror) {
-                // the caller's copy (pinned host memory reached over the
-                // chip-to-chip link): written once, never read back here
-                float4 *mir = reinterpret_cast<float4 *>(A.wave_mirror + orow * nb + o0 + 8 * lane);
-                mir[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                mir[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            }
         }
         if (A.tail_in && bp[jj].pad0) {
             // squared L2 norm of the waveform (acceptance test of the tail)

@@ -38,8 +38,8 @@ def run_gpu(w, host=False, deposit=0):
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
     lidar.lidar_set_deposit(L.handle, deposit)
     if host:
-        # pinned outputs: the kernels write them directly; pageable outputs:
-        # device staging buffers and chunked copies
+        # pinned outputs (asynchronous copies) or pageable ones (staged by the
+        # driver)
         planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
         outs = None
         if host == "pageable":
@@ -147,11 +147,10 @@ def test_full_frame_sampled_beams():
 
 @pytest.mark.parametrize("host", ["pinned", "pageable"])
 def test_full_frame_host_entry_point_matches_device_entry_point(host):
-    """The host-memory entry point, writing pinned outputs directly from the
-    kernels or (pageable outputs) splitting a large frame into several
-    launches whose results are copied back while the next runs: same
-    waveforms (up to the FP32 order of the deposits), echoes and counts as the
-    device entry point on the same frame."""
+    """The host-memory entry point splits a large frame into several launches
+    on two streams whose results are copied back while later ones run, into
+    pinned or pageable outputs: same waveforms (up to the FP32 order of the
+    deposits), echoes and counts as the device entry point on the same frame."""
     w = S.full_frame_boxes()
     _, wave_d, ech_d, cnt_d = run_gpu(w)
     _, wave_h, ech_h, cnt_h = run_gpu(w, host=host)
