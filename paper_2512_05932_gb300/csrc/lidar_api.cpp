@@ -353,6 +353,8 @@ void free_all(lidar_t *l)
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
     if (l->setup_ev) cudaEventDestroy(l->setup_ev);
+    for (cudaEvent_t &ev : l->band_ev)
+        if (ev) cudaEventDestroy(ev);
     if (l->join_ev) cudaEventDestroy(l->join_ev);
     tail_free(l);
 }
@@ -378,6 +380,8 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
     sa.pad = gbl::footprint_pad(l->M);
     long pb = (long)((pixels + 255) / 256);
     sa.pix_blocks = (int)std::min<long>(pb, 152L * 64);
+    sa.pix_begin = 0;
+    sa.pix_end = (long)pixels;
     sa.n_beams = sensor->n_beams;
     sa.dirs = sensor->d_dirs;
     for (int i = 0; i < 9; ++i) sa.R[i] = R[i];
@@ -459,7 +463,8 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
 // chunk runs).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
                        int32_t *counts, cudaStream_t s, int n_chunks = 1, const int *bounds = nullptr,
-                       cudaEvent_t *chunk_done = nullptr, cudaStream_t aux_stream = nullptr)
+                       cudaEvent_t *chunk_done = nullptr, cudaStream_t aux_stream = nullptr,
+                       int n_bands = 0, const long *band_pix = nullptr, cudaEvent_t *band_ready = nullptr)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -477,8 +482,27 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
     }
     if (ev0) cudaEventRecord(ev0, s);
-    cudaError_t e = gbl::launch_setup(sa, s);
-    if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    cudaError_t e = cudaSuccess;
+    if (n_bands <= 0) {
+        e = gbl::launch_setup(sa, s);
+        if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    } else {
+        // the planes arrive in bands of pixels (band b ready at band_ready[b]):
+        // the beams' set-up first (it reads no plane), then each band's pixels
+        gbl::SetupArgs sb = sa;
+        sb.pix_blocks = 0;
+        if ((e = gbl::launch_setup(sb, s)) != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+        for (int b = 0; b < n_bands; ++b) {
+            gbl::SetupArgs sp = sa;
+            sp.n_beams = 0;
+            sp.pix_begin = band_pix[b];
+            sp.pix_end = band_pix[b + 1];
+            sp.pix_blocks = (int)std::max<long>(1, std::min<long>(sa.pix_blocks, (sp.pix_end - sp.pix_begin + 255) / 256));
+            if ((e = cudaStreamWaitEvent(s, band_ready[b], 0)) != cudaSuccess ||
+                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, s)) != cudaSuccess))
+                return cuda_fail(l, e, "setup kernel launch");
+        }
+    }
     if (ev1) cudaEventRecord(ev1, s);
 
     gbl::FootprintArgs fa = model_args(l);
@@ -953,21 +977,21 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     const float *src[7] = {g->range, g->nx, g->ny, g->nz, g->rho_d, g->retro, g->ambient};
     lidar_gbuffer_t dg = *g;
     float *dst[7];
-    for (int i = 0; i < 7; ++i) {
-        dst[i] = l->d_planes + (size_t)i * pixels;
-        if ((e = cudaMemcpyAsync(dst[i], src[i], pixels * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-            return cuda_fail(l, e, "G-buffer upload");
-    }
+    for (int i = 0; i < 7; ++i) dst[i] = l->d_planes + (size_t)i * pixels;
     dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
     dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
     // A frame with many beam groups is simulated in kHostChunks launches,
     // alternating between two streams, whose results are copied back on a
-    // third stream while later ones run.
+    // third stream while later ones run; the last chunk is small, so that
+    // little copying is left when the kernels end. The G-buffer goes up on
+    // the copy stream in kHostBands bands of rows, each set up as it lands.
     const int G = l->deposit != 0 ? l->G_tc : l->G;
     const int ng = (l->n_beams + G - 1) / G;
     const int K = ng >= 8 * 152 ? kHostChunks : 1;
     int bounds[kHostChunks + 1];
-    for (int i = 0; i <= K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * i / K) * G);
+    bounds[0] = 0;
+    for (int i = 1; i < K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 19 * i / (20 * (K - 1))) * G);
+    bounds[K] = l->n_beams;
     if (K > 1) {
         if ((!l->copy_stream &&
              (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) ||
@@ -979,9 +1003,30 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
         if ((!l->setup_ev && (e = cudaEventCreateWithFlags(&l->setup_ev, cudaEventDisableTiming)) != cudaSuccess) ||
             (!l->join_ev && (e = cudaEventCreateWithFlags(&l->join_ev, cudaEventDisableTiming)) != cudaSuccess))
             return cuda_fail(l, e, "cudaEventCreate(chunk streams)");
+        for (int i = 0; i < kHostBands; ++i)
+            if (!l->band_ev[i] && (e = cudaEventCreateWithFlags(&l->band_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaEventCreate(G-buffer bands)");
+    }
+    const int NB = K > 1 ? kHostBands : 1;
+    long band_pix[kHostBands + 1];
+    for (int b = 0; b <= NB; ++b) band_pix[b] = (long)((long)g->V * b / NB) * g->U;
+    {
+        // the copy stream starts after the caller's earlier work on `stream`
+        cudaStream_t us = K > 1 ? l->copy_stream : s;
+        if (K > 1 && ((e = cudaEventRecord(l->setup_ev, s)) != cudaSuccess ||
+                      (e = cudaStreamWaitEvent(us, l->setup_ev, 0)) != cudaSuccess))
+            return cuda_fail(l, e, "G-buffer upload ordering");
+        for (int b = 0; b < NB; ++b) {
+            const size_t p0 = (size_t)band_pix[b], np = (size_t)(band_pix[b + 1] - band_pix[b]);
+            for (int i = 0; i < 7; ++i)
+                if (np && (e = cudaMemcpyAsync(dst[i] + p0, src[i] + p0, np * sizeof(float), cudaMemcpyHostToDevice,
+                                               us)) != cudaSuccess)
+                    return cuda_fail(l, e, "G-buffer upload");
+            if (K > 1 && (e = cudaEventRecord(l->band_ev[b], us)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+        }
     }
     if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K, bounds, l->chunk_ev,
-                      K > 1 ? l->aux_stream : nullptr)) != LIDAR_OK)
+                      K > 1 ? l->aux_stream : nullptr, K > 1 ? NB : 0, band_pix, l->band_ev)) != LIDAR_OK)
         return st;
     for (int i = 0; i < K; ++i) {
         const size_t b0 = (size_t)bounds[i], nb = (size_t)(bounds[i + 1] - bounds[i]);

@@ -62,6 +62,7 @@ struct lidar {
     cudaStream_t copy_stream = nullptr, aux_stream = nullptr;
     cudaEvent_t chunk_ev[8] = {};
     cudaEvent_t setup_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t band_ev[4] = {};  // G-buffer band b uploaded (copy_stream)
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
@@ -102,6 +103,8 @@ constexpr double kDeg = kPi / 180.0;
 constexpr double kMaxSupportDeg = 10.0;
 constexpr int kHostChunks = 8;  // footprint launches per frame of lidar_simulate_host (large frames)
 static_assert(kHostChunks == sizeof(lidar::chunk_ev) / sizeof(cudaEvent_t), "one event per chunk");
+constexpr int kHostBands = 4;  // G-buffer upload bands of lidar_simulate_host (large frames)
+static_assert(kHostBands == sizeof(lidar::band_ev) / sizeof(cudaEvent_t), "one event per band");
 
 lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...);
 lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what);

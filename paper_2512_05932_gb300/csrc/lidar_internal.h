@@ -48,6 +48,7 @@ struct SetupArgs {
     int bin_records;         // narrow records carry the first bin index (tensor-core deposit)
                              // instead of histogram positions (shared-memory atomics)
     int pix_blocks;
+    long pix_begin, pix_end; // setup_kernel: the pixels [pix_begin, pix_end) only
     // beams
     int n_beams;
     const float *dirs;       // [n_beams][3]

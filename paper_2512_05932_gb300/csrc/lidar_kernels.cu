@@ -261,8 +261,9 @@ __device__ void setup_beam(const SetupArgs &A, int b)
 __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A)
 {
     if ((int)blockIdx.x < A.pix_blocks) {
-        int n = A.U * A.V;
-        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += A.pix_blocks * blockDim.x)
+        const int n = (int)A.pix_end;
+        for (int idx = (int)A.pix_begin + blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+             idx += A.pix_blocks * blockDim.x)
             setup_pixel(A, idx);
     } else {
         int b = (blockIdx.x - A.pix_blocks) * blockDim.x + threadIdx.x;
