@@ -78,6 +78,30 @@ __global__ void __launch_bounds__(256) stack_inputs_kernel(StackArgs A)
     }
 }
 
+// hist[s - slo] += the intensities of the region's pixels of slice s (s > 0),
+// for the n region pixels; called by every thread of the block (whole warps).
+// Neighbouring pixels mostly share a slice: a warp whose 32 pixels all do
+// adds their sum with one atomic.
+__device__ __forceinline__ void region_hist(float *hist, const uint16_t *RS, const float *RI, int n, int slo)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int sv = i < n ? (int)RS[i] : 0;
+        const float w = sv ? RI[i] : 0.f;
+        int same = 0;
+        __match_all_sync(0xffffffffu, sv, &same);
+        if (same) {
+            float t = w;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0 && sv) atomicAdd(&hist[sv - slo], t);
+        } else if (sv) {
+            atomicAdd(&hist[sv - slo], w);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -128,8 +152,7 @@ __global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
         if (shi >= slo && shi - slo < kSpan) {
             for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
             __syncthreads();
-            for (int i = tid; i < RH * RW; i += blockDim.x)
-                if (RS[i]) atomicAdd(&hist[RS[i] - slo], RI[i]);
+            region_hist(hist, RS, RI, RH * RW, slo);
             __syncthreads();
             const float cut = A.thr * (1.f - 1e-5f);
             for (int i = tid; i < RH * RW; i += blockDim.x)
@@ -350,8 +373,7 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     if (use_hist) {
         for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
         __syncthreads();
-        for (int i = tid; i < RH * RWp; i += blockDim.x)
-            if (RS[i]) atomicAdd(&hist[RS[i] - slo], RI[i]);
+        region_hist(hist, RS, RI, RH * RWp, slo);
         __syncthreads();
     }
     // per region row: range of the slices on it (rows without slice s skip the row pass)
