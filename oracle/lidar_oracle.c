@@ -633,3 +633,41 @@ void orc_range_stack(int U, int V, const double *I, const int32_t *rbar, int kh,
     }
     free(slice);
 }
+
+/* Alg. 2 at single output pixels (v[q], u[q]), q < n: the same sums as
+ * orc_range_stack (per slice s, sum over the kernel window of K * I on the
+ * pixels of slice s, in the same (i, j) order, so the same rounding), and the
+ * same answer: the nearest slice reaching the threshold (the last one the
+ * far-to-near sweep writes), else s_max and 0. closest[q] = min over slices
+ * s <= S of |sum_s - thr| / thr (how near a decision came to flipping). */
+void orc_range_stack_at(int U, int V, const double *I, const int32_t *rbar, int kh, int kw, const double *K,
+                        double thr, int s_max, int n, const int32_t *v, const int32_t *u, int32_t *S, double *X,
+                        double *closest)
+{
+    const int m = kh / 2, h = kw / 2;
+    double *acc = malloc((size_t)(s_max + 1) * sizeof(double));
+    for (int q = 0; q < n; ++q) {
+        for (int s = 0; s <= s_max; ++s) acc[s] = 0.0;
+        for (int i = -m; i <= m; ++i) {
+            int vv = v[q] - i;
+            if (vv < 0 || vv >= V) continue;
+            for (int j = -h; j <= h; ++j) {
+                int uu = u[q] - j;
+                if (uu < 0 || uu >= U) continue;
+                int s = rbar[(long)vv * U + uu];
+                if (s >= 1 && s <= s_max) acc[s] += K[(long)(m + i) * kw + (h + j)] * I[(long)vv * U + uu];
+            }
+        }
+        S[q] = s_max;
+        X[q] = 0.0;
+        for (int s = 1; s <= s_max; ++s)
+            if (acc[s] >= thr) { S[q] = s; X[q] = acc[s]; break; }
+        double c = INFINITY;
+        for (int s = 1; s <= S[q]; ++s) {
+            double d = fabs(acc[s] - thr) / thr;
+            if (d < c) c = d;
+        }
+        closest[q] = c;
+    }
+    free(acc);
+}

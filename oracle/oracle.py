@@ -101,6 +101,8 @@ def lib():
         _lib.orc_offsets.argtypes = [p, p, p, i, p, p, p]
         _lib.orc_stack_inputs.argtypes = [C.POINTER(_GBuffer), d, p, p]
         _lib.orc_range_stack.argtypes = [i, i, p, p, i, i, p, d, i, p, p]
+        _lib.orc_range_stack_at.restype = None
+        _lib.orc_range_stack_at.argtypes = [i, i, p, p, i, i, p, d, i, i, p, p, p, p, p]
         _lib.orc_pixel.restype = i
     return _lib
 
@@ -290,6 +292,26 @@ def stack_inputs(gb, dr):
     rbar = np.zeros((gb.V, gb.U), np.int32)
     lib().orc_stack_inputs(C.byref(g), float(dr), I.ctypes.data, rbar.ctypes.data)
     return I, rbar
+
+
+def range_stack_at(I, rbar, kernel, threshold, s_max, v, u):
+    """Alg. 2 at the output pixels (v[q], u[q]) only: the values range_stack
+    gives there, plus how near each decision came to flipping (min over the
+    slices up to the answer of |sum - threshold| / threshold)."""
+    I = np.ascontiguousarray(I, np.float64)
+    rbar = np.ascontiguousarray(rbar, np.int32)
+    K = np.ascontiguousarray(kernel, np.float64)
+    v = np.ascontiguousarray(v, np.int32)
+    u = np.ascontiguousarray(u, np.int32)
+    V, U = I.shape
+    n = len(v)
+    S = np.zeros(n, np.int32)
+    X = np.zeros(n)
+    close = np.zeros(n)
+    lib().orc_range_stack_at(U, V, I.ctypes.data, rbar.ctypes.data, K.shape[0], K.shape[1], K.ctypes.data,
+                             float(threshold), int(s_max), n, v.ctypes.data, u.ctypes.data, S.ctypes.data,
+                             X.ctypes.data, close.ctypes.data)
+    return S, X, close
 
 
 def range_stack(I, rbar, kernel, threshold, s_max):

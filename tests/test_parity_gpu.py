@@ -163,6 +163,23 @@ def test_full_frame_host_entry_point_matches_device_entry_point(host):
         assert (a == b).mean() >= 0.999, k
 
 
+def test_ragged_large_frame_host_entry_point():
+    """A frame whose rows do not split evenly into the host path's upload bands
+    and whose beams do not fill the last group (25 597 beams on 2000x999): the
+    banded upload, per-band set-up and chunked launches on two streams give
+    the device entry point's results."""
+    w = S.full_frame_boxes(U=2000, V=999)
+    w.dirs = w.dirs[:25597]
+    _, wave_d, ech_d, cnt_d = run_gpu(w)
+    _, wave_h, ech_h, cnt_h = run_gpu(w, host="pinned")
+    rel = np.linalg.norm(wave_h - wave_d, axis=1) / np.maximum(np.linalg.norm(wave_d, axis=1), 1e-30)
+    assert rel.max() <= 1e-5, rel.max()
+    assert (cnt_h == cnt_d).mean() >= 0.999
+    same = cnt_h == cnt_d
+    for k in ("bin_start", "bin_end"):
+        assert (ech_h[k][same] == ech_d[k][same]).mean() >= 0.999, k
+
+
 def test_table_profile_anisotropic_with_roll():
     w = S.small_plane_retro()
     w.profile = S.table_profile(S.elliptic_gauss_table(41, 81, 0.01, 0.05, 0.1), 0.01)

@@ -121,3 +121,12 @@ def test_reprojection_rejects_bad_arguments():
     s = lidar.make_pinhole(ph, [p.data_ptr() for p in src])
     with pytest.raises(lidar.LidarError, match="target plane"):
         lidar.lidar_reproject_pinhole(s, lidar.make_gbuffer(grid, [0] * 7))
+
+
+def test_bench_frame_reprojection_every_pixel():
+    """The benchmark's pinhole frame (2048x1024 rendering of the boxes scene,
+    60 deg field of view) onto its 2048x1024 grid: every target pixel against
+    the FP64 reprojection."""
+    ph, grid, _ = S.pinhole_boxes_frame()
+    ref, sure = assert_planes_match(ph, grid)
+    assert sure.mean() > 0.999 and np.isfinite(ref.range).mean() > 0.5

@@ -204,3 +204,34 @@ def test_separable_rejects_bad_parameters():
         lidar.RangeStack(None, 1.0, 0.1, 10.0, separable=(np.ones(4), np.ones(5)))
     with pytest.raises(lidar.LidarError, match="row"):
         lidar.RangeStack(None, 1.0, 0.1, 10.0, separable=(np.ones(5), -np.ones(5)))
+
+
+@pytest.mark.parametrize("separable", [False, True])
+def test_bench_frame_sampled_pixels(separable):
+    """The benchmark's configuration (the 4096x1024 boxes frame, the 69x69 px
+    kernel or its separable centre column x row, 1200 slices of 2.5 cm): the
+    GPU's slices and intensities at 4096 sampled pixels against the oracle
+    evaluated pixel by pixel (range_stack_at), with the same near-threshold
+    exemption as the small cases."""
+    import bench
+    w, k, dr, rmax, thr = bench.stack_workload()
+    gb = w.gbuffer
+    sep = None
+    if separable:
+        c = k.shape[0] // 2
+        sep = ((k[:, c] / np.sqrt(k[c, c])).astype(np.float32), (k[c, :] / np.sqrt(k[c, c])).astype(np.float32))
+        K = np.outer(sep[0].astype(np.float64), sep[1].astype(np.float64))
+    else:
+        K = k.astype(np.float64)
+    S_g, X_g, s_max = run_gpu(gb, None if separable else k, thr, dr, rmax, separable=sep)
+    I, rb = O.stack_inputs(gb, dr)
+    g = np.random.default_rng(17)
+    v, u = g.integers(0, gb.V, 4096), g.integers(0, gb.U, 4096)
+    S_o, X_o, close = O.range_stack_at(I, rb, K, thr, s_max, v, u)
+    sure = close > 1e-5
+    assert sure.mean() > 0.98
+    np.testing.assert_array_equal(S_g[v, u][sure], S_o[sure])
+    hit = sure & (X_o > 0)
+    assert hit.sum() > 500
+    np.testing.assert_allclose(X_g[v, u][hit], X_o[hit], rtol=1e-5)
+    assert (X_g[v, u][sure & (X_o == 0)] == 0).all()

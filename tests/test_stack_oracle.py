@@ -75,3 +75,23 @@ def test_inputs_are_pixel_power_and_floor_range():
     assert (I[~hit] == 0).all() and (rb[~hit] == -1).all()
     r = w.gbuffer.range.astype(np.float64)
     np.testing.assert_array_equal(rb[hit], np.floor(r[hit] / dr).astype(np.int32))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_pixel_entry_equals_whole_image_sweep(seed):
+    """range_stack_at (one output pixel at a time, for sampled checks at full
+    size) gives exactly range_stack's slice and value at every pixel, with the
+    nearest-to-threshold distance consistent with the answer."""
+    g = np.random.default_rng(10 + seed)
+    V, U, s_max = 11, 14, 7
+    I = g.uniform(0, 1, (V, U))
+    rb = g.integers(-1, s_max + 2, (V, U)).astype(np.int32)
+    K = g.uniform(0, 1, (5, 7))
+    thr = 1.1
+    S_, X = O.range_stack(I, rb, K, thr, s_max)
+    vv, uu = np.meshgrid(np.arange(V), np.arange(U), indexing="ij")
+    S1, X1, close = O.range_stack_at(I, rb, K, thr, s_max, vv.ravel(), uu.ravel())
+    np.testing.assert_array_equal(S1.reshape(V, U), S_)
+    np.testing.assert_array_equal(X1.reshape(V, U), X)
+    hit = X1 > 0
+    assert (close[hit] <= np.abs(X1[hit] / thr - 1) + 1e-15).all()
