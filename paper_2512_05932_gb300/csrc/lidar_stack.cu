@@ -31,9 +31,9 @@
 namespace {
 
 constexpr int kTW = 32, kTH = 8;  // output tile (one thread per output pixel)
-constexpr int kSlots = 24;
+constexpr int kSlots = 16;         // slices one pass of the slot walk keeps (16: 76 registers, 3 CTAs per SM)
 constexpr int kMaxK = 129;
-constexpr int kSpan = 4096;       // slice range of a tile's region for which weak slices are dropped
+constexpr int kSpan = 2048;       // slice range of a tile's region for which weak slices are dropped (8 KB histogram)
 constexpr int kDense = 4;         // at most this many remaining slices: one dense pass per slice
 
 struct StackArgs {
@@ -102,7 +102,7 @@ __device__ __forceinline__ void region_hist(float *hist, const uint16_t *RS, con
     }
 }
 
-__global__ void __launch_bounds__(kTW * kTH) stack_tile_kernel(StackArgs A)
+__global__ void __launch_bounds__(kTW * kTH, 3) stack_tile_kernel(StackArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int kh = A.kh, kw = A.kw, m = kh / 2, n = kw / 2;
