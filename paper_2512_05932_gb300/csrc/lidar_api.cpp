@@ -349,13 +349,17 @@ void free_all(lidar_t *l)
     cudaFree(l->d_slot_busy);
     cudaFree(l->d_err);
     if (l->copy_stream) cudaStreamDestroy(l->copy_stream);
-    if (l->aux_stream) cudaStreamDestroy(l->aux_stream);
+    for (cudaStream_t &st : l->aux_stream)
+        if (st) cudaStreamDestroy(st);
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
-    if (l->setup_ev) cudaEventDestroy(l->setup_ev);
+    for (cudaEvent_t &ev : l->setup_ev)
+        if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t &ev : l->band_ev)
         if (ev) cudaEventDestroy(ev);
-    if (l->join_ev) cudaEventDestroy(l->join_ev);
+    for (cudaEvent_t &ev : l->join_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (l->start_ev) cudaEventDestroy(l->start_ev);
     tail_free(l);
 }
 
@@ -455,16 +459,30 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
     return LIDAR_OK;
 }
 
-// Enqueues the setup and footprint kernels of one frame; wave == NULL
-// selects the echo-only form (waveforms in the pooled slots). With n_chunks
-// > 1 the footprint kernel is launched once per range of whole beam groups,
-// chunk i covering beams [bounds[i], bounds[i + 1]), and chunk_done[i] is
-// recorded on `s` after it (so that its outputs can be copied while the next
-// chunk runs).
+// How lidar_simulate_host splits a frame: the G-buffer arrives in n_bands
+// bands of pixels [band_pix[b], band_pix[b + 1]) (band b uploaded at
+// band_ready[b]; set up on `s` as it lands, setup_done[b] recorded after it),
+// and the footprint kernel runs once per range of whole beam groups, chunk i
+// covering beams [bounds[i], bounds[i + 1]) on aux[i % 2] once the bands up
+// to chunk_band[i] are set up (chunk_done[i] recorded after it); `s` joins
+// both aux streams at the end (join[k]).
+struct ChunkPlan {
+    int n_chunks = 1;
+    const int *bounds = nullptr;
+    const int *chunk_band = nullptr;
+    cudaEvent_t *chunk_done = nullptr;
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t *join = nullptr;
+    int n_bands = 0;
+    const long *band_pix = nullptr;
+    cudaEvent_t *band_ready = nullptr, *setup_done = nullptr;
+};
+
+// Enqueues the setup and footprint kernels of one frame on `s` (or as
+// `plan` says); wave == NULL selects the echo-only form (waveforms in the
+// pooled slots).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
-                       int32_t *counts, cudaStream_t s, int n_chunks = 1, const int *bounds = nullptr,
-                       cudaEvent_t *chunk_done = nullptr, cudaStream_t aux_stream = nullptr,
-                       int n_bands = 0, const long *band_pix = nullptr, cudaEvent_t *band_ready = nullptr)
+                       int32_t *counts, cudaStream_t s, const ChunkPlan *plan = nullptr)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -483,23 +501,23 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     }
     if (ev0) cudaEventRecord(ev0, s);
     cudaError_t e = cudaSuccess;
-    if (n_bands <= 0) {
+    if (!plan || plan->n_bands <= 0) {
         e = gbl::launch_setup(sa, s);
         if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
     } else {
-        // the planes arrive in bands of pixels (band b ready at band_ready[b]):
         // the beams' set-up first (it reads no plane), then each band's pixels
         gbl::SetupArgs sb = sa;
         sb.pix_blocks = 0;
         if ((e = gbl::launch_setup(sb, s)) != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
-        for (int b = 0; b < n_bands; ++b) {
+        for (int b = 0; b < plan->n_bands; ++b) {
             gbl::SetupArgs sp = sa;
             sp.n_beams = 0;
-            sp.pix_begin = band_pix[b];
-            sp.pix_end = band_pix[b + 1];
+            sp.pix_begin = plan->band_pix[b];
+            sp.pix_end = plan->band_pix[b + 1];
             sp.pix_blocks = (int)std::max<long>(1, std::min<long>(sa.pix_blocks, (sp.pix_end - sp.pix_begin + 255) / 256));
-            if ((e = cudaStreamWaitEvent(s, band_ready[b], 0)) != cudaSuccess ||
-                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, s)) != cudaSuccess))
+            if ((e = cudaStreamWaitEvent(s, plan->band_ready[b], 0)) != cudaSuccess ||
+                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, s)) != cudaSuccess) ||
+                (e = cudaEventRecord(plan->setup_done[b], s)) != cudaSuccess)
                 return cuda_fail(l, e, "setup kernel launch");
         }
     }
@@ -521,33 +539,31 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.err = l->d_err;
     }
     const int G = tc ? l->G_tc : l->G;
-    if (n_chunks <= 1) {
+    if (!plan || plan->n_chunks <= 1) {
         e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
         if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     } else {
-        // odd chunks on aux (after the setup), even ones on s; s joins aux at the end
-        cudaStream_t aux = aux_stream ? aux_stream : s;
-        if (aux != s && ((e = cudaEventRecord(l->setup_ev, s)) != cudaSuccess ||
-                         (e = cudaStreamWaitEvent(aux, l->setup_ev, 0)) != cudaSuccess))
-            return cuda_fail(l, e, "chunk stream set-up");
-        for (int i = 0; i < n_chunks; ++i) {
-            const int b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
-            cudaStream_t cs = (i & 1) ? aux : s;
+        for (int i = 0; i < plan->n_chunks; ++i) {
+            const int b0 = plan->bounds[i], nb = plan->bounds[i + 1] - plan->bounds[i];
+            cudaStream_t cs = plan->aux[i & 1];
             gbl::FootprintArgs fc = fa;
             fc.beams = l->d_beams + b0;
             fc.n_beams = nb;
             fc.wave = wave + (size_t)b0 * l->n_bins;
             fc.echoes = echoes + (size_t)b0 * l->max_echoes;
             fc.counts = counts + b0;
+            if ((e = cudaStreamWaitEvent(cs, plan->setup_done[plan->chunk_band[i]], 0)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaStreamWaitEvent");
             if (nb > 0) {
                 e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs);
                 if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
             }
-            if ((e = cudaEventRecord(chunk_done[i], cs)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+            if ((e = cudaEventRecord(plan->chunk_done[i], cs)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
         }
-        if (aux != s && ((e = cudaEventRecord(l->join_ev, aux)) != cudaSuccess ||
-                         (e = cudaStreamWaitEvent(s, l->join_ev, 0)) != cudaSuccess))
-            return cuda_fail(l, e, "chunk stream join");
+        for (int k = 0; k < 2; ++k)
+            if ((e = cudaEventRecord(plan->join[k], plan->aux[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, plan->join[k], 0)) != cudaSuccess)
+                return cuda_fail(l, e, "chunk stream join");
     }
     if (ev2) cudaEventRecord(ev2, s);
     return LIDAR_OK;
@@ -890,8 +906,15 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     if (2 * gbl::footprint_smem_bytes(8, probe) > 226 * 1024) l->G_tc = 4;
     l->smem_tc = gbl::footprint_smem_bytes(l->G_tc, probe);
 
-    // device copies
+    // device copies (and the host copy of the pattern)
     size_t nd = (size_t)pat->n_beams * 3 * sizeof(float);
+    try {
+        l->h_dirs.assign(pat->dirs, pat->dirs + (size_t)pat->n_beams * 3);
+    } catch (...) {
+        free_all(l);
+        delete l;
+        return fail(nullptr, LIDAR_ENOMEM, "host allocation failed");
+    }
     if ((e = cudaMalloc(&l->d_dirs, nd)) != cudaSuccess ||
         (e = cudaMemcpy(l->d_dirs, pat->dirs, nd, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMalloc(&l->d_taps, tpad.size() * sizeof(float))) != cudaSuccess ||
@@ -984,7 +1007,10 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     // alternating between two streams, whose results are copied back on a
     // third stream while later ones run; the last chunk is small, so that
     // little copying is left when the kernels end. The G-buffer goes up on
-    // the copy stream in kHostBands bands of rows, each set up as it lands.
+    // the copy stream in kHostBands bands of rows, each set up as it lands,
+    // and a chunk starts once the rows its beams can reach are set up: with
+    // beams ordered by elevation (a line scan) the first chunks overlap the
+    // rest of the upload.
     const int G = l->deposit != 0 ? l->G_tc : l->G;
     const int ng = (l->n_beams + G - 1) / G;
     const int K = ng >= 8 * 152 ? kHostChunks : 1;
@@ -993,28 +1019,55 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     for (int i = 1; i < K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 19 * i / (20 * (K - 1))) * G);
     bounds[K] = l->n_beams;
     if (K > 1) {
-        if ((!l->copy_stream &&
-             (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) ||
-            (!l->aux_stream && (e = cudaStreamCreateWithFlags(&l->aux_stream, cudaStreamNonBlocking)) != cudaSuccess))
+        if (!l->copy_stream && (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
+        for (cudaStream_t &st2 : l->aux_stream)
+            if (!st2 && (e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
+        cudaEvent_t *evs[] = {&l->start_ev, &l->join_ev[0], &l->join_ev[1]};
+        for (cudaEvent_t *ev : evs)
+            if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaEventCreate(chunk streams)");
         for (int i = 0; i < kHostChunks; ++i)
             if (!l->chunk_ev[i] && (e = cudaEventCreateWithFlags(&l->chunk_ev[i], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventCreate(result copies)");
-        if ((!l->setup_ev && (e = cudaEventCreateWithFlags(&l->setup_ev, cudaEventDisableTiming)) != cudaSuccess) ||
-            (!l->join_ev && (e = cudaEventCreateWithFlags(&l->join_ev, cudaEventDisableTiming)) != cudaSuccess))
-            return cuda_fail(l, e, "cudaEventCreate(chunk streams)");
         for (int i = 0; i < kHostBands; ++i)
-            if (!l->band_ev[i] && (e = cudaEventCreateWithFlags(&l->band_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+            if ((!l->band_ev[i] && (e = cudaEventCreateWithFlags(&l->band_ev[i], cudaEventDisableTiming)) != cudaSuccess) ||
+                (!l->setup_ev[i] && (e = cudaEventCreateWithFlags(&l->setup_ev[i], cudaEventDisableTiming)) != cudaSuccess))
                 return cuda_fail(l, e, "cudaEventCreate(G-buffer bands)");
     }
     const int NB = K > 1 ? kHostBands : 1;
     long band_pix[kHostBands + 1];
-    for (int b = 0; b <= NB; ++b) band_pix[b] = (long)((long)g->V * b / NB) * g->U;
+    int band_row[kHostBands + 1];
+    for (int b = 0; b <= NB; ++b) {
+        band_row[b] = (int)((long)g->V * b / NB);
+        band_pix[b] = (long)band_row[b] * g->U;
+    }
+    // the last band a chunk needs: its beams reach rows within the profile's
+    // support radius of their elevation (the angle between two directions is
+    // at least their elevation difference; the same rotation and row formula
+    // as the beams' set-up, two rows wider on each side)
+    int chunk_band[kHostChunks];
+    for (int i = 0; i < K; ++i) {
+        double emax = -1e300;
+        for (int b = bounds[i]; b < bounds[i + 1]; ++b) {
+            const float *d = &l->h_dirs[3 * (size_t)b];
+            double a[3];
+            for (int r = 0; r < 3; ++r) a[r] = R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2];
+            const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            emax = std::max(emax, std::asin(std::fmin(1.0, std::fmax(-1.0, a[2] / na))));
+        }
+        double hi = std::ceil((emax + l->support_rad - g->el0) / g->del - 0.5) + 2;
+        if (!(hi < g->V - 1)) hi = g->V - 1;  // also NaN
+        int band = 0;
+        while (band + 1 < NB && band_row[band + 1] <= (int)std::max(0.0, hi)) ++band;
+        chunk_band[i] = band;
+    }
     {
         // the copy stream starts after the caller's earlier work on `stream`
         cudaStream_t us = K > 1 ? l->copy_stream : s;
-        if (K > 1 && ((e = cudaEventRecord(l->setup_ev, s)) != cudaSuccess ||
-                      (e = cudaStreamWaitEvent(us, l->setup_ev, 0)) != cudaSuccess))
+        if (K > 1 && ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess ||
+                      (e = cudaStreamWaitEvent(us, l->start_ev, 0)) != cudaSuccess))
             return cuda_fail(l, e, "G-buffer upload ordering");
         for (int b = 0; b < NB; ++b) {
             const size_t p0 = (size_t)band_pix[b], np = (size_t)(band_pix[b + 1] - band_pix[b]);
@@ -1025,8 +1078,21 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
             if (K > 1 && (e = cudaEventRecord(l->band_ev[b], us)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
         }
     }
-    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K, bounds, l->chunk_ev,
-                      K > 1 ? l->aux_stream : nullptr, K > 1 ? NB : 0, band_pix, l->band_ev)) != LIDAR_OK)
+    ChunkPlan plan;
+    if (K > 1) {
+        plan.n_chunks = K;
+        plan.bounds = bounds;
+        plan.chunk_band = chunk_band;
+        plan.chunk_done = l->chunk_ev;
+        plan.aux[0] = l->aux_stream[0];
+        plan.aux[1] = l->aux_stream[1];
+        plan.join = l->join_ev;
+        plan.n_bands = NB;
+        plan.band_pix = band_pix;
+        plan.band_ready = l->band_ev;
+        plan.setup_done = l->setup_ev;
+    }
+    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K > 1 ? &plan : nullptr)) != LIDAR_OK)
         return st;
     for (int i = 0; i < K; ++i) {
         const size_t b0 = (size_t)bounds[i], nb = (size_t)(bounds[i + 1] - bounds[i]);

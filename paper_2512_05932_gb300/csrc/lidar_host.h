@@ -42,6 +42,7 @@ struct lidar {
     int device = 0;
     // device memory owned by the library
     float *d_dirs = nullptr;
+    std::vector<float> h_dirs;  // host copy of the pattern (row ranges of lidar_simulate_host's beam chunks)
     float4 *d_quads = nullptr;
     float2 *d_pairs = nullptr;  // separable: qw H pairs, then qh V pairs
     float *d_taps = nullptr;
@@ -54,15 +55,18 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
-    // lidar_simulate_host: beam chunks alternate between the caller's stream
-    // and aux_stream (so one chunk's CTAs fill the SMs the previous one is
-    // leaving); the results of finished chunks are copied back on copy_stream
-    // while later chunks run (chunk_ev[i]: chunk i finished; setup_ev: the
-    // per-pixel setup done; join_ev: aux_stream's last chunk done)
-    cudaStream_t copy_stream = nullptr, aux_stream = nullptr;
+    // lidar_simulate_host: the G-buffer goes up in row bands on copy_stream
+    // (band_ev[b]: band b uploaded) and each band is set up on the caller's
+    // stream as it lands (setup_ev[b]: band b set up); beam chunks alternate
+    // between aux_stream[0] and [1] (so one chunk's CTAs fill the SMs the
+    // previous one is leaving), each starting once the bands its beams can
+    // reach are set up; the results of finished chunks are copied back on
+    // copy_stream while later chunks run (chunk_ev[i]: chunk i finished;
+    // start_ev: the caller's earlier work done; join_ev[k]: aux_stream[k] done)
+    cudaStream_t copy_stream = nullptr, aux_stream[2] = {nullptr, nullptr};
     cudaEvent_t chunk_ev[8] = {};
-    cudaEvent_t setup_ev = nullptr, join_ev = nullptr;
-    cudaEvent_t band_ev[4] = {};  // G-buffer band b uploaded (copy_stream)
+    cudaEvent_t band_ev[8] = {}, setup_ev[8] = {};
+    cudaEvent_t start_ev = nullptr, join_ev[2] = {nullptr, nullptr};
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
@@ -103,8 +107,9 @@ constexpr double kDeg = kPi / 180.0;
 constexpr double kMaxSupportDeg = 10.0;
 constexpr int kHostChunks = 8;  // footprint launches per frame of lidar_simulate_host (large frames)
 static_assert(kHostChunks == sizeof(lidar::chunk_ev) / sizeof(cudaEvent_t), "one event per chunk");
-constexpr int kHostBands = 4;  // G-buffer upload bands of lidar_simulate_host (large frames)
-static_assert(kHostBands == sizeof(lidar::band_ev) / sizeof(cudaEvent_t), "one event per band");
+constexpr int kHostBands = 8;  // G-buffer upload bands of lidar_simulate_host (large frames)
+static_assert(kHostBands == sizeof(lidar::band_ev) / sizeof(cudaEvent_t) &&
+                  kHostBands == sizeof(lidar::setup_ev) / sizeof(cudaEvent_t), "one event per band");
 
 lidar_status_t fail(lidar_t *l, lidar_status_t st, const char *fmt, ...);
 lidar_status_t cuda_fail(lidar_t *l, cudaError_t e, const char *what);

@@ -180,6 +180,28 @@ def test_ragged_large_frame_host_entry_point():
         assert (ech_h[k][same] == ech_d[k][same]).mean() >= 0.999, k
 
 
+def test_host_entry_point_right_after_another_frame():
+    """The host path starts each beam chunk once the rows its beams can reach
+    are set up: run right after a different frame (whose per-pixel records
+    are still in the scratch), it gives the device path's results on the same
+    frame, so no chunk reads a row before its set-up."""
+    wa, wb = S.full_frame_boxes(seed=2), S.full_frame_boxes(seed=9)
+    L = lidar.Lidar(wa.profile, wa.dirs, wa.pulse, wa.calib)
+    pa, pb = lidar.gbuffer_to_device(wa.gbuffer), lidar.gbuffer_to_device(wb.gbuffer)
+    wave_d, ech_d, cnt_d = L.simulate(wa.gbuffer, pa, wa.pose)
+    wave_d, ech_d, cnt_d = wave_d.cpu().numpy().astype(np.float64), lidar.echoes_numpy(ech_d), cnt_d.cpu().numpy()
+    hp = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in wa.gbuffer.planes()]
+    for _ in range(2):
+        L.simulate(wb.gbuffer, pb, wb.pose)
+        torch.cuda.synchronize()
+        wave_h, ech_h, cnt_h = L.simulate_host(wa.gbuffer, hp, wa.pose)
+        wave_h, ech_h, cnt_h = wave_h.numpy().astype(np.float64), lidar.echoes_numpy(ech_h), cnt_h.numpy()
+        rel = np.linalg.norm(wave_h - wave_d, axis=1) / np.maximum(np.linalg.norm(wave_d, axis=1), 1e-30)
+        assert rel.max() <= 1e-5, rel.max()
+        assert (cnt_h == cnt_d).mean() >= 0.999
+    L.close()
+
+
 def test_table_profile_anisotropic_with_roll():
     w = S.small_plane_retro()
     w.profile = S.table_profile(S.elliptic_gauss_table(41, 81, 0.01, 0.05, 0.1), 0.01)
