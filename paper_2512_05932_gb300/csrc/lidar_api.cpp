@@ -351,6 +351,7 @@ void free_all(lidar_t *l)
     if (l->copy_stream) cudaStreamDestroy(l->copy_stream);
     for (cudaStream_t &st : l->aux_stream)
         if (st) cudaStreamDestroy(st);
+    if (l->setup_stream) cudaStreamDestroy(l->setup_stream);
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t &ev : l->setup_ev)
@@ -476,6 +477,8 @@ struct ChunkPlan {
     int n_bands = 0;
     const long *band_pix = nullptr;
     cudaEvent_t *band_ready = nullptr, *setup_done = nullptr;
+    cudaStream_t setup_stream = nullptr;  // runs the set-up after `start` (recorded on s)
+    cudaEvent_t start = nullptr;
 };
 
 // Enqueues the setup and footprint kernels of one frame on `s` (or as
@@ -506,22 +509,25 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
     } else {
         // the beams' set-up first (it reads no plane), then each band's pixels
+        cudaStream_t ss = plan->setup_stream;
         gbl::SetupArgs sb = sa;
         sb.pix_blocks = 0;
-        if ((e = gbl::launch_setup(sb, s)) != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+        if ((e = cudaStreamWaitEvent(ss, plan->start, 0)) != cudaSuccess ||
+            (e = gbl::launch_setup(sb, ss)) != cudaSuccess)
+            return cuda_fail(l, e, "setup kernel launch");
         for (int b = 0; b < plan->n_bands; ++b) {
             gbl::SetupArgs sp = sa;
             sp.n_beams = 0;
             sp.pix_begin = plan->band_pix[b];
             sp.pix_end = plan->band_pix[b + 1];
             sp.pix_blocks = (int)std::max<long>(1, std::min<long>(sa.pix_blocks, (sp.pix_end - sp.pix_begin + 255) / 256));
-            if ((e = cudaStreamWaitEvent(s, plan->band_ready[b], 0)) != cudaSuccess ||
-                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, s)) != cudaSuccess) ||
-                (e = cudaEventRecord(plan->setup_done[b], s)) != cudaSuccess)
+            if ((e = cudaStreamWaitEvent(ss, plan->band_ready[b], 0)) != cudaSuccess ||
+                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, ss)) != cudaSuccess) ||
+                (e = cudaEventRecord(plan->setup_done[b], ss)) != cudaSuccess)
                 return cuda_fail(l, e, "setup kernel launch");
         }
     }
-    if (ev1) cudaEventRecord(ev1, s);
+    if (ev1) cudaEventRecord(ev1, plan && plan->n_bands > 0 ? plan->setup_stream : s);
 
     gbl::FootprintArgs fa = model_args(l);
     fa.U = g->U; fa.V = g->V; fa.panorama = sa.panorama;
@@ -1024,6 +1030,12 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
         for (cudaStream_t &st2 : l->aux_stream)
             if (!st2 && (e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
+        if (!l->setup_stream) {
+            int least = 0, greatest = 0;
+            if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
+                (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
+        }
         cudaEvent_t *evs[] = {&l->start_ev, &l->join_ev[0], &l->join_ev[1]};
         for (cudaEvent_t *ev : evs)
             if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -1091,6 +1103,8 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
         plan.band_pix = band_pix;
         plan.band_ready = l->band_ev;
         plan.setup_done = l->setup_ev;
+        plan.setup_stream = l->setup_stream;
+        plan.start = l->start_ev;
     }
     if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K > 1 ? &plan : nullptr)) != LIDAR_OK)
         return st;

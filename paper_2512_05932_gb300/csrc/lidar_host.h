@@ -62,8 +62,11 @@ struct lidar {
     // previous one is leaving), each starting once the bands its beams can
     // reach are set up; the results of finished chunks are copied back on
     // copy_stream while later chunks run (chunk_ev[i]: chunk i finished;
-    // start_ev: the caller's earlier work done; join_ev[k]: aux_stream[k] done)
+    // start_ev: the caller's earlier work done; join_ev[k]: aux_stream[k] done).
+    // The set-up runs on setup_stream, whose CTAs the SMs take before pending
+    // footprint CTAs.
     cudaStream_t copy_stream = nullptr, aux_stream[2] = {nullptr, nullptr};
+    cudaStream_t setup_stream = nullptr;  // the bands' set-up, at the highest stream priority
     cudaEvent_t chunk_ev[8] = {};
     cudaEvent_t band_ev[8] = {}, setup_ev[8] = {};
     cudaEvent_t start_ev = nullptr, join_ev[2] = {nullptr, nullptr};
