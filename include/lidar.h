@@ -274,10 +274,14 @@ lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuf
  * [n_beams][n_bins], echoes [n_beams][max_echoes], counts [n_beams]). The
  * library copies the inputs to device buffers it owns, simulates, copies the
  * results back and synchronises `stream` before returning. A frame of at
- * least 1216 beam groups is simulated in 8 launches that alternate between
- * `stream` and a library-owned stream (so that one launch's CTAs fill the SMs
- * the previous one is leaving), and the results of each are copied back on a
- * third, library-owned stream while later ones run. Page-locked host memory
+ * least 1216 beam groups is pipelined on library-owned streams that start
+ * after the work already queued on `stream`: the G-buffer goes up in 8 bands
+ * of rows, each set up as it lands; the beams run as 8 launches alternating
+ * between two streams (one launch's CTAs fill the SMs the previous one is
+ * leaving), each started once the rows its beams can reach (the profile's
+ * support radius around their elevation) are set up, so that with beams
+ * ordered by elevation the first launches overlap the upload; the results of
+ * each launch are copied back while later ones run. Page-locked host memory
  * gives asynchronous, full-bandwidth copies. */
 lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,

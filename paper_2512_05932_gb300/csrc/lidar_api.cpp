@@ -352,6 +352,7 @@ void free_all(lidar_t *l)
     for (cudaStream_t &st : l->aux_stream)
         if (st) cudaStreamDestroy(st);
     if (l->setup_stream) cudaStreamDestroy(l->setup_stream);
+    if (l->d2h_stream) cudaStreamDestroy(l->d2h_stream);
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t &ev : l->setup_ev)
@@ -460,32 +461,22 @@ lidar_status_t ensure_slots(lidar_t *l, int G, bool tc)
     return LIDAR_OK;
 }
 
-// How lidar_simulate_host splits a frame: the G-buffer arrives in n_bands
-// bands of pixels [band_pix[b], band_pix[b + 1]) (band b uploaded at
-// band_ready[b]; set up on `s` as it lands, setup_done[b] recorded after it),
-// and the footprint kernel runs once per range of whole beam groups, chunk i
-// covering beams [bounds[i], bounds[i + 1]) on aux[i % 2] once the bands up
-// to chunk_band[i] are set up (chunk_done[i] recorded after it); `s` joins
-// both aux streams at the end (join[k]).
-struct ChunkPlan {
-    int n_chunks = 1;
-    const int *bounds = nullptr;
-    const int *chunk_band = nullptr;
-    cudaEvent_t *chunk_done = nullptr;
-    cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t *join = nullptr;
-    int n_bands = 0;
-    const long *band_pix = nullptr;
-    cudaEvent_t *band_ready = nullptr, *setup_done = nullptr;
-    cudaStream_t setup_stream = nullptr;  // runs the set-up after `start` (recorded on s)
-    cudaEvent_t start = nullptr;
-};
+// Footprint-kernel arguments of one frame (outputs not set).
+gbl::FootprintArgs frame_args(const lidar_t *l, const lidar_gbuffer_t *g, const gbl::SetupArgs &sa)
+{
+    gbl::FootprintArgs fa = model_args(l);
+    fa.U = g->U; fa.V = g->V; fa.panorama = sa.panorama;
+    fa.az0 = sa.az0; fa.el0 = sa.el0; fa.daz = sa.daz; fa.del = sa.del;
+    fa.rec = l->d_rec;
+    fa.beams = l->d_beams;
+    fa.n_beams = l->n_beams;
+    return fa;
+}
 
-// Enqueues the setup and footprint kernels of one frame on `s` (or as
-// `plan` says); wave == NULL selects the echo-only form (waveforms in the
-// pooled slots).
+// Enqueues the setup and footprint kernels of one frame on `s`; wave == NULL
+// selects the echo-only form (waveforms in the pooled slots).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
-                       int32_t *counts, cudaStream_t s, const ChunkPlan *plan = nullptr)
+                       int32_t *counts, cudaStream_t s)
 {
     const bool tc = l->deposit != 0;
     if (!wave) {
@@ -504,37 +495,11 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
     }
     if (ev0) cudaEventRecord(ev0, s);
     cudaError_t e = cudaSuccess;
-    if (!plan || plan->n_bands <= 0) {
-        e = gbl::launch_setup(sa, s);
-        if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
-    } else {
-        // the beams' set-up first (it reads no plane), then each band's pixels
-        cudaStream_t ss = plan->setup_stream;
-        gbl::SetupArgs sb = sa;
-        sb.pix_blocks = 0;
-        if ((e = cudaStreamWaitEvent(ss, plan->start, 0)) != cudaSuccess ||
-            (e = gbl::launch_setup(sb, ss)) != cudaSuccess)
-            return cuda_fail(l, e, "setup kernel launch");
-        for (int b = 0; b < plan->n_bands; ++b) {
-            gbl::SetupArgs sp = sa;
-            sp.n_beams = 0;
-            sp.pix_begin = plan->band_pix[b];
-            sp.pix_end = plan->band_pix[b + 1];
-            sp.pix_blocks = (int)std::max<long>(1, std::min<long>(sa.pix_blocks, (sp.pix_end - sp.pix_begin + 255) / 256));
-            if ((e = cudaStreamWaitEvent(ss, plan->band_ready[b], 0)) != cudaSuccess ||
-                (sp.pix_end > sp.pix_begin && (e = gbl::launch_setup(sp, ss)) != cudaSuccess) ||
-                (e = cudaEventRecord(plan->setup_done[b], ss)) != cudaSuccess)
-                return cuda_fail(l, e, "setup kernel launch");
-        }
-    }
-    if (ev1) cudaEventRecord(ev1, plan && plan->n_bands > 0 ? plan->setup_stream : s);
+    e = gbl::launch_setup(sa, s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    if (ev1) cudaEventRecord(ev1, s);
 
-    gbl::FootprintArgs fa = model_args(l);
-    fa.U = g->U; fa.V = g->V; fa.panorama = sa.panorama;
-    fa.az0 = sa.az0; fa.el0 = sa.el0; fa.daz = sa.daz; fa.del = sa.del;
-    fa.rec = l->d_rec;
-    fa.beams = l->d_beams;
-    fa.n_beams = l->n_beams;
+    gbl::FootprintArgs fa = frame_args(l, g, sa);
     fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
     if (!wave) {
         fa.slot_pool = l->d_slot_pool;
@@ -545,32 +510,8 @@ lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], 
         fa.err = l->d_err;
     }
     const int G = tc ? l->G_tc : l->G;
-    if (!plan || plan->n_chunks <= 1) {
-        e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
-        if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
-    } else {
-        for (int i = 0; i < plan->n_chunks; ++i) {
-            const int b0 = plan->bounds[i], nb = plan->bounds[i + 1] - plan->bounds[i];
-            cudaStream_t cs = plan->aux[i & 1];
-            gbl::FootprintArgs fc = fa;
-            fc.beams = l->d_beams + b0;
-            fc.n_beams = nb;
-            fc.wave = wave + (size_t)b0 * l->n_bins;
-            fc.echoes = echoes + (size_t)b0 * l->max_echoes;
-            fc.counts = counts + b0;
-            if ((e = cudaStreamWaitEvent(cs, plan->setup_done[plan->chunk_band[i]], 0)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaStreamWaitEvent");
-            if (nb > 0) {
-                e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs);
-                if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
-            }
-            if ((e = cudaEventRecord(plan->chunk_done[i], cs)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
-        }
-        for (int k = 0; k < 2; ++k)
-            if ((e = cudaEventRecord(plan->join[k], plan->aux[k])) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(s, plan->join[k], 0)) != cudaSuccess)
-                return cuda_fail(l, e, "chunk stream join");
-    }
+    e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fa, s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "footprint kernel launch");
     if (ev2) cudaEventRecord(ev2, s);
     return LIDAR_OK;
 }
@@ -977,6 +918,146 @@ lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const
     return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
+// lidar_simulate_host for large frames. The G-buffer goes up in kHostBands
+// bands of rows on copy_stream; each band is set up on setup_stream (highest
+// priority, so its CTAs are scheduled ahead of pending footprint CTAs) as soon
+// as it lands; the beams run as kHostChunks footprint launches alternating
+// between aux_stream[0] and [1] (one launch's CTAs fill the SMs the previous
+// one is leaving), each launched once the rows its beams can reach are set up;
+// each launch's results go down on d2h_stream while later ones run, and the
+// last launch holds 5 % of the beams so that little copying is left at the
+// end. The host enqueues in that order (band, its set-up, the launches it
+// completes), so the first launches are queued before the last bands' copies.
+static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t *dg, const double R[9],
+                                              const float *const src[7], float *const dst[7], float *wave,
+                                              lidar_echo_t *echoes, int32_t *counts, cudaStream_t s)
+{
+    cudaError_t e;
+    const bool tc = l->deposit != 0;
+    const int G = tc ? l->G_tc : l->G;
+    const int ng = (l->n_beams + G - 1) / G;
+    const int K = kHostChunks, NB = kHostBands;
+    const size_t pixels = (size_t)dg->U * dg->V;
+    lidar_status_t st = ensure_scratch(l, pixels);
+    if (st != LIDAR_OK) return st;
+    cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream, &l->aux_stream[0], &l->aux_stream[1]};
+    for (cudaStream_t *p : streams)
+        if (!*p && (e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamCreate(host pipeline)");
+    if (!l->setup_stream) {
+        int least = 0, greatest = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
+    }
+    std::vector<cudaEvent_t *> evs = {&l->start_ev, &l->join_ev[0], &l->join_ev[1], &l->join_ev[2]};
+    for (int i = 0; i < K; ++i) evs.push_back(&l->chunk_ev[i]);
+    for (int i = 0; i < NB; ++i) { evs.push_back(&l->band_ev[i]); evs.push_back(&l->setup_ev[i]); }
+    for (cudaEvent_t *ev : evs)
+        if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaEventCreate(host pipeline)");
+
+    int bounds[kHostChunks + 1];
+    bounds[0] = 0;
+    for (int i = 1; i < K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 19 * i / (20 * (K - 1))) * G);
+    bounds[K] = l->n_beams;
+    int band_row[kHostBands + 1];
+    for (int b = 0; b <= NB; ++b) band_row[b] = (int)((long)dg->V * b / NB);
+    // the last band a chunk needs: its beams reach rows within the profile's
+    // support radius of their elevation (the angle between two directions is
+    // at least their elevation difference; the same rotation and row formula
+    // as the beams' set-up, two rows wider on each side)
+    int chunk_band[kHostChunks];
+    for (int i = 0; i < K; ++i) {
+        double emax = -1e300;
+        for (int b = bounds[i]; b < bounds[i + 1]; ++b) {
+            const float *d = &l->h_dirs[3 * (size_t)b];
+            double a[3];
+            for (int r = 0; r < 3; ++r) a[r] = R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2];
+            const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            emax = std::max(emax, std::asin(std::fmin(1.0, std::fmax(-1.0, a[2] / na))));
+        }
+        double hi = std::ceil((emax + l->support_rad - dg->el0) / dg->del - 0.5) + 2;
+        if (!(hi < dg->V - 1)) hi = dg->V - 1;  // also NaN
+        int band = 0;
+        while (band + 1 < NB && band_row[band + 1] <= (int)std::max(0.0, hi)) ++band;
+        chunk_band[i] = band;
+    }
+
+    gbl::SetupArgs sa = setup_args(l, l, dg, R, l->d_rec, l->d_beams);
+    gbl::FootprintArgs fa = frame_args(l, dg, sa);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    if (l->prof) {
+        size_t mark = l->ev_used;
+        ev0 = next_event(l); ev1 = next_event(l); ev2 = next_event(l);
+        if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
+    }
+    cudaStream_t ss = l->setup_stream, us = l->copy_stream, ds = l->d2h_stream;
+    // every stream of the pipeline starts after the caller's earlier work on `s`
+    if ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+    for (cudaStream_t x : {ss, us, ds, l->aux_stream[0], l->aux_stream[1]})
+        if ((e = cudaStreamWaitEvent(x, l->start_ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
+    if (ev0) cudaEventRecord(ev0, ss);
+    gbl::SetupArgs sb = sa;
+    sb.pix_blocks = 0;  // the beams' set-up (reads no plane)
+    if ((e = gbl::launch_setup(sb, ss)) != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    int next = 0;
+    for (int b = 0; b < NB; ++b) {
+        const long p0 = (long)band_row[b] * dg->U, p1 = (long)band_row[b + 1] * dg->U;
+        for (int i = 0; i < 7 && p1 > p0; ++i)
+            if ((e = cudaMemcpyAsync(dst[i] + p0, src[i] + p0, (size_t)(p1 - p0) * sizeof(float), cudaMemcpyHostToDevice,
+                                     us)) != cudaSuccess)
+                return cuda_fail(l, e, "G-buffer upload");
+        gbl::SetupArgs sp = sa;
+        sp.n_beams = 0;
+        sp.pix_begin = p0;
+        sp.pix_end = p1;
+        sp.pix_blocks = (int)std::max<long>(1, std::min<long>(sa.pix_blocks, (p1 - p0 + 255) / 256));
+        if ((e = cudaEventRecord(l->band_ev[b], us)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ss, l->band_ev[b], 0)) != cudaSuccess ||
+            (p1 > p0 && (e = gbl::launch_setup(sp, ss)) != cudaSuccess) ||
+            (e = cudaEventRecord(l->setup_ev[b], ss)) != cudaSuccess)
+            return cuda_fail(l, e, "setup kernel launch");
+        if (b == NB - 1 && ev1) cudaEventRecord(ev1, ss);
+        for (; next < K && chunk_band[next] <= b; ++next) {
+            const int i = next, b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
+            cudaStream_t cs = l->aux_stream[i & 1];
+            gbl::FootprintArgs fc = fa;
+            fc.beams = l->d_beams + b0;
+            fc.n_beams = nb;
+            fc.wave = l->d_wave + (size_t)b0 * l->n_bins;
+            fc.echoes = l->d_echo + (size_t)b0 * l->max_echoes;
+            fc.counts = l->d_counts + b0;
+            if ((e = cudaStreamWaitEvent(cs, l->setup_ev[b], 0)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaStreamWaitEvent");
+            if (nb > 0 && (e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs)) !=
+                              cudaSuccess)
+                return cuda_fail(l, e, "footprint kernel launch");
+            if ((e = cudaEventRecord(l->chunk_ev[i], cs)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess)
+                return cuda_fail(l, e, "cudaEventRecord");
+            if (nb > 0 &&
+                ((e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
+                                      (size_t)nb * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost, ds)) != cudaSuccess ||
+                 (e = cudaMemcpyAsync(echoes + (size_t)b0 * l->max_echoes, l->d_echo + (size_t)b0 * l->max_echoes,
+                                      (size_t)nb * l->max_echoes * sizeof(lidar_echo_t), cudaMemcpyDeviceToHost, ds)) !=
+                     cudaSuccess ||
+                 (e = cudaMemcpyAsync(counts + b0, l->d_counts + b0, (size_t)nb * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                      ds)) != cudaSuccess))
+                return cuda_fail(l, e, "result download");
+        }
+    }
+    // `s` joins the pipeline
+    cudaStream_t tails[3] = {l->aux_stream[0], l->aux_stream[1], ds};
+    for (int k = 0; k < 3; ++k)
+        if ((e = cudaEventRecord(l->join_ev[k], tails[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, l->join_ev[k], 0)) != cudaSuccess)
+            return cuda_fail(l, e, "pipeline join");
+    if (ev2) cudaEventRecord(ev2, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+    return LIDAR_OK;
+}
+
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
                                    lidar_echo_t *echoes, int32_t *counts, void *stream)
 {
@@ -1009,122 +1090,25 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     for (int i = 0; i < 7; ++i) dst[i] = l->d_planes + (size_t)i * pixels;
     dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
     dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
-    // A frame with many beam groups is simulated in kHostChunks launches,
-    // alternating between two streams, whose results are copied back on a
-    // third stream while later ones run; the last chunk is small, so that
-    // little copying is left when the kernels end. The G-buffer goes up on
-    // the copy stream in kHostBands bands of rows, each set up as it lands,
-    // and a chunk starts once the rows its beams can reach are set up: with
-    // beams ordered by elevation (a line scan) the first chunks overlap the
-    // rest of the upload.
     const int G = l->deposit != 0 ? l->G_tc : l->G;
     const int ng = (l->n_beams + G - 1) / G;
-    const int K = ng >= 8 * 152 ? kHostChunks : 1;
-    int bounds[kHostChunks + 1];
-    bounds[0] = 0;
-    for (int i = 1; i < K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 19 * i / (20 * (K - 1))) * G);
-    bounds[K] = l->n_beams;
-    if (K > 1) {
-        if (!l->copy_stream && (e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
-        for (cudaStream_t &st2 : l->aux_stream)
-            if (!st2 && (e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaStreamCreate(chunk streams)");
-        if (!l->setup_stream) {
-            int least = 0, greatest = 0;
-            if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
-                (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
-        }
-        cudaEvent_t *evs[] = {&l->start_ev, &l->join_ev[0], &l->join_ev[1]};
-        for (cudaEvent_t *ev : evs)
-            if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaEventCreate(chunk streams)");
-        for (int i = 0; i < kHostChunks; ++i)
-            if (!l->chunk_ev[i] && (e = cudaEventCreateWithFlags(&l->chunk_ev[i], cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaEventCreate(result copies)");
-        for (int i = 0; i < kHostBands; ++i)
-            if ((!l->band_ev[i] && (e = cudaEventCreateWithFlags(&l->band_ev[i], cudaEventDisableTiming)) != cudaSuccess) ||
-                (!l->setup_ev[i] && (e = cudaEventCreateWithFlags(&l->setup_ev[i], cudaEventDisableTiming)) != cudaSuccess))
-                return cuda_fail(l, e, "cudaEventCreate(G-buffer bands)");
-    }
-    const int NB = K > 1 ? kHostBands : 1;
-    long band_pix[kHostBands + 1];
-    int band_row[kHostBands + 1];
-    for (int b = 0; b <= NB; ++b) {
-        band_row[b] = (int)((long)g->V * b / NB);
-        band_pix[b] = (long)band_row[b] * g->U;
-    }
-    // the last band a chunk needs: its beams reach rows within the profile's
-    // support radius of their elevation (the angle between two directions is
-    // at least their elevation difference; the same rotation and row formula
-    // as the beams' set-up, two rows wider on each side)
-    int chunk_band[kHostChunks];
-    for (int i = 0; i < K; ++i) {
-        double emax = -1e300;
-        for (int b = bounds[i]; b < bounds[i + 1]; ++b) {
-            const float *d = &l->h_dirs[3 * (size_t)b];
-            double a[3];
-            for (int r = 0; r < 3; ++r) a[r] = R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2];
-            const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-            emax = std::max(emax, std::asin(std::fmin(1.0, std::fmax(-1.0, a[2] / na))));
-        }
-        double hi = std::ceil((emax + l->support_rad - g->el0) / g->del - 0.5) + 2;
-        if (!(hi < g->V - 1)) hi = g->V - 1;  // also NaN
-        int band = 0;
-        while (band + 1 < NB && band_row[band + 1] <= (int)std::max(0.0, hi)) ++band;
-        chunk_band[i] = band;
-    }
-    {
-        // the copy stream starts after the caller's earlier work on `stream`
-        cudaStream_t us = K > 1 ? l->copy_stream : s;
-        if (K > 1 && ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess ||
-                      (e = cudaStreamWaitEvent(us, l->start_ev, 0)) != cudaSuccess))
-            return cuda_fail(l, e, "G-buffer upload ordering");
-        for (int b = 0; b < NB; ++b) {
-            const size_t p0 = (size_t)band_pix[b], np = (size_t)(band_pix[b + 1] - band_pix[b]);
-            for (int i = 0; i < 7; ++i)
-                if (np && (e = cudaMemcpyAsync(dst[i] + p0, src[i] + p0, np * sizeof(float), cudaMemcpyHostToDevice,
-                                               us)) != cudaSuccess)
-                    return cuda_fail(l, e, "G-buffer upload");
-            if (K > 1 && (e = cudaEventRecord(l->band_ev[b], us)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
-        }
-    }
-    ChunkPlan plan;
-    if (K > 1) {
-        plan.n_chunks = K;
-        plan.bounds = bounds;
-        plan.chunk_band = chunk_band;
-        plan.chunk_done = l->chunk_ev;
-        plan.aux[0] = l->aux_stream[0];
-        plan.aux[1] = l->aux_stream[1];
-        plan.join = l->join_ev;
-        plan.n_bands = NB;
-        plan.band_pix = band_pix;
-        plan.band_ready = l->band_ev;
-        plan.setup_done = l->setup_ev;
-        plan.setup_stream = l->setup_stream;
-        plan.start = l->start_ev;
-    }
-    if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s, K > 1 ? &plan : nullptr)) != LIDAR_OK)
-        return st;
-    for (int i = 0; i < K; ++i) {
-        const size_t b0 = (size_t)bounds[i], nb = (size_t)(bounds[i + 1] - bounds[i]);
-        cudaStream_t cs = K > 1 ? l->copy_stream : s;
-        if (K > 1 && (e = cudaStreamWaitEvent(cs, l->chunk_ev[i], 0)) != cudaSuccess)
-            return cuda_fail(l, e, "cudaStreamWaitEvent");
-        if ((e = cudaMemcpyAsync(wave + b0 * l->n_bins, l->d_wave + b0 * l->n_bins, nb * l->n_bins * sizeof(float),
-                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(echoes + b0 * l->max_echoes, l->d_echo + b0 * l->max_echoes,
-                                 nb * l->max_echoes * sizeof(lidar_echo_t), cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(counts + b0, l->d_counts + b0, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, cs)) !=
+    if (ng < 8 * 152) {
+        // small frame: one pass on `stream`
+        for (int i = 0; i < 7; ++i)
+            if ((e = cudaMemcpyAsync(dst[i], src[i], pixels * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                return cuda_fail(l, e, "G-buffer upload");
+        if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s)) != LIDAR_OK) return st;
+        if ((e = cudaMemcpyAsync(wave, l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost,
+                                 s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
+                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess)
             return cuda_fail(l, e, "result download");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
+        return LIDAR_OK;
     }
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
-    if (K > 1 && (e = cudaStreamSynchronize(l->copy_stream)) != cudaSuccess)
-        return cuda_fail(l, e, "cudaStreamSynchronize(result copies)");
-    return LIDAR_OK;
+    return simulate_host_pipelined(l, &dg, R, src, dst, wave, echoes, counts, s);
 }
 
 lidar_status_t lidar_simulate_noalloc(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,

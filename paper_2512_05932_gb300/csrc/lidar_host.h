@@ -55,21 +55,17 @@ struct lidar {
     float *d_wave = nullptr;
     lidar_echo_t *d_echo = nullptr;
     int32_t *d_counts = nullptr;
-    // lidar_simulate_host: the G-buffer goes up in row bands on copy_stream
-    // (band_ev[b]: band b uploaded) and each band is set up on the caller's
-    // stream as it lands (setup_ev[b]: band b set up); beam chunks alternate
-    // between aux_stream[0] and [1] (so one chunk's CTAs fill the SMs the
-    // previous one is leaving), each starting once the bands its beams can
-    // reach are set up; the results of finished chunks are copied back on
-    // copy_stream while later chunks run (chunk_ev[i]: chunk i finished;
-    // start_ev: the caller's earlier work done; join_ev[k]: aux_stream[k] done).
-    // The set-up runs on setup_stream, whose CTAs the SMs take before pending
-    // footprint CTAs.
-    cudaStream_t copy_stream = nullptr, aux_stream[2] = {nullptr, nullptr};
-    cudaStream_t setup_stream = nullptr;  // the bands' set-up, at the highest stream priority
+    // lidar_simulate_host on large frames (simulate_host_pipelined): uploads on
+    // copy_stream (band_ev[b]: band b uploaded), set-up on setup_stream at the
+    // highest priority (setup_ev[b]: band b set up), footprint launches on
+    // aux_stream[0] and [1] (chunk_ev[i]: launch i finished), result copies on
+    // d2h_stream; start_ev: the caller's earlier work done; join_ev: the
+    // streams the caller's stream joins at the end.
+    cudaStream_t copy_stream = nullptr, d2h_stream = nullptr, setup_stream = nullptr;
+    cudaStream_t aux_stream[2] = {nullptr, nullptr};
     cudaEvent_t chunk_ev[8] = {};
     cudaEvent_t band_ev[8] = {}, setup_ev[8] = {};
-    cudaEvent_t start_ev = nullptr, join_ev[2] = {nullptr, nullptr};
+    cudaEvent_t start_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
