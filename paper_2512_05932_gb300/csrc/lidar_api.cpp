@@ -918,16 +918,33 @@ lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const
     return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
+// Device address of page-locked host memory mapped into the device's address
+// space (cudaHostAlloc, cudaHostRegister with mapping), or null for anything
+// else (pageable or device memory).
+static const float *mapped_host(const float *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not known to CUDA: pageable memory
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<const float *>(a.devicePointer);
+}
+
 // lidar_simulate_host for large frames. The G-buffer goes up in kHostBands
 // bands of rows on copy_stream; each band is set up on setup_stream (highest
 // priority, so its CTAs are scheduled ahead of pending footprint CTAs) as soon
 // as it lands; the beams run as kHostChunks footprint launches alternating
 // between aux_stream[0] and [1] (one launch's CTAs fill the SMs the previous
 // one is leaving), each launched once the rows its beams can reach are set up;
-// each launch's results go down on d2h_stream while later ones run, and the
-// last launch holds 5 % of the beams so that little copying is left at the
-// end. The host enqueues in that order (band, its set-up, the launches it
-// completes), so the first launches are queued before the last bands' copies.
+// each launch's waveforms go down on d2h_stream while later ones run (echoes
+// and counts at the end), and the last launch holds 5 % of the beams so that
+// little copying is left at the end. The host enqueues in that order (band,
+// its set-up, the launches it completes), so the first launches are queued
+// before the last bands' copies. Planes in page-locked, device-mapped host
+// memory are not copied at all: the set-up kernel reads each band over the
+// host link where it lies.
 static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t *dg, const double R[9],
                                               const float *const src[7], float *const dst[7], float *wave,
                                               lidar_echo_t *echoes, int32_t *counts, cudaStream_t s)
@@ -986,6 +1003,13 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
 
     gbl::SetupArgs sa = setup_args(l, l, dg, R, l->d_rec, l->d_beams);
     gbl::FootprintArgs fa = frame_args(l, dg, sa);
+    const float *mp[7];
+    bool mapped = true;
+    for (int i = 0; i < 7 && mapped; ++i) mapped = (mp[i] = mapped_host(src[i])) != nullptr;
+    if (mapped) {
+        sa.range = mp[0]; sa.nx = mp[1]; sa.ny = mp[2]; sa.nz = mp[3];
+        sa.rho = mp[4]; sa.retro = mp[5]; sa.amb = mp[6];
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     if (l->prof) {
         size_t mark = l->ev_used;
@@ -1004,7 +1028,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     int next = 0;
     for (int b = 0; b < NB; ++b) {
         const long p0 = (long)band_row[b] * dg->U, p1 = (long)band_row[b + 1] * dg->U;
-        for (int i = 0; i < 7 && p1 > p0; ++i)
+        for (int i = 0; i < 7 && p1 > p0 && !mapped; ++i)
             if ((e = cudaMemcpyAsync(dst[i] + p0, src[i] + p0, (size_t)(p1 - p0) * sizeof(float), cudaMemcpyHostToDevice,
                                      us)) != cudaSuccess)
                 return cuda_fail(l, e, "G-buffer upload");
@@ -1036,17 +1060,18 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             if ((e = cudaEventRecord(l->chunk_ev[i], cs)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventRecord");
-            if (nb > 0 &&
-                ((e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
-                                      (size_t)nb * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost, ds)) != cudaSuccess ||
-                 (e = cudaMemcpyAsync(echoes + (size_t)b0 * l->max_echoes, l->d_echo + (size_t)b0 * l->max_echoes,
-                                      (size_t)nb * l->max_echoes * sizeof(lidar_echo_t), cudaMemcpyDeviceToHost, ds)) !=
-                     cudaSuccess ||
-                 (e = cudaMemcpyAsync(counts + b0, l->d_counts + b0, (size_t)nb * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                      ds)) != cudaSuccess))
+            if (nb > 0 && (e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
+                                               (size_t)nb * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost, ds)) !=
+                              cudaSuccess)
                 return cuda_fail(l, e, "result download");
         }
     }
+    // echoes and counts (small) once every launch is done
+    if ((e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
+                             cudaMemcpyDeviceToHost, ds)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, ds)) !=
+            cudaSuccess)
+        return cuda_fail(l, e, "result download");
     // `s` joins the pipeline
     cudaStream_t tails[3] = {l->aux_stream[0], l->aux_stream[1], ds};
     for (int k = 0; k < 3; ++k)

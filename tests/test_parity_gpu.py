@@ -38,9 +38,12 @@ def run_gpu(w, host=False, deposit=0):
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
     lidar.lidar_set_deposit(L.handle, deposit)
     if host:
-        # pinned outputs (asynchronous copies) or pageable ones (staged by the
-        # driver)
-        planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
+        # pinned planes (read by the set-up kernel where they lie) or pageable
+        # ones (copied up); pinned outputs (asynchronous copies) or pageable
+        # ones (staged by the driver)
+        planes = [torch.from_numpy(np.ascontiguousarray(p)) for p in w.gbuffer.planes()]
+        if host != "pageable_planes":
+            planes = [p.pin_memory() for p in planes]
         outs = None
         if host == "pageable":
             outs = (torch.empty((L.n_beams, L.n_bins), dtype=torch.float32),
@@ -145,12 +148,14 @@ def test_full_frame_sampled_beams():
     assert st["echoes"] > 0
 
 
-@pytest.mark.parametrize("host", ["pinned", "pageable"])
+@pytest.mark.parametrize("host", ["pinned", "pageable", "pageable_planes"])
 def test_full_frame_host_entry_point_matches_device_entry_point(host):
-    """The host-memory entry point splits a large frame into several launches
-    on two streams whose results are copied back while later ones run, into
-    pinned or pageable outputs: same waveforms (up to the FP32 order of the
-    deposits), echoes and counts as the device entry point on the same frame."""
+    """The host-memory entry point pipelines a large frame (bands of rows set
+    up as they arrive, launches on two streams whose results are copied back
+    while later ones run), with pinned planes read in place or pageable ones
+    copied up, into pinned or pageable outputs: same waveforms (up to the FP32
+    order of the deposits), echoes and counts as the device entry point on the
+    same frame."""
     w = S.full_frame_boxes()
     _, wave_d, ech_d, cnt_d = run_gpu(w)
     _, wave_h, ech_h, cnt_h = run_gpu(w, host=host)
