@@ -856,7 +856,13 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     // device copies (and the host copy of the pattern)
     size_t nd = (size_t)pat->n_beams * 3 * sizeof(float);
     try {
-        l->h_dirs.assign(pat->dirs, pat->dirs + (size_t)pat->n_beams * 3);
+        // unit vectors (the beams' set-up normalises them the same way)
+        l->h_dirs.resize((size_t)pat->n_beams * 3);
+        for (int b = 0; b < pat->n_beams; ++b) {
+            const double x = pat->dirs[3 * b], y = pat->dirs[3 * b + 1], z = pat->dirs[3 * b + 2];
+            const double n = std::sqrt(x * x + y * y + z * z);
+            l->h_dirs[3 * b] = (float)(x / n); l->h_dirs[3 * b + 1] = (float)(y / n); l->h_dirs[3 * b + 2] = (float)(z / n);
+        }
     } catch (...) {
         free_all(l);
         delete l;
@@ -974,9 +980,12 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(l, e, "cudaEventCreate(host pipeline)");
 
+    // launch sizes: 91 % of the groups in K - 2 equal launches, then 6 % and
+    // 3 %, so that little copying is left when the last launches end
     int bounds[kHostChunks + 1];
     bounds[0] = 0;
-    for (int i = 1; i < K; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 19 * i / (20 * (K - 1))) * G);
+    for (int i = 1; i < K - 1; ++i) bounds[i] = std::min(l->n_beams, (int)((long)ng * 91 * i / (100 * (K - 2))) * G);
+    bounds[K - 1] = std::min(l->n_beams, (int)((long)ng * 97 / 100) * G);
     bounds[K] = l->n_beams;
     int band_row[kHostBands + 1];
     for (int b = 0; b <= NB; ++b) band_row[b] = (int)((long)dg->V * b / NB);
@@ -985,15 +994,14 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     // at least their elevation difference; the same rotation and row formula
     // as the beams' set-up, two rows wider on each side)
     int chunk_band[kHostChunks];
+    const float r6 = (float)R[6], r7 = (float)R[7], r8 = (float)R[8];
     for (int i = 0; i < K; ++i) {
-        double emax = -1e300;
-        for (int b = bounds[i]; b < bounds[i + 1]; ++b) {
-            const float *d = &l->h_dirs[3 * (size_t)b];
-            double a[3];
-            for (int r = 0; r < 3; ++r) a[r] = R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2];
-            const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-            emax = std::max(emax, std::asin(std::fmin(1.0, std::fmax(-1.0, a[2] / na))));
-        }
+        // the largest height of a rotated unit direction (FP32; its error, ~1e-7
+        // rad, is far below the two-row margin)
+        float zmax = -2.f;
+        const float *d = l->h_dirs.data() + 3 * (size_t)bounds[i];
+        for (int b = bounds[i]; b < bounds[i + 1]; ++b, d += 3) zmax = std::max(zmax, r6 * d[0] + r7 * d[1] + r8 * d[2]);
+        const double emax = std::asin(std::fmin(1.0, std::fmax(-1.0, (double)zmax)));
         double hi = std::ceil((emax + l->support_rad - dg->el0) / dg->del - 0.5) + 2;
         if (!(hi < dg->V - 1)) hi = dg->V - 1;  // also NaN
         int band = 0;
