@@ -352,7 +352,8 @@ void free_all(lidar_t *l)
     for (cudaStream_t &st : l->aux_stream)
         if (st) cudaStreamDestroy(st);
     if (l->setup_stream) cudaStreamDestroy(l->setup_stream);
-    if (l->d2h_stream) cudaStreamDestroy(l->d2h_stream);
+    for (cudaStream_t &st : l->d2h_stream)
+        if (st) cudaStreamDestroy(st);
     for (cudaEvent_t &ev : l->chunk_ev)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t &ev : l->setup_ev)
@@ -963,7 +964,8 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     const size_t pixels = (size_t)dg->U * dg->V;
     lidar_status_t st = ensure_scratch(l, pixels);
     if (st != LIDAR_OK) return st;
-    cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream, &l->aux_stream[0], &l->aux_stream[1]};
+    cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream[0], &l->d2h_stream[1], &l->aux_stream[0],
+                               &l->aux_stream[1]};
     for (cudaStream_t *p : streams)
         if (!*p && (e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(host pipeline)");
@@ -973,7 +975,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
     }
-    std::vector<cudaEvent_t *> evs = {&l->start_ev, &l->join_ev[0], &l->join_ev[1], &l->join_ev[2]};
+    std::vector<cudaEvent_t *> evs = {&l->start_ev, &l->join_ev[0], &l->join_ev[1], &l->join_ev[2], &l->join_ev[3]};
     for (int i = 0; i < K; ++i) evs.push_back(&l->chunk_ev[i]);
     for (int i = 0; i < NB; ++i) { evs.push_back(&l->band_ev[i]); evs.push_back(&l->setup_ev[i]); }
     for (cudaEvent_t *ev : evs)
@@ -1024,10 +1026,10 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         ev0 = next_event(l); ev1 = next_event(l); ev2 = next_event(l);
         if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
     }
-    cudaStream_t ss = l->setup_stream, us = l->copy_stream, ds = l->d2h_stream;
+    cudaStream_t ss = l->setup_stream, us = l->copy_stream;
     // every stream of the pipeline starts after the caller's earlier work on `s`
     if ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
-    for (cudaStream_t x : {ss, us, ds, l->aux_stream[0], l->aux_stream[1]})
+    for (cudaStream_t x : {ss, us, l->d2h_stream[0], l->d2h_stream[1], l->aux_stream[0], l->aux_stream[1]})
         if ((e = cudaStreamWaitEvent(x, l->start_ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
     if (ev0) cudaEventRecord(ev0, ss);
     gbl::SetupArgs sb = sa;
@@ -1065,6 +1067,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             if (nb > 0 && (e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs)) !=
                               cudaSuccess)
                 return cuda_fail(l, e, "footprint kernel launch");
+            cudaStream_t ds = l->d2h_stream[i & 1];
             if ((e = cudaEventRecord(l->chunk_ev[i], cs)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventRecord");
@@ -1075,14 +1078,17 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         }
     }
     // echoes and counts (small) once every launch is done
+    cudaStream_t ds = l->d2h_stream[0];
+    for (int i = 1; i < K; i += 2)
+        if ((e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
     if ((e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
                              cudaMemcpyDeviceToHost, ds)) != cudaSuccess ||
         (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, ds)) !=
             cudaSuccess)
         return cuda_fail(l, e, "result download");
     // `s` joins the pipeline
-    cudaStream_t tails[3] = {l->aux_stream[0], l->aux_stream[1], ds};
-    for (int k = 0; k < 3; ++k)
+    cudaStream_t tails[4] = {l->aux_stream[0], l->aux_stream[1], l->d2h_stream[0], l->d2h_stream[1]};
+    for (int k = 0; k < 4; ++k)
         if ((e = cudaEventRecord(l->join_ev[k], tails[k])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, l->join_ev[k], 0)) != cudaSuccess)
             return cuda_fail(l, e, "pipeline join");
