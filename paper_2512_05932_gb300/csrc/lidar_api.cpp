@@ -964,26 +964,18 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     const size_t pixels = (size_t)dg->U * dg->V;
     lidar_status_t st = ensure_scratch(l, pixels);
     if (st != LIDAR_OK) return st;
-    cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream[0], &l->d2h_stream[1]};
+    cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream[0], &l->d2h_stream[1], &l->aux_stream[0],
+                               &l->aux_stream[1]};
     for (cudaStream_t *p : streams)
         if (!*p && (e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(host pipeline)");
     if (!l->setup_stream) {
-        // the set-up at the highest priority, then the launches in order (an
-        // earlier launch's CTAs are scheduled before a later one's, so that
-        // launches finish, and their results go down, one after another)
         int least = 0, greatest = 0;
         if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
             (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
-        for (int i = 0; i < K; ++i) {
-            const int prio = std::min(least, greatest + 1 + i);  // greatest < least numerically
-            if ((e = cudaStreamCreateWithPriority(&l->aux_stream[i], cudaStreamNonBlocking, prio)) != cudaSuccess)
-                return cuda_fail(l, e, "cudaStreamCreate(launch streams)");
-        }
     }
-    std::vector<cudaEvent_t *> evs = {&l->start_ev};
-    for (cudaEvent_t &j : l->join_ev) evs.push_back(&j);
+    std::vector<cudaEvent_t *> evs = {&l->start_ev, &l->join_ev[0], &l->join_ev[1], &l->join_ev[2], &l->join_ev[3]};
     for (int i = 0; i < K; ++i) evs.push_back(&l->chunk_ev[i]);
     for (int i = 0; i < NB; ++i) { evs.push_back(&l->band_ev[i]); evs.push_back(&l->setup_ev[i]); }
     for (cudaEvent_t *ev : evs)
@@ -1037,9 +1029,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     cudaStream_t ss = l->setup_stream, us = l->copy_stream;
     // every stream of the pipeline starts after the caller's earlier work on `s`
     if ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
-    std::vector<cudaStream_t> all = {ss, us, l->d2h_stream[0], l->d2h_stream[1]};
-    all.insert(all.end(), l->aux_stream, l->aux_stream + K);
-    for (cudaStream_t x : all)
+    for (cudaStream_t x : {ss, us, l->d2h_stream[0], l->d2h_stream[1], l->aux_stream[0], l->aux_stream[1]})
         if ((e = cudaStreamWaitEvent(x, l->start_ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
     if (ev0) cudaEventRecord(ev0, ss);
     gbl::SetupArgs sb = sa;
@@ -1065,7 +1055,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         if (b == NB - 1 && ev1) cudaEventRecord(ev1, ss);
         for (; next < K && chunk_band[next] <= b; ++next) {
             const int i = next, b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
-            cudaStream_t cs = l->aux_stream[i];
+            cudaStream_t cs = l->aux_stream[i & 1];
             gbl::FootprintArgs fc = fa;
             fc.beams = l->d_beams + b0;
             fc.n_beams = nb;
@@ -1097,10 +1087,8 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             cudaSuccess)
         return cuda_fail(l, e, "result download");
     // `s` joins the pipeline
-    std::vector<cudaStream_t> tails(l->aux_stream, l->aux_stream + K);
-    tails.push_back(l->d2h_stream[0]);
-    tails.push_back(l->d2h_stream[1]);
-    for (size_t k = 0; k < tails.size(); ++k)
+    cudaStream_t tails[4] = {l->aux_stream[0], l->aux_stream[1], l->d2h_stream[0], l->d2h_stream[1]};
+    for (int k = 0; k < 4; ++k)
         if ((e = cudaEventRecord(l->join_ev[k], tails[k])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, l->join_ev[k], 0)) != cudaSuccess)
             return cuda_fail(l, e, "pipeline join");

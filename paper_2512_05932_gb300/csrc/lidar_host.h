@@ -57,15 +57,15 @@ struct lidar {
     int32_t *d_counts = nullptr;
     // lidar_simulate_host on large frames (simulate_host_pipelined): uploads on
     // copy_stream (band_ev[b]: band b uploaded), set-up on setup_stream at the
-    // highest priority (setup_ev[b]: band b set up), footprint launch i on
-    // aux_stream[i] (chunk_ev[i]: launch i finished), result copies on
+    // highest priority (setup_ev[b]: band b set up), footprint launches on
+    // aux_stream[0] and [1] (chunk_ev[i]: launch i finished), result copies on
     // d2h_stream[0] and [1] (two copy engines); start_ev: the caller's earlier work done; join_ev: the
     // streams the caller's stream joins at the end.
     cudaStream_t copy_stream = nullptr, d2h_stream[2] = {nullptr, nullptr}, setup_stream = nullptr;
-    cudaStream_t aux_stream[8] = {};  // launch i on aux_stream[i], priorities descending with i
+    cudaStream_t aux_stream[2] = {nullptr, nullptr};
     cudaEvent_t chunk_ev[8] = {};
     cudaEvent_t band_ev[8] = {}, setup_ev[8] = {};
-    cudaEvent_t start_ev = nullptr, join_ev[10] = {};
+    cudaEvent_t start_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;
