@@ -275,14 +275,15 @@ lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuf
  * library copies the inputs to device buffers it owns, simulates, copies the
  * results back and synchronises `stream` before returning. A frame of at
  * least 1216 beam groups is pipelined on library-owned streams that start
- * after the work already queued on `stream`: the G-buffer goes up in 8 bands
- * of rows, each set up as it lands; the beams run as 8 launches alternating
- * between two streams (one launch's CTAs fill the SMs the previous one is
- * leaving), each started once the rows its beams can reach (the profile's
- * support radius around their elevation) are set up, so that with beams
- * ordered by elevation the first launches overlap the upload; the results of
- * each launch are copied back while later ones run. Page-locked host memory
- * gives asynchronous, full-bandwidth copies. */
+ * after the work already queued on `stream`: the G-buffer is set up in 8
+ * bands of rows (planes in page-locked, device-mapped host memory are read in
+ * place by the set-up kernel, others are first copied up band by band); the
+ * beams run as 8 launches alternating between two streams (one launch's CTAs
+ * fill the SMs the previous one is leaving), each started once the rows its
+ * beams can reach (the profile's support radius around their elevation) are
+ * set up, so that with beams ordered by elevation the first launches start
+ * early; the waveforms of each launch are copied back while later ones run.
+ * The planes must hold U*V floats each, the outputs the sizes above. */
 lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);
