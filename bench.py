@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--echo-only", action="store_true",
                     help="frame workload through lidar_simulate_echoes (echoes and counts, no waveform output)")
-    ap.add_argument("--cpu-beams", type=int, default=384, help="oracle beam sample for the CPU baseline")
+    ap.add_argument("--cpu-beams", type=int, default=1024, help="oracle beam sample for the CPU baseline (about 20 s of CPU work on 16 cores)")
     ap.add_argument("--deposit", default="atomic", choices=["atomic", "tc_split", "tc_bf16"],
                     help="deposit form of the footprint kernel (lidar_set_deposit)")
     ap.add_argument("--workload", default="frame", choices=["frame", "batch64", "wide", "split", "stack", "pinhole"],
