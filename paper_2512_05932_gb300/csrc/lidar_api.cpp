@@ -336,7 +336,8 @@ void free_all(lidar_t *l)
     free_batch(l);
     free_events(l);
     cudaFree(l->d_dirs);
-    cudaFree(l->d_quads);
+    if (l->node_tex) cudaDestroyTextureObject(l->node_tex);
+    if (l->d_nodes) cudaFreeArray(l->d_nodes);
     cudaFree(l->d_pairs);
     cudaFree(l->d_taps);
     cudaFree(l->d_beams);
@@ -409,7 +410,7 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     gbl::FootprintArgs fa{};
     fa.kg = l->kg; fa.trunc2 = l->trunc2; fa.tail_amp = l->tail_amp; fa.tc2_inv = l->tc2_inv; fa.tail_hp = l->tail_hp;
     fa.invZ = (float)(1.0 / l->Z);
-    fa.quads = l->d_quads; fa.qw = l->qw; fa.qh = l->qh;
+    fa.nodes = l->node_tex; fa.qw = l->qw; fa.qh = l->qh;
     fa.hpairs = l->d_pairs;
     fa.vpairs = l->d_pairs ? l->d_pairs + l->qw : nullptr;
     fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
@@ -720,7 +721,8 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     l->max_echoes = ca->max_echoes;
 
     // profile normalisation and device form
-    std::vector<float4> quads;
+    std::vector<float> nodes;  // table: zero-ringed nodes / Z
+    int nodes_w = 0, nodes_h = 0;
     std::vector<float2> pairs;
     if (p->kind == LIDAR_PROFILE_RADIAL) {
         l->Z = radial_norm(p);
@@ -748,13 +750,12 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
             for (int i = 0; i < l->qw; ++i) pairs.push_back(make_float2((float)hz(i), (float)hz(i + 1)));
             for (int j = 0; j < l->qh; ++j) pairs.push_back(make_float2((float)vz(j), (float)vz(j + 1)));
         } else {
-            quads.resize((size_t)l->qw * l->qh);
-            for (int j = 0; j < l->qh; ++j)
-                for (int i = 0; i < l->qw; ++i) {
-                    auto at = [&](int ii, int jj) { return (float)(padded[(size_t)jj * pw + ii] / l->Z); };
-                    quads[(size_t)j * l->qw + i] =
-                        make_float4(at(i, j), at(i + 1, j), at(i, j + 1), at(i + 1, j + 1));
-                }
+            // cell (i, j) of the lookup spans nodes (i..i+1, j..j+1) of the
+            // zero-ringed grid, gathered by the footprint kernel from a texture
+            nodes.resize((size_t)pw * ph);
+            for (size_t k = 0; k < nodes.size(); ++k) nodes[k] = (float)(padded[k] / l->Z);
+            nodes_w = pw;
+            nodes_h = ph;
         }
         l->tk = (float)(1.0 / (p->pitch_deg * kDeg));
         l->tcu = (float)(0.5 * (p->table_w - 1) + 1.0);
@@ -878,13 +879,28 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         delete l;
         return cuda_fail(nullptr, e, "device allocation at create");
     }
-    if (!quads.empty()) {
-        if ((e = cudaMalloc(&l->d_quads, quads.size() * sizeof(float4))) != cudaSuccess ||
-            (e = cudaMemcpy(l->d_quads, quads.data(), quads.size() * sizeof(float4), cudaMemcpyHostToDevice)) !=
-                cudaSuccess) {
+    if (!nodes.empty()) {
+        cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+        cudaResourceDesc rd{};
+        cudaTextureDesc td{};
+        td.addressMode[0] = cudaAddressModeBorder;  // zero outside the grid
+        td.addressMode[1] = cudaAddressModeBorder;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        if ((e = cudaMallocArray(&l->d_nodes, &ch, nodes_w, nodes_h)) != cudaSuccess ||
+            (e = cudaMemcpy2DToArray(l->d_nodes, 0, 0, nodes.data(), nodes_w * sizeof(float), nodes_w * sizeof(float),
+                                     nodes_h, cudaMemcpyHostToDevice)) != cudaSuccess) {
             free_all(l);
             delete l;
             return cuda_fail(nullptr, e, "profile table upload");
+        }
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = l->d_nodes;
+        if ((e = cudaCreateTextureObject(&l->node_tex, &rd, &td, nullptr)) != cudaSuccess) {
+            free_all(l);
+            delete l;
+            return cuda_fail(nullptr, e, "profile table texture");
         }
     }
     if (!pairs.empty()) {

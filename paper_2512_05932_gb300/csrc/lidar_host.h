@@ -43,7 +43,8 @@ struct lidar {
     // device memory owned by the library
     float *d_dirs = nullptr;
     std::vector<float> h_dirs;  // host copy of the pattern (row ranges of lidar_simulate_host's beam chunks)
-    float4 *d_quads = nullptr;
+    cudaArray_t d_nodes = nullptr;           // table profile: zero-ringed nodes / Z ((w + 2) x (h + 2) floats)
+    cudaTextureObject_t node_tex = 0;        // point-sampled, zero border, unnormalised coordinates
     float2 *d_pairs = nullptr;  // separable: qw H pairs, then qh V pairs
     float *d_taps = nullptr;
     gbl::BeamParam *d_beams = nullptr;

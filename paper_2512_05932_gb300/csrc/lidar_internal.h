@@ -72,7 +72,7 @@ struct FootprintArgs {
     float trunc2;      // support radius^2, rad^2 (radial)
     float tail_amp, tc2_inv, tail_hp;  // radial tail: amp * min(1, (t2 * tc2_inv)^hp)
     float invZ;
-    const float4 *quads;   // (h+1) rows of (w+1) corner quads, already divided by Z (table)
+    cudaTextureObject_t nodes;  // table: (w+2) x (h+2) zero-ringed nodes divided by Z (zero outside)
     int qw, qh;
     // separable profile P = H(u) V(v) (kind LIDAR_PROFILE_SEPARABLE):
     const float2 *hpairs;  // [qw]: (H[i], H[i+1]) of the zero-padded H, divided by Z

@@ -417,17 +417,25 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
         float fu = fmaf(x, f, A.tcu);
         float fv = fmaf(y, f, A.tcv);
         float iu = floorf(fu), iv = floorf(fv);
-        int i = (int)iu, j = (int)iv;
-        r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
         r.fx = fu - iu;
         r.fy = fv - iv;
-        if (!r.ok) {
-            r.q = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else if (KIND == LIDAR_PROFILE_SEPARABLE) {
-            const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
-            r.q = make_float4(h.x, h.y, v.x, v.y);
+        if (KIND == LIDAR_PROFILE_SEPARABLE) {
+            int i = (int)iu, j = (int)iv;
+            r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
+            if (!r.ok) {
+                r.q = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const float2 h = __ldg(A.hpairs + i), v = __ldg(A.vpairs + j);
+                r.q = make_float4(h.x, h.y, v.x, v.y);
+            }
         } else {
-            r.q = __ldg(A.quads + (j * A.qw + i));  // at most 4097 x 4097 quads
+            // the cell's corner nodes (i..i+1, j..j+1) in one gather: it takes
+            // the 2 x 2 texels around (i + 1, j + 1) - 1/2 and returns them in
+            // the order (i, j+1), (i+1, j+1), (i+1, j), (i, j); texels outside
+            // the grid read 0 (border), as the zero-extended profile is there
+            const float4 g = tex2Dgather<float4>(A.nodes, iu + 1.f, iv + 1.f, 0);
+            r.q = make_float4(g.w, g.z, g.x, g.y);
+            r.ok = act;
         }
     }
     return r;
