@@ -379,6 +379,23 @@ enum {
 };
 lidar_status_t lidar_set_deposit(lidar_t *lidar, int32_t mode);
 
+/* Which echoes a beam reports (Sec. II-C: a sensor reports echoes, not the
+ * waveform; the single-return mode of a sensor keeps one of them):
+ *   LIDAR_ECHOES_NEAREST    the first max_echoes runs above T, nearest first
+ *                           (default).
+ *   LIDAR_ECHOES_STRONGEST  every run is evaluated and only the echo of largest
+ *                           intensity is reported (the nearest of equal ones):
+ *                           out_echoes->echoes[b][0], counts[b] 0 or 1, the
+ *                           other entries zeroed.
+ * Applies to later lidar_simulate*, lidar_simulate_echoes and
+ * lidar_simulate_batch calls of this simulator (a batch uses its executor's
+ * mode). LIDAR_EINVAL for another value. */
+enum {
+    LIDAR_ECHOES_NEAREST = 0,
+    LIDAR_ECHOES_STRONGEST = 1
+};
+lidar_status_t lidar_set_echo_mode(lidar_t *lidar, int32_t mode);
+
 /* Per-kernel timing. While enabled, every lidar_simulate call records CUDA
  * events on its stream around each of its kernels (setup, footprint_wave).
  * lidar_profile_read synchronises those events, writes the summed device time

@@ -216,6 +216,16 @@ def extract_echoes(xi, pu, threshold, coef=(0.0, 0.0, 0.0), max_out=64):
     return out[:n]
 
 
+def strongest_echo(echoes):
+    """The single-return selection (LIDAR_ECHOES_STRONGEST): of all echoes of a
+    waveform (extract_echoes, nearest first), the one of largest intensity,
+    the nearest of equal ones; empty if there is none."""
+    if len(echoes) == 0:
+        return echoes[:0]
+    k = int(np.argmax(echoes["intensity"]))  # first maximum: the nearest on ties
+    return echoes[k:k + 1]
+
+
 def fit_epw(pu, threshold) -> np.ndarray:
     coef = np.zeros(3, np.float64)
     used = lib().orc_fit_epw(C.byref(_pulse(pu)), float(threshold), coef.ctypes.data)

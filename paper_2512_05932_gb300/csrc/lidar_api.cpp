@@ -417,6 +417,7 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
     fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
     fa.T = (float)l->T; fa.s_amb = (float)l->s_amb; fa.max_echoes = l->max_echoes;
+    fa.strongest = l->echo_mode == LIDAR_ECHOES_STRONGEST ? 1 : 0;
     fa.c0 = (float)l->coef[0]; fa.c1 = (float)l->coef[1]; fa.c2 = (float)l->coef[2];
     fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
     fa.rB = (float)(0.5 * kC * l->dt);
@@ -1242,6 +1243,15 @@ lidar_status_t lidar_autotune_batch(lidar_t *l, const lidar_frame_t *frames, int
     if (st != LIDAR_OK) return st;
     l->batch_G = bestG;
     l->batch_cps = bestC;
+    return LIDAR_OK;
+}
+
+lidar_status_t lidar_set_echo_mode(lidar_t *l, int32_t mode)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (mode != LIDAR_ECHOES_NEAREST && mode != LIDAR_ECHOES_STRONGEST)
+        return fail(l, LIDAR_EINVAL, "echo mode %d unknown", mode);
+    l->echo_mode = mode;
     return LIDAR_OK;
 }
 

@@ -37,6 +37,7 @@ struct lidar {
     // deposit form: 0 shared-memory atomics (FP32), 1 tensor cores BF16 hi/lo
     // split (3 MMAs), 2 tensor cores plain BF16; G_tc/smem_tc: its group shape
     int32_t deposit = 0;
+    int32_t echo_mode = 0;  // LIDAR_ECHOES_NEAREST or LIDAR_ECHOES_STRONGEST
     int32_t G_tc = 8;
     size_t smem_tc = 0;
     int device = 0;

@@ -107,6 +107,7 @@ struct FootprintArgs {
     // calibration
     float T, s_amb;
     int max_echoes;
+    int strongest;           // 1: only the echo of largest intensity (first on ties) is kept
     float c0, c1, c2;
     float rA, rB;          // range of bin-centre coordinate x: rA + x * rB
     // outputs

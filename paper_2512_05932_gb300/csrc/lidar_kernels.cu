@@ -1171,13 +1171,16 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         bool open = false;
         int bs = 0, pk = 0;
         float pv = 0.f;
+        // the strongest-echo form scans every run and keeps the best one (lane 0)
+        const int cap = A.strongest ? INT_MAX : A.max_echoes;
+        lidar_echo_t best{};
         const int cfirst = kbeg >> 5, clast = kend >> 5;
         float v = 0.f, prev_last = 0.f;
         if (kbeg <= kend) {
             v = xw[32 * cfirst + lane];
             prev_last = cfirst > 0 ? xw[32 * cfirst - 1] : 0.f;
         }
-        for (int c = cfirst; c <= clast && kbeg <= kend && count < A.max_echoes; ++c) {
+        for (int c = cfirst; c <= clast && kbeg <= kend && count < cap; ++c) {
             const int k = 32 * c + lane;
             const float v_next = (k + 32 < nb) ? xw[k + 32] : 0.f;
             float vn = __shfl_down_sync(0xffffffffu, v, 1);
@@ -1193,7 +1196,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             uint32_t Em = __ballot_sync(0xffffffffu, en);
             int seg_lo = 0;
             uint32_t ev = Sm | Em;
-            while (ev && count < A.max_echoes) {
+            while (ev && count < cap) {
                 int i = __ffs(ev) - 1;
                 ev &= ev - 1;
                 if ((Sm >> i) & 1u) { open = true; bs = 32 * c + i; pv = -1.f; pk = bs; seg_lo = i; }
@@ -1286,7 +1289,8 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
                         e.bin_start = bs;
                         e.bin_end = be;
                         e.flags = fl;
-                        eo[count] = e;
+                        if (!A.strongest) eo[count] = e;
+                        else if (count == 0 || e.intensity > best.intensity) best = e;
                     }
                     if (gated) {
                         // every other bin of the run must stay below the peak
@@ -1317,7 +1321,13 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             v = v_next;
         }
         if (lane == 0) {
-            for (int e = count; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
+            if (A.strongest) {
+                eo[0] = best;  // zero when there is no echo
+                count = count > 0 ? 1 : 0;
+                for (int e = 1; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
+            } else {
+                for (int e = count; e < A.max_echoes; ++e) eo[e] = lidar_echo_t{};
+            }
             A.counts[beam] = count;
         }
         if (gated && __any_sync(0xffffffffu, gfail) && lane == 0) A.fb_flags[beam] = 1;

@@ -92,7 +92,8 @@ assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_reproject_pinhole", "lidar_simulate_host", "lidar_simulate_noalloc",
            "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
-           "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_profile_enable", "lidar_profile_read", "lidar_last_error",
+           "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_set_echo_mode", "lidar_profile_enable",
+           "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
 # include/lidar_tail.h
 TAIL_SYMBOLS = ("lidar_tail_configure", "lidar_tail_features", "lidar_tail_exact", "lidar_simulate_split",
@@ -157,6 +158,8 @@ def load(path: str = LIB_PATH):
     lib.lidar_launches_per_simulate.argtypes = [C.c_void_p]
     lib.lidar_set_deposit.restype = C.c_int
     lib.lidar_set_deposit.argtypes = [C.c_void_p, C.c_int32]
+    lib.lidar_set_echo_mode.restype = C.c_int
+    lib.lidar_set_echo_mode.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_enable.restype = C.c_int
     lib.lidar_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_read.restype = C.c_int
@@ -580,6 +583,13 @@ DEPOSIT_ATOMIC, DEPOSIT_TC_SPLIT, DEPOSIT_TC_BF16 = 0, 1, 2
 
 def lidar_set_deposit(handle, mode: int) -> None:
     _check(load().lidar_set_deposit(handle, int(mode)), handle)
+
+
+ECHOES_NEAREST, ECHOES_STRONGEST = 0, 1
+
+
+def lidar_set_echo_mode(handle, mode: int) -> None:
+    _check(load().lidar_set_echo_mode(handle, int(mode)), handle)
 
 
 def lidar_profile_enable(handle, enable: bool) -> None:

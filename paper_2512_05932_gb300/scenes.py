@@ -408,6 +408,24 @@ def grid_pattern(n_az, n_el, fov_az, fov_el, az_c=0.0, el_c=0.0):
     return _dirs_from_angles(A.ravel(), E.ravel())
 
 
+def edge_two_depths(n_beams=41, span_deg=0.2, threshold=1e-6):
+    """A 2x2 m board at 7 m (rho_d 0.3) covering the left half of the view in
+    front of a plane at 10 m (rho_d 0.5), 512x256 at 0.01 deg, and a row of
+    beams across the board's edge (azimuth within +-span_deg of it): beams
+    near the edge return both surfaces, the nearer or the farther being the
+    stronger depending on how much of the footprint each covers."""
+    deg = math.pi / 180
+    board = Rect(np.array([7.0, -1.0, 0.0]), np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]), 1.0, 1.0, 0.3, 0.0)
+    sc = Scene(planes=[Plane(np.array([1.0, 0.0, 0.0]), 10.0, 0.5)], rects=[board], ambient="uniform",
+               ambient_level=0.01)
+    pitch = 0.01 * deg
+    U, V = 512, 256
+    gb = raycast(sc, U, V, -U * pitch / 2, -V * pitch / 2, pitch, pitch)
+    az = np.linspace(-span_deg, span_deg, n_beams) * deg
+    dirs = _dirs_from_angles(az, np.zeros_like(az))
+    return Workload("edge_two_depths", gb, dirs, radial_profile(), pulse(1024, 0.1e-9), calib(threshold, 1e-5, 3, True))
+
+
 def linescan_pattern(rows, cols, fov_az, fov_el):
     return grid_pattern(cols, rows, fov_az, fov_el)
 

@@ -120,3 +120,64 @@ def test_rejects_null_outputs():
     with pytest.raises(lidar.LidarError, match="NULL"):
         lidar.lidar_simulate_echoes(L.handle, g, lidar.make_pose(w.pose), 0, 0)
     L.close()
+
+
+@pytest.mark.parametrize("echo_only", [False, True])
+def test_strongest_echo_mode(echo_only):
+    """LIDAR_ECHOES_STRONGEST on beams across a board's edge in front of a
+    plane (two echoes near the edge, the farther one the stronger for half of
+    them): every beam reports the oracle's strongest echo alone (count 0 or 1,
+    the other entries zero), in the waveform and the echo-only forms. A beam
+    with a waveform bin in the guard band, or whose two strongest oracle echoes
+    are within 1e-3 in intensity, only has to report one of its echoes."""
+    w = S.edge_two_depths()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    lidar.lidar_set_echo_mode(L.handle, lidar.ECHOES_STRONGEST)
+    planes = lidar.gbuffer_to_device(w.gbuffer)
+    if echo_only:
+        ech, cnt = L.simulate_echoes(w.gbuffer, planes, w.pose)
+    else:
+        _, ech, cnt = L.simulate(w.gbuffer, planes, w.pose)
+    torch.cuda.synchronize()
+    lidar.lidar_sync(L.handle, 0)
+    ech, cnt = lidar.echoes_numpy(ech), cnt.cpu().numpy()
+    beams = np.arange(len(w.dirs), dtype=np.int32)
+    ref = O.simulate_workload(w, beams=beams, nthreads=NTHREADS, max_out=64)
+    T = w.calib["threshold"]
+    assert set(np.unique(cnt)) <= {0, 1}
+    assert (ech[:, 1:]["bin_end"] == 0).all() and (ech[:, 1:]["flags"] == 0).all()
+    far_wins = 0
+    for b in beams:
+        oe = ref["echoes"][b][:int(ref["counts"][b])]
+        assert cnt[b] == (1 if len(oe) else 0), b
+        if not len(oe):
+            continue
+        g = ech[b, 0]
+        ambiguous = np.any(np.abs(ref["xi"][b] - T) <= 1e-4 * T)
+        top = np.sort(oe["intensity"])[::-1]
+        if ambiguous or (len(oe) > 1 and top[1] >= top[0] * (1 - 1e-3)):
+            assert any((g["bin_start"], g["bin_end"]) == (o["bin_start"], o["bin_end"]) for o in oe), b
+            continue
+        o = O.strongest_echo(oe)[0]
+        far_wins += int(o["bin_start"] != oe[0]["bin_start"])
+        assert (g["bin_start"], g["bin_end"]) == (o["bin_start"], o["bin_end"]), (b, g, o)
+        assert g["intensity"] == pytest.approx(o["intensity"], rel=1e-3)
+        assert abs(g["range_m"] - o["range_m"]) <= 1e-3
+    assert far_wins >= 5
+    # the default (nearest first) on the same frame meets the parity bar
+    lidar.lidar_set_echo_mode(L.handle, lidar.ECHOES_NEAREST)
+    wave, ech2, cnt2 = L.simulate(w.gbuffer, planes, w.pose)
+    torch.cuda.synchronize()
+    from tests.test_parity_gpu import compare
+    st = compare(ref, wave.cpu().numpy().astype(np.float64), lidar.echoes_numpy(ech2), cnt2.cpu().numpy(), beams, T,
+                 w.calib["max_echoes"], w.pulse)
+    assert st["echoes"] >= 60
+    L.close()
+
+
+def test_echo_mode_rejects_unknown_values():
+    w = S.tiny_case()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    with pytest.raises(lidar.LidarError, match="echo mode"):
+        lidar.lidar_set_echo_mode(L.handle, 2)
+    L.close()

@@ -597,3 +597,26 @@ def test_golden_closed_forms(orc):
     assert orc.fit_epw(PU1, 1e-5)[1] == pytest.approx(g["epw_c1_per_m2"]["value"], rel=5e-3)
     taps = orc.pulse_taps(PU1)
     assert len(taps) == g["pulse_taps_4ns_0p1ns"]["value"]
+
+
+def test_strongest_echo_selection(orc):
+    """The single-return selection (LIDAR_ECHOES_STRONGEST): of three point
+    targets the calibrated intensities follow the amplitudes (the EPW law), so
+    the strongest echo is the largest target's; of two equal targets, the
+    nearer one; no echo, no selection."""
+    pu = S.pulse(1024, 0.1e-9, 0.0, 4e-9, 6.0)
+    T = 1e-5
+    taps, coef = orc.pulse_taps(pu), orc.fit_epw(pu, T)
+    h = np.zeros(1024)
+    h[200], h[500], h[800] = 3e-3, 2e-2, 8e-3
+    e = orc.extract_echoes(orc.convolve(h, taps), pu, T, coef)
+    assert [x["bin_peak"] for x in e] == [200, 500, 800]
+    assert e[1]["intensity"] > e[2]["intensity"] > e[0]["intensity"]
+    s = orc.strongest_echo(e)
+    assert len(s) == 1 and s[0]["bin_peak"] == 500 and s[0]["intensity"] == e[1]["intensity"]
+    # equal intensities: the nearer echo
+    e2 = np.zeros(3, e.dtype)
+    e2["bin_peak"] = [100, 300, 700]
+    e2["intensity"] = [0.5, 2.0, 2.0]
+    assert orc.strongest_echo(e2)[0]["bin_peak"] == 300
+    assert len(orc.strongest_echo(orc.extract_echoes(np.zeros(64), PU, 1.0))) == 0
