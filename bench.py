@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--echo-mode", default="nearest", choices=["nearest", "strongest"],
+                    help="frame workloads: echoes nearest first (up to 3) or the single strongest return")
     ap.add_argument("--echo-only", action="store_true",
                     help="frame workload through lidar_simulate_echoes (echoes and counts, no waveform output)")
     ap.add_argument("--cpu-beams", type=int, default=1024, help="oracle beam sample for the CPU baseline (about 20 s of CPU work on 16 cores)")
@@ -369,6 +371,8 @@ def run_gb300(args, rank, world, local_rank):
     w = workload()
     L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
     lidar.lidar_set_deposit(L.handle, DEPOSIT[args.deposit])
+    lidar.lidar_set_echo_mode(L.handle, lidar.ECHOES_STRONGEST if args.echo_mode == "strongest" else
+                              lidar.ECHOES_NEAREST)
     planes = lidar.gbuffer_to_device(w.gbuffer, dev)
     outs = L.alloc_outputs(dev)
     if args.echo_only:
@@ -487,7 +491,7 @@ def run_gb300(args, rank, world, local_rank):
                "sample": f"{args.cpu_beams} evenly spaced beams of the frame, all pixels each ({dt:.1f} s wall)"}
 
     extra = {"l2": "flushed between timed steps (258 MB write)", "parallelism": f"replicas x{world}",
-             "deposit": args.deposit}
+             "deposit": args.deposit, "echo_mode": args.echo_mode}
     if args.echo_only:
         extra["output"] = "echoes and counts only (lidar_simulate_echoes)"
     line = {"metric": METRIC_ECHO if args.echo_only else METRIC, "value": value, "unit": UNIT, "n_gpus": world,
