@@ -488,6 +488,194 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// General kernel, dense form (kernels whose 32 x 32 tile layout fits shared
+// memory). As the separable kernel: 32 x 32 output tiles, the region's strong
+// slices listed 64 at a time nearest first, one pass per slice, the first
+// slice reaching the threshold kept. A pass computes the full 2-D sum,
+// out(y, x) = sum_a sum_b K[a][b] I_s(y + 2m - a, x + 2n - b), register-blocked
+// as the separable row pass (4 outputs of a row per thread, 4-element window
+// chunks, each kernel row zero-padded), and skips every kernel row whose
+// region row holds no pixel of the slice (an exact bit per listed slice and
+// region row): on a surface seen at grazing incidence a slice covers a few
+// rows of the region, so most of the kh rows of a pass are skipped.
+// ---------------------------------------------------------------------------
+
+struct DenseLayout {
+    int nC;       // window chunks per row
+    int pr;       // zero taps in front of each kernel row
+    int Lr;       // padded kernel row length (multiple of 4)
+    int RH, RW, RWp;
+};
+
+__host__ __device__ inline DenseLayout dense_layout(int kh, int kw)
+{
+    DenseLayout L;
+    L.nC = (kw + 6) >> 2;
+    L.pr = ((kw - 1) & 3) ? 5 : 3;
+    L.Lr = (L.pr + kw + 4 + 3) & ~3;
+    L.RH = kSH + kh - 1;
+    L.RW = kSW + kw - 1;
+    L.RWp = kSW + 4 * L.nC;
+    return L;
+}
+
+__global__ void __launch_bounds__(256) stack_dense_kernel(StackArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int kh = A.kh, kw = A.kw, m = kh / 2, n = kw / 2;
+    const DenseLayout L = dense_layout(kh, kw);
+    const int RH = L.RH, RW = L.RW, RWp = L.RWp;
+    float *Kp = reinterpret_cast<float *>(smem);                  // [kh][Lr]: K[a][b] at a Lr + pr + b
+    float *RI = Kp + kh * L.Lr;                                    // region intensity [RH][RWp]
+    uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RWp);    // region slice [RH][RWp]
+    unsigned long long *rmask = reinterpret_cast<unsigned long long *>(RS + RH * RWp);  // [RH]: listed slices on the row
+    __shared__ float hist[kSpan];
+    __shared__ signed char lpos[kSpan];  // list position of a slice (bin - slo), or -1
+    __shared__ int lst[kList];
+    __shared__ int s_lo, s_hi, s_cnt, s_min;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int u0 = blockIdx.x * kSW, v0 = blockIdx.y * kSH;
+    for (int i = tid; i < kh * L.Lr; i += blockDim.x) {
+        const int a = i / L.Lr, c = i - a * L.Lr;
+        Kp[i] = (c >= L.pr && c < L.pr + kw) ? A.K[a * kw + c - L.pr] : 0.f;
+    }
+    for (int i = tid; i < RH * RWp; i += blockDim.x) {
+        const int ry = i / RWp, rx = i - ry * RWp;
+        const int v = v0 - m + ry, u = u0 - n + rx;
+        float w = 0.f;
+        uint16_t s = 0;
+        if (rx < RW && v >= 0 && v < A.V && u >= 0 && u < A.U) {
+            const long idx = (long)v * A.U + u;
+            w = A.I[idx];
+            s = A.S[idx];
+        }
+        RI[i] = w;
+        RS[i] = s;
+    }
+    for (int i = tid; i < kSpan; i += blockDim.x) lpos[i] = -1;
+    if (tid == 0) { s_lo = INT_MAX; s_hi = 0; }
+    __syncthreads();
+    {
+        int lo_ = INT_MAX, hi_ = 0;
+        for (int i = tid; i < RH * RWp; i += blockDim.x)
+            if (RS[i]) { lo_ = min(lo_, (int)RS[i]); hi_ = max(hi_, (int)RS[i]); }
+        atomicMin(&s_lo, lo_);
+        atomicMax(&s_hi, hi_);
+    }
+    __syncthreads();
+    const int slo = s_lo, shi = s_hi;
+    const bool use_hist = shi >= slo && shi - slo < kSpan;
+    const float cut = A.thr * (1.f - 1e-5f);
+    if (use_hist) {
+        for (int i = tid; i <= shi - slo; i += blockDim.x) hist[i] = 0.f;
+        __syncthreads();
+        region_hist(hist, RS, RI, RH * RWp, slo);
+        __syncthreads();
+    }
+
+    // this thread's outputs: row y, columns 4 cg + o
+    const int y = tid >> 3, cg = tid & 7;
+    int outS[4];
+    float outX[4];
+    int done = 0;  // bit o: output (y, 4 cg + o) has its answer (or is outside the image)
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        outS[o] = A.s_max;
+        outX[o] = 0.f;
+        if (!(u0 + 4 * cg + o < A.U && v0 + y < A.V)) done |= 1 << o;
+    }
+    const int kbase = L.pr + 2 * n - 3;  // taps of chunk 0 in each padded kernel row (multiple of 4)
+    int lo = 0;  // slices <= lo have been processed
+    bool finished = __syncthreads_and(done == 0xF) != 0;
+    while (!finished) {
+        // the next (up to kList) slices above lo, nearest first
+        if (tid == 0) { s_cnt = 0; s_min = INT_MAX; }
+        __syncthreads();
+        if (use_hist) {
+            if (tid < 32) {
+                int cnt = 0;
+                for (int b0 = max(0, lo + 1 - slo); b0 <= shi - slo && cnt < kList; b0 += 32) {
+                    const int bin = b0 + tid;
+                    const bool keep = bin <= shi - slo && hist[bin] > 0.f && hist[bin] * A.kmax >= cut;
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    const int pos = cnt + __popc(bal & ((1u << tid) - 1u));
+                    if (keep && pos < kList) lst[pos] = slo + bin;
+                    cnt += __popc(bal);
+                }
+                if (tid == 0) s_cnt = min(cnt, kList);
+            }
+        } else {
+            int mn = INT_MAX;
+            for (int i = tid; i < RH * RWp; i += blockDim.x)
+                if (RS[i] > lo) mn = min(mn, (int)RS[i]);
+            atomicMin(&s_min, mn);
+            __syncthreads();
+            if (tid == 0 && s_min != INT_MAX) { lst[0] = s_min; s_cnt = 1; }
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        if (cnt == 0) break;
+        // which listed slices lie on each region row (one warp per row)
+        if (use_hist && tid < cnt) lpos[lst[tid] - slo] = (signed char)tid;
+        __syncthreads();
+        for (int r = warp; r < RH; r += (int)(blockDim.x >> 5)) {
+            unsigned mlo = 0u, mhi = 0u;
+            for (int x = lane; x < RW; x += 32) {
+                const int sv = RS[r * RWp + x];
+                int k = -1;
+                if (use_hist) { if (sv >= slo && sv <= shi) k = lpos[sv - slo]; }
+                else if (sv == lst[0]) k = 0;
+                if (k >= 0) { if (k < 32) mlo |= 1u << k; else mhi |= 1u << (k - 32); }
+            }
+            mlo = __reduce_or_sync(0xffffffffu, mlo);
+            mhi = __reduce_or_sync(0xffffffffu, mhi);
+            if (lane == 0) rmask[r] = ((unsigned long long)mhi << 32) | mlo;
+        }
+        __syncthreads();
+        if (use_hist && tid < cnt) lpos[lst[tid] - slo] = -1;
+        for (int k = 0; k < cnt && !finished; ++k) {
+            const int s = lst[k];
+            const unsigned long long bit = 1ull << k;
+            if (done != 0xF) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int a = 0; a < kh; ++a) {
+                    const int r = y + 2 * m - a;  // region row of kernel row a for output row y
+                    if (!(rmask[r] & bit)) continue;
+                    const float4 *wI = reinterpret_cast<const float4 *>(RI + r * RWp + 4 * cg);
+                    const uint2 *wS = reinterpret_cast<const uint2 *>(RS + r * RWp + 4 * cg);
+                    const float4 *K4 = reinterpret_cast<const float4 *>(Kp + a * L.Lr + kbase);
+                    float4 hi = K4[1];
+                    for (int c = 0; c < L.nC; ++c) {
+                        const float4 x = wI[c];
+                        const uint2 t = wS[c];
+                        const float w[4] = {(int)(t.x & 0xFFFFu) == s ? x.x : 0.f, (int)(t.x >> 16) == s ? x.y : 0.f,
+                                            (int)(t.y & 0xFFFFu) == s ? x.z : 0.f, (int)(t.y >> 16) == s ? x.w : 0.f};
+                        const float4 lo4 = K4[-c];
+                        chunk_fma(acc, w, lo4, hi);
+                        hi = lo4;
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < 4; ++o)
+                    if (!((done >> o) & 1) && acc[o] >= A.thr) { outS[o] = s; outX[o] = acc[o]; done |= 1 << o; }
+            }
+            finished = __syncthreads_and(done == 0xF) != 0;
+        }
+        lo = lst[cnt - 1];
+        __syncthreads();  // every thread has read lst (and rmask) before the next round overwrites them
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int u = u0 + 4 * cg + o, v = v0 + y;
+        if (u < A.U && v < A.V) {
+            const long idx = (long)v * A.U + u;
+            A.out_slice[idx] = outS[o];
+            A.out_val[idx] = outX[o];
+        }
+    }
+}
+
 thread_local char g_stack_err[512] = "no error";
 
 }  // namespace
@@ -497,6 +685,7 @@ struct lidar_stack {
     double dr = 0, thr = 0;
     float kmax = 0.f;
     bool sep = false;           // separable kernel: row/column passes
+    bool dense = false;         // general kernel in the dense form (its tile layout fits shared memory)
     float *d_K = nullptr;       // [kh][kw], or col[kh] then row[kw] when sep
     float *d_I = nullptr;
     uint16_t *d_S = nullptr;
@@ -525,6 +714,14 @@ size_t tile_smem(int kh, int kw)
 {
     const size_t RH = kTH + kh - 1, RW = kTW + kw - 1;
     return (size_t)kh * kw * 4 + RH * RW * 4 + RH * RW * 2;
+}
+
+// dynamic shared memory of stack_dense_kernel: padded kernel rows, region
+// (float + uint16), per-row slice masks
+size_t dense_smem(int kh, int kw)
+{
+    const DenseLayout L = dense_layout(kh, kw);
+    return (size_t)kh * L.Lr * 4 + (size_t)L.RH * L.RWp * 6 + (size_t)L.RH * 8;
 }
 
 // dynamic shared memory of stack_sep_kernel: padded taps, row-pass result,
@@ -573,10 +770,14 @@ lidar_status_t lidar_stack_create(const lidar_stack_params_t *p, lidar_stack_t *
     h->kh = p->kh; h->kw = p->kw; h->s_max = (int)sm; h->dr = p->dr; h->thr = p->threshold;
     for (int i = 0; i < p->kh * p->kw; ++i) h->kmax = std::max(h->kmax, p->kernel[i]);
     cudaError_t e;
+    // the dense form where its layout leaves room for the static arrays (~10 KB)
+    h->dense = dense_smem(p->kh, p->kw) <= 200 * 1024;
     if ((e = cudaMalloc(&h->d_K, (size_t)p->kh * p->kw * sizeof(float))) != cudaSuccess ||
         (e = cudaMemcpy(h->d_K, p->kernel, (size_t)p->kh * p->kw * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(stack_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tile_smem(p->kh, p->kw))) != cudaSuccess) {
+                                  (int)tile_smem(p->kh, p->kw))) != cudaSuccess ||
+        (h->dense && (e = cudaFuncSetAttribute(stack_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)dense_smem(p->kh, p->kw))) != cudaSuccess)) {
         lidar_status_t st = scuda(nullptr, e, "range stacking set-up");
         lidar_stack_destroy(h);
         return st;
@@ -625,6 +826,12 @@ lidar_status_t lidar_range_stack(lidar_stack_t *h, const lidar_gbuffer_t *g, int
         dim3 sg((g->U + kSW - 1) / kSW, (g->V + kSH - 1) / kSH);
         stack_sep_kernel<<<sg, 256, sep_smem(h->kh, h->kw), s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking separable kernel launch");
+        return LIDAR_OK;
+    }
+    if (h->dense) {
+        dim3 dg((g->U + kSW - 1) / kSW, (g->V + kSH - 1) / kSH);
+        stack_dense_kernel<<<dg, 256, dense_smem(h->kh, h->kw), s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return scuda(h, e, "range stacking dense kernel launch");
         return LIDAR_OK;
     }
     dim3 tg((g->U + kTW - 1) / kTW, (g->V + kTH - 1) / kTH);
