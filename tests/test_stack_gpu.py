@@ -81,6 +81,19 @@ def test_ragged_asymmetric_kernel():
     check(w.gbuffer, k, thr=float(np.median(I[I > 0])) * 3, dr=0.01, r_max=20.0)
 
 
+@pytest.mark.parametrize("kh,kw", [(1, 1), (3, 5), (113, 101), (129, 129)])
+def test_general_kernel_sizes(kh, kw):
+    """A single tap, a small asymmetric kernel, one near the largest the dense
+    form (per-slice passes with row masks) holds in shared memory, and the
+    largest kernel, which runs the slot walk instead."""
+    w = S.tiny_case()
+    g = np.random.default_rng(kh * 1000 + kw + 7)
+    K = g.uniform(0.1, 1, (kh, kw)).astype(np.float32)
+    I, _ = O.stack_inputs(w.gbuffer, 0.01)
+    st = check(w.gbuffer, K, thr=float(np.median(I[I > 0])) * 2, dr=0.01, r_max=20.0)
+    assert st["echoes"] > 0
+
+
 def test_many_slices_per_stencil():
     """Ground at grazing angles puts dozens of slices under one stencil: the
     24-slot passes must still find the nearest slice above the threshold."""
