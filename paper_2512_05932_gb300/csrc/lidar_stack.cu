@@ -309,8 +309,19 @@ __host__ __device__ inline SepLayout sep_layout(int kh, int kw)
     L.RH = kSH + kh - 1;
     L.RW = kSW + kw - 1;
     L.RWp = kSW + 4 * L.nCr;
+    L.RWp += (8 - L.RWp % 16 + 16) % 16;  // rows 4 apart: disjoint banks for a half warp's slice ids
     L.RHb = kSH + 4 * L.nCc;
     return L;
+}
+
+// Output row (of a 32-row tile) of thread `tid` in a block of 256 whose lanes
+// make 4 outputs each (8 lanes a row): the quarter warps of warp w take rows
+// b, b + 4, b + 1, b + 5 with b = 8 (w / 2) + 2 (w % 2), so that each half warp
+// reads two region rows 4 apart.
+__device__ __forceinline__ int quad_row(int tid)
+{
+    const int w = tid >> 5, q = (tid >> 3) & 3;
+    return 8 * (w >> 1) + 2 * (w & 1) + (q >> 1) + 4 * (q & 1);
 }
 
 // acc[o] += sum_q w[q] k[3 + o - q], k = (lo, hi) the chunk's 8 taps
@@ -435,9 +446,10 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
             const int s = lst[k];
             // row pass: item = (region row ry, column group cg of 4 outputs);
             // the 8 items of a row are adjacent threads (one 128-byte row of
-            // 16-byte loads per quarter warp)
-            for (int it = tid; it < RH * (kSW / 4); it += blockDim.x) {
-                const int ry = it >> 3, cg = it & 7;
+            // 16-byte loads per quarter warp), blocks of 32 rows as quad_row
+            for (int it = tid; it < ((RH + 31) & ~31) * (kSW / 4); it += blockDim.x) {
+                const int ry = 32 * (it >> 8) + quad_row(it & 255), cg = it & 7;
+                if (ry >= RH) continue;
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 if (s >= rmin[ry] && s <= rmax[ry]) {
                     const float4 *wI = reinterpret_cast<const float4 *>(RI + ry * RWp + 4 * cg);
@@ -516,7 +528,11 @@ __host__ __device__ inline DenseLayout dense_layout(int kh, int kw)
     L.Lr = (L.pr + kw + 4 + 3) & ~3;
     L.RH = kSH + kh - 1;
     L.RW = kSW + kw - 1;
+    // row stride = 8 (mod 16) floats: rows 4 apart are 16 (mod 32) words of
+    // slice ids apart, so a half warp reading two such rows (8 bytes a lane)
+    // hits each bank once
     L.RWp = kSW + 4 * L.nC;
+    L.RWp += (8 - L.RWp % 16 + 16) % 16;
     return L;
 }
 
@@ -575,7 +591,7 @@ __global__ void __launch_bounds__(256) stack_dense_kernel(StackArgs A)
     }
 
     // this thread's outputs: row y, columns 4 cg + o
-    const int y = tid >> 3, cg = tid & 7;
+    const int y = quad_row(tid), cg = tid & 7;
     int outS[4];
     float outX[4];
     int done = 0;  // bit o: output (y, 4 cg + o) has its answer (or is outside the image)
