@@ -549,6 +549,7 @@ __global__ void __launch_bounds__(256) stack_dense_kernel(StackArgs A)
     __shared__ float hist[kSpan];
     __shared__ signed char lpos[kSpan];  // list position of a slice (bin - slo), or -1
     __shared__ int lst[kList];
+    __shared__ short srow[kList][2];     // first and last region row holding listed slice k
     __shared__ int s_lo, s_hi, s_cnt, s_min;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int u0 = blockIdx.x * kSW, v0 = blockIdx.y * kSH;
@@ -649,13 +650,23 @@ __global__ void __launch_bounds__(256) stack_dense_kernel(StackArgs A)
             if (lane == 0) rmask[r] = ((unsigned long long)mhi << 32) | mlo;
         }
         __syncthreads();
-        if (use_hist && tid < cnt) lpos[lst[tid] - slo] = -1;
+        if (tid < cnt) {
+            if (use_hist) lpos[lst[tid] - slo] = -1;
+            int r0 = RH, r1 = -1;
+            for (int r = 0; r < RH; ++r)
+                if ((rmask[r] >> tid) & 1ull) { r0 = min(r0, r); r1 = r; }
+            srow[tid][0] = (short)r0;
+            srow[tid][1] = (short)r1;
+        }
+        __syncthreads();
         for (int k = 0; k < cnt && !finished; ++k) {
             const int s = lst[k];
             const unsigned long long bit = 1ull << k;
             if (done != 0xF) {
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int a = 0; a < kh; ++a) {
+                // kernel rows a whose region row y + 2m - a lies in the slice's rows
+                const int a0 = max(0, y + 2 * m - srow[k][1]), a1 = min(kh - 1, y + 2 * m - srow[k][0]);
+                for (int a = a0; a <= a1; ++a) {
                     const int r = y + 2 * m - a;  // region row of kernel row a for output row y
                     if (!(rmask[r] & bit)) continue;
                     const float4 *wI = reinterpret_cast<const float4 *>(RI + r * RWp + 4 * cg);
