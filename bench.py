@@ -38,6 +38,7 @@ L2_BYTES = 129 * 1024 * 1024
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "footprint_wave_boxes2048x1024.traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2512_05932_gb300", "csrc", "lidar_kernels.cu")
 STACK_SEP_COUNTERS = os.path.join(ROOT, "profiles", "stack_sep_boxes4096x1024.counters.json")
+STACK_DENSE_COUNTERS = os.path.join(ROOT, "profiles", "stack_dense_boxes4096x1024.counters.json")
 STACK_SRC = os.path.join(ROOT, "paper_2512_05932_gb300", "csrc", "lidar_stack.cu")
 
 
@@ -873,15 +874,16 @@ def run_stack(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": "range stacking step", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
             "traffic": None, "algorithmic_bytes": alg}
-    if sep:
-        # the separable kernel is bound by instruction issue (ncu counters of
-        # the same source, step time: the per-pixel input kernel adds ~4 %)
-        cnt = committed_counters(STACK_SEP_COUNTERS, STACK_SRC, "boxes_4096x1024_stack_kernel69_1200slices_separable")
-        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        roof["issue"] = issue_roofline(None, ms, clocks.get("sm_mhz"), n_sm, counters=cnt or {})
-        if roof["issue"]:
-            roof["issue"]["kernel"] = "stack_sep_kernel (time: whole step)"
-        roof["traffic"] = cnt.get("bytes_per_launch") if cnt else None
+    # both stacking kernels are bound by instruction issue (ncu counters of the
+    # same source; step time: the per-pixel input kernel adds ~1-4 %)
+    kname = "stack_sep_kernel" if sep else "stack_dense_kernel"
+    cnt = (committed_counters(STACK_SEP_COUNTERS, STACK_SRC, "boxes_4096x1024_stack_kernel69_1200slices_separable")
+           if sep else committed_counters(STACK_DENSE_COUNTERS, STACK_SRC, "boxes_4096x1024_stack_kernel69_1200slices "))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof["issue"] = issue_roofline(None, ms, clocks.get("sm_mhz"), n_sm, counters=cnt or {})
+    if roof["issue"]:
+        roof["issue"]["kernel"] = f"{kname} (time: whole step)"
+    roof["traffic"] = cnt.get("bytes_per_launch") if cnt else None
     if rank == 0:
         line = {"metric": "range stacking: pixel-centred beams/s (nearest slice above threshold, Alg. 2)",
                 "value": world * npx / (ms * 1e-3), "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
