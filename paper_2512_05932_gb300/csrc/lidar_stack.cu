@@ -345,10 +345,11 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
     float *Rb = Kr + L.Lr;                          // row-pass result [RHb][kSW]
     float *RI = Rb + L.RHb * kSW;                   // region intensity [RH][RWp]
     uint16_t *RS = reinterpret_cast<uint16_t *>(RI + RH * RWp);  // region slice [RH][RWp]
-    int *rmin = reinterpret_cast<int *>(RS + RH * RWp);          // per region row: slice range
-    int *rmax = rmin + RH;
+    unsigned long long *rmask = reinterpret_cast<unsigned long long *>(RS + RH * RWp);  // [RH]: listed slices on the row
     __shared__ float hist[kSpan];
+    __shared__ signed char lpos[kSpan];  // list position of a slice (bin - slo), or -1
     __shared__ int lst[kList];
+    __shared__ short srow[kList][2];     // first and last region row holding listed slice k
     __shared__ int s_lo, s_hi, s_cnt, s_min;
     const int tid = threadIdx.x;
     const int u0 = blockIdx.x * kSW, v0 = blockIdx.y * kSH;
@@ -368,6 +369,7 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
         RI[i] = w;
         RS[i] = s;
     }
+    for (int i = tid; i < kSpan; i += blockDim.x) lpos[i] = -1;
     if (tid == 0) { s_lo = INT_MAX; s_hi = 0; }
     __syncthreads();
     {
@@ -387,17 +389,6 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
         region_hist(hist, RS, RI, RH * RWp, slo);
         __syncthreads();
     }
-    // per region row: range of the slices on it (rows without slice s skip the row pass)
-    for (int ry = tid; ry < RH; ry += blockDim.x) {
-        int a = INT_MAX, b = 0;
-        for (int rx = 0; rx < RW; ++rx) {
-            const int s = RS[ry * RWp + rx];
-            if (s) { a = min(a, s); b = max(b, s); }
-        }
-        rmin[ry] = a;
-        rmax[ry] = b;
-    }
-    __syncthreads();
 
     // column pass: this thread's outputs are rows 4 g + o of column tx
     const int tx = tid % kSW, g = tid / kSW;
@@ -442,8 +433,37 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
         __syncthreads();
         const int cnt = s_cnt;
         if (cnt == 0) break;
+        // which listed slices lie on each region row (one warp per row), and
+        // the first and last row of each
+        const int lane = tid & 31, warp = tid >> 5;
+        if (use_hist && tid < cnt) lpos[lst[tid] - slo] = (signed char)tid;
+        __syncthreads();
+        for (int r = warp; r < RH; r += (int)(blockDim.x >> 5)) {
+            unsigned mlo = 0u, mhi = 0u;
+            for (int x = lane; x < RW; x += 32) {
+                const int sv = RS[r * RWp + x];
+                int q = -1;
+                if (use_hist) { if (sv >= slo && sv <= shi) q = lpos[sv - slo]; }
+                else if (sv == lst[0]) q = 0;
+                if (q >= 0) { if (q < 32) mlo |= 1u << q; else mhi |= 1u << (q - 32); }
+            }
+            mlo = __reduce_or_sync(0xffffffffu, mlo);
+            mhi = __reduce_or_sync(0xffffffffu, mhi);
+            if (lane == 0) rmask[r] = ((unsigned long long)mhi << 32) | mlo;
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            if (use_hist) lpos[lst[tid] - slo] = -1;
+            int r0 = RH, r1 = -1;
+            for (int r = 0; r < RH; ++r)
+                if ((rmask[r] >> tid) & 1ull) { r0 = min(r0, r); r1 = r; }
+            srow[tid][0] = (short)r0;
+            srow[tid][1] = (short)r1;
+        }
+        __syncthreads();
         for (int k = 0; k < cnt && !finished; ++k) {
             const int s = lst[k];
+            const unsigned long long bit = 1ull << k;
             // row pass: item = (region row ry, column group cg of 4 outputs);
             // the 8 items of a row are adjacent threads (one 128-byte row of
             // 16-byte loads per quarter warp), blocks of 32 rows as quad_row
@@ -451,7 +471,7 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
                 const int ry = 32 * (it >> 8) + quad_row(it & 255), cg = it & 7;
                 if (ry >= RH) continue;
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                if (s >= rmin[ry] && s <= rmax[ry]) {
+                if (rmask[ry] & bit) {
                     const float4 *wI = reinterpret_cast<const float4 *>(RI + ry * RWp + 4 * cg);
                     const uint2 *wS = reinterpret_cast<const uint2 *>(RS + ry * RWp + 4 * cg);
                     float4 hi = Kr4[1];
@@ -468,17 +488,23 @@ __global__ void __launch_bounds__(256) stack_sep_kernel(StackArgs A)
                 reinterpret_cast<float4 *>(Rb + ry * kSW)[cg] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             }
             __syncthreads();
-            // column pass and the threshold test
+            // column pass and the threshold test, over the chunks of rows
+            // 4 g + 4 c .. + 3 that meet the rows holding the slice (the row
+            // sums are zero elsewhere)
             if (done != 0xF) {
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 const float *col = Rb + 4 * g * kSW + tx;
-                float4 hi = Kc4[1];
-                for (int c = 0; c < L.nCc; ++c) {
-                    const float *r = col + 4 * c * kSW;
-                    const float w[4] = {r[0], r[kSW], r[2 * kSW], r[3 * kSW]};
-                    const float4 lo4 = Kc4[-c];
-                    chunk_fma(acc, w, lo4, hi);
-                    hi = lo4;
+                const int x0 = srow[k][0] - 4 * g, x1 = srow[k][1] - 4 * g;
+                const int c0 = x0 > 0 ? x0 >> 2 : 0, c1 = x1 >= 0 ? min(L.nCc - 1, x1 >> 2) : -1;
+                if (c0 <= c1) {  // then 0 <= c0 <= nCc - 1: the taps Kc4[1 - c0] exist
+                    float4 hi = Kc4[1 - c0];
+                    for (int c = c0; c <= c1; ++c) {
+                        const float *r = col + 4 * c * kSW;
+                        const float w[4] = {r[0], r[kSW], r[2 * kSW], r[3 * kSW]};
+                        const float4 lo4 = Kc4[-c];
+                        chunk_fma(acc, w, lo4, hi);
+                        hi = lo4;
+                    }
                 }
 #pragma unroll
                 for (int o = 0; o < 4; ++o)
