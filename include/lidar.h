@@ -283,7 +283,10 @@ lidar_status_t lidar_simulate_echoes(lidar_t *lidar, const lidar_gbuffer_t *gbuf
  * beams can reach (the profile's support radius around their elevation) are
  * set up, so that with beams ordered by elevation the first launches start
  * early; the waveforms of each launch are copied back while later ones run.
- * The planes must hold U*V floats each, the outputs the sizes above. */
+ * The planes must hold U*V floats each, the outputs the sizes above.
+ * `wave` may be NULL: the echo-only form of lidar_simulate_echoes (waveforms
+ * kept in L2-sized slots, only echoes and counts copied back; a slot-claim
+ * timeout returns LIDAR_ETIMEOUT). */
 lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffer, const lidar_pose_t *pose,
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);

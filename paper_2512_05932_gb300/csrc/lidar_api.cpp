@@ -981,6 +981,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     const size_t pixels = (size_t)dg->U * dg->V;
     lidar_status_t st = ensure_scratch(l, pixels);
     if (st != LIDAR_OK) return st;
+    if (!wave && (st = ensure_slots(l, G, tc)) != LIDAR_OK) return st;  // echo-only form
     cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream[0], &l->d2h_stream[1], &l->aux_stream[0],
                                &l->aux_stream[1]};
     for (cudaStream_t *p : streams)
@@ -1030,6 +1031,15 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
 
     gbl::SetupArgs sa = setup_args(l, l, dg, R, l->d_rec, l->d_beams);
     gbl::FootprintArgs fa = frame_args(l, dg, sa);
+    if (!wave) {
+        // echo-only form: each CTA's waveforms stay in a slot of the pool
+        fa.slot_pool = l->d_slot_pool;
+        fa.slot_busy = l->d_slot_busy;
+        fa.n_slots = l->n_slots;
+        fa.slot_sms = kSlotSms;
+        fa.slots_per_sm = l->slots_per_sm;
+        fa.err = l->d_err;
+    }
     const float *mp[7];
     bool mapped = true;
     for (int i = 0; i < 7 && mapped; ++i) mapped = (mp[i] = mapped_host(src[i])) != nullptr;
@@ -1076,7 +1086,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             gbl::FootprintArgs fc = fa;
             fc.beams = l->d_beams + b0;
             fc.n_beams = nb;
-            fc.wave = l->d_wave + (size_t)b0 * l->n_bins;
+            fc.wave = wave ? l->d_wave + (size_t)b0 * l->n_bins : nullptr;
             fc.echoes = l->d_echo + (size_t)b0 * l->max_echoes;
             fc.counts = l->d_counts + b0;
             if ((e = cudaStreamWaitEvent(cs, l->setup_ev[b], 0)) != cudaSuccess)
@@ -1088,7 +1098,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             if ((e = cudaEventRecord(l->chunk_ev[i], cs)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventRecord");
-            if (nb > 0 && (e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
+            if (wave && nb > 0 && (e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
                                                (size_t)nb * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost, ds)) !=
                               cudaSuccess)
                 return cuda_fail(l, e, "result download");
@@ -1110,8 +1120,8 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             (e = cudaStreamWaitEvent(s, l->join_ev[k], 0)) != cudaSuccess)
             return cuda_fail(l, e, "pipeline join");
     if (ev2) cudaEventRecord(ev2, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
-    return LIDAR_OK;
+    return wave ? (((e = cudaStreamSynchronize(s)) != cudaSuccess) ? cuda_fail(l, e, "cudaStreamSynchronize") : LIDAR_OK)
+                : lidar_sync(l, s);  // also reports a slot-claim timeout of the echo-only form
 }
 
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
@@ -1122,7 +1132,7 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     if (st != LIDAR_OK) return st;
     double R[9];
     if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
-    if (!wave || !echoes || !counts) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    if (!echoes || !counts) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     size_t pixels = (size_t)g->U * g->V;
     cudaError_t e;
@@ -1134,12 +1144,13 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
             return cuda_fail(l, e, "cudaMalloc(G-buffer staging)");
         l->planes_cap = pixels;
     }
-    if (!l->d_wave) {
-        if ((e = cudaMalloc(&l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t))) != cudaSuccess ||
+    if (!l->d_echo) {
+        if ((e = cudaMalloc(&l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t))) != cudaSuccess ||
             (e = cudaMalloc(&l->d_counts, (size_t)l->n_beams * sizeof(int32_t))) != cudaSuccess)
             return cuda_fail(l, e, "cudaMalloc(output staging)");
     }
+    if (wave && !l->d_wave && (e = cudaMalloc(&l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float))) != cudaSuccess)
+        return cuda_fail(l, e, "cudaMalloc(output staging)");
     const float *src[7] = {g->range, g->nx, g->ny, g->nz, g->rho_d, g->retro, g->ambient};
     lidar_gbuffer_t dg = *g;
     float *dst[7];
@@ -1153,14 +1164,15 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
         for (int i = 0; i < 7; ++i)
             if ((e = cudaMemcpyAsync(dst[i], src[i], pixels * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
                 return cuda_fail(l, e, "G-buffer upload");
-        if ((st = enqueue(l, &dg, R, l->d_wave, l->d_echo, l->d_counts, s)) != LIDAR_OK) return st;
-        if ((e = cudaMemcpyAsync(wave, l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost,
-                                 s)) != cudaSuccess ||
+        if ((st = enqueue(l, &dg, R, wave ? l->d_wave : nullptr, l->d_echo, l->d_counts, s)) != LIDAR_OK) return st;
+        if ((wave && (e = cudaMemcpyAsync(wave, l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float),
+                                          cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
             (e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
                                  cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess)
             return cuda_fail(l, e, "result download");
+        if (!wave) return lidar_sync(l, s);  // also reports a slot-claim timeout of the echo-only form
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamSynchronize");
         return LIDAR_OK;
     }

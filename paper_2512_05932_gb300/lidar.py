@@ -665,18 +665,20 @@ class Lidar:
         return (torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, device=device),
                 torch.empty((self.n_beams,), dtype=torch.int32, device=device))
 
-    def simulate_host(self, geom, host_planes, pose=None, outputs=None, stream=None):
-        """Host-memory entry point: planes and outputs are (pinned) CPU tensors."""
+    def simulate_host(self, geom, host_planes, pose=None, outputs=None, stream=None, echo_only=False):
+        """Host-memory entry point: planes and outputs are (pinned) CPU tensors.
+        echo_only: no waveforms (outputs = (None, echoes, counts) or allocated)."""
         import torch
         if outputs is None:
-            outputs = (torch.empty((self.n_beams, self.n_bins), dtype=torch.float32, pin_memory=True),
+            outputs = (None if echo_only else
+                       torch.empty((self.n_beams, self.n_bins), dtype=torch.float32, pin_memory=True),
                        torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, pin_memory=True),
                        torch.empty((self.n_beams,), dtype=torch.int32, pin_memory=True))
         wave, echoes, counts = outputs
         g = make_gbuffer(geom, [p.data_ptr() for p in host_planes])
         s = (stream or torch.cuda.current_stream()).cuda_stream
-        lidar_simulate_host(self.handle, g, make_pose(np.eye(3) if pose is None else pose), wave.data_ptr(),
-                            echoes.data_ptr(), counts.data_ptr(), s)
+        lidar_simulate_host(self.handle, g, make_pose(np.eye(3) if pose is None else pose),
+                            wave.data_ptr() if wave is not None else None, echoes.data_ptr(), counts.data_ptr(), s)
         return wave, echoes, counts
 
     def close(self):

@@ -181,3 +181,28 @@ def test_echo_mode_rejects_unknown_values():
     with pytest.raises(lidar.LidarError, match="echo mode"):
         lidar.lidar_set_echo_mode(L.handle, 2)
     L.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "full_frame"])
+def test_host_entry_point_echo_only(case):
+    """lidar_simulate_host with no waveform output (the echo-only form through
+    the host entry point; the full frame takes the pipelined path): the echoes
+    and counts of lidar_simulate_echoes on the same frame, pinned or pageable
+    planes."""
+    w = S.tiny_case() if case == "tiny" else S.full_frame_boxes()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    planes = lidar.gbuffer_to_device(w.gbuffer)
+    ech_d, cnt_d = L.simulate_echoes(w.gbuffer, planes, w.pose)
+    torch.cuda.synchronize()
+    lidar.lidar_sync(L.handle, 0)
+    ech_d, cnt_d = ech_d.cpu().numpy(), cnt_d.cpu().numpy()
+    for pin in (True, False):
+        hp = [torch.from_numpy(np.ascontiguousarray(p)) for p in w.gbuffer.planes()]
+        if pin:
+            hp = [p.pin_memory() for p in hp]
+        outs = (None, torch.full((L.n_beams, L.max_echoes, 8), -5, dtype=torch.int32, pin_memory=True),
+                torch.full((L.n_beams,), -5, dtype=torch.int32, pin_memory=True))
+        wave, ech_h, cnt_h = L.simulate_host(w.gbuffer, hp, w.pose, outs, echo_only=True)
+        assert wave is None
+        assert_identical(ech_d, cnt_d, [(ech_h.numpy(), cnt_h.numpy())])
+    L.close()
