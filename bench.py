@@ -431,13 +431,8 @@ def run_gb300(args, rank, world, local_rank):
 
     def frame_host():
         if args.echo_only:
-            # pinned G-buffer up, echo-only call, echoes and counts down
-            for d, h in zip(planes, host_planes):
-                d.copy_(h, non_blocking=True)
-            L.simulate_echoes(w.gbuffer, planes, w.pose, (outs[1], outs[2]), stream)
-            host_out[1].copy_(outs[1], non_blocking=True)
-            host_out[2].copy_(outs[2], non_blocking=True)
-            stream.synchronize()
+            # the host entry point's echo-only form: pinned planes in, echoes and counts out
+            L.simulate_host(w.gbuffer, host_planes, w.pose, (None, host_out[1], host_out[2]), stream, echo_only=True)
         else:
             L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
 
