@@ -168,6 +168,17 @@ def test_full_frame_host_entry_point_matches_device_entry_point(host):
         assert (a == b).mean() >= 0.999, k
 
 
+def test_full_frame_host_entry_point_tensor_core_deposit():
+    """The pipelined host path with the tensor-core deposit (its own beams per
+    CTA and launch shape): the device entry point's results in the same mode."""
+    w = S.full_frame_boxes()
+    _, wave_d, ech_d, cnt_d = run_gpu(w, deposit=1)
+    _, wave_h, ech_h, cnt_h = run_gpu(w, host="pinned", deposit=1)
+    rel = np.linalg.norm(wave_h - wave_d, axis=1) / np.maximum(np.linalg.norm(wave_d, axis=1), 1e-30)
+    assert rel.max() <= 1e-5, rel.max()
+    assert (cnt_h == cnt_d).mean() >= 0.999
+
+
 def test_ragged_large_frame_host_entry_point():
     """A frame whose rows do not split evenly into the host path's upload bands
     and whose beams do not fill the last group (25 597 beams on 2000x999): the
