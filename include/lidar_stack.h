@@ -1,5 +1,5 @@
 /*
- * Range stacking (the paper's Alg. 2, Sec. II-D): a pixel-dense image of the
+ * Range stacking (the paper's Alg. 2, Sec. II-C): a pixel-dense image of the
  * nearest range slice whose kernel-weighted intensity reaches a threshold.
  *
  * Every pixel is treated as the centre of a beam. Per-pixel inputs come from
@@ -13,11 +13,16 @@
  * value. Result per pixel: the smallest such s and its value, or s_max and 0.
  * s_max = floor(r_max / dr).
  *
- * The GPU evaluates each output pixel's stencil once per pass, keeping the 24
- * nearest slices it meets with their sums in registers; a pixel whose nearest
- * 24 slices all stay below the threshold while more slices were present is
- * evaluated again above them. Empty slices cost nothing, and so do slices too
- * weak to reach the threshold anywhere in a 32x8-pixel output tile.
+ * The GPU takes the slices present in each 32x32-pixel output tile's region
+ * nearest first and convolves each one densely over the tile, visiting only
+ * the kernel rows whose region rows hold pixels of the slice, until every
+ * output of the tile has its answer; the result is the same as the far-to-near
+ * sweep's. Empty slices cost nothing, and so do slices too weak to reach the
+ * threshold anywhere in the tile. Kernels whose tile layout does not fit
+ * shared memory (square kernels from 119x119) are evaluated instead by walking
+ * each output's stencil once per pass while keeping the 16 nearest slices met
+ * with their sums in registers (a pass repeats above them while a nearer
+ * answer is still possible).
  */
 #ifndef LIDAR_STACK_H
 #define LIDAR_STACK_H
