@@ -69,15 +69,18 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
     sincosf(el, &se, &ce);
     // exact solid angle of the cell: daz (sin(el + del/2) - sin(el - del/2))
     float domega = 2.f * A.daz * ce * A.sv;
+    // all seven planes are loaded up front, so that their latencies overlap
+    // (a sky pixel reads five values it does not use)
     float L = A.amb[idx];
     float a = isfinite(L) ? L * domega : 0.f;
     float rr = A.range[idx];
+    const float nx = A.nx[idx], ny = A.ny[idx], nz = A.nz[idx];
+    const float rho = A.rho[idx], retro = A.retro[idx];
     uint32_t kab = kNoDeposit, kq = kNoDeposit;
     float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, cr = 0.f;
     if (isfinite(rr) && rr > 0.f) {
-        float nx = A.nx[idx], ny = A.ny[idx], nz = A.nz[idx];
         float dn = ce * (ca * nx + sa * ny) + se * nz;
-        float beta = A.rho[idx] * (1.f / CUDART_PI_F) + A.retro[idx];
+        float beta = rho * (1.f / CUDART_PI_F) + retro;
         // rho_hat d omega = beta |cos theta_i| / R^2 * d omega
         float w = beta * fabsf(dn) / (rr * rr) * domega;
         // range interval: plane through the hit point, extrapolated to the four
@@ -156,7 +159,10 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
 // setup: per-beam parameters (FP64)
 // --------------------------------------------------------------------------
 
-__device__ void setup_beam(const SetupArgs &A, int b)
+// Not inlined: its FP64 work needs more registers than the per-pixel path, and
+// inlined it would set the register count (and so the occupancy) of the whole
+// setup kernel; as a call it spills inside itself instead.
+__device__ __noinline__ void setup_beam(const SetupArgs &A, int b)
 {
     const int src = A.beam_ids ? A.beam_ids[b] : b;
     double d[3] = {A.dirs[3 * src], A.dirs[3 * src + 1], A.dirs[3 * src + 2]};
@@ -258,23 +264,28 @@ __device__ void setup_beam(const SetupArgs &A, int b)
     A.beams[b] = P;
 }
 
-__global__ void __launch_bounds__(256) setup_kernel(SetupArgs A)
+// Blocks [0, gridDim.x - pix_blocks) set up the beams, the rest the pixels: the
+// beams' FP64 blocks start first and run beside the pixel blocks instead of
+// trailing them. Six blocks per SM (40 registers) for the memory-latency-bound
+// pixel path.
+__global__ void __launch_bounds__(256, 6) setup_kernel(SetupArgs A)
 {
-    if ((int)blockIdx.x < A.pix_blocks) {
+    const int beam_blocks = (int)gridDim.x - A.pix_blocks;
+    if ((int)blockIdx.x < beam_blocks) {
+        int b = blockIdx.x * blockDim.x + threadIdx.x;
+        if (b < A.n_beams) setup_beam(A, b);
+    } else {
         const int n = (int)A.pix_end;
-        for (int idx = (int)A.pix_begin + blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+        for (int idx = (int)A.pix_begin + ((int)blockIdx.x - beam_blocks) * blockDim.x + threadIdx.x; idx < n;
              idx += A.pix_blocks * blockDim.x)
             setup_pixel(A, idx);
-    } else {
-        int b = (blockIdx.x - A.pix_blocks) * blockDim.x + threadIdx.x;
-        if (b < A.n_beams) setup_beam(A, b);
     }
 }
 
 // Batched setup: frame f owns pixel blocks [pix_blk[f], pix_blk[f+1]) and beam
 // blocks [beam_blk[f], beam_blk[f+1]) (pixel blocks first). Block 0 also resets
 // the work counter of the batched footprint kernel that follows on the stream.
-__global__ void __launch_bounds__(256) setup_batch_kernel(const SetupArgs *frames, const int *pix_blk,
+__global__ void __launch_bounds__(256, 6) setup_batch_kernel(const SetupArgs *frames, const int *pix_blk,
                                                           const int *beam_blk, int n_frames, int *counter)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
