@@ -291,6 +291,34 @@ lidar_status_t lidar_simulate_host(lidar_t *lidar, const lidar_gbuffer_t *gbuffe
                                    float *out_waveforms, lidar_echo_t *out_echoes, int32_t *out_counts,
                                    void *stream);
 
+/* A sequence of frames from host memory (Alg. 1 per frame, as a sensor
+ * stream of scans): frame f is described by gbuffer[f] and pose[f] (host
+ * planes, as for lidar_simulate_host) and its results go to out_waveforms[f]
+ * ([n_beams][n_bins] floats), out_echoes[f] and out_counts[f]. Each frame's
+ * results are those of lidar_simulate_host on the same inputs (up to the order
+ * of the FP32 deposit additions); the difference is that consecutive frames
+ * overlap: frames alternate between two sets of library-owned device buffers,
+ * so frame f + 1 is read over the host link and set up while frame f's beams
+ * run and its waveforms come back, and frame f + 2 waits only for frame f.
+ *   - Frames of fewer than 1216 beam groups, and a single frame, are run one
+ *     after the other by lidar_simulate_host.
+ *   - The frames may differ in size and field of view (each passes the checks
+ *     of lidar_simulate_host); the second buffer set is allocated (cudaMalloc)
+ *     on first use and grown to the largest frame.
+ *   - Consecutive frames must not share output arrays (they are written
+ *     concurrently); frames f and f + 2 may (f + 2 writes after f).
+ *   - out_waveforms may be NULL: the echo-only form for every frame.
+ *   - Per-kernel timing (lidar_profile_enable) is not recorded.
+ * The pipeline starts after the work already queued on `stream` and the call
+ * returns once every frame's results are in host memory. Errors: LIDAR_EINVAL
+ * for n_frames < 0, a NULL array or output pointer, or a frame that fails the
+ * checks of lidar_simulate_host (nothing is enqueued then); CUDA errors as for
+ * lidar_simulate_host. n_frames == 0 does nothing. */
+lidar_status_t lidar_simulate_host_frames(lidar_t *lidar, int n_frames, const lidar_gbuffer_t *gbuffer,
+                                          const lidar_pose_t *pose, float *const *out_waveforms,
+                                          lidar_echo_t *const *out_echoes, int32_t *const *out_counts,
+                                          void *stream);
+
 /* Same computation as lidar_simulate, for callers that cannot let the library
  * allocate device memory during a call: a host whose memory pool has already
  * reserved the GPU, or a real-time loop that must not allocate once running

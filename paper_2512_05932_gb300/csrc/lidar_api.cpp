@@ -346,6 +346,12 @@ void free_all(lidar_t *l)
     cudaFree(l->d_wave);
     cudaFree(l->d_echo);
     cudaFree(l->d_counts);
+    cudaFree(l->d_rec2);
+    cudaFree(l->d_beams2);
+    cudaFree(l->d_planes2);
+    cudaFree(l->d_wave2);
+    cudaFree(l->d_echo2);
+    cudaFree(l->d_counts2);
     cudaFree(l->d_slot_pool);
     cudaFree(l->d_slot_busy);
     cudaFree(l->d_err);
@@ -363,6 +369,9 @@ void free_all(lidar_t *l)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t &ev : l->join_ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto &set : l->done_ev)
+        for (cudaEvent_t &ev : set)
+            if (ev) cudaEventDestroy(ev);
     if (l->start_ev) cudaEventDestroy(l->start_ev);
     tail_free(l);
 }
@@ -963,25 +972,34 @@ static const float *mapped_host(const float *p)
 // between aux_stream[0] and [1] (one launch's CTAs fill the SMs the previous
 // one is leaving), each launched once the rows its beams can reach are set up;
 // each launch's waveforms go down on d2h_stream while later ones run (echoes
-// and counts at the end), and the last launch holds 5 % of the beams so that
-// little copying is left at the end. The host enqueues in that order (band,
-// its set-up, the launches it completes), so the first launches are queued
-// before the last bands' copies. Planes in page-locked, device-mapped host
-// memory are not copied at all: the set-up kernel reads each band over the
-// host link where it lies.
-static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t *dg, const double R[9],
-                                              const float *const src[7], float *const dst[7], float *wave,
-                                              lidar_echo_t *echoes, int32_t *counts, cudaStream_t s)
+// and counts at the end), and the last two launches hold 6 % and 3 % of the
+// beams so that little copying is left at the end. The host enqueues in that
+// order (band, its set-up, the launches it completes), so the first launches
+// are queued before the last bands' copies. Planes in page-locked,
+// device-mapped host memory are not copied at all: the set-up kernel reads
+// each band over the host link where it lies.
+
+// The device buffers one frame of the host pipeline uses.
+struct HostFrameBufs {
+    float4 *rec;
+    gbl::BeamParam *beams;
+    float *wave;
+    lidar_echo_t *echo;
+    int32_t *counts;
+};
+
+// The pipeline's six streams, in the order of the join and done events.
+static void pipeline_streams(lidar_t *l, cudaStream_t out[6])
+{
+    out[0] = l->aux_stream[0]; out[1] = l->aux_stream[1];
+    out[2] = l->d2h_stream[0]; out[3] = l->d2h_stream[1];
+    out[4] = l->setup_stream; out[5] = l->copy_stream;
+}
+
+// Creates the pipeline's streams and events on first use.
+static lidar_status_t ensure_pipeline(lidar_t *l)
 {
     cudaError_t e;
-    const bool tc = l->deposit != 0;
-    const int G = tc ? l->G_tc : l->G;
-    const int ng = (l->n_beams + G - 1) / G;
-    const int K = kHostChunks, NB = kHostBands;
-    const size_t pixels = (size_t)dg->U * dg->V;
-    lidar_status_t st = ensure_scratch(l, pixels);
-    if (st != LIDAR_OK) return st;
-    if (!wave && (st = ensure_slots(l, G, tc)) != LIDAR_OK) return st;  // echo-only form
     cudaStream_t *streams[] = {&l->copy_stream, &l->d2h_stream[0], &l->d2h_stream[1], &l->aux_stream[0],
                                &l->aux_stream[1]};
     for (cudaStream_t *p : streams)
@@ -993,12 +1011,58 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             (e = cudaStreamCreateWithPriority(&l->setup_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess)
             return cuda_fail(l, e, "cudaStreamCreate(set-up stream)");
     }
-    std::vector<cudaEvent_t *> evs = {&l->start_ev, &l->join_ev[0], &l->join_ev[1], &l->join_ev[2], &l->join_ev[3]};
-    for (int i = 0; i < K; ++i) evs.push_back(&l->chunk_ev[i]);
-    for (int i = 0; i < NB; ++i) { evs.push_back(&l->band_ev[i]); evs.push_back(&l->setup_ev[i]); }
+    std::vector<cudaEvent_t *> evs = {&l->start_ev};
+    for (cudaEvent_t &ev : l->join_ev) evs.push_back(&ev);
+    for (auto &set : l->done_ev)
+        for (cudaEvent_t &ev : set) evs.push_back(&ev);
+    for (int i = 0; i < kHostChunks; ++i) evs.push_back(&l->chunk_ev[i]);
+    for (int i = 0; i < kHostBands; ++i) { evs.push_back(&l->band_ev[i]); evs.push_back(&l->setup_ev[i]); }
     for (cudaEvent_t *ev : evs)
         if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(l, e, "cudaEventCreate(host pipeline)");
+    return LIDAR_OK;
+}
+
+// Every stream of the pipeline starts after the caller's earlier work on `s`.
+static lidar_status_t pipeline_start(lidar_t *l, cudaStream_t s)
+{
+    cudaError_t e;
+    cudaStream_t st[6];
+    pipeline_streams(l, st);
+    if ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
+    for (cudaStream_t x : st)
+        if ((e = cudaStreamWaitEvent(x, l->start_ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
+    return LIDAR_OK;
+}
+
+// Records ev[k] at the current end of pipeline stream k; if `join` is set,
+// stream `s` (which may be the default stream, 0) waits for all six.
+static lidar_status_t pipeline_mark(lidar_t *l, cudaEvent_t ev[6], bool join, cudaStream_t s)
+{
+    cudaError_t e;
+    cudaStream_t st[6];
+    pipeline_streams(l, st);
+    for (int k = 0; k < 6; ++k)
+        if ((e = cudaEventRecord(ev[k], st[k])) != cudaSuccess ||
+            (join && (e = cudaStreamWaitEvent(s, ev[k], 0)) != cudaSuccess))
+            return cuda_fail(l, e, "pipeline join");
+    return LIDAR_OK;
+}
+
+// Enqueues one large frame on the pipeline streams, using the buffers B (no
+// start or join: see simulate_host_pipelined and lidar_simulate_host_frames).
+// dg holds the device staging planes of B, src the caller's host planes.
+// prof: record the frame's per-kernel timing events (lidar_profile_enable).
+static lidar_status_t enqueue_host_frame(lidar_t *l, const lidar_gbuffer_t *dg, const double R[9],
+                                         const float *const src[7], float *const dst[7], const HostFrameBufs &B,
+                                         float *wave, lidar_echo_t *echoes, int32_t *counts, bool prof,
+                                         cudaEvent_t *end_ev)
+{
+    cudaError_t e;
+    const bool tc = l->deposit != 0;
+    const int G = tc ? l->G_tc : l->G;
+    const int ng = (l->n_beams + G - 1) / G;
+    const int K = kHostChunks, NB = kHostBands;
 
     // launch sizes: 91 % of the groups in K - 2 equal launches, then 6 % and
     // 3 %, so that little copying is left when the last launches end
@@ -1029,8 +1093,10 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         chunk_band[i] = band;
     }
 
-    gbl::SetupArgs sa = setup_args(l, l, dg, R, l->d_rec, l->d_beams);
+    gbl::SetupArgs sa = setup_args(l, l, dg, R, B.rec, B.beams);
     gbl::FootprintArgs fa = frame_args(l, dg, sa);
+    fa.rec = B.rec;
+    fa.beams = B.beams;
     if (!wave) {
         // echo-only form: each CTA's waveforms stay in a slot of the pool
         fa.slot_pool = l->d_slot_pool;
@@ -1048,16 +1114,13 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
         sa.rho = mp[4]; sa.retro = mp[5]; sa.amb = mp[6];
     }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-    if (l->prof) {
+    if (prof && l->prof) {
         size_t mark = l->ev_used;
         ev0 = next_event(l); ev1 = next_event(l); ev2 = next_event(l);
         if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
     }
+    *end_ev = ev2;  // recorded by the caller once its stream has joined the pipeline
     cudaStream_t ss = l->setup_stream, us = l->copy_stream;
-    // every stream of the pipeline starts after the caller's earlier work on `s`
-    if ((e = cudaEventRecord(l->start_ev, s)) != cudaSuccess) return cuda_fail(l, e, "cudaEventRecord");
-    for (cudaStream_t x : {ss, us, l->d2h_stream[0], l->d2h_stream[1], l->aux_stream[0], l->aux_stream[1]})
-        if ((e = cudaStreamWaitEvent(x, l->start_ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
     if (ev0) cudaEventRecord(ev0, ss);
     gbl::SetupArgs sb = sa;
     sb.pix_blocks = 0;  // the beams' set-up (reads no plane)
@@ -1084,11 +1147,11 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             const int i = next, b0 = bounds[i], nb = bounds[i + 1] - bounds[i];
             cudaStream_t cs = l->aux_stream[i & 1];
             gbl::FootprintArgs fc = fa;
-            fc.beams = l->d_beams + b0;
+            fc.beams = B.beams + b0;
             fc.n_beams = nb;
-            fc.wave = wave ? l->d_wave + (size_t)b0 * l->n_bins : nullptr;
-            fc.echoes = l->d_echo + (size_t)b0 * l->max_echoes;
-            fc.counts = l->d_counts + b0;
+            fc.wave = wave ? B.wave + (size_t)b0 * l->n_bins : nullptr;
+            fc.echoes = B.echo + (size_t)b0 * l->max_echoes;
+            fc.counts = B.counts + b0;
             if ((e = cudaStreamWaitEvent(cs, l->setup_ev[b], 0)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaStreamWaitEvent");
             if (nb > 0 && (e = gbl::launch_footprint(l->kind, G, tc, l->threads, tc ? l->smem_tc : l->smem, fc, cs)) !=
@@ -1098,7 +1161,7 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
             if ((e = cudaEventRecord(l->chunk_ev[i], cs)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess)
                 return cuda_fail(l, e, "cudaEventRecord");
-            if (wave && nb > 0 && (e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, l->d_wave + (size_t)b0 * l->n_bins,
+            if (wave && nb > 0 && (e = cudaMemcpyAsync(wave + (size_t)b0 * l->n_bins, B.wave + (size_t)b0 * l->n_bins,
                                                (size_t)nb * l->n_bins * sizeof(float), cudaMemcpyDeviceToHost, ds)) !=
                               cudaSuccess)
                 return cuda_fail(l, e, "result download");
@@ -1108,20 +1171,108 @@ static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t 
     cudaStream_t ds = l->d2h_stream[0];
     for (int i = 1; i < K; i += 2)
         if ((e = cudaStreamWaitEvent(ds, l->chunk_ev[i], 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
-    if ((e = cudaMemcpyAsync(echoes, l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
+    if ((e = cudaMemcpyAsync(echoes, B.echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t),
                              cudaMemcpyDeviceToHost, ds)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(counts, l->d_counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, ds)) !=
+        (e = cudaMemcpyAsync(counts, B.counts, (size_t)l->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost, ds)) !=
             cudaSuccess)
         return cuda_fail(l, e, "result download");
-    // `s` joins the pipeline
-    cudaStream_t tails[4] = {l->aux_stream[0], l->aux_stream[1], l->d2h_stream[0], l->d2h_stream[1]};
-    for (int k = 0; k < 4; ++k)
-        if ((e = cudaEventRecord(l->join_ev[k], tails[k])) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s, l->join_ev[k], 0)) != cudaSuccess)
-            return cuda_fail(l, e, "pipeline join");
-    if (ev2) cudaEventRecord(ev2, s);
+    return LIDAR_OK;
+}
+
+// One large frame of lidar_simulate_host: the pipeline starts after the
+// caller's earlier work on `s`, runs the frame on the first buffer set, and `s`
+// joins the ends of all six streams (the set-up and upload streams too, so
+// that nothing reads the caller's planes after the return).
+static lidar_status_t simulate_host_pipelined(lidar_t *l, const lidar_gbuffer_t *dg, const double R[9],
+                                              const float *const src[7], float *const dst[7], float *wave,
+                                              lidar_echo_t *echoes, int32_t *counts, cudaStream_t s)
+{
+    cudaError_t e;
+    const bool tc = l->deposit != 0;
+    lidar_status_t st = ensure_scratch(l, (size_t)dg->U * dg->V);
+    if (st != LIDAR_OK) return st;
+    if (!wave && (st = ensure_slots(l, tc ? l->G_tc : l->G, tc)) != LIDAR_OK) return st;  // echo-only form
+    if ((st = ensure_pipeline(l)) != LIDAR_OK || (st = pipeline_start(l, s)) != LIDAR_OK) return st;
+    const HostFrameBufs B{l->d_rec, l->d_beams, l->d_wave, l->d_echo, l->d_counts};
+    cudaEvent_t end_ev = nullptr;
+    if ((st = enqueue_host_frame(l, dg, R, src, dst, B, wave, echoes, counts, true, &end_ev)) != LIDAR_OK) return st;
+    if ((st = pipeline_mark(l, l->join_ev, true, s)) != LIDAR_OK) return st;
+    if (end_ev) cudaEventRecord(end_ev, s);
     return wave ? (((e = cudaStreamSynchronize(s)) != cudaSuccess) ? cuda_fail(l, e, "cudaStreamSynchronize") : LIDAR_OK)
                 : lidar_sync(l, s);  // also reports a slot-claim timeout of the echo-only form
+}
+
+// The caller's host planes of frame g (src), the staging planes of a buffer
+// set (dst), and the frame's G-buffer description over the staging planes (dg).
+static void host_frame_planes(const lidar_gbuffer_t *g, float *planes, const float *src[7], float *dst[7],
+                              lidar_gbuffer_t *dg)
+{
+    const size_t pixels = (size_t)g->U * g->V;
+    const float *in[7] = {g->range, g->nx, g->ny, g->nz, g->rho_d, g->retro, g->ambient};
+    for (int i = 0; i < 7; ++i) {
+        src[i] = in[i];
+        dst[i] = planes + (size_t)i * pixels;
+    }
+    *dg = *g;
+    dg->range = dst[0]; dg->nx = dst[1]; dg->ny = dst[2]; dg->nz = dst[3];
+    dg->rho_d = dst[4]; dg->retro = dst[5]; dg->ambient = dst[6];
+}
+
+// Frames of at least 8 x 152 beam groups (8 footprint launches of at least one
+// CTA per SM) take the pipelined host path; smaller ones one pass on the
+// caller's stream.
+static bool pipelined_frame(const lidar_t *l)
+{
+    const int G = l->deposit != 0 ? l->G_tc : l->G;
+    return (l->n_beams + G - 1) / G >= 8 * 152;
+}
+
+// Device buffers of the host entry points' buffer set `set` (0: the frame
+// buffers of lidar_simulate_host; 1: the second set of
+// lidar_simulate_host_frames) for frames of up to `pixels` pixels: staging
+// planes, records, beam parameters, results (waveforms only if `wave`).
+static lidar_status_t ensure_host_set(lidar_t *l, int set, size_t pixels, bool wave, HostFrameBufs *B, float **planes)
+{
+    cudaError_t e;
+    float *&pl = set ? l->d_planes2 : l->d_planes;
+    size_t &pcap = set ? l->planes2_cap : l->planes_cap;
+    if (pixels > pcap) {
+        cudaFree(pl);
+        pl = nullptr;
+        pcap = 0;
+        if ((e = cudaMalloc(&pl, 7 * pixels * sizeof(float))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(G-buffer staging)");
+        pcap = pixels;
+    }
+    lidar_echo_t *&echo = set ? l->d_echo2 : l->d_echo;
+    int32_t *&counts = set ? l->d_counts2 : l->d_counts;
+    if (!echo) {
+        if ((e = cudaMalloc(&echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t))) != cudaSuccess ||
+            (e = cudaMalloc(&counts, (size_t)l->n_beams * sizeof(int32_t))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(output staging)");
+    }
+    float *&wv = set ? l->d_wave2 : l->d_wave;
+    if (wave && !wv && (e = cudaMalloc(&wv, (size_t)l->n_beams * l->n_bins * sizeof(float))) != cudaSuccess)
+        return cuda_fail(l, e, "cudaMalloc(output staging)");
+    if (set == 0) {
+        lidar_status_t st = ensure_scratch(l, pixels);
+        if (st != LIDAR_OK) return st;
+    } else {
+        if (pixels > l->rec2_cap) {
+            cudaFree(l->d_rec2);
+            l->d_rec2 = nullptr;
+            l->rec2_cap = 0;
+            if ((e = cudaMalloc(&l->d_rec2, pixels * 2 * sizeof(float4))) != cudaSuccess)
+                return cuda_fail(l, e, "cudaMalloc(per-pixel records)");
+            l->rec2_cap = pixels;
+        }
+        if (!l->d_beams2 &&
+            (e = cudaMalloc(&l->d_beams2, (size_t)l->n_beams * sizeof(gbl::BeamParam))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(beam parameters)");
+    }
+    *B = HostFrameBufs{set ? l->d_rec2 : l->d_rec, set ? l->d_beams2 : l->d_beams, wv, echo, counts};
+    *planes = pl;
+    return LIDAR_OK;
 }
 
 lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,
@@ -1136,30 +1287,14 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
     cudaStream_t s = (cudaStream_t)stream;
     size_t pixels = (size_t)g->U * g->V;
     cudaError_t e;
-    if (pixels > l->planes_cap) {
-        cudaFree(l->d_planes);
-        l->d_planes = nullptr;
-        l->planes_cap = 0;
-        if ((e = cudaMalloc(&l->d_planes, 7 * pixels * sizeof(float))) != cudaSuccess)
-            return cuda_fail(l, e, "cudaMalloc(G-buffer staging)");
-        l->planes_cap = pixels;
-    }
-    if (!l->d_echo) {
-        if ((e = cudaMalloc(&l->d_echo, (size_t)l->n_beams * l->max_echoes * sizeof(lidar_echo_t))) != cudaSuccess ||
-            (e = cudaMalloc(&l->d_counts, (size_t)l->n_beams * sizeof(int32_t))) != cudaSuccess)
-            return cuda_fail(l, e, "cudaMalloc(output staging)");
-    }
-    if (wave && !l->d_wave && (e = cudaMalloc(&l->d_wave, (size_t)l->n_beams * l->n_bins * sizeof(float))) != cudaSuccess)
-        return cuda_fail(l, e, "cudaMalloc(output staging)");
-    const float *src[7] = {g->range, g->nx, g->ny, g->nz, g->rho_d, g->retro, g->ambient};
-    lidar_gbuffer_t dg = *g;
+    HostFrameBufs B0;
+    float *planes0 = nullptr;
+    if ((st = ensure_host_set(l, 0, pixels, wave != nullptr, &B0, &planes0)) != LIDAR_OK) return st;
+    const float *src[7];
     float *dst[7];
-    for (int i = 0; i < 7; ++i) dst[i] = l->d_planes + (size_t)i * pixels;
-    dg.range = dst[0]; dg.nx = dst[1]; dg.ny = dst[2]; dg.nz = dst[3];
-    dg.rho_d = dst[4]; dg.retro = dst[5]; dg.ambient = dst[6];
-    const int G = l->deposit != 0 ? l->G_tc : l->G;
-    const int ng = (l->n_beams + G - 1) / G;
-    if (ng < 8 * 152) {
+    lidar_gbuffer_t dg;
+    host_frame_planes(g, planes0, src, dst, &dg);
+    if (!pipelined_frame(l)) {
         // small frame: one pass on `stream`
         for (int i = 0; i < 7; ++i)
             if ((e = cudaMemcpyAsync(dst[i], src[i], pixels * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -1177,6 +1312,67 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
         return LIDAR_OK;
     }
     return simulate_host_pipelined(l, &dg, R, src, dst, wave, echoes, counts, s);
+}
+
+lidar_status_t lidar_simulate_host_frames(lidar_t *l, int n_frames, const lidar_gbuffer_t *g,
+                                          const lidar_pose_t *pose, float *const *wave, lidar_echo_t *const *echoes,
+                                          int32_t *const *counts, void *stream)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (n_frames < 0) return fail(l, LIDAR_EINVAL, "n_frames < 0");
+    if (n_frames == 0) return LIDAR_OK;
+    if (!g || !pose || !echoes || !counts) return fail(l, LIDAR_EINVAL, "frame array is NULL");
+    std::vector<double> Rs(9 * (size_t)n_frames);
+    size_t max_pixels = 0;
+    lidar_status_t st;
+    for (int f = 0; f < n_frames; ++f) {
+        if ((st = check_gbuffer(l, g + f)) != LIDAR_OK || (st = check_pose(l, pose + f, Rs.data() + 9 * f)) != LIDAR_OK)
+            return st;
+        if (!echoes[f] || !counts[f] || (wave && !wave[f])) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+        max_pixels = std::max(max_pixels, (size_t)g[f].U * g[f].V);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!pipelined_frame(l) || n_frames == 1) {
+        // small frames (one pass each) or a single frame: lidar_simulate_host per frame
+        for (int f = 0; f < n_frames; ++f)
+            if ((st = lidar_simulate_host(l, g + f, pose + f, wave ? wave[f] : nullptr, echoes[f], counts[f], stream)) !=
+                LIDAR_OK)
+                return st;
+        return LIDAR_OK;
+    }
+    const bool tc = l->deposit != 0;
+    HostFrameBufs B[2];
+    float *planes[2];
+    for (int p = 0; p < 2; ++p)
+        if ((st = ensure_host_set(l, p, max_pixels, wave != nullptr, &B[p], &planes[p])) != LIDAR_OK) return st;
+    if (!wave && (st = ensure_slots(l, tc ? l->G_tc : l->G, tc)) != LIDAR_OK) return st;  // echo-only form
+    if ((st = ensure_pipeline(l)) != LIDAR_OK || (st = pipeline_start(l, s)) != LIDAR_OK) return st;
+    cudaError_t e;
+    cudaStream_t streams[6];
+    pipeline_streams(l, streams);
+    for (int f = 0; f < n_frames; ++f) {
+        const int p = f & 1;
+        if (f >= 2)
+            // frame f - 2 used the same buffers: every stream waits for all of it
+            for (cudaStream_t x : streams)
+                for (cudaEvent_t ev : l->done_ev[p])
+                    if ((e = cudaStreamWaitEvent(x, ev, 0)) != cudaSuccess) return cuda_fail(l, e, "cudaStreamWaitEvent");
+        const float *src[7];
+        float *dst[7];
+        lidar_gbuffer_t dg;
+        host_frame_planes(g + f, planes[p], src, dst, &dg);
+        cudaEvent_t end_ev = nullptr;
+        if ((st = enqueue_host_frame(l, &dg, Rs.data() + 9 * f, src, dst, B[p], wave ? wave[f] : nullptr, echoes[f],
+                                     counts[f], false, &end_ev)) != LIDAR_OK ||
+            (st = pipeline_mark(l, l->done_ev[p], false, s)) != LIDAR_OK)
+            return st;
+    }
+    // `s` joins the last frame of each set
+    for (int p = 0; p < 2; ++p)
+        for (cudaEvent_t ev : l->done_ev[p])
+            if ((e = cudaStreamWaitEvent(s, ev, 0)) != cudaSuccess) return cuda_fail(l, e, "pipeline join");
+    return wave ? (((e = cudaStreamSynchronize(s)) != cudaSuccess) ? cuda_fail(l, e, "cudaStreamSynchronize") : LIDAR_OK)
+                : lidar_sync(l, s);  // also reports a slot-claim timeout of the echo-only form
 }
 
 lidar_status_t lidar_simulate_noalloc(lidar_t *l, const lidar_gbuffer_t *g, const lidar_pose_t *pose, float *wave,

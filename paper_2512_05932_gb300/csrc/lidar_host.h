@@ -62,12 +62,25 @@ struct lidar {
     // highest priority (setup_ev[b]: band b set up), footprint launches on
     // aux_stream[0] and [1] (chunk_ev[i]: launch i finished), result copies on
     // d2h_stream[0] and [1] (two copy engines); start_ev: the caller's earlier work done; join_ev: the
-    // streams the caller's stream joins at the end.
+    // ends of the six pipeline streams, which the caller's stream joins.
     cudaStream_t copy_stream = nullptr, d2h_stream[2] = {nullptr, nullptr}, setup_stream = nullptr;
     cudaStream_t aux_stream[2] = {nullptr, nullptr};
     cudaEvent_t chunk_ev[8] = {};
     cudaEvent_t band_ev[8] = {}, setup_ev[8] = {};
-    cudaEvent_t start_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t start_ev = nullptr, join_ev[6] = {};
+    // lidar_simulate_host_frames: frames of odd index use this second set of
+    // frame buffers (records, beam parameters, staged planes, results), so
+    // that a frame is set up while the previous one runs; done_ev[p]: the ends
+    // of the six pipeline streams after the last frame that used set p.
+    float4 *d_rec2 = nullptr;
+    size_t rec2_cap = 0;  // pixels
+    gbl::BeamParam *d_beams2 = nullptr;
+    float *d_planes2 = nullptr;
+    size_t planes2_cap = 0;  // pixels
+    float *d_wave2 = nullptr;
+    lidar_echo_t *d_echo2 = nullptr;
+    int32_t *d_counts2 = nullptr;
+    cudaEvent_t done_ev[2][6] = {};
     // echo-only waveform pool (lidar_simulate_echoes): n_slots slots of
     // slot_floats / n_slots floats, their busy flags, and an error word
     float *d_slot_pool = nullptr;

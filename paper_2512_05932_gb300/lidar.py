@@ -89,7 +89,8 @@ ECHO_DTYPE = np.dtype([("range_m", "f4"), ("epw_m", "f4"), ("intensity", "f4"), 
 assert ECHO_DTYPE.itemsize == C.sizeof(lidar_echo_t) == 32
 
 # exported symbols (every function declared in include/lidar.h)
-SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_reproject_pinhole", "lidar_simulate_host", "lidar_simulate_noalloc",
+SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_reproject_pinhole", "lidar_simulate_host",
+           "lidar_simulate_host_frames", "lidar_simulate_noalloc",
            "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
            "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_set_echo_mode", "lidar_profile_enable",
@@ -140,6 +141,9 @@ def load(path: str = LIB_PATH):
     lib.lidar_simulate_host.restype = C.c_int
     lib.lidar_simulate_host.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
+    lib.lidar_simulate_host_frames.restype = C.c_int
+    lib.lidar_simulate_host_frames.argtypes = [C.c_void_p, C.c_int, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
+                                               C.c_void_p, C.c_void_p, C.c_void_p]
     lib.lidar_simulate_noalloc.restype = C.c_int
     lib.lidar_simulate_noalloc.argtypes = [C.c_void_p, P(lidar_gbuffer_t), P(lidar_pose_t), C.c_void_p,
                                            P(lidar_echoes_t), C.c_void_p]
@@ -354,6 +358,23 @@ def lidar_simulate_host(handle, gbuffer: lidar_gbuffer_t, pose: lidar_pose_t, ou
                         out_echoes: int, out_counts: int, stream: int = 0) -> None:
     st = load().lidar_simulate_host(handle, C.byref(gbuffer), C.byref(pose), out_waveforms, out_echoes,
                                     out_counts, stream)
+    _check(st, handle)
+
+
+def lidar_simulate_host_frames(handle, gbuffers, poses, out_waveforms, out_echoes, out_counts,
+                               stream: int = 0) -> None:
+    """gbuffers, poses: sequences of lidar_gbuffer_t / lidar_pose_t; out_*:
+    sequences of host addresses, one per frame (out_waveforms None: echo-only)."""
+    n = len(gbuffers)
+    if not (len(poses) == len(out_echoes) == len(out_counts) == n) or (
+            out_waveforms is not None and len(out_waveforms) != n):
+        raise ValueError("one pose and one output set per frame")
+    garr = (lidar_gbuffer_t * max(n, 1))(*gbuffers)
+    parr = (lidar_pose_t * max(n, 1))(*poses)
+    ptrs = lambda xs: (C.c_void_p * max(n, 1))(*xs)
+    st = load().lidar_simulate_host_frames(handle, n, garr, parr,
+                                           None if out_waveforms is None else ptrs(out_waveforms),
+                                           ptrs(out_echoes), ptrs(out_counts), stream)
     _check(st, handle)
 
 
@@ -680,6 +701,26 @@ class Lidar:
         lidar_simulate_host(self.handle, g, make_pose(np.eye(3) if pose is None else pose),
                             wave.data_ptr() if wave is not None else None, echoes.data_ptr(), counts.data_ptr(), s)
         return wave, echoes, counts
+
+    def simulate_host_frames(self, geoms, host_planes, poses=None, outputs=None, stream=None, echo_only=False):
+        """A sequence of frames from host memory (lidar_simulate_host_frames):
+        geoms[f], host_planes[f] (pinned CPU tensors) and poses[f] describe frame
+        f; outputs[f] = (waveforms or None, echoes, counts) receives its results.
+        Consecutive frames must not share output tensors."""
+        import torch
+        n = len(geoms)
+        poses = [np.eye(3)] * n if poses is None else poses
+        if outputs is None:
+            outputs = [(None if echo_only else
+                        torch.empty((self.n_beams, self.n_bins), dtype=torch.float32, pin_memory=True),
+                        torch.empty((self.n_beams, self.max_echoes, 8), dtype=torch.int32, pin_memory=True),
+                        torch.empty((self.n_beams,), dtype=torch.int32, pin_memory=True)) for _ in range(n)]
+        gs = [make_gbuffer(geom, [p.data_ptr() for p in planes]) for geom, planes in zip(geoms, host_planes)]
+        ps = [make_pose(p) for p in poses]
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        lidar_simulate_host_frames(self.handle, gs, ps, None if echo_only else [o[0].data_ptr() for o in outputs],
+                                   [o[1].data_ptr() for o in outputs], [o[2].data_ptr() for o in outputs], s)
+        return outputs
 
     def close(self):
         if self.handle:
