@@ -121,6 +121,21 @@ def test_new_entry_points_reject_null(lib):
         lidar.lidar_simulate_echoes(None, g, lidar.make_pose(np.eye(3)), 0, 0, 0)
 
 
+def test_host_frames_rejects_null_handle_and_mismatched_lists(lib):
+    """The frame-sequence call: a NULL handle is rejected by the library before
+    any CUDA call; per-frame lists of different lengths are rejected by the
+    binding before the library is called."""
+    g, pose = lidar.lidar_gbuffer_t(), lidar.make_pose(np.eye(3))
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_simulate_host_frames(None, [g], [pose], None, [0], [0], 0)
+    with pytest.raises(lidar.LidarError):
+        lidar.lidar_simulate_host(None, g, pose, 0, 0, 0, 0)
+    with pytest.raises(ValueError):
+        lidar.lidar_simulate_host_frames(None, [g, g], [pose], None, [0, 0], [0, 0], 0)
+    with pytest.raises(ValueError):
+        lidar.lidar_simulate_host_frames(None, [g], [pose], [0, 0], [0], [0], 0)
+
+
 def test_frame_struct_layout(lib):
     # lidar_frame_t: sensor pointer, gbuffer, pose, waveforms pointer, echoes
     assert C.sizeof(lidar.lidar_frame_t) == 8 + C.sizeof(lidar.lidar_gbuffer_t) + 36 + 4 + 8 + 16
