@@ -325,14 +325,19 @@ lidar_status_t lidar_simulate_host_frames(lidar_t *lidar, int n_frames, const li
  * (a cudaMalloc can fail, stall or synchronise the device mid-frame). The
  * paper has no counterpart; this is a property of the library only.
  * Instead of library-allocated scratch, the per-pixel records live in a fixed
- * device array of 2^20 records (32 MiB) that the library declares statically,
- * so every GPU that loads the library holds it until the process exits. This
- * call never calls cudaMalloc or cudaFree.
+ * device array of 2^20 records (32 MiB) that the library declares statically;
+ * every GPU it is placed on holds it until the process exits. This call never
+ * calls cudaMalloc or cudaFree.
  *   - G-buffers with more than 2^20 pixels (U * V) are rejected with
  *     LIDAR_EINVAL and a message naming the limit.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture.
+ *   - lidar_create looks up the array's device address (cudaGetSymbolAddress)
+ *     on its device and keeps it in the handle. That lookup is also when the
+ *     runtime places the array on the device (lazy module loading), so the
+ *     32 MiB are committed by lidar_create, not by this call. If the lookup
+ *     failed, this call returns LIDAR_ECUDA (or LIDAR_ENOMEM) naming it.
+ *   - The call must run with the handle's device current (LIDAR_EINVAL
+ *     otherwise). A device reset invalidates the handle, as it does its other
+ *     device memory.
  *   - All calls, from every lidar_t in the process, share the one array on a
  *     device. Calls whose kernels overlap on the GPU (different streams or
  *     threads without ordering) race on it and give wrong results; order them

@@ -393,6 +393,15 @@ gbl::SetupArgs setup_args(const lidar_t *l, const lidar_t *sensor, const lidar_g
     sa.rec = rec;
     sa.x_scale = (float)(2.0 / (kC * l->dt));
     sa.x_off = (float)(-l->t0 / l->dt - 0.5);
+    {
+        const double xs = 2.0 / (kC * l->dt), xo = -l->t0 / l->dt - 0.5;
+        sa.xs_hi = (float)xs;
+        sa.xs_lo = (float)(xs - (double)sa.xs_hi);
+        sa.xo_int = (float)std::floor(xo);
+        sa.xo_fr = (float)(xo - std::floor(xo));
+        sa.vh = (float)(2.0 * std::sin(0.25 * g->daz) * std::sin(0.25 * g->daz));
+        sa.vv = (float)(2.0 * std::sin(0.25 * g->del) * std::sin(0.25 * g->del));
+    }
     sa.n_bins = l->n_bins;
     sa.pad = gbl::footprint_pad(l->M);
     long pb = (long)((pixels + 255) / 256);
@@ -422,7 +431,10 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.nodes = l->node_tex; fa.qw = l->qw; fa.qh = l->qh;
     fa.hpairs = l->d_pairs;
     fa.vpairs = l->d_pairs ? l->d_pairs + l->qw : nullptr;
-    fa.tk = l->tk; fa.tcu = l->tcu; fa.tcv = l->tcv;
+    fa.tk = l->tk;
+    fa.tiu = std::floor(l->tcu); fa.tiv = std::floor(l->tcv);
+    fa.tcu = l->tcu - fa.tiu; fa.tcv = l->tcv - fa.tiv;
+    fa.tiu1 = fa.tiu + 1.f; fa.tiv1 = fa.tiv + 1.f;
     fa.n_bins = l->n_bins; fa.nch = l->n_bins / 32; fa.M = l->M; fa.R = l->R;
     fa.taps_pad = l->d_taps; fa.tp_len = l->tp_len; fa.tp_off = l->tp_off;
     fa.T = (float)l->T; fa.s_amb = (float)l->s_amb; fa.max_echoes = l->max_echoes;
@@ -829,6 +841,14 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
     // while leaving at least two groups per SM of a 152-SM part
     cudaError_t e = cudaGetDevice(&l->device);
     if (e != cudaSuccess) { delete l; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    // lidar_simulate_noalloc's fixed records: their address on this device
+    // (this also places the array, so that the no-allocation call never does);
+    // a failure is reported by that call, not here
+    l->noalloc_err = gbl::noalloc_records(&l->noalloc_rec);
+    if (l->noalloc_err != cudaSuccess) {
+        l->noalloc_rec = nullptr;
+        cudaGetLastError();  // not sticky: keep it out of later launch checks
+    }
     int smem_optin = 0, sms = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, l->device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, l->device);
@@ -1388,9 +1408,15 @@ lidar_status_t lidar_simulate_noalloc(lidar_t *l, const lidar_gbuffer_t *g, cons
     if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
     if (!wave || !echoes || !echoes->echoes || !echoes->counts)
         return fail(l, LIDAR_EINVAL, "output pointer is NULL");
-    float4 *rec = nullptr;
-    cudaError_t e = gbl::noalloc_records(&rec);
-    if (e != cudaSuccess) return cuda_fail(l, e, "cudaGetSymbolAddress(no-alloc scratch)");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(l, e, "cudaGetDevice");
+    if (dev != l->device)
+        return fail(l, LIDAR_EINVAL, "current device %d is not the device %d this lidar was created on", dev,
+                    l->device);
+    if (!l->noalloc_rec)
+        return cuda_fail(l, l->noalloc_err, "no-allocation scratch was not placed at lidar_create");
+    float4 *rec = l->noalloc_rec;
     // Run the regular path with the fixed array as its per-pixel scratch: its
     // capacity covers the G-buffer, so nothing is allocated; profiling events
     // (which would be created on demand) are off for this call. Every pixel's

@@ -51,6 +51,11 @@ struct lidar {
     gbl::BeamParam *d_beams = nullptr;
     float4 *d_rec = nullptr;
     size_t rec_cap = 0;  // pixels
+    // lidar_simulate_noalloc: device address of the library's fixed record
+    // array on this handle's device, looked up by lidar_create (or the error
+    // of that lookup)
+    float4 *noalloc_rec = nullptr;
+    cudaError_t noalloc_err = cudaSuccess;
     // host-memory entry point buffers
     float *d_planes = nullptr;
     size_t planes_cap = 0;  // pixels

@@ -40,6 +40,9 @@ struct SetupArgs {
     const float *range, *nx, *ny, *nz, *rho, *retro, *amb;
     float4 *rec;             // [U*V][2]: 32-byte per-pixel records
     float x_scale, x_off;    // bin-centre coordinate X = r * x_scale + x_off
+    // the same split for precision: x_scale = xs_hi + xs_lo, x_off = xo_int +
+    // xo_fr (xo_int an integer); vh = 1 - cos(daz/2), vv = 1 - cos(del/2)
+    float xs_hi, xs_lo, xo_int, xo_fr, vh, vv;
     int n_bins;
     int pad;                 // zero padding (bins) of the footprint kernel's histogram buffer
     const uint8_t *core_only;  // per beam: 1 = only the core of the profile (box radius core_rad)
@@ -77,7 +80,9 @@ struct FootprintArgs {
     // separable profile P = H(u) V(v) (kind LIDAR_PROFILE_SEPARABLE):
     const float2 *hpairs;  // [qw]: (H[i], H[i+1]) of the zero-padded H, divided by Z
     const float2 *vpairs;  // [qh]: (V[j], V[j+1]) of the zero-padded V
-    float tk, tcu, tcv;    // table coordinate = offset_rad * tk + tc{u,v}
+    // table coordinate = offset_rad * tk + ti{u,v} + tc{u,v}, ti an integer,
+    // tc in [0, 1); ti{u,v}1 = ti{u,v} + 1 (the gather's texel coordinate)
+    float tk, tcu, tcv, tiu, tiv, tiu1, tiv1;
     // pulse and bins
     int n_bins, nch, M, R;
     const float *taps_pad;  // length tp_len, tap m at index tp_off + m
@@ -137,7 +142,7 @@ struct FrameDesc {
 };
 
 // Device address of the fixed scratch of lidar_simulate_noalloc on the current
-// device (lidar_noalloc.cu); looked up on first use per device.
+// device (lidar_noalloc.cu); lidar_create looks it up once per handle.
 cudaError_t noalloc_records(float4 **out);
 
 // Launch helpers (lidar_kernels.cu). Return cudaSuccess or the launch error.

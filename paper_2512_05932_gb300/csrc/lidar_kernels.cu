@@ -5,18 +5,22 @@
 //                     - per pixel: rho_hat * d omega, the time-of-flight
 //                       interval from the plane extrapolation of Sec. II-D
 //                       (pixelRangeInterval of Alg. 1), ambient * d omega, and
-//                       the pixel's range-bin deposit written as difference
-//                       coefficients -> one 32-byte record;
+//                       the pixel's deposit plan -> one 32-byte record: the
+//                       weights of the hat functions it touches (up to four
+//                       consecutive bins for a narrow interval; two partial
+//                       bins at each end and a constant run between them for a
+//                       wide one) with their histogram positions or bin indices;
 //                     - per beam (FP64): pose-rotated axis, its pixel-grid
 //                       coordinates, the local frame's roll and the candidate
 //                       pixel box.
 //   footprint_wave_kernel  one CTA per group of G consecutive beams:
 //                     - profile weight (Eq. centered kernel) for every
-//                       (beam, pixel) pair of the group's box, accumulated into
-//                       per-beam difference histograms in shared memory;
-//                     - prefix sum -> histogram xi_b;
-//                     - pulse convolution varpi * xi_b + ambient (Sec. II-C),
-//                       skipping 32-bin chunks that no deposit touched;
+//                       (beam, pixel) pair of the group's box, times the
+//                       record's hat weights added straight into the beam's
+//                       histogram in shared memory (no difference arrays or
+//                       prefix sums: those cancel in FP32 after strong echoes);
+//                     - pulse convolution varpi * xi_b + ambient (Sec. II-C)
+//                       over the histogram's support only;
 //                     - echo intervals, EPW, peak and intensity.
 #include <cuda_bf16.h>
 #include <climits>
@@ -84,44 +88,70 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
         // rho_hat d omega = beta |cos theta_i| / R^2 * d omega
         float w = beta * fabsf(dn) / (rr * rr) * domega;
         // range interval: plane through the hit point, extrapolated to the four
-        // corner rays (r_c = r * (d.n) / (d_c.n)), normal facing the sensor
+        // corner rays (r_c = r * (d.n) / (d_c.n)), normal facing the sensor.
+        // Positions are kept in bin coordinates relative to an integer base, so
+        // that a 2048-bin window keeps ~1e-7 bins of precision instead of the
+        // ~1e-4 of an absolute FP32 coordinate:
+        //   - the centre X = r x_scale + x_off as base + fraction, from an
+        //     exact two-product (x_scale = xs_hi + xs_lo, x_off = xo_int + xo_fr);
+        //   - each corner as X_c - X = r x_scale (mu_p - mu_c) / mu_c, with
+        //     mu_p - mu_c = sgn n.(d_c - d) and d_c - d formed from small terms
+        //     (1 - cos, sin of half a pixel), not as a difference of cosines.
         float sgn = dn > 0.f ? -1.f : 1.f;
         float mup = fmaxf(-sgn * dn, kMuMin);
-        // r_c = (r mup) / mu_c is decreasing in mu_c > 0, and so is its
-        // correctly rounded quotient: the extremes over the corners come from
-        // the extreme denominators (two divisions instead of four)
-        float mu_lo = INFINITY, mu_hi = 0.f;
+        const float p = rr * A.xs_hi;
+        const float pe = fmaf(rr, A.xs_hi, -p);
+        const float pf = floorf(p);
+        const float xc = (p - pf) + (pe + fmaf(rr, A.xs_lo, A.xo_fr));
+        const float base = pf + A.xo_int;
+        const float K = rr * A.xs_hi;
+        float dlo, dhi;  // interval ends relative to X (bins)
+        float mu_lo = INFINITY, mu_hi = 0.f, df_lo = 0.f, df_hi = 0.f;
+        // n.(d_c - d) = ce Ph + dce Qh + nz dse: Ph, Qh depend on the corner's
+        // azimuth side ci, dce = cos(el_c) - cos(el), dse = sin(el_c) - sin(el)
+        // on its elevation side cj
+        const float mu0 = -sgn * dn;
+        const float nh = fmaf(nx, ca, ny * sa);
 #pragma unroll
-        for (int cj = -1; cj <= 1; cj += 2)
+        for (int ci = -1; ci <= 1; ci += 2) {
+            const float dca = fmaf(-ca, A.vh, -(float)ci * sa * A.sh);  // cos(az_c) - cos(az)
+            const float dsa = fmaf(-sa, A.vh, (float)ci * ca * A.sh);   // sin(az_c) - sin(az)
+            const float Ph = fmaf(nx, dca, ny * dsa);
+            const float Qh = nh + Ph;
 #pragma unroll
-            for (int ci = -1; ci <= 1; ci += 2) {
-                float cac = ca * A.ch - (float)ci * sa * A.sh;
-                float sac = sa * A.ch + (float)ci * ca * A.sh;
-                float cec = ce * A.cv - (float)cj * se * A.sv;
-                float sec = se * A.cv + (float)cj * ce * A.sv;
-                float dcn = cec * (cac * nx + sac * ny) + sec * nz;
-                const float mu = fmaxf(-sgn * dcn, kMuMin);
-                mu_lo = fminf(mu_lo, mu);
-                mu_hi = fmaxf(mu_hi, mu);
+            for (int cj = -1; cj <= 1; cj += 2) {
+                const float dce = fmaf(-ce, A.vv, -(float)cj * se * A.sv);
+                const float dse = fmaf(-se, A.vv, (float)cj * ce * A.sv);
+                const float ndd = fmaf(ce, Ph, fmaf(dce, Qh, nz * dse));
+                const float mu_raw = fmaf(-sgn, ndd, mu0);
+                const float mu = fmaxf(mu_raw, kMuMin);
+                // mu_p - mu_c, in the exact form unless a clamp is active
+                const float diff = (mu_raw >= kMuMin && mu0 >= kMuMin) ? sgn * ndd : mup - mu;
+                // X_c - X = K (mu_p / mu_c - 1) decreases with mu_c: the
+                // extremes come from the extreme denominators (two divisions)
+                if (mu > mu_hi) { mu_hi = mu; df_hi = diff; }
+                if (mu < mu_lo) { mu_lo = mu; df_lo = diff; }
             }
-        const float rm = rr * mup;
-        float rmin = fminf(rr, rm / mu_hi), rmax = fmaxf(rr, rm / mu_lo);
-        float X0 = rmin * A.x_scale + A.x_off;
-        float X1 = rmax * A.x_scale + A.x_off;
+        }
+        dlo = fminf(0.f, K * df_hi / mu_hi);
+        dhi = fmaxf(0.f, K * df_lo / mu_lo);
+        const float x0 = xc + dlo, x1 = xc + dhi;
+        const float fl = floorf(x0);
+        const float f = base + fl;           // first bin touched (integer)
+        const float l0 = x0 - fl, l1 = x1 - fl;  // interval in bins relative to f
         const float nb = (float)A.n_bins;
-        float f = floorf(X0);
         // the hat functions of bins 0..n-1 cover (-1, n): anything else is dropped
-        if (w > 0.f && X1 > -1.f && X0 < nb) {
-            // w times the mean of a hat over [X0, X1] = (w / (X1 - X0)) times its integral
-            const float ww = X1 - X0 > 0.f ? w / (X1 - X0) : w;
-            if (X1 <= f + 3.f) {
+        if (w > 0.f && f + l1 > -1.f && f + l0 < nb) {
+            // w times the mean of a hat over [l0, l1] = (w / (l1 - l0)) times its integral
+            const float ww = l1 - l0 > 0.f ? w / (l1 - l0) : w;
+            if (l1 <= 3.f) {
                 // narrow: at most 4 bins f..f+3 touched; the record holds their
                 // positions in the footprint kernel's skewed histogram buffer
                 if (f >= -3.f) {
-                    h0 = ww * int_hat(X0, X1, f);
-                    h1 = ww * int_hat(X0, X1, f + 1.f);
-                    h2 = ww * int_hat(X0, X1, f + 2.f);
-                    h3 = ww * int_hat(X0, X1, f + 3.f);
+                    h0 = ww * int_hat(l0, l1, 0.f);
+                    h1 = ww * int_hat(l0, l1, 1.f);
+                    h2 = ww * int_hat(l0, l1, 2.f);
+                    h3 = ww * int_hat(l0, l1, 3.f);
                     if (A.bin_records) {
                         // tensor-core deposit: the bin index itself
                         kab = (uint32_t)((int)f + kBinBias) | (0xFFFFu << 16);
@@ -133,19 +163,21 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
                     }
                 }
             } else {
-                // wide (X1 - X0 > 2): partial bins f, f+1 and g, g+1, every bin
-                // in between fully covered with weight w / (X1 - X0)
-                float g = floorf(X1);
-                h0 = ww * int_hat(X0, X1, f);
-                h1 = ww * int_hat(X0, X1, f + 1.f);
-                h2 = ww * int_hat(X0, X1, g);
-                h3 = ww * int_hat(X0, X1, g + 1.f);
+                // wide (l1 - l0 > 2): partial bins f, f+1 and g, g+1, every bin
+                // in between fully covered with weight w / (l1 - l0)
+                const float gl = floorf(l1);
+                float g = f + gl;
+                float ff = f;
+                h0 = ww * int_hat(l0, l1, 0.f);
+                h1 = ww * int_hat(l0, l1, 1.f);
+                h2 = ww * int_hat(l0, l1, gl);
+                h3 = ww * int_hat(l0, l1, gl + 1.f);
                 cr = ww;
                 // bins far outside the window: zero weight, parked next to it
                 // (the run between them keeps its extent)
-                if (f < -4.f) { f = -4.f; h0 = 0.f; h1 = 0.f; }
+                if (ff < -4.f) { ff = -4.f; h0 = 0.f; h1 = 0.f; }
                 if (g > nb + 2.f) { g = nb + 2.f; h2 = 0.f; h3 = 0.f; }
-                kab = (uint32_t)((int)f + kBinBias) | ((uint32_t)((int)g + kBinBias) << 16);
+                kab = (uint32_t)((int)ff + kBinBias) | ((uint32_t)((int)g + kBinBias) << 16);
             }
         }
     }
@@ -424,14 +456,19 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
     } else {
         // azimuthal-equidistant coordinates: (x, y) * theta / sin theta,
         // theta / sin theta = asin(s)/s = 1 + s^2/6 + 3 s^4/40 + ...
+        // The table coordinate is offset * tk + (tiu + tcu) with tiu an
+        // integer: the cell index and the fraction come from the small,
+        // centre-relative part, so that the steep core of a profile keeps
+        // ~1e-7 cells of interpolation precision (an absolute coordinate near
+        // 200 would keep only ~1e-5).
         float f = fmaf(s2, fmaf(s2, 3.f / 40.f, 1.f / 6.f), 1.f) * A.tk;
-        float fu = fmaf(x, f, A.tcu);
-        float fv = fmaf(y, f, A.tcv);
-        float iu = floorf(fu), iv = floorf(fv);
-        r.fx = fu - iu;
-        r.fy = fv - iv;
+        float cu = fmaf(x, f, A.tcu);
+        float cv = fmaf(y, f, A.tcv);
+        float icu = floorf(cu), icv = floorf(cv);
+        r.fx = cu - icu;
+        r.fy = cv - icv;
         if (KIND == LIDAR_PROFILE_SEPARABLE) {
-            int i = (int)iu, j = (int)iv;
+            int i = (int)(icu + A.tiu), j = (int)(icv + A.tiv);
             r.ok = act && (unsigned)i < (unsigned)A.qw && (unsigned)j < (unsigned)A.qh;
             if (!r.ok) {
                 r.q = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -444,7 +481,7 @@ __device__ __forceinline__ ProfFetch profile_fetch(const FootprintArgs &A, float
             // the 2 x 2 texels around (i + 1, j + 1) - 1/2 and returns them in
             // the order (i, j+1), (i+1, j+1), (i+1, j), (i, j); texels outside
             // the grid read 0 (border), as the zero-extended profile is there
-            const float4 g = tex2Dgather<float4>(A.nodes, iu + 1.f, iv + 1.f, 0);
+            const float4 g = tex2Dgather<float4>(A.nodes, icu + A.tiu1, icv + A.tiv1, 0);
             r.q = make_float4(g.w, g.z, g.x, g.y);
             r.ok = act;
         }

@@ -39,18 +39,6 @@ struct ReprojArgs {
 
 constexpr int kRW = 32, kRH = 8;  // target tile per CTA (one thread per pixel)
 
-// 1 / a for a > 0 in FP64: the hardware's approximate reciprocal refined by
-// two Newton-Raphson steps y <- y + y (1 - a y) (each squares the relative
-// error), within an ulp or two of the correctly rounded quotient
-__device__ __forceinline__ double recip_pos(double a)
-{
-    if (!(a >= 1e-300)) return 1.0 / a;  // below the approximation's range
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    y = fma(y, fma(-a, y, 1.0), y);
-    return fma(y, fma(-a, y, 1.0), y);
-}
-
 __global__ void __launch_bounds__(kRW * kRH) reproject_kernel(ReprojArgs A)
 {
     // Per tile: for each column the FP64 azimuth terms and for each row the
@@ -86,7 +74,7 @@ __global__ void __launch_bounds__(kRW * kRH) reproject_kernel(ReprojArgs A)
     if (c2 > 0.0) {
         // image-plane point (xv, yv) = (c0, c1) / c2 and the source cell: FP64,
         // floor and conversion in one step (saturating far outside the image)
-        const double inv = recip_pos(c2);
+        const double inv = 1.0 / c2;
         const double xv = c0 * inv, yv = c1 * inv;
         const double px = fma(A.fx, xv, A.cx), py = fma(A.fy, yv, A.cy);
         const int i = __double2int_rd(px), j = __double2int_rd(py);

@@ -539,22 +539,25 @@ class Workload:
 DEG = math.pi / 180.0
 
 
-def small_plane_retro(seed: int = 1, size: int = 256) -> Workload:
+def small_plane_retro(seed: int = 13, size: int = 256) -> Workload:
     """Plain FP32 small instance: 256x256 G-buffer at 0.02 deg pitch looking at a
     Lambertian plane at 10 m (reflectance 0.5) with a centred 0.5 x 0.5 m
     retroreflective patch (gain 100), uniform ambient 0.01, 32x16 grid beams,
     Gaussian (sigma 0.05 deg) + 1e-4 (theta/0.05 deg)^-3 tail truncated at 1 deg,
     1024 bins of 0.1 ns, 4 ns FWHM Gaussian pulse, up to 3 echoes.
 
-    The seed jitters the patch centre by up to +-1 mm (the scene family); the
-    pattern and all parameters are fixed."""
+    The seed jitters the patch centre and the plane's distance by up to +-1 mm
+    each (the scene family); the pattern and all parameters are fixed. With the
+    default seed no bin of any beam's FP64 waveform lies within 7e-4 T of the
+    threshold T, so every echo of the instance is compared bit-exactly."""
     g = rng(seed)
-    jit = g.uniform(-1e-3, 1e-3, size=2)
+    jit = g.uniform(-1e-3, 1e-3, size=3)
     pitch = 0.02 * DEG
     fov = size * pitch
-    decal = Rect(np.array([10.0, jit[0], jit[1]]), np.array([0.0, 1.0, 0.0]),
+    dist = 10.0 + jit[2]
+    decal = Rect(np.array([dist, jit[0], jit[1]]), np.array([0.0, 1.0, 0.0]),
                  np.array([0.0, 0.0, 1.0]), 0.25, 0.25, rho_d=0.5, retro=100.0)
-    scene = Scene(planes=[Plane(np.array([1.0, 0.0, 0.0]), 10.0, 0.5, 0.0, decal)],
+    scene = Scene(planes=[Plane(np.array([1.0, 0.0, 0.0]), dist, 0.5, 0.0, decal)],
                   ambient="uniform", ambient_level=0.01)
     gb = raycast(scene, size, size, -fov / 2, -fov / 2, pitch, pitch)
     dirs = grid_pattern(32, 16, 5.12 * DEG, 5.12 * DEG)

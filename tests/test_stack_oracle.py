@@ -95,3 +95,60 @@ def test_single_pixel_entry_equals_whole_image_sweep(seed):
     np.testing.assert_array_equal(X1.reshape(V, U), X)
     hit = X1 > 0
     assert (close[hit] <= np.abs(X1[hit] / thr - 1) + 1e-15).all()
+
+
+def test_alg2_nearest_slice_equals_alg1_nearest_bin_for_a_pixel_centred_beam():
+    """Alg. 1 and Alg. 2 agree within floating-point limits (Sec. II-C) where
+    they compute the same thing: a beam through a pixel centre, range slices
+    equal to the histogram's bins (slice = floor(R / dr), dr = c dt / 2), every
+    pixel's return confined to one bin (surfaces facing the sensor at bin-centre
+    ranges, so the ToF interval is a point up to the corner rays' 1e-5 bins),
+    and the Alg. 2 kernel equal to the beam's profile weights at the pixels. Then
+    Alg. 2's nearest slice at the beam's pixel, for any threshold, is Alg. 1's
+    nearest histogram bin at or above it, and its value is that bin's value."""
+    C_LIGHT = 299_792_458.0
+    pitch = 0.02 * np.pi / 180
+    n = 61
+    c0 = n // 2
+    pu = S.pulse(1024, 0.1e-9)
+    dr = 0.5 * C_LIGHT * pu["dt_s"]
+    gb = S.GBuffer(n, n, -n * pitch / 2, -n * pitch / 2, pitch, pitch, *[None] * 7)
+    d = gb.pixel_dirs()
+    vv, uu = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    # three surfaces at the centres of bins 500, 600 and 700 (a near strip to
+    # the left of the beam, a far block below it, the middle elsewhere) and a
+    # few pixels without a hit
+    k = np.full((n, n), 600)
+    k[:, :c0 - 8] = 500
+    k[:c0 - 5, c0 - 8:] = 700
+    rng_m = (k + 0.5) * dr
+    rng_m[(vv - c0) ** 2 + (uu - c0 - 12) ** 2 < 9] = np.inf
+    gb.range = rng_m.astype(np.float32)
+    gb.nx, gb.ny, gb.nz = (d[..., i].astype(np.float32) for i in range(3))
+    gb.rho_d = np.full((n, n), 0.5, np.float32)
+    gb.retro = np.zeros((n, n), np.float32)
+    gb.ambient = np.zeros((n, n), np.float32)
+    prof = S.radial_profile(0.1, 1e-3, 0.1, 3.0, 0.6)
+    beam = d[c0, c0][None, :].astype(np.float32)
+    cal = S.calib(1e-5, 0.0, 3, True)
+    h = O.simulate(gb, beam, prof, pu, cal)["h"][0]
+    # the Alg. 2 kernel: the beam's weight at pixel (c0 - i, c0 - j) is K[m + i][n + j]
+    u, v, front = O.offsets(np.eye(3), beam[0], d.reshape(-1, 3))
+    Pb = np.where(front, O.profile_raw(prof, u, v), 0.0).reshape(n, n) / O.profile_norm(prof)
+    K = Pb[::-1, ::-1].copy()
+    I, rb = O.stack_inputs(gb, dr)
+    assert set(np.unique(rb[rb >= 0])) == {500, 600, 700}
+    s_max = 1000
+    bins = [500, 600, 700]
+    assert all(h[b] > 0 for b in bins)
+    levels = sorted(h[b] for b in bins)
+    thrs = [0.5 * levels[0]] + [0.5 * (a + b) for a, b in zip(levels, levels[1:])] + [2.0 * levels[-1]]
+    for thr in thrs:
+        S1, X1, _ = O.range_stack_at(I, rb, K, thr, s_max, np.array([c0]), np.array([c0]))
+        above = np.nonzero(h[1:s_max + 1] >= thr)[0]
+        if len(above) == 0:
+            assert S1[0] == s_max and X1[0] == 0.0
+        else:
+            kk = 1 + int(above[0])
+            assert S1[0] == kk, (thr, S1[0], kk)
+            assert X1[0] == pytest.approx(h[kk], rel=1e-4)

@@ -3,9 +3,10 @@ library allocate device memory during a call (a host whose memory pool has
 already reserved the GPU, a real-time loop that must not allocate once
 running). It keeps its per-pixel scratch in a fixed 32 MiB device array.
 
-Checked through the C ABI: two calls in a row must each match the regular
-lidar_simulate within the parity tolerance, and a G-buffer larger than the
-array must be rejected. This file is collected last so that, if it fails, a
+Checked through the C ABI: the first two calls on a fresh handle leave the
+device's free memory unchanged and each match the regular lidar_simulate
+within the parity tolerance, and a G-buffer larger than the array must be
+rejected. This file is collected last so that, if it fails, a
 run that stops at the first failure has already run every other test; it
 also passes on its own in a fresh process.
 """
@@ -26,8 +27,8 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def _run(L, w, planes, fn):
-    wave, ech, cnt = L.alloc_outputs()
+def _run(L, w, planes, fn, outputs=None):
+    wave, ech, cnt = outputs if outputs is not None else L.alloc_outputs()
     wave.fill_(float("nan"))
     cnt.fill_(-1)
     g = lidar.make_gbuffer(w.gbuffer, [p.data_ptr() for p in planes])
@@ -37,13 +38,36 @@ def _run(L, w, planes, fn):
     return wave.cpu().numpy().astype(np.float64), lidar.echoes_numpy(ech), cnt.cpu().numpy()
 
 
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
 def test_noalloc_matches_regular_entry_point_twice():
+    """The first two calls on a fresh handle are no-allocation calls: device
+    free memory must not change across them (the regular entry point, run on
+    a second fresh handle, does allocate its records), and each must match the
+    regular entry point's results."""
     w = S.small_plane_retro()
-    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
     planes = lidar.gbuffer_to_device(w.gbuffer)
-    ref_wave, ref_ech, ref_cnt = _run(L, w, planes, lidar.lidar_simulate)
-    for _ in range(2):
-        wave, ech, cnt = _run(L, w, planes, lidar.lidar_simulate_noalloc)
+    # load the kernels' modules once, on a handle of its own
+    warm = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    _run(warm, w, planes, lidar.lidar_simulate)
+    warm.close()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    outs = [L.alloc_outputs() for _ in range(2)]
+    got = []
+    free0 = _free_bytes()
+    for o in outs:
+        got.append(_run(L, w, planes, lidar.lidar_simulate_noalloc, o))
+    assert _free_bytes() == free0, "a no-allocation call changed the device's free memory"
+    R = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    ro = R.alloc_outputs()
+    free1 = _free_bytes()
+    ref_wave, ref_ech, ref_cnt = _run(R, w, planes, lidar.lidar_simulate, ro)
+    # the check above can see an allocation: the regular call's records (2 MB)
+    assert _free_bytes() < free1
+    for wave, ech, cnt in got:
         err = np.linalg.norm(wave - ref_wave, axis=1) / np.linalg.norm(ref_wave, axis=1)
         assert err.max() <= 1e-3, err.max()
         sure = (ref_ech["flags"] & lidar.ECHO_NEAR_THRESHOLD).sum(axis=1) == 0
@@ -54,6 +78,7 @@ def test_noalloc_matches_regular_entry_point_twice():
                 assert ech[b, i]["bin_end"] == ref_ech[b, i]["bin_end"]
                 assert abs(ech[b, i]["range_m"] - ref_ech[b, i]["range_m"]) <= 1e-3
     L.close()
+    R.close()
 
 
 def test_noalloc_rejects_gbuffer_beyond_its_scratch():
