@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--profile", default="table", choices=["table", "separable"],
                     help="frame workload: the 401x401 table, or the separable profile H(u) V(v) of its "
                          "centre row and column (two 401-node tables)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default run: leave out the records of the other workloads (wide frame exact and "
+                         "split, 64-frame batch)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
                     help="network weights of --tail net")
     return ap.parse_args()
@@ -88,7 +91,17 @@ PROFILE = "table"
 CONV_FLOPS_PER_BEAM = 2 * (1024 * 32 * 18 + 256 * 32 * 306 + 64 * 32 * 306)  # three convolutions
 
 
+_SCENES = {}
+
+
 def workload():
+    key = (WORKLOAD if WORKLOAD != "split" else "wide", SIZE, PROFILE)
+    if key not in _SCENES:
+        _SCENES[key] = _make_workload()
+    return _SCENES[key]
+
+
+def _make_workload():
     from paper_2512_05932_gb300 import scenes
     if WORKLOAD == "split" and SIZE == "small":
         return scenes.wide_frame(U=2048, V=1024, n_az=100, n_el=80)
@@ -138,16 +151,61 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def oracle_rate(w, n_sample, nthreads):
-    """Oracle beams/s on an evenly spaced beam sample of the workload."""
+_ORACLE = {}
+
+
+def oracle_cached(w, beams, nthreads):
+    """The oracle's result on these beams of this workload (computed once per
+    run: the wide frame's exact and split records share it)."""
+    key = (w.name, tuple(int(b) for b in beams))
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle_rate(w, len(beams), nthreads, beams=beams)
+    return _ORACLE[key]
+
+
+def oracle_rate(w, n_sample, nthreads, beams=None):
+    """Oracle beams/s on an evenly spaced beam sample of the workload (or the
+    given beams); also returns the oracle's result for the parity check."""
     from oracle import oracle as O
     O.build()
     nb = len(w.dirs)
-    beams = np.linspace(0, nb - 1, n_sample).round().astype(np.int32)
+    if beams is None:
+        beams = np.unique(np.linspace(0, nb - 1, n_sample).round().astype(np.int32))
     t = time.perf_counter()
-    O.simulate_workload(w, beams=beams, nthreads=nthreads, max_out=4)
+    ref = O.simulate_workload(w, beams=beams, nthreads=nthreads, max_out=8)
     dt = time.perf_counter() - t
-    return n_sample / dt, dt, beams
+    return len(beams) / dt, dt, beams, ref
+
+
+# Echo bins are compared bit-exactly outside a band of PARITY_BAND * T around
+# the threshold (oracle/parity.py); the GPU's largest deviation from the
+# oracle at bins near T on these workloads is below 1e-5 T.
+PARITY_BAND = 1e-5
+PARITY_FAILED = []
+
+
+def parity_check(name, w, beams, ref, wave_rows, echoes, counts, parts=None):
+    """Judges the GPU result of the frame a step computed against the oracle on
+    the sampled beams: wave_rows are the GPU waveforms of `beams` in order
+    (None for echo-only output), echoes / counts the GPU's for every beam.
+    parts: further (w, beams, ref, wave_rows, echoes, counts) tuples judged
+    together with the first (frames of a batch)."""
+    from oracle import parity as PR
+    tot = PR.Stats()
+    fails = []
+    for (w_, b_, r_, wr_, e_, c_) in [(w, beams, ref, wave_rows, echoes, counts)] + list(parts or []):
+        wave = None if wr_ is None else {int(b): wr_[i] for i, b in enumerate(b_)}
+        st, f = PR.compare_frame(r_, b_, wave, e_, c_, w_.calib["threshold"], w_.calib["max_echoes"], PARITY_BAND)
+        tot.merge({k: v for k, v in st.items() if k != "failures"})
+        fails += f
+    ok = not fails and tot["ambiguous"] <= 1e-3 * tot["echoes"]
+    if not ok:
+        PARITY_FAILED.append(name)
+        sys.stderr.write(f"parity failed on {name}: {dict(tot)} {fails[:5]}\n")
+    return {"beams": int(tot["beams"]), "echoes": int(tot["echoes"]), "echo_bin_mismatches": int(tot["mismatched"]),
+            "failures": int(len(fails)), "ambiguous_echoes": int(tot["ambiguous"]), "band_T": PARITY_BAND,
+            "max_rel_l2": None if wave_rows is None else float(tot["max_l2"]),
+            "max_range_err_m": float(tot["max_dr"]), "max_epw_err_m": float(tot["max_depw"]), "ok": bool(ok)}
 
 
 class ClockSampler:
@@ -355,7 +413,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_gb300(args, rank, world, local_rank):
+def run_gb300(args, rank, world, local_rank, sub=False):
+    """One frame per step through lidar_simulate (lidar_simulate_echoes with
+    --echo-only). Returns the JSON line (rank 0). sub: a record of the default
+    run's `configs` (no end-to-end leg; the oracle only for the parity check)."""
     import torch
 
     import __graft_entry__
@@ -421,6 +482,14 @@ def run_gb300(args, rank, world, local_rank):
     lidar.lidar_profile_enable(L.handle, False)
     nbeams = len(w.dirs)
     value, ms_per_step = job_rate(sum(step_ms), nbeams, args.steps, world, dist, dev)
+    # the timed steps' result (every step simulates the same frame), for the
+    # parity check of the oracle leg
+    sample = np.unique(np.linspace(0, nbeams - 1, args.cpu_beams).round().astype(np.int32))
+    res_wave = None if args.echo_only else outs[0][torch.as_tensor(sample, device=dev, dtype=torch.long)].cpu().numpy()
+    res_ech, res_cnt = lidar.echoes_numpy(outs[1]), outs[2].cpu().numpy()
+
+    if sub:
+        return sub_record(args, w, L, kern, value, ms_per_step, sample, res_wave, res_ech, res_cnt, clk)
 
     # ---- end to end through the host-memory entry point ----
     host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
@@ -501,11 +570,13 @@ def run_gb300(args, rank, world, local_rank):
                                "truncated support and the G-buffer"}
 
     cpu = None
+    parity = None
     if not args.no_cpu_baseline:
         cores = cpu_cores()
-        rate, dt, beams = oracle_rate(w, args.cpu_beams, cores)
+        rate, dt, beams, ref = oracle_rate(w, args.cpu_beams, cores, beams=sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_beams} evenly spaced beams of the frame, all pixels each ({dt:.1f} s wall)"}
+               "sample": f"{len(beams)} evenly spaced beams of the frame, all pixels each ({dt:.1f} s wall)"}
+        parity = parity_check(w.name, w, beams, ref, res_wave, res_ech, res_cnt)
 
     extra = {"l2": "flushed between timed steps (258 MB write)", "parallelism": f"replicas x{world}",
              "deposit": args.deposit, "echo_mode": args.echo_mode}
@@ -515,23 +586,47 @@ def run_gb300(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.deposit == "tc_bf16" else "f32",
             "data": "synthetic", "config": config_of(w, extra),
-            "roofline": roof, "cpu_baseline": cpu, "pixel_samples": pixel_samples,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "pixel_samples": pixel_samples,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": f"lidar_simulate_host_frames, {args.steps} frames per call",
                     "single_call": {"value": e2e_single, "api": "lidar_simulate_host, one frame per call"}},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),
             "clocks": clocks,
             "kernel_ms": {k: tot[k] / max(1, kern[k][1]) for k in names}}
-    print(json.dumps(line), flush=True)
     L.close()
     if dist:
         dist.destroy_process_group()
+    return line
 
 
-def run_split(args, rank, world, local_rank):
+def sub_record(args, w, L, kern, value, ms_per_step, sample, res_wave, res_ech, res_cnt, clk):
+    """Compact record of a frame workload run as one of the default run's
+    `configs`: rate, step time, the dominant kernel's roofline and the parity
+    of the timed frame on the sampled beams."""
+    from paper_2512_05932_gb300 import lidar
+    names = lidar.KERNELS
+    tot = {k: kern[k][0] for k in names}
+    dom = max(names, key=lambda k: tot[k])
+    avg_ms = tot[dom] / max(1, kern[dom][1])
+    peak, peak_kind = load_peaks()
+    alg = algorithmic_bytes(w)
+    rec = {"workload": w.name, "value": value, "unit": UNIT, "ms_per_step": ms_per_step, "steps": args.steps,
+           "roofline": {"bound": "hbm", "kernel": dom, "avg_launch_ms": avg_ms,
+                        "frac": alg / (avg_ms * 1e-3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs"},
+           "dtype": "bf16" if args.deposit == "tc_bf16" else "f32", "deposit": args.deposit,
+           "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        _, dt, beams, ref = oracle_cached(w, sample, cpu_cores())
+        rec["parity"] = parity_check(w.name + "/" + args.deposit, w, beams, ref, res_wave, res_ech, res_cnt)
+    L.close()
+    return rec
+
+
+def run_split(args, rank, world, local_rank, sub=False):
     """Wide-tail frame with the core/tail split: per step, the tail features
     (cell sums, bounds, prior) and the split simulation (exact core + tail
-    estimate, acceptance test, exact re-run of the beams that fail it)."""
+    estimate, acceptance test, exact re-run of the beams that fail it).
+    Returns the JSON line (rank 0), or with sub a compact record."""
     import torch
 
     import __graft_entry__
@@ -625,10 +720,29 @@ def run_split(args, rank, world, local_rank):
                 "peak_source": f"{tkind} bf16_tflops_sustained (FP16 at the same nominal rate)", "traffic": None,
                 "algorithmic_flops": flops, "avg_launch_ms": conv_ms, "launches_per_step": conv[1] / args.steps}
     cpu = None
+    parity = None
     if not args.no_cpu_baseline and rank == 0:
-        rate, dt, _ = oracle_rate(w, 96, cpu_cores())
+        sample = np.unique(np.linspace(0, nbeams - 1, args.cpu_beams).round().astype(np.int32))
+        rate, dt, beams, ref = oracle_cached(w, sample, cpu_cores())
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"96 evenly spaced beams of the frame, full profile ({dt:.1f} s wall)"}
+               "sample": f"{len(beams)} evenly spaced beams of the frame, full profile ({dt:.1f} s wall)"}
+        bi = torch.as_tensor(beams, device=dev, dtype=torch.long)
+        parity = parity_check(w.name + ("/net" if net else "/prior"), w, beams, ref, wave[bi].cpu().numpy(),
+                              lidar.echoes_numpy(ech), cnt.cpu().numpy())
+    if sub:
+        if net:
+            net.close()
+        L.close()
+        rec = {"workload": w.name + " split (" + ("learned network" if net else "physics prior") + ")",
+               "value": nbeams / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+               "roofline": {k: roof[k] for k in ("bound", "kernel", "frac", "peak_source") if k in roof},
+               "stage_ms": {"features": sum(feat) / args.steps, "network": sum(prd) / max(1, len(prd)),
+                            "split": sum(spl) / args.steps},
+               "fallback_beams": int(np.median(nfb)), "dtype": "f32", "parity": parity}
+        if net:
+            rec["dense_layers"] = dense_summary(dense, nbeams, nc, args)
+        rec["clocks"] = clk.summary()
+        return rec
     if rank == 0:
         line = {"metric": METRIC, "value": world * nbeams / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -647,11 +761,11 @@ def run_split(args, rank, world, local_rank):
                 # split: setup + footprint + compaction (+ setup + footprint of the re-run)
                 "gpu_launches": int(args.steps * (6 + (5 * -(-nbeams // 65536) if net else 0) + 3
                                                   + (2 if np.median(nfb) > 0 else 0))),
-                "clocks": clk.summary()}
-        print(json.dumps(line), flush=True)
+                "clocks": clk.summary(), "parity": parity}
     if net:
         net.close()
     L.close()
+    return line if rank == 0 else None
 
 
 def dense_summary(dense, nbeams, nc, args):
@@ -922,8 +1036,9 @@ def run_stack(args, rank, world, local_rank):
     st.close()
 
 
-def run_batch(args, rank, world, local_rank):
-    """64-frame batched workload through lidar_simulate_batch (autotuned)."""
+def run_batch(args, rank, world, local_rank, sub=False):
+    """64-frame batched workload through lidar_simulate_batch (autotuned).
+    Returns the JSON line (rank 0), or with sub a compact record."""
     import torch
 
     import __graft_entry__
@@ -967,19 +1082,34 @@ def run_batch(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     achieved = alg / (ms * 1e-3) / 1e9
     cpu = None
+    parity = None
     if not args.no_cpu_baseline and rank == 0:
         from oracle import oracle as O
         O.build()
         g = np.random.default_rng(0)
-        t = time.perf_counter()
+        dt = 0.0
         n_s = 0
-        for f in g.choice(len(frames), 8, replace=False):
-            b = np.sort(g.choice(len(frames[f].dirs), 24, replace=False)).astype(np.int32)
-            O.simulate_workload(frames[f], beams=b, nthreads=cpu_cores(), max_out=4)
+        parts = []
+        for f in range(len(frames)):
+            b = np.sort(g.choice(len(frames[f].dirs), 16, replace=False)).astype(np.int32)
+            t1 = time.perf_counter()
+            ref = O.simulate_workload(frames[f], beams=b, nthreads=cpu_cores(), max_out=8)
+            dt += time.perf_counter() - t1
             n_s += len(b)
-        dt = time.perf_counter() - t
+            bi = torch.as_tensor(b, device=dev, dtype=torch.long)
+            parts.append((frames[f], b, ref, outs[f][0][bi].cpu().numpy(), lidar.echoes_numpy(outs[f][1]),
+                          outs[f][2].cpu().numpy()))
+        parity = parity_check("batch64", *parts[0], parts=parts[1:])
         cpu = {"value": n_s / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{n_s} random beams from 8 random frames ({dt:.1f} s wall)"}
+               "sample": f"{n_s} random beams, 16 from each of the {len(frames)} frames ({dt:.1f} s wall)"}
+    if sub:
+        for s_ in sensors:
+            s_.close()
+        return {"clocks": clk.summary(), "workload": f"batch of {len(frames)} frames (512x256..4096x2048, 1k..100k beams), 1024 bins",
+                "value": nbeams / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+                "roofline": {"bound": "hbm", "kernel": "batch step (setup + persistent footprint)",
+                             "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"},
+                "beams_per_cta": G, "ctas_per_sm": cps, "dtype": "f32", "parity": parity}
     if rank == 0:
         line = {"metric": METRIC, "value": world * nbeams / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -992,11 +1122,34 @@ def run_batch(args, rank, world, local_rank):
                              "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "traffic": None,
                              "algorithmic_bytes": alg},
-                "cpu_baseline": cpu, "e2e": None,
+                "cpu_baseline": cpu, "e2e": None, "parity": parity,
                 "gpu_launches": int(args.steps * 2), "clocks": clk.summary()}
-        print(json.dumps(line), flush=True)
     for s_ in sensors:
         s_.close()
+    return line if rank == 0 else None
+
+
+def run_configs(args, local_rank):
+    """The other workloads, as compact records of the default run's line: the
+    wide-tail frame exact (FP32 deposit), the wide frame with the core/tail
+    split (physics prior, learned network) and the 64-frame batch. Each record
+    carries its rate, step time, roofline fraction, clocks and the parity of
+    its timed result against the oracle on sampled beams."""
+    global WORKLOAD
+    out = {}
+    base = dict(vars(args))
+    runs = [("wide_exact", "wide", dict(steps=5, warmup=3, cpu_beams=2000, deposit="atomic"), run_gb300),
+            ("wide_split_prior", "split", dict(steps=10, warmup=3, cpu_beams=2000, tail="prior"), run_split),
+            ("wide_split_net", "split", dict(steps=10, warmup=3, cpu_beams=2000, tail="net"), run_split),
+            ("batch64", "batch64", dict(steps=5, warmup=3), run_batch)]
+    for key, wl, over, fn in runs:
+        a = argparse.Namespace(**dict(base, workload=wl, **over))
+        WORKLOAD = wl
+        t = time.perf_counter()
+        out[key] = fn(a, 0, 1, local_rank, sub=True)
+        out[key]["wall_s"] = time.perf_counter() - t
+    WORKLOAD = args.workload
+    return out
 
 
 def main():
@@ -1008,18 +1161,28 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    line = None
     if args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload == "batch64":
-        run_batch(args, rank, world, local_rank)
+        line = run_batch(args, rank, world, local_rank)
     elif args.workload == "split":
-        run_split(args, rank, world, local_rank)
+        line = run_split(args, rank, world, local_rank)
     elif args.workload == "stack":
         run_stack(args, rank, world, local_rank)
     elif args.workload == "pinhole":
         run_pinhole(args, rank, world, local_rank)
     else:
-        run_gb300(args, rank, world, local_rank)
+        line = run_gb300(args, rank, world, local_rank)
+        default = (args.workload == "frame" and args.profile == "table" and args.deposit == "atomic"
+                   and not args.echo_only and args.echo_mode == "nearest")
+        if line is not None and world == 1 and default and not args.no_configs:
+            line["configs"] = run_configs(args, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if PARITY_FAILED:
+        sys.stderr.write(f"parity bar missed on: {', '.join(PARITY_FAILED)}\n")
+        sys.exit(3)
 
 
 if __name__ == "__main__":

@@ -217,6 +217,12 @@ __device__ __noinline__ void setup_beam(const SetupArgs &A, int b)
     if (A.panorama) {
         while (az_b < A.az0d) az_b += two_pi;
         while (az_b >= A.az0d + two_pi) az_b -= two_pi;
+    } else {
+        // the representative within pi of the G-buffer's centre: its azimuth
+        // range may cross the +-pi seam of atan2
+        const double azc = A.az0d + 0.5 * (double)A.U * A.dazd;
+        while (az_b < azc - CUDART_PI) az_b += two_pi;
+        while (az_b >= azc + CUDART_PI) az_b -= two_pi;
     }
     double sab, cab, seb, ceb;
     sincos(az_b, &sab, &cab);
@@ -757,6 +763,187 @@ __device__ __forceinline__ float phase1_tc(const FootprintArgs &A, const Layout 
     return amb_acc;
 }
 
+// Adds an accumulated deposit to a beam's histogram: narrow (kq holds the
+// positions of bins f+2, f+3) or wide (kq == kNoDeposit, end bins in kab).
+__device__ __forceinline__ void dep_flush(float *hj, uint32_t kab, uint32_t kq, float a0, float a1, float a2, float a3,
+                                          float c, int pad, int nb)
+{
+    if (kq != kNoDeposit) {
+        atomicAdd(hj + (kab & 0xFFFFu), a0);
+        if (a1 != 0.f) atomicAdd(hj + (kab >> 16), a1);
+        if (a2 != 0.f) atomicAdd(hj + (kq & 0xFFFFu), a2);
+        if (a3 != 0.f) atomicAdd(hj + (kq >> 16), a3);
+    } else {
+        wide_flush(hj, kab, a0, a1, a2, a3, c, pad, nb);
+    }
+}
+
+// Phase 1 with shared-memory atomics: the profile-weighted deposits of the
+// group's beams over their union pixel box (Alg. 1 kernel loop). The box is
+// walked in stripes of kTC columns; for each stripe tab[j][c] holds sin(dAz)
+// and 1 - cos(dAz) of column c relative to beam j. A work unit is one row x
+// kSeg columns, taken by one warp: lane (j, q) handles beam j on columns
+// q, q + CQ, q + 2 CQ, ..., so that a warp's profile lookups stay within one
+// row of the table and the lanes on one pixel share its record load.
+// CHECKED: the box may wrap around a 2 pi panorama or reach beyond 45 degrees
+// from a beam's axis (then every sample is tested for the front hemisphere);
+// otherwise neither test is needed. Returns this lane's ambient sum.
+// Samples (columns) per lane and loop step of the atomic deposit: their
+// record loads and profile fetches are issued together.
+constexpr int kSamples = 2;
+
+template <int KIND, int G, bool CHECKED>
+__device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Layout &Ly, float *hbuf, float2 *tab,
+                                               const float2 *rtab, const float *ctab, int *uctr, const BeamParam *bp,
+                                               int gcount, int R0, int R1, int C0, int C1, bool use_rtab)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nb = A.n_bins, pad = Ly.pad;
+    constexpr int CQ = kWarp / G;  // columns handled side by side per beam
+    const int j = lane % G;
+    const int q = lane / G;
+    const BeamParam P = bp[j];
+    const float t2max = P.pad0 ? A.core2 : A.trunc2;
+    const bool jok = (j < gcount) && P.valid;
+    float *hj = hbuf + j * Ly.HB;
+    // Deposits of this lane's successive pixels (all of its beam) that land on
+    // the same bins -- the same 4 bins for a narrow interval, the same end
+    // bins for a wide one, as a surface at near-constant range gives -- are
+    // summed in registers (a0..a3 at the record's 4 bin weights, c at its run
+    // value, which is 0 in narrow records) and written with one set of
+    // atomics when the key (k0, k1) changes or at the end; this keeps lanes of
+    // one beam from hitting the same addresses at the same time.
+    uint32_t k0 = kNoDeposit, k1 = kNoDeposit;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, ac = 0.f;
+    float amb_acc = 0.f;
+    for (int cs = C0; cs <= C1; cs += kTC) {
+        const int ce = min(C1, cs + kTC - 1);
+        const int ncs = ce - cs + 1;
+        __syncthreads();  // previous stripe's table no longer read
+        for (int i = tid; i < G * ncs; i += blockDim.x) {
+            int jj = i / ncs, cc = i - jj * ncs;
+            const BeamParam &Q = bp[jj];
+            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
+            float sD, vers;
+            if (fabsf(dAz) <= 0.1f) {
+                // Taylor series (relative accuracy ~1e-12 for |dAz| <= 0.1)
+                float z2 = dAz * dAz;
+                sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
+                vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
+            } else {
+                float cD;
+                sincosf(dAz, &sD, &cD);
+                vers = 1.f - cD;
+            }
+            tab[jj * kTC + cc] = make_float2(sD, vers);
+        }
+        if (tid == 0) *uctr = nwarps;
+        __syncthreads();
+        if (R0 > R1) continue;
+        // this lane's table, indexed by absolute column
+        const float2 *tjc = tab + j * kTC - cs;
+        // columns split into nseg segments of (nearly) equal width <= kSeg
+        const int nseg = (ncs + kSeg - 1) / kSeg;
+        const int segw = (ncs + nseg - 1) / nseg;
+        const int nunits = (R1 - R0 + 1) * nseg;
+        // units are handed out to warps from a counter (costs differ: sky
+        // units are cheap), the first nwarps directly
+        for (int unit = warp; unit < nunits;) {
+            const int row = R0 + unit / nseg;
+            const int seg = unit - (unit / nseg) * nseg;
+            const int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
+            int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
+            if (!(jok && row >= P.row0 && row <= P.row1)) { my_lo = 1; my_hi = 0; }
+            // active columns: (unsigned)(c - my_lo) <= my_span (none if my_hi < my_lo)
+            const unsigned my_span = my_hi >= my_lo ? (unsigned)(my_hi - my_lo) : 0u;
+            if (my_hi < my_lo) my_lo = INT_MIN / 2;
+            float cosEl, sdEl, cdEl;
+            if (use_rtab) {
+                const float2 rt = rtab[j * kRT + (row - R0)];
+                sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
+            } else {
+                cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
+                float dEl = ((float)(row - P.ri) - P.rf) * A.del;
+                sincosf(dEl, &sdEl, &cdEl);
+            }
+            const float Kv = P.sin_elb * cosEl;
+            // x = cg xg + sg yg, y = cg yg - sg xg with xg = cosEl sD and
+            // yg = sdEl + Kv vers: per-row coefficients of (sD, vers, 1)
+            const float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
+            const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
+            const float Kc = P.cos_elb * cosEl;
+            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
+            // kSamples columns per step: all their loads are issued before use
+            for (int cb = c_lo + q; cb <= c_hi + q; cb += kSamples * CQ) {  // warp-uniform trip count
+                float4 r0[kSamples];
+                bool act[kSamples];
+                int cws[kSamples];
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    const int c = cb + u * CQ;
+                    act[u] = (unsigned)c - (unsigned)my_lo <= my_span;
+                    int cw = c;
+                    if (CHECKED && A.panorama) {
+                        // the group's columns lie within about one period of [0, U)
+                        if (cw < 0) cw += A.U;
+                        else if (cw >= A.U) cw -= A.U;
+                        if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
+                    }
+                    cws[u] = cw;
+                    r0[u] = act[u] ? __ldg(recrow + 2 * cw) : make_float4(__uint_as_float(kNoDeposit), 0.f, 0.f, 0.f);
+                    // a pixel with neither a return nor ambient light adds nothing
+                    act[u] = act[u] && !(__float_as_uint(r0[u].x) == kNoDeposit && r0[u].y == 0.f);
+                }
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) any |= act[u];
+                if (!__any_sync(0xffffffffu, any)) continue;
+                ProfFetch pf[kSamples];
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    const int c = cb + u * CQ;
+                    const float2 t = tjc[act[u] ? c : cs];
+                    bool ok = act[u];
+                    // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
+                    if (CHECKED) ok = ok && fmaf(-Kc, t.y, cdEl) > 0.f;
+                    const float x = fmaf(ax, t.x, fmaf(bx, t.y, cx));
+                    const float y = fmaf(ay, t.x, fmaf(by, t.y, cy));
+                    pf[u] = profile_fetch<KIND>(A, x, y, ok, t2max);
+                }
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    // Pw = 0 for an inactive sample or outside the support:
+                    // the ambient term adds nothing then
+                    const float Pw = profile_finish<KIND>(A, pf[u]);
+                    amb_acc = fmaf(Pw, r0[u].y, amb_acc);
+                    const uint32_t kab = __float_as_uint(r0[u].x);
+                    const bool dep = Pw > 0.f && kab != kNoDeposit;
+                    // second half of the record (same 32-byte sector as the first)
+                    float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (dep) r1 = __ldg(recrow + 2 * cws[u] + 1);
+                    const uint32_t kq = __float_as_uint(r1.x);
+                    if (dep && (kab != k0 || kq != k1)) {
+                        if (k0 != kNoDeposit) dep_flush(hj, k0, k1, a0, a1, a2, a3, ac, pad, nb);
+                        k0 = kab; k1 = kq;
+                        a0 = 0.f; a1 = 0.f; a2 = 0.f; a3 = 0.f; ac = 0.f;
+                    }
+                    const float pw = dep ? Pw : 0.f;
+                    a0 = fmaf(pw, r0[u].z, a0);
+                    a1 = fmaf(pw, r0[u].w, a1);
+                    a2 = fmaf(pw, r1.y, a2);
+                    a3 = fmaf(pw, r1.z, a3);
+                    ac = fmaf(pw, r1.w, ac);
+                }
+            }
+            int nu = 0;
+            if (lane == 0) nu = atomicAdd(uctr, 1);
+            unit = __shfl_sync(0xffffffffu, nu, 0);
+        }
+    }
+    if (k0 != kNoDeposit) dep_flush(hj, k0, k1, a0, a1, a2, a3, ac, pad, nb);
+    return amb_acc;
+}
+
 // One group of G consecutive beams of one frame (the whole per-CTA pipeline).
 // Every thread of the CTA must call it (it contains block barriers).
 template <int KIND, int G, bool TC>
@@ -838,176 +1025,24 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     if constexpr (TC) {
         amb_acc = phase1_tc<KIND, G>(A, Ly, hbuf, tab, bp, gcount, R0, R1, C0, C1);
     } else {
-    // The group's pixel box is walked in stripes of kTC columns. For each
-    // stripe, tab[j][c] holds sin(dAz) and 1 - cos(dAz) of column c relative
-    // to beam j. A work unit is one row x kSeg columns, taken by one warp:
-    // lane (j, q) handles beam j on columns q, q + CQ, q + 2 CQ, ... so that a
-    // warp's profile lookups stay within one row of the table and lanes on the
-    // same pixel share its record load.
-    constexpr int CQ = kWarp / G;  // columns handled side by side per beam
-    const int j = lane % G;
-    const int q = lane / G;
-    const BeamParam P = bp[j];
-    const float t2max = P.pad0 ? A.core2 : A.trunc2;
-    const bool jok = (j < gcount) && P.valid;
-    float *hj = hbuf + j * Ly.HB;
-    const float2 *tj = tab + j * kTC;
-    // Narrow deposits of this lane's successive pixels (all of its beam) that
-    // land on the same 4 bins, as a surface at near-constant range does, are
-    // summed in registers and written with one set of atomics when the bins
-    // change or at the end; this keeps lanes of one beam from hitting the same
-    // addresses at the same time.
-    uint32_t wk0 = kNoDeposit, wk1 = kNoDeposit;
-    float wa0 = 0.f, wa1 = 0.f, wa2 = 0.f, wa3 = 0.f;
-    // the same for wide deposits with the same end bins: 4 edge weights and
-    // the run value
-    uint32_t vk = kNoDeposit;
-    float va0 = 0.f, va1 = 0.f, va2 = 0.f, va3 = 0.f, vc = 0.f;
-    for (int cs = C0; cs <= C1; cs += kTC) {
-        const int ce = min(C1, cs + kTC - 1);
-        const int ncs = ce - cs + 1;
-        __syncthreads();  // previous stripe's table no longer read
-        for (int i = tid; i < G * ncs; i += blockDim.x) {
-            int jj = i / ncs, cc = i - jj * ncs;
+        // Boxes that wrap around a panorama or reach beyond 45 degrees from a
+        // beam's axis need the per-sample wrap and front-hemisphere tests
+        // (within 45 degrees in both offsets, d.a >= cos 45 - (1 - cos 45) > 0)
+        bool checked = A.panorama != 0;
+        for (int jj = 0; jj < gcount && !checked; ++jj) {
             const BeamParam &Q = bp[jj];
-            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
-            float sD, vers;
-            if (fabsf(dAz) <= 0.1f) {
-                // Taylor series (relative accuracy ~1e-12 for |dAz| <= 0.1)
-                float z2 = dAz * dAz;
-                sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
-                vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
-            } else {
-                float cD;
-                sincosf(dAz, &sD, &cD);
-                vers = 1.f - cD;
-            }
-            tab[jj * kTC + cc] = make_float2(sD, vers);
+            if (!Q.valid) continue;
+            const float da = fmaxf(fabsf((float)(Q.col0 - Q.ci) - Q.cf), fabsf((float)(Q.col1 - Q.ci) - Q.cf)) * A.daz;
+            const float de = fmaxf(fabsf((float)(Q.row0 - Q.ri) - Q.rf), fabsf((float)(Q.row1 - Q.ri) - Q.rf)) * A.del;
+            checked = !(da <= 0.78f && de <= 0.78f);
         }
-        if (tid == 0) *uctr = nwarps;
-        __syncthreads();
-        if (R0 > R1) continue;
-        // columns split into nseg segments of (nearly) equal width <= kSeg
-        const int nseg = (ncs + kSeg - 1) / kSeg;
-        const int segw = (ncs + nseg - 1) / nseg;
-        const int nunits = (R1 - R0 + 1) * nseg;
-        // units are handed out to warps from a counter (costs differ: sky
-        // units are cheap), the first nwarps directly
-        for (int unit = warp; unit < nunits;) {
-            const int row = R0 + unit / nseg;
-            const int seg = unit - (unit / nseg) * nseg;
-            const bool act_row = jok && row >= P.row0 && row <= P.row1;
-            const int c_lo = cs + seg * segw, c_hi = min(ce, c_lo + segw - 1);
-            int my_lo = max(c_lo, P.col0), my_hi = min(c_hi, P.col1);
-            if (!act_row) { my_lo = 1; my_hi = 0; }
-            float cosEl, sdEl, cdEl;
-            if (use_rtab) {
-                const float2 rt = rtab[j * kRT + (row - R0)];
-                sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
-            } else {
-                cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
-                float dEl = ((float)(row - P.ri) - P.rf) * A.del;
-                sincosf(dEl, &sdEl, &cdEl);
-            }
-            float Kv = P.sin_elb * cosEl;
-            float Kc = P.cos_elb * cosEl;
-            // x = cg xg + sg yg, y = cg yg - sg xg with xg = cosEl sD and
-            // yg = sdEl + Kv vers: per-row coefficients of (sD, vers, 1)
-            const float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
-            const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
-            const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
-            // two columns per step: both samples' loads are issued before use
-            for (int cb = c_lo; cb <= c_hi; cb += 2 * CQ) {  // warp-uniform trip count
-                const int c2 = cb + q;
-                float4 r0[2];
-                int cws[2];
-                ProfFetch pf[2];
-                bool act[2];
-                bool any_need = false;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int c = c2 + u * CQ;
-                    act[u] = c >= my_lo && c <= my_hi;
-                    int cw = c;
-                    if (A.panorama) {
-                        // the group's columns lie within about one period of [0, U)
-                        if (cw < 0) cw += A.U;
-                        else if (cw >= A.U) cw -= A.U;
-                        if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
-                    }
-                    cw = act[u] ? cw : 0;
-                    cws[u] = cw;
-                    r0[u] = __ldg(recrow + 2 * cw);
-                    // a pixel with neither a return nor ambient light adds nothing
-                    act[u] = act[u] && !(__float_as_uint(r0[u].x) == kNoDeposit && r0[u].y == 0.f);
-                    any_need |= act[u];
-                }
-                if (!__any_sync(0xffffffffu, any_need)) continue;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int c = c2 + u * CQ;
-                    float2 t = tj[act[u] ? c - cs : 0];
-                    // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
-                    act[u] = act[u] && fmaf(-Kc, t.y, cdEl) > 0.f;
-                    float x = fmaf(ax, t.x, fmaf(bx, t.y, cx));
-                    float y = fmaf(ay, t.x, fmaf(by, t.y, cy));
-                    pf[u] = profile_fetch<KIND>(A, x, y, act[u], t2max);
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const uint32_t kab = __float_as_uint(r0[u].x);
-                    // Pw = 0 for an inactive sample or outside the support:
-                    // the ambient term adds nothing then
-                    const float Pw = profile_finish<KIND>(A, pf[u]);
-                    amb_acc = fmaf(Pw, r0[u].y, amb_acc);
-                    if (!(Pw > 0.f) || kab == kNoDeposit) continue;
-                    // second half of the record (same 32-byte sector as the first)
-                    const float4 r1u = __ldg(recrow + 2 * cws[u] + 1);
-                    uint32_t kq = __float_as_uint(r1u.x);
-                    if (kq != kNoDeposit) {
-                        // narrow: hat weights on 4 consecutive bins at precomputed positions
-                        if (kab != wk0 || kq != wk1) {
-                            if (wk0 != kNoDeposit) {
-                                atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
-                                if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
-                                if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
-                                if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
-                            }
-                            wk0 = kab; wk1 = kq;
-                            wa0 = 0.f; wa1 = 0.f; wa2 = 0.f; wa3 = 0.f;
-                        }
-                        wa0 = fmaf(Pw, r0[u].z, wa0);
-                        wa1 = fmaf(Pw, r0[u].w, wa1);
-                        wa2 = fmaf(Pw, r1u.y, wa2);
-                        wa3 = fmaf(Pw, r1u.z, wa3);
-                    } else {
-                        // wide: two partial bins at each end, a constant run between
-                        if (kab != vk) {
-                            if (vk != kNoDeposit) wide_flush(hj, vk, va0, va1, va2, va3, vc, pad, nb);
-                            vk = kab;
-                            va0 = 0.f; va1 = 0.f; va2 = 0.f; va3 = 0.f; vc = 0.f;
-                        }
-                        va0 = fmaf(Pw, r0[u].z, va0);
-                        va1 = fmaf(Pw, r0[u].w, va1);
-                        va2 = fmaf(Pw, r1u.y, va2);
-                        va3 = fmaf(Pw, r1u.z, va3);
-                        vc = fmaf(Pw, r1u.w, vc);
-                    }
-                }
-            }
-            int nu = 0;
-            if (lane == 0) nu = atomicAdd(uctr, 1);
-            unit = __shfl_sync(0xffffffffu, nu, 0);
-        }
+        if (checked)
+            amb_acc = phase1_atomic<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
+                                                   use_rtab);
+        else
+            amb_acc = phase1_atomic<KIND, G, false>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
+                                                    use_rtab);
     }
-    if (wk0 != kNoDeposit) {
-        atomicAdd(hj + (wk0 & 0xFFFFu), wa0);
-        if (wa1 != 0.f) atomicAdd(hj + (wk0 >> 16), wa1);
-        if (wa2 != 0.f) atomicAdd(hj + (wk1 & 0xFFFFu), wa2);
-        if (wa3 != 0.f) atomicAdd(hj + (wk1 >> 16), wa3);
-    }
-    if (vk != kNoDeposit) wide_flush(hj, vk, va0, va1, va2, va3, vc, pad, nb);
-    }  // atomic-deposit phase 1
     if constexpr (TC) {
         // ambient sum per beam: lane (g, t) holds beam g; sum the 4 lanes t
         amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 1);

@@ -2,13 +2,18 @@
 
 Bar (per beam): waveform relative L2 error <= 1e-3; echo counts and bins
 (start, end, peak) bit-exact; echo range and EPW within 1 mm; intensity and
-peak within 1e-3 relative. Beams whose oracle waveform has a bin within
-1e-4 T of the threshold are ambiguous (float rounding may legitimately move a
-crossing): they are excluded from the comparison with the oracle's echoes,
-counted, and must stay below 2 % of the beams (a 1e-4 band around each of an
-echo's two crossings catches roughly 0.4 % of echoes). An echo whose peak has a runner-up within 1e-4 is compared except for
-its peak bin and range. For the ambiguous beams the echo extraction is still
-checked exactly, by running the FP64 extraction on the GPU's own waveform.
+peak within 1e-3 relative (oracle/parity.py).
+
+Guard band. The echo scan compares bins with the threshold T strictly; an
+echo whose run or its two neighbouring bins hold an oracle value within
+BAND * T of T may legitimately differ in FP32, so it is left out of the
+bit-exact comparison (the echo alone, not its beam), counted, and must stay
+at or below 0.1 % of the compared echoes. BAND = 1e-5 lies above the largest
+deviation between the GPU waveform and the oracle's at bins near T that the
+full-size workloads show (2.3e-6 T on the full frame, 7.4e-6 T on the
+wide-tail frame), so an echo outside the band cannot flip. For beams with an
+ambiguous echo the echo extraction is still checked exactly, by running the
+FP64 extraction on the GPU's own waveform.
 """
 import math
 import os
@@ -17,6 +22,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from oracle import parity as PR
 from paper_2512_05932_gb300 import lidar
 from paper_2512_05932_gb300 import scenes as S
 
@@ -73,41 +79,29 @@ def check_own_waveform(b, wave_b, ech_b, cnt_b, pulse, T, coef, max_echoes):
         assert abs(g["epw_m"] - e[i]["epw_m"]) <= 1e-4 and abs(g["range_m"] - e[i]["range_m"]) <= 1e-4
 
 
+BAND = 1e-5
+MAX_AMBIGUOUS = 1e-3  # fraction of the compared echoes
+
+
+def ambiguous_ok(st, strict=False):
+    """At most 0.1 % of the compared echoes are ambiguous; a check on fewer
+    than 1000 echoes may have one (strict: the 0.1 % alone, for the large
+    samples of the full-size workloads)."""
+    lim = MAX_AMBIGUOUS * st["echoes"]
+    return st["ambiguous"] <= (lim if strict else max(1.0, lim))
+
+
 def compare(ref, wave, ech, cnt, beams, T, max_echoes, pulse=None, tol_l2=1e-3):
-    stats = dict(beams=len(beams), ambiguous=0, echoes=0, max_l2=0.0, max_dr=0.0)
+    st, fails = PR.compare_frame(ref, beams, wave, ech, cnt, T, max_echoes, BAND, tol_l2)
+    assert not fails, fails[:10]
+    # beams with an echo in the band: the extraction itself, on the GPU's waveform
     for s, b in enumerate(beams):
-        x = ref["xi"][s]
-        nrm = np.linalg.norm(x)
-        err = np.linalg.norm(wave[b] - x) / nrm if nrm > 0 else np.abs(wave[b]).max()
-        stats["max_l2"] = max(stats["max_l2"], err)
-        assert err <= tol_l2, f"beam {b}: waveform rel. L2 error {err:.3g}"
-        if np.any(np.abs(x - T) <= 1e-4 * T):
-            # a bin within the guard band: FP32 rounding may legitimately move
-            # this crossing, so only the extraction logic itself is checked
-            stats["ambiguous"] += 1
+        if np.any(np.abs(ref["xi"][s] - T) <= BAND * T):
             check_own_waveform(b, wave[b], ech[b], cnt[b], pulse, T, ref["coef"], max_echoes)
-            continue
-        n_ref = min(int(ref["counts"][s]), max_echoes)
-        assert cnt[b] == n_ref, f"beam {b}: {cnt[b]} echoes vs oracle {n_ref}"
-        for i in range(n_ref):
-            o, g = ref["echoes"][s][i], ech[b, i]
-            stats["echoes"] += 1
-            assert (g["bin_start"], g["bin_end"]) == (o["bin_start"], o["bin_end"]), (b, i, g, o)
-            assert abs(g["epw_m"] - o["epw_m"]) <= 1e-3, (b, i, g["epw_m"], o["epw_m"])
-            assert g["intensity"] == pytest.approx(o["intensity"], rel=1e-3)
-            assert g["flags"] & 3 == o["flags"] & 3
-            if not (o["flags"] & O.PEAK_AMBIGUOUS):
-                assert g["bin_peak"] == o["bin_peak"], (b, i, g, o)
-                dr = abs(g["range_m"] - o["range_m"])
-                stats["max_dr"] = max(stats["max_dr"], dr)
-                assert dr <= 1e-3, (b, i, g["range_m"], o["range_m"])
-                assert g["peak"] == pytest.approx(o["peak"], rel=1e-3)
-        for i in range(n_ref, max_echoes):
-            assert ech[b, i]["bin_end"] == 0 and ech[b, i]["flags"] == 0
-    return stats
+    return st
 
 
-def check_workload(w, beams=None, host=False, max_ambiguous_frac=0.02, deposit=0):
+def check_workload(w, beams=None, host=False, deposit=0, strict=False):
     L, wave, ech, cnt = run_gpu(w, host, deposit)
     if beams is None:
         beams = np.arange(len(w.dirs), dtype=np.int32)
@@ -116,7 +110,7 @@ def check_workload(w, beams=None, host=False, max_ambiguous_frac=0.02, deposit=0
     assert info["profile_norm"] == pytest.approx(ref["Z"], rel=1e-7)
     np.testing.assert_allclose(info["epw_coef"], ref["coef"], rtol=1e-9, atol=1e-12)
     st = compare(ref, wave, ech, cnt, beams, w.calib["threshold"], w.calib["max_echoes"], w.pulse)
-    assert st["ambiguous"] <= max(1, max_ambiguous_frac * len(beams)), st
+    assert ambiguous_ok(st, strict), st
     L.close()
     return st
 
@@ -125,8 +119,9 @@ def check_workload(w, beams=None, host=False, max_ambiguous_frac=0.02, deposit=0
 
 
 def test_small_plane_retro_all_beams():
+    # seeded so that no bin lies within 7e-4 T of T: every echo is compared
     st = check_workload(S.small_plane_retro())
-    assert st["echoes"] >= 500
+    assert st["echoes"] >= 500 and st["ambiguous"] == 0
 
 
 def test_tiny_ragged_rolled_pose():
@@ -139,13 +134,14 @@ def test_tiny_host_entry_point(host):
 
 
 def test_full_frame_sampled_beams():
+    """The benchmarked full frame on 1024 evenly spaced beams (the sample the
+    benchmark checks) plus the first, last and row-end beams."""
     w = S.full_frame_boxes()
-    g = S.rng(77)
     n = len(w.dirs)
-    beams = np.unique(np.concatenate([[0, 1, 1599, 1600, n // 2, n - 1600, n - 1],
-                                      g.choice(n, 57, replace=False)])).astype(np.int32)
-    st = check_workload(w, beams=beams)
-    assert st["echoes"] > 0
+    beams = np.unique(np.concatenate([np.linspace(0, n - 1, 1024).astype(np.int64),
+                                      [0, 1, 1599, 1600, n // 2, n - 1600, n - 1]])).astype(np.int32)
+    st = check_workload(w, beams=beams, strict=True)
+    assert st["echoes"] >= 500, st
 
 
 @pytest.mark.parametrize("host", ["pinned", "pageable", "pageable_planes"])
@@ -312,6 +308,19 @@ def test_panorama_wraps_at_seam():
     check_workload(w)
 
 
+def test_gbuffer_across_the_azimuth_seam():
+    """A G-buffer (not a panorama) whose azimuth range crosses +-180 deg, seen
+    by a sensor facing backwards: beams on both sides of the seam."""
+    base = S.small_plane_retro()
+    R = S.pose_ypr(math.pi, 0.01, 0.0)
+    gb = S.plane_retro_frame(S.rng(21), 320, 160, R)
+    assert gb.az0 < math.pi < gb.az0 + gb.U * gb.daz
+    dirs = S.grid_pattern(24, 10, 5.0 * DEG, 2.5 * DEG)
+    w = S.Workload("seam", gb, dirs, base.profile, base.pulse, base.calib, R)
+    st = check_workload(w)
+    assert st["echoes"] >= 200, st
+
+
 def test_yaw_pose_matches_rotated_pattern():
     w = S.small_plane_retro()
     L, wave0, _, cnt0 = run_gpu(w)
@@ -353,11 +362,9 @@ def test_invalid_gbuffer_rejected_on_device_call():
 
 def test_wide_tail_frame_sampled_beams():
     """8192x4096 G-buffer, 200k beams, tail truncated at 2 deg, 4096 bins of
-    0.05 ns: the full-size instance, sampled beams against the oracle."""
+    0.05 ns: the full-size instance on a seeded 1 % subsample (2000 beams)."""
     w = S.wide_frame()
-    g = S.rng(31)
     n = len(w.dirs)
-    rows, cols = g.integers(120, 280, 16), g.integers(100, 400, 16)
-    beams = np.unique(np.concatenate([rows * 500 + cols, g.choice(n, 8, replace=False), [0, n - 1]])).astype(np.int32)
-    st = check_workload(w, beams=beams)
-    assert st["echoes"] >= 8
+    beams = np.sort(S.rng(2000).choice(n, 2000, replace=False)).astype(np.int32)
+    st = check_workload(w, beams=beams, strict=True)
+    assert st["echoes"] >= 1000, st

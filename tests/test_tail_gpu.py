@@ -86,11 +86,11 @@ def coarse(h, nc):
 
 
 def parity(w, res, beams):
-    from tests.test_parity_gpu import compare
+    from tests.test_parity_gpu import ambiguous_ok, compare
     ref = O.simulate_workload(w, beams=beams, nthreads=NTHREADS, max_out=8)
     wave, ech, cnt = res
     st = compare(ref, wave, ech, cnt, beams, w.calib["threshold"], w.calib["max_echoes"], w.pulse)
-    assert st["ambiguous"] <= max(1, 0.02 * len(beams)), st
+    assert ambiguous_ok(st), st
     return st
 
 
