@@ -405,13 +405,29 @@ int32_t lidar_launches_per_simulate(const lidar_t *lidar);
  *                          relative error ~2^-16 per product).
  *   LIDAR_DEPOSIT_TC_BF16  the same with plain BF16 factors (one product,
  *                          relative error ~2^-8 per product).
- * The tensor-core forms process 8 beams per CTA (4 when two CTAs of 8 would
- * not share an SM). Applies to later lidar_simulate* and lidar_simulate_batch
- * calls of this simulator (a batch uses its executor's mode). */
+ *   LIDAR_DEPOSIT_TCGEN05_BF16  5th-generation tensor cores (tcgen05): 16
+ *                          beams per CTA keep their histograms in tensor memory
+ *                          (FP32); per 64-pixel tile and 128-bin block,
+ *                          (bins x pixels) hat weights times (pixels x beams)
+ *                          profile weights, both BF16 (relative error ~2^-8 per
+ *                          product). The hat weights are built once per pixel
+ *                          and tile for all 16 beams.
+ *   LIDAR_DEPOSIT_TCGEN05_FP16  the same with FP16 factors, each side scaled
+ *                          by a power of two (per CTA: the frame's largest
+ *                          pixel weight and the profile's maximum near 2^14;
+ *                          relative error ~2^-11 per product).
+ * The mma.sync forms process 8 beams per CTA (4 when two CTAs of 8 would not
+ * share an SM). The tcgen05 forms take n_bins <= 4096 and serve lidar_simulate,
+ * lidar_simulate_noalloc and lidar_simulate_batch; the echo-only and the host
+ * entry points reject them (LIDAR_EINVAL). Applies to later calls of this
+ * simulator (a batch uses its executor's mode); LIDAR_EINVAL for an unknown
+ * mode or one the simulator's n_bins does not allow. */
 enum {
     LIDAR_DEPOSIT_ATOMIC = 0,
     LIDAR_DEPOSIT_TC_SPLIT = 1,
-    LIDAR_DEPOSIT_TC_BF16 = 2
+    LIDAR_DEPOSIT_TC_BF16 = 2,
+    LIDAR_DEPOSIT_TCGEN05_BF16 = 3,
+    LIDAR_DEPOSIT_TCGEN05_FP16 = 4
 };
 lidar_status_t lidar_set_deposit(lidar_t *lidar, int32_t mode);
 
@@ -431,6 +447,20 @@ enum {
     LIDAR_ECHOES_STRONGEST = 1
 };
 lidar_status_t lidar_set_echo_mode(lidar_t *lidar, int32_t mode);
+
+/* Testing aid for the bounded wait of the echo-only form (the paper has no
+ * counterpart): marks every slot of this simulator's echo-only waveform pool
+ * held (held != 0) or free (held == 0), allocating the pool first if the
+ * current deposit form has none yet. While the slots are held, a
+ * lidar_simulate_echoes call cannot claim one: each of its CTAs polls a
+ * bounded number of times (1024 passes over the pool, ~1 us apart), gives up,
+ * writes nothing for its beams and sets the simulator's error word, which the
+ * next lidar_sync reports as LIDAR_ETIMEOUT (and clears). Nothing waits
+ * forever and no fault is raised. Synchronous: returns after the device has
+ * finished the change; do not call it while a simulation of this simulator is
+ * in flight. LIDAR_EINVAL for a NULL simulator, LIDAR_ECUDA / LIDAR_ENOMEM
+ * from the allocation or the memset. */
+lidar_status_t lidar_hold_echo_slots(lidar_t *lidar, int32_t held);
 
 /* Per-kernel timing. While enabled, every lidar_simulate call records CUDA
  * events on its stream around each of its kernels (setup, footprint_wave).

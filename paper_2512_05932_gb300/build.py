@@ -16,7 +16,7 @@ SOURCES = ["lidar_api.cpp", "lidar_kernels.cu", "lidar_noalloc.cu", "lidar_tail.
            "lidar_pinhole.cu"]
 HEADERS = [os.path.join(INCLUDE, "lidar.h"), os.path.join(INCLUDE, "lidar_tail.h"), os.path.join(INCLUDE, "lidar_stack.h"), os.path.join(CSRC, "lidar_internal.h"),
            os.path.join(CSRC, "lidar_host.h"), os.path.join(CSRC, "lidar_tail_internal.h"),
-           os.path.join(CSRC, "lidar_net_internal.h")]
+           os.path.join(CSRC, "lidar_net_internal.h"), os.path.join(CSRC, "lidar_deposit_umma.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -335,6 +335,8 @@ void free_all(lidar_t *l)
 {
     free_batch(l);
     free_events(l);
+    cudaFree(l->d_wmax);
+    cudaFree(l->d_perm);
     cudaFree(l->d_dirs);
     if (l->node_tex) cudaDestroyTextureObject(l->node_tex);
     if (l->d_nodes) cudaFreeArray(l->d_nodes);
@@ -443,6 +445,8 @@ gbl::FootprintArgs model_args(const lidar_t *l)
     fa.rA = (float)(0.5 * kC * (l->t0 + 0.5 * l->dt));
     fa.rB = (float)(0.5 * kC * l->dt);
     fa.tc_split = l->deposit == 1 ? 1 : 0;
+    fa.umma_pmax = (float)l->pmax;
+    fa.umma_wmax = nullptr;
     fa.inner2 = -1.f;  // no annulus: the whole profile
     return fa;
 }
@@ -497,11 +501,84 @@ gbl::FootprintArgs frame_args(const lidar_t *l, const lidar_gbuffer_t *g, const 
     return fa;
 }
 
+// Order of the beams for the tcgen05 deposit's groups of 16: beams in bands
+// of height s of the pattern's (azimuth * cos(elevation), elevation) plane,
+// each band by azimuth, s the side of the square that holds 16 beams at the
+// pattern's mean density. Consecutive slots are then near each other in both
+// directions (a grid gives groups of about 4 x 4 beams; a line scan whose rows
+// are farther apart than s keeps its rows), which keeps a group's union pixel
+// box close to one beam's.
+std::vector<int32_t> group_order(const lidar_t *l)
+{
+    const int n = l->n_beams;
+    std::vector<double> x(n), y(n);
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int b = 0; b < n; ++b) {
+        const double dx = l->h_dirs[3 * b], dy = l->h_dirs[3 * b + 1], dz = l->h_dirs[3 * b + 2];
+        const double el = std::asin(std::max(-1.0, std::min(1.0, dz)));
+        y[b] = el;
+        x[b] = std::atan2(dy, dx) * std::cos(el);
+        x0 = std::min(x0, x[b]); x1 = std::max(x1, x[b]);
+        y0 = std::min(y0, y[b]); y1 = std::max(y1, y[b]);
+    }
+    std::vector<int32_t> order(n);
+    for (int b = 0; b < n; ++b) order[b] = b;
+    const double area = std::max(x1 - x0, 1e-9) * std::max(y1 - y0, 1e-9);
+    const double side = 4.0 * std::sqrt(area / std::max(n, 1));
+    std::vector<long> band(n);
+    for (int b = 0; b < n; ++b) band[b] = (long)std::floor((y[b] - y0) / std::max(side, 1e-12));
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+        if (band[a] != band[c]) return band[a] < band[c];
+        return x[a] < x[c];
+    });
+    return order;
+}
+
+// One frame with the tcgen05 deposit: the setup kernel (with the frame's
+// largest record weight for FP16 operands) and the tensor-core footprint kernel.
+lidar_status_t enqueue_umma(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave,
+                            lidar_echo_t *echoes, int32_t *counts, cudaStream_t s)
+{
+    const bool bf16 = l->deposit == LIDAR_DEPOSIT_TCGEN05_BF16;
+    lidar_status_t st = ensure_scratch(l, (size_t)g->U * g->V);
+    if (st != LIDAR_OK) return st;
+    gbl::SetupArgs sa = setup_args(l, l, g, R, l->d_rec, l->d_beams);
+    sa.beam_ids = l->d_perm;  // beam slots in group order
+    cudaError_t e;
+    if (!bf16) {
+        sa.wmax = l->d_wmax;
+        if ((e = cudaMemsetAsync(l->d_wmax, 0, sizeof(unsigned), s)) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMemsetAsync(weight maximum)");
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    if (l->prof) {
+        size_t mark = l->ev_used;
+        ev0 = next_event(l); ev1 = next_event(l); ev2 = next_event(l);
+        if (!ev0 || !ev1 || !ev2) { l->ev_used = mark; ev0 = ev1 = ev2 = nullptr; }
+    }
+    if (ev0) cudaEventRecord(ev0, s);
+    if ((e = gbl::launch_setup(sa, s)) != cudaSuccess) return cuda_fail(l, e, "setup kernel launch");
+    if (ev1) cudaEventRecord(ev1, s);
+    gbl::FootprintArgs fa = frame_args(l, g, sa);
+    fa.wave = wave; fa.echoes = echoes; fa.counts = counts;
+    fa.err = l->d_err;
+    fa.out_ids = l->d_perm;  // slot b writes the outputs of pattern beam d_perm[b]
+    fa.umma_wmax = bf16 ? nullptr : l->d_wmax;
+    if ((e = gbl::launch_umma(l->kind, bf16, l->smem_um, fa, s)) != cudaSuccess)
+        return cuda_fail(l, e, "tcgen05 footprint kernel launch");
+    if (ev2) cudaEventRecord(ev2, s);
+    return LIDAR_OK;
+}
+
 // Enqueues the setup and footprint kernels of one frame on `s`; wave == NULL
 // selects the echo-only form (waveforms in the pooled slots).
 lidar_status_t enqueue(lidar_t *l, const lidar_gbuffer_t *g, const double R[9], float *wave, lidar_echo_t *echoes,
                        int32_t *counts, cudaStream_t s)
 {
+    if (l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16) {
+        if (!wave) return fail(l, LIDAR_EINVAL, "the tcgen05 deposit has no echo-only form");
+        return enqueue_umma(l, g, R, wave, echoes, counts, s);
+    }
     const bool tc = l->deposit != 0;
     if (!wave) {
         lidar_status_t st0 = ensure_slots(l, tc ? l->G_tc : l->G, tc);
@@ -561,7 +638,7 @@ lidar_status_t grow(lidar_t *l, T **p, size_t *cap, size_t need, const char *wha
 
 // Builds the descriptor blob of a batch (host copy) and returns its layout.
 struct BlobLayout {
-    size_t off_setup, off_pix, off_beam, off_frames, off_items, size;
+    size_t off_setup, off_pix, off_beam, off_frames, off_items, off_wmax, size;
     int n_items, total_blocks;
 };
 
@@ -615,7 +692,9 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
         return l->support_rad * l->support_rad / (g.daz * g.del);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    if (l->deposit != 0 && G != 4 && G != 8) G = l->G_tc;
+    const bool um = l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16;
+    if (um) G = gbl::kUmmaBeams;
+    else if (l->deposit != 0 && G != 4 && G != 8) G = l->G_tc;
     std::vector<int2> items;
     for (int f : order) {
         int groups = (fr[f].sensor->n_beams + G - 1) / G;
@@ -627,7 +706,8 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
     B.off_beam = align16(B.off_pix + (n + 1) * sizeof(int));
     B.off_frames = align16(B.off_beam + (n + 1) * sizeof(int));
     B.off_items = align16(B.off_frames + n * sizeof(gbl::FrameDesc));
-    B.size = align16(B.off_items + items.size() * sizeof(int2));
+    B.off_wmax = align16(B.off_items + items.size() * sizeof(int2));
+    B.size = align16(B.off_wmax + n * sizeof(unsigned));
     B.n_items = (int)items.size();
     // the previous batch's graph may still be reading the pinned staging copy
     if (l->blob_pending) {
@@ -664,22 +744,29 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
         D.az0 = hs[f].az0; D.el0 = hs[f].el0; D.daz = hs[f].daz; D.del = hs[f].del;
         D.rec = rec; D.beams = bp;
         D.wave = F.out_waveforms; D.echoes = F.out_echoes.echoes; D.counts = F.out_echoes.counts;
+        if (l->deposit == LIDAR_DEPOSIT_TCGEN05_FP16) {
+            // the frame's largest record weight: zero in the uploaded blob, maximised by the setup kernel
+            unsigned *wm = reinterpret_cast<unsigned *>(l->d_blob + B.off_wmax) + f;
+            hs[f].wmax = wm;
+            D.wmax = wm;
+        }
         hf[f] = D;
     }
+    std::memset(hb + B.off_wmax, 0, n * sizeof(unsigned));
     hpix[n] = pb;
     hbeam[n] = bb;
     B.total_blocks = pb + bb;
     std::memcpy(hb + B.off_items, items.data(), items.size() * sizeof(int2));
 
     // persistent grid size
-    const bool tc = l->deposit != 0;
+    const bool tc = l->deposit != 0 && !um;
     if (tc && G != 4 && G != 8) G = l->G_tc;  // tensor-core form: 4 or 8 beams per CTA
-    size_t smem = gbl::footprint_smem_bytes(G, model_args(l));
-    if ((e = gbl::prepare_footprint_batch(l->kind, G, tc, smem)) != cudaSuccess)
+    size_t smem = um ? l->smem_um : gbl::footprint_smem_bytes(G, model_args(l));
+    if (!um && (e = gbl::prepare_footprint_batch(l->kind, G, tc, smem)) != cudaSuccess)
         return cuda_fail(l, e, "cudaFuncSetAttribute");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, l->device);
-    int per_sm = cps > 0 ? cps : 2;
+    int per_sm = um ? 1 : (cps > 0 ? cps : 2);  // tcgen05: one CTA per SM (its tensor memory)
     int grid = std::max(1, std::min(B.n_items, per_sm * sms));
 
     // graph keyed on everything the captured launches depend on
@@ -697,10 +784,19 @@ lidar_status_t batch_run(lidar_t *l, const lidar_frame_t *fr, int n, cudaStream_
                                                  reinterpret_cast<const int *>(db + B.off_beam), n, B.total_blocks,
                                                  l->d_counter, l->cap_stream);
         gbl::FootprintArgs base = model_args(l);
-        cudaError_t e3 = gbl::launch_footprint_batch(l->kind, G, tc, l->threads, grid, smem, base,
-                                                     reinterpret_cast<const gbl::FrameDesc *>(db + B.off_frames),
-                                                     reinterpret_cast<const int2 *>(db + B.off_items), B.n_items,
-                                                     l->d_counter, l->cap_stream);
+        cudaError_t e3;
+        if (um) {
+            base.err = l->d_err;
+            e3 = gbl::launch_umma_batch(l->kind, l->deposit == LIDAR_DEPOSIT_TCGEN05_BF16, grid, smem, base,
+                                        reinterpret_cast<const gbl::FrameDesc *>(db + B.off_frames),
+                                        reinterpret_cast<const int2 *>(db + B.off_items), B.n_items, l->d_counter,
+                                        l->cap_stream);
+        } else {
+            e3 = gbl::launch_footprint_batch(l->kind, G, tc, l->threads, grid, smem, base,
+                                             reinterpret_cast<const gbl::FrameDesc *>(db + B.off_frames),
+                                             reinterpret_cast<const int2 *>(db + B.off_items), B.n_items,
+                                             l->d_counter, l->cap_stream);
+        }
         e = cudaStreamEndCapture(l->cap_stream, &graph);
         if (e1 != cudaSuccess) return cuda_fail(l, e1, "descriptor upload capture");
         if (e2 != cudaSuccess) return cuda_fail(l, e2, "batch setup launch capture");
@@ -791,6 +887,22 @@ lidar_status_t lidar_create(const lidar_profile_t *p, const lidar_pattern_t *pat
         double Z = l->Z;
         delete l;
         return fail(nullptr, LIDAR_ENUMERIC, "profile integrates to %g", Z);
+    }
+    // the profile's maximum (after normalisation), for the FP16 deposit's scale
+    if (p->kind == LIDAR_PROFILE_RADIAL) {
+        l->pmax = (1.0 + std::max(0.0, p->tail_amp)) / l->Z;
+    } else {
+        double m = 0.0;
+        const int n = l->separable ? p->table_w + p->table_h : p->table_w * p->table_h;
+        if (l->separable) {
+            double mh = 0.0, mv = 0.0;
+            for (int i = 0; i < p->table_w; ++i) mh = std::max(mh, (double)p->table[i]);
+            for (int j = 0; j < p->table_h; ++j) mv = std::max(mv, (double)p->table[p->table_w + j]);
+            m = mh * mv;
+        } else {
+            for (int i = 0; i < n; ++i) m = std::max(m, (double)p->table[i]);
+        }
+        l->pmax = m / l->Z;
     }
 
     // pulse taps, zero-padded so that every tap index of the 32x32 blocks of
@@ -968,6 +1080,8 @@ lidar_status_t lidar_simulate_echoes(lidar_t *l, const lidar_gbuffer_t *g, const
     double R[9];
     if ((st = check_pose(l, pose, R)) != LIDAR_OK) return st;
     if (!echoes || !echoes->echoes || !echoes->counts) return fail(l, LIDAR_EINVAL, "output pointer is NULL");
+    if (l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16)
+        return fail(l, LIDAR_EINVAL, "the tcgen05 deposit has no echo-only form");
     return enqueue(l, g, R, nullptr, echoes->echoes, echoes->counts, (cudaStream_t)stream);
 }
 
@@ -1299,6 +1413,8 @@ lidar_status_t lidar_simulate_host(lidar_t *l, const lidar_gbuffer_t *g, const l
                                    lidar_echo_t *echoes, int32_t *counts, void *stream)
 {
     if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16)
+        return fail(l, LIDAR_EINVAL, "the host entry points do not take the tcgen05 deposit");
     lidar_status_t st = check_gbuffer(l, g);
     if (st != LIDAR_OK) return st;
     double R[9];
@@ -1339,6 +1455,8 @@ lidar_status_t lidar_simulate_host_frames(lidar_t *l, int n_frames, const lidar_
                                           int32_t *const *counts, void *stream)
 {
     if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    if (l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16)
+        return fail(l, LIDAR_EINVAL, "the host entry points do not take the tcgen05 deposit");
     if (n_frames < 0) return fail(l, LIDAR_EINVAL, "n_frames < 0");
     if (n_frames == 0) return LIDAR_OK;
     if (!g || !pose || !echoes || !counts) return fail(l, LIDAR_EINVAL, "frame array is NULL");
@@ -1489,11 +1607,48 @@ lidar_status_t lidar_set_echo_mode(lidar_t *l, int32_t mode)
     return LIDAR_OK;
 }
 
+lidar_status_t lidar_hold_echo_slots(lidar_t *l, int32_t held)
+{
+    if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
+    const bool tc = l->deposit != 0;
+    lidar_status_t st = ensure_slots(l, tc ? l->G_tc : l->G, tc);
+    if (st != LIDAR_OK) return st;
+    // a nonzero busy word is a held slot (claims compare against 0)
+    cudaError_t e = cudaMemset(l->d_slot_busy, held ? 1 : 0, (size_t)l->n_slots * sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? LIDAR_OK : cuda_fail(l, e, "slot pool memset");
+}
+
 lidar_status_t lidar_set_deposit(lidar_t *l, int32_t mode)
 {
     if (!l) return fail(nullptr, LIDAR_EINVAL, "lidar is NULL");
-    if (mode < LIDAR_DEPOSIT_ATOMIC || mode > LIDAR_DEPOSIT_TC_BF16)
+    if (mode < LIDAR_DEPOSIT_ATOMIC || mode > LIDAR_DEPOSIT_TCGEN05_FP16)
         return fail(l, LIDAR_EINVAL, "deposit mode %d unknown", mode);
+    if (mode >= LIDAR_DEPOSIT_TCGEN05_BF16) {
+        if (l->n_bins > gbl::kUmmaMaxBins)
+            return fail(l, LIDAR_EINVAL, "the tcgen05 deposit takes n_bins <= %d (got %d)", gbl::kUmmaMaxBins,
+                        l->n_bins);
+        const size_t smem = gbl::umma_smem_bytes(l->n_bins, l->M);
+        if ((long)smem > 227L * 1024) return fail(l, LIDAR_EINVAL, "n_bins too large for the tcgen05 deposit");
+        const bool bf16 = mode == LIDAR_DEPOSIT_TCGEN05_BF16;
+        cudaError_t e = gbl::prepare_umma(l->kind, bf16, smem);
+        if (e != cudaSuccess) return cuda_fail(l, e, "cudaFuncSetAttribute");
+        // its error word (bounded pipeline waits) and the frame's weight maximum
+        if ((!l->d_err && (e = cudaMalloc(&l->d_err, sizeof(int))) != cudaSuccess) ||
+            (!l->d_wmax && (e = cudaMalloc(&l->d_wmax, sizeof(unsigned))) != cudaSuccess) ||
+            (e = cudaMemset(l->d_err, 0, sizeof(int))) != cudaSuccess)
+            return cuda_fail(l, e, "cudaMalloc(tcgen05 deposit words)");
+        if (!l->d_perm) {
+            std::vector<int32_t> order = group_order(l);
+            if ((e = cudaMalloc(&l->d_perm, order.size() * sizeof(int32_t))) != cudaSuccess ||
+                (e = cudaMemcpy(l->d_perm, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                return cuda_fail(l, e, "beam group order upload");
+        }
+        l->smem_um = smem;
+        l->deposit = mode;
+        return LIDAR_OK;
+    }
     if (mode != LIDAR_DEPOSIT_ATOMIC && (long)l->smem_tc > 227L * 1024)
         return fail(l, LIDAR_EINVAL, "n_bins too large for the tensor-core deposit");
     if (mode != LIDAR_DEPOSIT_ATOMIC) {
@@ -1525,6 +1680,10 @@ lidar_status_t lidar_sync(lidar_t *l, void *stream)
             return cuda_fail(l, e, "error word download");
         if (h) {
             cudaMemset(l->d_err, 0, sizeof(int));
+            if (l->deposit >= LIDAR_DEPOSIT_TCGEN05_BF16)
+                return fail(l, LIDAR_ETIMEOUT,
+                            "tcgen05 deposit: a CTA's pipeline wait gave up (code 0x%08x: wait site, stage, "
+                            "stages claimed); its beams were not written", (unsigned)h);
             return fail(l, LIDAR_ETIMEOUT, "echo-only simulation: a CTA found no free waveform slot; its beams' "
                                            "echoes were not written");
         }

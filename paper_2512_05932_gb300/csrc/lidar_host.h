@@ -40,6 +40,13 @@ struct lidar {
     int32_t echo_mode = 0;  // LIDAR_ECHOES_NEAREST or LIDAR_ECHOES_STRONGEST
     int32_t G_tc = 8;
     size_t smem_tc = 0;
+    // tcgen05 deposit (LIDAR_DEPOSIT_TCGEN05_*): shared memory per CTA, the
+    // profile's maximum (divided by Z) and the frame's largest record weight
+    // (written by the setup kernel; FP16 operands only)
+    size_t smem_um = 0;
+    double pmax = 0.0;
+    unsigned *d_wmax = nullptr;
+    int32_t *d_perm = nullptr;  // beam slot -> pattern beam: groups of 16 nearby beams
     int device = 0;
     // device memory owned by the library
     float *d_dirs = nullptr;

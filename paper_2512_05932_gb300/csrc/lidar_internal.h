@@ -52,6 +52,7 @@ struct SetupArgs {
                              // instead of histogram positions (shared-memory atomics)
     int pix_blocks;
     long pix_begin, pix_end; // setup_kernel: the pixels [pix_begin, pix_end) only
+    unsigned *wmax;          // non-NULL: atomic max of the records' deposit weights (FP32 bits)
     // beams
     int n_beams;
     const float *dirs;       // [n_beams][3]
@@ -127,7 +128,11 @@ struct FootprintArgs {
     int *slot_busy;
     int n_slots;             // slot_sms * slots_per_sm
     int slot_sms, slots_per_sm;
-    int *err;                // set to 1 if a slot claim gives up
+    int *err;                // set to 1 if a slot claim or a tensor-core pipeline wait gives up
+    // tcgen05 deposit (FP16 operands): the frame's largest record weight
+    // (FP32 bits, from the setup kernel) and the profile's maximum
+    const unsigned *umma_wmax;
+    float umma_pmax;
 };
 
 // Per-frame fields of the batched footprint kernel.
@@ -139,6 +144,7 @@ struct FrameDesc {
     float *wave;
     lidar_echo_t *echoes;
     int32_t *counts;
+    const unsigned *wmax;    // tcgen05 deposit with FP16 operands: the frame's largest record weight
 };
 
 // Device address of the fixed scratch of lidar_simulate_noalloc on the current
@@ -156,6 +162,15 @@ cudaError_t launch_footprint(int kind, int G, bool tc, int threads, size_t smem,
 cudaError_t launch_setup_batch(const SetupArgs *frames, const int *pix_blk, const int *beam_blk, int n_frames,
                                int total_blocks, int *counter, cudaStream_t s);
 cudaError_t prepare_footprint_batch(int kind, int G, bool tc, size_t smem);
+// tcgen05 deposit (16 beams per CTA, histograms in tensor memory)
+size_t umma_smem_bytes(int n_bins, int M);
+constexpr int kUmmaBeams = 16;
+constexpr int kUmmaThreads = 288;
+constexpr int kUmmaMaxBins = 4096;  // 32 blocks of 128 bins x 16 beams = 512 TMEM columns
+cudaError_t prepare_umma(int kind, bool bf16, size_t smem);
+cudaError_t launch_umma(int kind, bool bf16, size_t smem, const FootprintArgs &a, cudaStream_t s);
+cudaError_t launch_umma_batch(int kind, bool bf16, int grid, size_t smem, const FootprintArgs &base,
+                              const FrameDesc *frames, const int2 *items, int n_items, int *counter, cudaStream_t s);
 cudaError_t launch_footprint_batch(int kind, int G, bool tc, int threads, int grid, size_t smem,
                                    const FootprintArgs &base, const FrameDesc *frames, const int2 *items,
                                    int n_items, int *counter, cudaStream_t s);

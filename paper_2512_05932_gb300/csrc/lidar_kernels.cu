@@ -62,7 +62,8 @@ __device__ float int_hat(float X0, float X1, float k)
     return acc;
 }
 
-__device__ void setup_pixel(const SetupArgs &A, int idx)
+// Returns the largest deposit weight the pixel's record holds (0 without one).
+__device__ float setup_pixel(const SetupArgs &A, int idx)
 {
     int v = idx / A.U;
     int u = idx - v * A.U;
@@ -185,6 +186,16 @@ __device__ void setup_pixel(const SetupArgs &A, int idx)
     float4 r1 = make_float4(__uint_as_float(kq), h2, h3, cr);
     A.rec[2 * (size_t)idx] = r0;
     A.rec[2 * (size_t)idx + 1] = r1;
+    return fmaxf(fmaxf(fmaxf(h0, h1), fmaxf(h2, h3)), cr);
+}
+
+// Adds a thread's largest record weight to the frame's maximum (FP32 bits
+// of a non-negative value order as unsigned integers): one atomic per warp.
+__device__ __forceinline__ void wmax_reduce(unsigned *wmax, float m)
+{
+    const unsigned mask = __activemask();
+    const unsigned v = __reduce_max_sync(mask, __float_as_uint(fmaxf(m, 0.f)));
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicMax(wmax, v);
 }
 
 // --------------------------------------------------------------------------
@@ -314,9 +325,11 @@ __global__ void __launch_bounds__(256, 6) setup_kernel(SetupArgs A)
         if (b < A.n_beams) setup_beam(A, b);
     } else {
         const int n = (int)A.pix_end;
+        float m = 0.f;
         for (int idx = (int)A.pix_begin + ((int)blockIdx.x - beam_blocks) * blockDim.x + threadIdx.x; idx < n;
              idx += A.pix_blocks * blockDim.x)
-            setup_pixel(A, idx);
+            m = fmaxf(m, setup_pixel(A, idx));
+        if (A.wmax) wmax_reduce(A.wmax, m);
     }
 }
 
@@ -337,7 +350,8 @@ __global__ void __launch_bounds__(256, 6) setup_batch_kernel(const SetupArgs *fr
         }
         const SetupArgs &A = frames[lo];
         int idx = (b - pix_blk[lo]) * blockDim.x + threadIdx.x;
-        if (idx < A.U * A.V) setup_pixel(A, idx);
+        const float m = idx < A.U * A.V ? setup_pixel(A, idx) : 0.f;
+        if (A.wmax) wmax_reduce(A.wmax, m);
     } else {
         const int bb = b - total_pix_blk;
         int lo = 0, hi = n_frames - 1;
@@ -873,15 +887,25 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
             const float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
             const float Kc = P.cos_elb * cosEl;
             const float4 *recrow = A.rec + 2 * (size_t)row * A.U;
-            // kSamples columns per step: all their loads are issued before use
-            for (int cb = c_lo + q; cb <= c_hi + q; cb += kSamples * CQ) {  // warp-uniform trip count
-                float4 r0[kSamples];
+            // kSamples columns per step: all their loads are issued before use.
+            // With CQ >= 8 column phases, lane q takes a contiguous run of Lq
+            // columns (its successive deposits then share their bins more
+            // often, which saves flushes); with fewer phases the columns are
+            // interleaved (q, q + CQ, ...), which keeps a warp's table lookups
+            // and record loads within a narrower stretch of the row.
+            constexpr bool kContig = CQ >= 8;
+            const int Lq = kContig ? (c_hi - c_lo + CQ) / CQ : 0;
+            const int nsteps = kContig ? (Lq + kSamples - 1) / kSamples
+                                       : (c_hi - c_lo + kSamples * CQ) / (kSamples * CQ);
+            for (int st = 0; st < nsteps; ++st) {  // warp-uniform trip count
+                const int cb = kContig ? c_lo + q * Lq + st * kSamples : c_lo + q + st * kSamples * CQ;
+                constexpr int du = kContig ? 1 : CQ;  // column step between a lane's samples
+                float4 r0[kSamples], r1s[kSamples];
                 bool act[kSamples];
-                int cws[kSamples];
 #pragma unroll
                 for (int u = 0; u < kSamples; ++u) {
-                    const int c = cb + u * CQ;
-                    act[u] = (unsigned)c - (unsigned)my_lo <= my_span;
+                    const int c = cb + u * du;
+                    act[u] = (unsigned)c - (unsigned)my_lo <= my_span && (!kContig || st * kSamples + u < Lq);
                     int cw = c;
                     if (CHECKED && A.panorama) {
                         // the group's columns lie within about one period of [0, U)
@@ -889,8 +913,9 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
                         else if (cw >= A.U) cw -= A.U;
                         if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
                     }
-                    cws[u] = cw;
+                    // both halves of the record (one 32-byte sector), issued together
                     r0[u] = act[u] ? __ldg(recrow + 2 * cw) : make_float4(__uint_as_float(kNoDeposit), 0.f, 0.f, 0.f);
+                    r1s[u] = act[u] ? __ldg(recrow + 2 * cw + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
                     // a pixel with neither a return nor ambient light adds nothing
                     act[u] = act[u] && !(__float_as_uint(r0[u].x) == kNoDeposit && r0[u].y == 0.f);
                 }
@@ -901,7 +926,7 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
                 ProfFetch pf[kSamples];
 #pragma unroll
                 for (int u = 0; u < kSamples; ++u) {
-                    const int c = cb + u * CQ;
+                    const int c = cb + u * du;
                     const float2 t = tjc[act[u] ? c : cs];
                     bool ok = act[u];
                     // front hemisphere only: d.a = cos(dEl) - cos el_b cos el (1 - cos dAz)
@@ -918,9 +943,7 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
                     amb_acc = fmaf(Pw, r0[u].y, amb_acc);
                     const uint32_t kab = __float_as_uint(r0[u].x);
                     const bool dep = Pw > 0.f && kab != kNoDeposit;
-                    // second half of the record (same 32-byte sector as the first)
-                    float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (dep) r1 = __ldg(recrow + 2 * cws[u] + 1);
+                    const float4 r1 = r1s[u];
                     const uint32_t kq = __float_as_uint(r1.x);
                     if (dep && (kab != k0 || kq != k1)) {
                         if (k0 != kNoDeposit) dep_flush(hj, k0, k1, a0, a1, a2, a3, ac, pad, nb);
@@ -944,118 +967,21 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
     return amb_acc;
 }
 
-// One group of G consecutive beams of one frame (the whole per-CTA pipeline).
-// Every thread of the CTA must call it (it contains block barriers).
-template <int KIND, int G, bool TC>
-__device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
+// Phases 2-4 of a group whose histograms are in hbuf (G slots; slot jj for
+// beam slot b0 + jj, jj < gcount): window edges and support, pulse convolution +
+// ambient with the waveform written out, echo extraction. Every thread of the
+// CTA must call it (it contains block barriers). The echo-only form keeps the
+// waveforms in rows slot_row0 + jj of the CTA's pool slot of slot_rows rows.
+__device__ __forceinline__ void footprint_finish(const FootprintArgs &A, const Layout &Ly, float *hbuf,
+                                              const float *taps, float *amb_s, int *supp, int *tsupp,
+                                              float *nrm2_s, float *tmass_s, const BeamParam *bp, int b0,
+                                              int gcount, int G, int slot_row0, int slot_rows)
 {
     const int nb = A.n_bins, M = A.M;
-    const Layout Ly = make_layout(G, nb, M);
     const int pad = Ly.pad;
-    float *hbuf = reinterpret_cast<float *>(smem_raw);
-    float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
-    float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
-    int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
-    int *tsupp = reinterpret_cast<int *>(smem_raw + Ly.off_tsupp);  // coarse support of an added tail
-    float *nrm2_s = reinterpret_cast<float *>(smem_raw + Ly.off_nrm);
-    float *tmass_s = reinterpret_cast<float *>(smem_raw + Ly.off_tmass);  // mass of an added tail
-    float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
-    float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
-    float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
-    int *uctr = reinterpret_cast<int *>(smem_raw + Ly.off_ctr);
-    BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int b0 = group * G;
-    const int gcount = min(G, A.n_beams - b0);
-
-    // ---- phase 0: clear, load parameters, union box ----------------------
-    for (int i = tid; i < G * Ly.HB; i += blockDim.x) hbuf[i] = 0.f;
-    for (int i = tid; i < Ly.taps_len; i += blockDim.x) {
-        int m = i - Ly.taps_off;
-        taps[skew_pos(i)] = (m >= -M && m <= M) ? A.taps_pad[A.tp_off + m] : 0.f;
-    }
-    if (tid < G) {
-        amb_s[tid] = 0.f;
-        nrm2_s[tid] = 0.f;
-        BeamParam P;
-        if (tid < gcount) P = A.beams[b0 + tid];
-        else { P = BeamParam{}; P.valid = 0; }
-        bp[tid] = P;
-    }
-    __syncthreads();
-    if (tid < G && A.panorama) {
-        // keep all boxes of the group in the unwrapped period of the first valid beam
-        int ref = -1;
-        for (int j = 0; j < gcount; ++j) if (bp[j].valid) { ref = bp[j].ci; break; }
-        BeamParam &P = bp[tid];
-        if (P.valid && ref >= 0) {
-            int sh = 0;
-            while (P.ci + sh - ref > A.U / 2) sh -= A.U;
-            while (P.ci + sh - ref < -A.U / 2) sh += A.U;
-            P.ci += sh; P.col0 += sh; P.col1 += sh;
-        }
-    }
-    __syncthreads();
-    int R0 = 1 << 30, R1 = -(1 << 30), C0 = 1 << 30, C1 = -(1 << 30);
-    for (int j = 0; j < gcount; ++j) {
-        const BeamParam &P = bp[j];
-        if (!P.valid) continue;
-        R0 = min(R0, P.row0); R1 = max(R1, P.row1);
-        C0 = min(C0, P.col0); C1 = max(C1, P.col1);
-    }
-    // per-(beam, row) sin and cos of the elevation offset and per-row cos(el)
-    const bool use_rtab = R0 <= R1 && R1 - R0 + 1 <= kRT;
-    if (use_rtab) {
-        const int nr = R1 - R0 + 1;
-        for (int i = tid; i < G * nr; i += blockDim.x) {
-            int jj = i / nr, rr = i - jj * nr;
-            const BeamParam &Q = bp[jj];
-            float dEl = ((float)(R0 + rr - Q.ri) - Q.rf) * A.del;
-            float sv, cv;
-            sincosf(dEl, &sv, &cv);
-            rtab[jj * kRT + rr] = make_float2(sv, cv);
-            if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
-        }
-    }
-
-    // ---- phase 1: profile-weighted deposits into the range bins -----------
-    float amb_acc = 0.f;
-    if constexpr (TC) {
-        amb_acc = phase1_tc<KIND, G>(A, Ly, hbuf, tab, bp, gcount, R0, R1, C0, C1);
-    } else {
-        // Boxes that wrap around a panorama or reach beyond 45 degrees from a
-        // beam's axis need the per-sample wrap and front-hemisphere tests
-        // (within 45 degrees in both offsets, d.a >= cos 45 - (1 - cos 45) > 0)
-        bool checked = A.panorama != 0;
-        for (int jj = 0; jj < gcount && !checked; ++jj) {
-            const BeamParam &Q = bp[jj];
-            if (!Q.valid) continue;
-            const float da = fmaxf(fabsf((float)(Q.col0 - Q.ci) - Q.cf), fabsf((float)(Q.col1 - Q.ci) - Q.cf)) * A.daz;
-            const float de = fmaxf(fabsf((float)(Q.row0 - Q.ri) - Q.rf), fabsf((float)(Q.row1 - Q.ri) - Q.rf)) * A.del;
-            checked = !(da <= 0.78f && de <= 0.78f);
-        }
-        if (checked)
-            amb_acc = phase1_atomic<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
-                                                   use_rtab);
-        else
-            amb_acc = phase1_atomic<KIND, G, false>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
-                                                    use_rtab);
-    }
-    if constexpr (TC) {
-        // ambient sum per beam: lane (g, t) holds beam g; sum the 4 lanes t
-        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 1);
-        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 2);
-        if ((lane & 3) == 0 && (lane >> 2) < G && amb_acc != 0.f) atomicAdd(amb_s + (lane >> 2), amb_acc);
-    } else {
-        // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
-#pragma unroll
-        for (int o = G; o < kWarp; o <<= 1) amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, o);
-        if (lane < G && amb_acc != 0.f) atomicAdd(amb_s + lane, amb_acc);
-    }
-    __syncthreads();
-
+    (void)tid;
     // ---- phase 2: drop contributions outside the window, support ----------
     for (int jj = warp; jj < G; jj += nwarps) {
         float *hj = hbuf + jj * Ly.HB;
@@ -1184,7 +1110,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         }
         if (o0 + 8 * lane < nb) {
             const size_t orow = A.out_ids ? (size_t)A.out_ids[b0 + jj] : (size_t)(b0 + jj);
-            float *wrow = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * G + jj) * nb : A.wave + orow * nb;
+            float *wrow = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * slot_rows + slot_row0 + jj) * nb : A.wave + orow * nb;
             float4 *dst = reinterpret_cast<float4 *>(wrow + o0 + 8 * lane);
             dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
             dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
@@ -1209,7 +1135,7 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     // run, so the scan covers [lo - M - 1, hi + M + 1]. Loads run one chunk ahead.
     for (int jj = warp; jj < gcount; jj += nwarps) {
         const int beam = A.out_ids ? A.out_ids[b0 + jj] : b0 + jj;
-        const float *xw = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * G + jj) * nb : A.wave + (size_t)beam * nb;
+        const float *xw = A.slot_pool ? A.slot_pool + ((size_t)s_wave_slot * slot_rows + slot_row0 + jj) * nb : A.wave + (size_t)beam * nb;
         lidar_echo_t *eo = A.echoes + (size_t)beam * A.max_echoes;
         const float T = A.T;
         const float ambv = amb_s[jj] * A.s_amb;
@@ -1417,6 +1343,119 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     }
 }
 
+// One group of G consecutive beams of one frame (the whole per-CTA pipeline).
+// Every thread of the CTA must call it (it contains block barriers).
+template <int KIND, int G, bool TC>
+__device__ __forceinline__ void footprint_group(const FootprintArgs &A, const int group, unsigned char *smem_raw)
+{
+    const int nb = A.n_bins, M = A.M;
+    const Layout Ly = make_layout(G, nb, M);
+    float *hbuf = reinterpret_cast<float *>(smem_raw);
+    float *taps = reinterpret_cast<float *>(smem_raw + Ly.off_taps);
+    float *amb_s = reinterpret_cast<float *>(smem_raw + Ly.off_amb);
+    int *supp = reinterpret_cast<int *>(smem_raw + Ly.off_supp);
+    int *tsupp = reinterpret_cast<int *>(smem_raw + Ly.off_tsupp);  // coarse support of an added tail
+    float *nrm2_s = reinterpret_cast<float *>(smem_raw + Ly.off_nrm);
+    float *tmass_s = reinterpret_cast<float *>(smem_raw + Ly.off_tmass);  // mass of an added tail
+    float2 *tab = reinterpret_cast<float2 *>(smem_raw + Ly.off_tab);
+    float2 *rtab = reinterpret_cast<float2 *>(smem_raw + Ly.off_rtab);
+    float *ctab = reinterpret_cast<float *>(smem_raw + Ly.off_ctab);
+    int *uctr = reinterpret_cast<int *>(smem_raw + Ly.off_ctr);
+    BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + Ly.off_bp);
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int b0 = group * G;
+    const int gcount = min(G, A.n_beams - b0);
+
+    // ---- phase 0: clear, load parameters, union box ----------------------
+    for (int i = tid; i < G * Ly.HB; i += blockDim.x) hbuf[i] = 0.f;
+    for (int i = tid; i < Ly.taps_len; i += blockDim.x) {
+        int m = i - Ly.taps_off;
+        taps[skew_pos(i)] = (m >= -M && m <= M) ? A.taps_pad[A.tp_off + m] : 0.f;
+    }
+    if (tid < G) {
+        amb_s[tid] = 0.f;
+        nrm2_s[tid] = 0.f;
+        BeamParam P;
+        if (tid < gcount) P = A.beams[b0 + tid];
+        else { P = BeamParam{}; P.valid = 0; }
+        bp[tid] = P;
+    }
+    __syncthreads();
+    if (tid < G && A.panorama) {
+        // keep all boxes of the group in the unwrapped period of the first valid beam
+        int ref = -1;
+        for (int j = 0; j < gcount; ++j) if (bp[j].valid) { ref = bp[j].ci; break; }
+        BeamParam &P = bp[tid];
+        if (P.valid && ref >= 0) {
+            int sh = 0;
+            while (P.ci + sh - ref > A.U / 2) sh -= A.U;
+            while (P.ci + sh - ref < -A.U / 2) sh += A.U;
+            P.ci += sh; P.col0 += sh; P.col1 += sh;
+        }
+    }
+    __syncthreads();
+    int R0 = 1 << 30, R1 = -(1 << 30), C0 = 1 << 30, C1 = -(1 << 30);
+    for (int j = 0; j < gcount; ++j) {
+        const BeamParam &P = bp[j];
+        if (!P.valid) continue;
+        R0 = min(R0, P.row0); R1 = max(R1, P.row1);
+        C0 = min(C0, P.col0); C1 = max(C1, P.col1);
+    }
+    // per-(beam, row) sin and cos of the elevation offset and per-row cos(el)
+    const bool use_rtab = R0 <= R1 && R1 - R0 + 1 <= kRT;
+    if (use_rtab) {
+        const int nr = R1 - R0 + 1;
+        for (int i = tid; i < G * nr; i += blockDim.x) {
+            int jj = i / nr, rr = i - jj * nr;
+            const BeamParam &Q = bp[jj];
+            float dEl = ((float)(R0 + rr - Q.ri) - Q.rf) * A.del;
+            float sv, cv;
+            sincosf(dEl, &sv, &cv);
+            rtab[jj * kRT + rr] = make_float2(sv, cv);
+            if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)(R0 + rr) + 0.5f) * A.del);
+        }
+    }
+
+    // ---- phase 1: profile-weighted deposits into the range bins -----------
+    float amb_acc = 0.f;
+    if constexpr (TC) {
+        amb_acc = phase1_tc<KIND, G>(A, Ly, hbuf, tab, bp, gcount, R0, R1, C0, C1);
+    } else {
+        // Boxes that wrap around a panorama or reach beyond 45 degrees from a
+        // beam's axis need the per-sample wrap and front-hemisphere tests
+        // (within 45 degrees in both offsets, d.a >= cos 45 - (1 - cos 45) > 0)
+        bool checked = A.panorama != 0;
+        for (int jj = 0; jj < gcount && !checked; ++jj) {
+            const BeamParam &Q = bp[jj];
+            if (!Q.valid) continue;
+            const float da = fmaxf(fabsf((float)(Q.col0 - Q.ci) - Q.cf), fabsf((float)(Q.col1 - Q.ci) - Q.cf)) * A.daz;
+            const float de = fmaxf(fabsf((float)(Q.row0 - Q.ri) - Q.rf), fabsf((float)(Q.row1 - Q.ri) - Q.rf)) * A.del;
+            checked = !(da <= 0.78f && de <= 0.78f);
+        }
+        if (checked)
+            amb_acc = phase1_atomic<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
+                                                   use_rtab);
+        else
+            amb_acc = phase1_atomic<KIND, G, false>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
+                                                    use_rtab);
+    }
+    if constexpr (TC) {
+        // ambient sum per beam: lane (g, t) holds beam g; sum the 4 lanes t
+        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 1);
+        amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, 2);
+        if ((lane & 3) == 0 && (lane >> 2) < G && amb_acc != 0.f) atomicAdd(amb_s + (lane >> 2), amb_acc);
+    } else {
+        // ambient sum per beam: lanes j, j+G, j+2G, ... of each warp
+#pragma unroll
+        for (int o = G; o < kWarp; o <<= 1) amb_acc += __shfl_xor_sync(0xffffffffu, amb_acc, o);
+        if (lane < G && amb_acc != 0.f) atomicAdd(amb_s + lane, amb_acc);
+    }
+    __syncthreads();
+
+    footprint_finish(A, Ly, hbuf, taps, amb_s, supp, tsupp, nrm2_s, tmass_s, bp, b0, gcount, G, 0, G);
+}
+
 // Claims a free slot of the echo-only waveform pool. The pool has
 // slots_per_sm slots for each SM id below slot_sms; a CTA first tries the
 // slots of its own SM, of which at most slots_per_sm - 1 are held by the
@@ -1497,6 +1536,57 @@ __global__ void __launch_bounds__(512, TC ? 1 : 2) footprint_batch_kernel(Footpr
         footprint_group<KIND, G, TC>(A, fg.y, smem_raw);
         __syncthreads();  // shared memory is reused by the next item
     }
+}
+
+#include "lidar_deposit_umma.cuh"
+
+size_t umma_smem_bytes(int n_bins, int M) { return umd::um_layout(n_bins, M).total; }
+
+#define GBL_UMMA_EACH(X) X(0, true) X(0, false) X(1, true) X(1, false) X(2, true) X(2, false)
+
+cudaError_t prepare_umma(int kind, bool bf16, size_t smem)
+{
+#define GBL_CASE(K, B)                                                                                      \
+    if (kind == K && bf16 == B) {                                                                           \
+        cudaError_t e = cudaFuncSetAttribute(footprint_umma_kernel<K, B>,                                   \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        if (e != cudaSuccess) return e;                                                                     \
+        return cudaFuncSetAttribute(footprint_umma_batch_kernel<K, B>,                                      \
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
+    }
+    GBL_UMMA_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_umma(int kind, bool bf16, size_t smem, const FootprintArgs &a, cudaStream_t s)
+{
+    if (a.n_bins > kUmmaMaxBins || smem < umma_smem_bytes(a.n_bins, a.M)) return cudaErrorInvalidValue;
+    const int groups = (a.n_beams + kUmmaBeams - 1) / kUmmaBeams;
+    if (groups == 0) return cudaSuccess;
+#define GBL_CASE(K, B)                                                                    \
+    if (kind == K && bf16 == B) {                                                         \
+        footprint_umma_kernel<K, B><<<groups, umd::kUThreads, smem, s>>>(a);              \
+        return cudaGetLastError();                                                        \
+    }
+    GBL_UMMA_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_umma_batch(int kind, bool bf16, int grid, size_t smem, const FootprintArgs &base,
+                              const FrameDesc *frames, const int2 *items, int n_items, int *counter, cudaStream_t s)
+{
+    if (base.n_bins > kUmmaMaxBins || smem < umma_smem_bytes(base.n_bins, base.M)) return cudaErrorInvalidValue;
+#define GBL_CASE(K, B)                                                                                      \
+    if (kind == K && bf16 == B) {                                                                           \
+        footprint_umma_batch_kernel<K, B><<<grid, umd::kUThreads, smem, s>>>(base, frames, items, n_items,  \
+                                                                             counter);                      \
+        return cudaGetLastError();                                                                          \
+    }
+    GBL_UMMA_EACH(GBL_CASE)
+#undef GBL_CASE
+    return cudaErrorInvalidValue;
 }
 
 size_t footprint_smem_bytes(int G, const FootprintArgs &a)

@@ -93,7 +93,8 @@ SYMBOLS = ("lidar_create", "lidar_simulate", "lidar_simulate_echoes", "lidar_rep
            "lidar_simulate_host_frames", "lidar_simulate_noalloc",
            "lidar_sync",
            "lidar_simulate_batch", "lidar_autotune_batch", "lidar_batch_config", "lidar_get_info",
-           "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_set_echo_mode", "lidar_profile_enable",
+           "lidar_launches_per_simulate", "lidar_set_deposit", "lidar_set_echo_mode", "lidar_hold_echo_slots",
+           "lidar_profile_enable",
            "lidar_profile_read", "lidar_last_error",
            "lidar_destroy")
 # include/lidar_tail.h
@@ -164,6 +165,8 @@ def load(path: str = LIB_PATH):
     lib.lidar_set_deposit.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_set_echo_mode.restype = C.c_int
     lib.lidar_set_echo_mode.argtypes = [C.c_void_p, C.c_int32]
+    lib.lidar_hold_echo_slots.restype = C.c_int
+    lib.lidar_hold_echo_slots.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_enable.restype = C.c_int
     lib.lidar_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.lidar_profile_read.restype = C.c_int
@@ -599,7 +602,7 @@ def lidar_launches_per_simulate(handle) -> int:
     return int(load().lidar_launches_per_simulate(handle))
 
 
-DEPOSIT_ATOMIC, DEPOSIT_TC_SPLIT, DEPOSIT_TC_BF16 = 0, 1, 2
+DEPOSIT_ATOMIC, DEPOSIT_TC_SPLIT, DEPOSIT_TC_BF16, DEPOSIT_TCGEN05_BF16, DEPOSIT_TCGEN05_FP16 = 0, 1, 2, 3, 4
 
 
 def lidar_set_deposit(handle, mode: int) -> None:
@@ -611,6 +614,10 @@ ECHOES_NEAREST, ECHOES_STRONGEST = 0, 1
 
 def lidar_set_echo_mode(handle, mode: int) -> None:
     _check(load().lidar_set_echo_mode(handle, int(mode)), handle)
+
+
+def lidar_hold_echo_slots(handle, held: bool) -> None:
+    _check(load().lidar_hold_echo_slots(handle, int(bool(held))), handle)
 
 
 def lidar_profile_enable(handle, enable: bool) -> None:

@@ -206,3 +206,35 @@ def test_host_entry_point_echo_only(case):
         assert wave is None
         assert_identical(ech_d, cnt_d, [(ech_h.numpy(), cnt_h.numpy())])
     L.close()
+
+
+def test_slot_claim_gives_up_and_reports_timeout():
+    """The bounded wait of the echo-only form: with every waveform slot held
+    (lidar_hold_echo_slots), the CTAs give up their claim after a bounded
+    number of polls, write nothing, and lidar_sync reports LIDAR_ETIMEOUT;
+    once the slots are free again the same call gives the normal result."""
+    w = S.small_plane_retro()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    planes = lidar.gbuffer_to_device(w.gbuffer)
+    ech0, cnt0 = L.simulate_echoes(w.gbuffer, planes, w.pose)
+    lidar.lidar_sync(L.handle, 0)
+    ref_e, ref_c = lidar.echoes_numpy(ech0), cnt0.cpu().numpy()
+    assert ref_c.sum() >= 500
+    lidar.lidar_hold_echo_slots(L.handle, True)
+    ech, cnt = L._alloc_echoes("cuda")
+    cnt.fill_(-7)
+    L.simulate_echoes(w.gbuffer, planes, w.pose, (ech, cnt))
+    with pytest.raises(lidar.LidarError) as ei:
+        lidar.lidar_sync(L.handle, 0)
+    assert ei.value.status == lidar.LIDAR_ETIMEOUT
+    assert (cnt.cpu().numpy() == -7).all()  # nothing was written
+    lidar.lidar_sync(L.handle, 0)  # the error word was cleared by the report
+    lidar.lidar_hold_echo_slots(L.handle, False)
+    L.simulate_echoes(w.gbuffer, planes, w.pose, (ech, cnt))
+    lidar.lidar_sync(L.handle, 0)
+    assert (cnt.cpu().numpy() == ref_c).all()
+    e = lidar.echoes_numpy(ech)
+    for b in range(len(ref_c)):
+        for i in range(ref_c[b]):
+            assert e[b, i]["bin_start"] == ref_e[b, i]["bin_start"] and e[b, i]["bin_end"] == ref_e[b, i]["bin_end"]
+    L.close()

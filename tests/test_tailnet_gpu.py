@@ -230,3 +230,36 @@ def test_surrogate_simulation_meets_parity():
     assert ambiguous_ok(st), st
     net.close()
     L.close()
+
+
+def test_committed_network_on_the_wide_frame():
+    """The learned surrogate as shipped: the trained weights
+    (weights/tailnet_wide.bin) on the 8192x4096 wide-tail frame with 200k
+    beams, exact core 0.3 deg; the gated result on a seeded 1 % subsample
+    (2000 beams) against the oracle, at the parity bar."""
+    path = os.path.join(os.path.dirname(lidar.__file__), "weights", "tailnet_wide.bin")
+    w = S.wide_frame()
+    L = lidar.Lidar(w.profile, w.dirs, w.pulse, w.calib)
+    lidar.lidar_tail_configure(L.handle, 0.3, 256)
+    net = lidar.TailNet(256)
+    net.load(path)
+    planes = lidar.gbuffer_to_device(w.gbuffer)
+    g = lidar.make_gbuffer(w.gbuffer, [p.data_ptr() for p in planes])
+    wave, ech, cnt = L.alloc_outputs()
+    n = lidar.lidar_simulate_surrogate(L.handle, net.handle, g, lidar.make_pose(w.pose), wave.data_ptr(),
+                                       ech.data_ptr(), cnt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    lidar.lidar_sync(L.handle, 0)
+    net.sync(0)
+    # most beams keep the network's tail; the re-run ones are a few percent
+    assert 0 < n < 0.05 * len(w.dirs), n
+    from tests.test_parity_gpu import ambiguous_ok, compare
+    beams = np.sort(S.rng(2000).choice(len(w.dirs), 2000, replace=False)).astype(np.int32)
+    ref = O.simulate_workload(w, beams=beams, nthreads=NTHREADS, max_out=8)
+    bi = torch.as_tensor(beams, device="cuda", dtype=torch.long)
+    rows = {int(b): r for b, r in zip(beams, wave[bi].cpu().numpy().astype(np.float64))}
+    st = compare(ref, rows, lidar.echoes_numpy(ech), cnt.cpu().numpy(), beams, w.calib["threshold"],
+                 w.calib["max_echoes"], w.pulse)
+    assert st["echoes"] >= 1000 and ambiguous_ok(st, strict=True), st
+    net.close()
+    L.close()
