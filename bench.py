@@ -507,55 +507,60 @@ def run_gb300(args, rank, world, local_rank, sub=False):
 
     if sub:
         return sub_record(args, w, L, kern, value, ms_per_step, sample, res_wave, res_ech, res_cnt, clk)
+    # the host entry points have no tcgen05 form: no end-to-end leg for it
+    host_leg = not args.deposit.startswith("tcgen05")
 
-    # ---- end to end through the host-memory entry point ----
-    host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
-    host_out = (torch.empty((nbeams, L.n_bins), dtype=torch.float32, pin_memory=True) if not args.echo_only else
-                torch.empty((0,), dtype=torch.float32),
-                torch.empty((nbeams, L.max_echoes, 8), dtype=torch.int32, pin_memory=True),
-                torch.empty((nbeams,), dtype=torch.int32, pin_memory=True))
+    e2e_value = e2e_single = None
+    h2d = d2h = 0
+    if host_leg:
+        # ---- end to end through the host-memory entry point ----
+        host_planes = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in w.gbuffer.planes()]
+        host_out = (torch.empty((nbeams, L.n_bins), dtype=torch.float32, pin_memory=True) if not args.echo_only else
+                    torch.empty((0,), dtype=torch.float32),
+                    torch.empty((nbeams, L.max_echoes, 8), dtype=torch.int32, pin_memory=True),
+                    torch.empty((nbeams,), dtype=torch.int32, pin_memory=True))
 
-    def frame_host():
-        if args.echo_only:
-            # the host entry point's echo-only form: pinned planes in, echoes and counts out
-            L.simulate_host(w.gbuffer, host_planes, w.pose, (None, host_out[1], host_out[2]), stream, echo_only=True)
-        else:
-            L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
+        def frame_host():
+            if args.echo_only:
+                # the host entry point's echo-only form: pinned planes in, echoes and counts out
+                L.simulate_host(w.gbuffer, host_planes, w.pose, (None, host_out[1], host_out[2]), stream, echo_only=True)
+            else:
+                L.simulate_host(w.gbuffer, host_planes, w.pose, host_out, stream)
 
-    for _ in range(2):
-        frame_host()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        frame_host()
-    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_single = world * nbeams * args.steps / float(e2e_s.item())
+        for _ in range(2):
+            frame_host()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            frame_host()
+        e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+        e2e_single = world * nbeams * args.steps / float(e2e_s.item())
 
-    # the same frames as one sequence (lidar_simulate_host_frames): each step
-    # still reads its G-buffer from pinned host memory and copies its results
-    # back; consecutive steps overlap, and their outputs alternate between two
-    # pinned sets (consecutive frames may not share outputs)
-    host_out2 = tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) if t.numel() else t for t in host_out)
-    seq_out = [host_out if f % 2 == 0 else host_out2 for f in range(args.steps)]
+        # the same frames as one sequence (lidar_simulate_host_frames): each step
+        # still reads its G-buffer from pinned host memory and copies its results
+        # back; consecutive steps overlap, and their outputs alternate between two
+        # pinned sets (consecutive frames may not share outputs)
+        host_out2 = tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) if t.numel() else t for t in host_out)
+        seq_out = [host_out if f % 2 == 0 else host_out2 for f in range(args.steps)]
 
-    def frames_host(n):
-        L.simulate_host_frames([w.gbuffer] * n, [host_planes] * n, [w.pose] * n, seq_out[:n], stream,
-                               echo_only=args.echo_only)
+        def frames_host(n):
+            L.simulate_host_frames([w.gbuffer] * n, [host_planes] * n, [w.pose] * n, seq_out[:n], stream,
+                                   echo_only=args.echo_only)
 
-    frames_host(min(args.steps, 4))
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    frames_host(args.steps)
-    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = world * nbeams * args.steps / float(e2e_s.item())
-    h2d = sum(p.numel() * 4 for p in host_planes)
-    d2h = sum(t.numel() * t.element_size() for t in host_out)
+        frames_host(min(args.steps, 4))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        frames_host(args.steps)
+        e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+        e2e_value = world * nbeams * args.steps / float(e2e_s.item())
+        h2d = sum(p.numel() * 4 for p in host_planes)
+        d2h = sum(t.numel() * t.element_size() for t in host_out)
 
     if rank != 0:
         if dist:
@@ -604,7 +609,8 @@ def run_gb300(args, rank, world, local_rank, sub=False):
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(args.deposit, "f32"),
             "data": "synthetic", "config": config_of(w, extra),
             "roofline": roof, "cpu_baseline": cpu, "parity": parity, "pixel_samples": pixel_samples,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "e2e": None if not host_leg else
+                   {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": f"lidar_simulate_host_frames, {args.steps} frames per call",
                     "single_call": {"value": e2e_single, "api": "lidar_simulate_host, one frame per call"}},
             "gpu_launches": int(args.steps * lidar.lidar_launches_per_simulate(L.handle)),

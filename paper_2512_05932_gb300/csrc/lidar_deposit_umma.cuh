@@ -46,13 +46,13 @@ namespace umd {
 constexpr int kUN = 16;                        // beams per CTA (MMA N)
 constexpr int kUK = 64;                        // pixels per tile (MMA K: four steps of 16)
 constexpr int kUMr = 128;                      // bins per block (MMA M, TMEM lanes)
-constexpr int kUS = 4;                         // stages of the operand ring
-constexpr int kUP = 8;                         // producer warps
+constexpr int kUS = 8;                         // stages of the operand ring
+constexpr int kUP = 16;                        // producer warps
 constexpr int kUThreads = 32 * (kUP + 1);
 constexpr uint32_t kUA = kUMr * 128;           // A buffer: 128 rows x 128 bytes
 constexpr uint32_t kUB = kUN * 128;            // B buffer: 16 rows x 128 bytes
 constexpr long kUWait = 1L << 22;              // bounded mbarrier polls
-constexpr int kUTab = 256;                     // columns per offset-table stripe (4 tiles)
+constexpr int kUTab = 128;                     // columns per offset-table stripe (2 tiles)
 
 struct UmSmem {  // at a 1024-byte aligned offset (swizzle atoms)
     unsigned char a[kUS][kUA];
@@ -77,7 +77,8 @@ __device__ __forceinline__ void um_fail(UmSmem &S, int site, int seq)
 struct UmLayout {
     Layout fin;       // hbuf / taps of the finishing phases (kUG beams at a time)
     int G;            // kUG
-    size_t off_um, off_hbuf, off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_bp, total;
+    size_t off_um, off_hbuf, off_taps, off_amb, off_nrm, off_tmass, off_supp, off_tsupp, off_tab, off_bp, off_pix,
+        total;
 };
 
 // Beams per finishing round: the largest of 8, 4, 2 whose histograms fit
@@ -101,6 +102,7 @@ __host__ __device__ inline UmLayout um_layout(int n_bins, int M)
         off = (off + 15) & ~(size_t)15;
         L.off_tab = off; off += (size_t)kUN * kUTab * sizeof(float2);
         L.off_bp = off; off += (size_t)kUN * sizeof(BeamParam);
+        L.off_pix = off; off += (size_t)kUP * kUK * sizeof(float2);
         L.total = off;
         if (L.total <= 227 * 1024 || G == 2) break;
     }
@@ -209,6 +211,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
     int *tsupp = reinterpret_cast<int *>(smem_raw + UL.off_tsupp);
     float2 *tab = reinterpret_cast<float2 *>(smem_raw + UL.off_tab);
     BeamParam *bp = reinterpret_cast<BeamParam *>(smem_raw + UL.off_bp);
+    float2 *pixall = reinterpret_cast<float2 *>(smem_raw + UL.off_pix);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b0 = group * kUN;
@@ -297,6 +300,8 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
     } else {
         // ---- producers -----------------------------------------------------
         const int pw = warp - 1, ptid = tid - 32;
+        // the tile's pixels as this warp's lanes loaded them: (record word 0, ambient)
+        float2 *pix = pixall + pw * kUK;
         const int j = lane & 15, h = lane >> 4;  // B: beam j, pixels 32h .. 32h + 31 of a tile
         const BeamParam P = bp[j];
         const bool jok = (j < gcount) && P.valid;
@@ -351,6 +356,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                     const bool in = c <= c_hi;
                     q0[i] = in ? __ldg(recrow + 2 * cw) : make_float4(__uint_as_float(kNoDeposit), 0.f, 0.f, 0.f);
                     q1[i] = in ? __ldg(recrow + 2 * cw + 1) : make_float4(__uint_as_float(kNoDeposit), 0.f, 0.f, 0.f);
+                    pix[lane + 32 * i] = make_float2(q0[i].x, q0[i].y);
                     const uint32_t kab = __float_as_uint(q0[i].x);
                     if (kab != kNoDeposit) {
                         const int f = (int)(kab & 0xFFFFu) - kBinBias;
@@ -365,6 +371,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) bmask |= __shfl_xor_sync(0xffffffffu, bmask, o);
+                __syncwarp();  // the pixel table is written
                 // (2) B: beam j at pixels 32h .. 32h + 31, profile and ambient in FP32
                 uint32_t bw[16];
                 const float cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
@@ -380,17 +387,11 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                     float pv[2];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const int c = c_lo + 32 * h + 2 * t2 + e;
+                        const int tc = 32 * h + 2 * t2 + e;  // column within the tile
+                        const int c = c_lo + tc;
                         bool ok = rowok && c >= my_lo && c <= my_hi;
-                        int cw = c;
-                        if (A.panorama) {
-                            if (cw < 0) cw += A.U;
-                            else if (cw >= A.U) cw -= A.U;
-                            if ((unsigned)cw >= (unsigned)A.U) { cw = c % A.U; if (cw < 0) cw += A.U; }
-                        }
-                        // the record's first word and ambient (the same 32-byte sector the A side read)
-                        const float2 ka = ok ? __ldg(reinterpret_cast<const float2 *>(recrow + 2 * cw))
-                                             : make_float2(__uint_as_float(kNoDeposit), 0.f);
+                        // the record's first word and ambient, from the warp's pixel table
+                        const float2 ka = ok ? pix[tc] : make_float2(__uint_as_float(kNoDeposit), 0.f);
                         const bool dep = __float_as_uint(ka.x) != kNoDeposit;
                         ok = ok && (dep || ka.y != 0.f);
                         const float2 tt = tjc[ok ? c : cs];
@@ -492,6 +493,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                         um_arrive(su32(&S.full[s]));
                     }
                 }
+                __syncwarp();  // this tile's pixel-table reads come before the next tile's writes
                 int nu = nunits;
                 if (lane == 0 && !*(volatile int *)&S.abort) nu = atomicAdd(&S.ctr, 1);
                 unit = __shfl_sync(0xffffffffu, nu, 0);
@@ -672,5 +674,5 @@ __global__ void __launch_bounds__(umd::kUThreads, 1)
     umma_cta_end(tmem, ncols);
 }
 
-static_assert(umd::kUThreads == kUmmaThreads && umd::kUN == kUmmaBeams, "tcgen05 deposit launch shape");
+static_assert(umd::kUN == kUmmaBeams, "tcgen05 deposit group size");
 static_assert(umd::kUMr * 32 == kUmmaMaxBins, "32 blocks of 128 bins fill 512 TMEM columns at 16 beams");

@@ -165,7 +165,6 @@ cudaError_t prepare_footprint_batch(int kind, int G, bool tc, size_t smem);
 // tcgen05 deposit (16 beams per CTA, histograms in tensor memory)
 size_t umma_smem_bytes(int n_bins, int M);
 constexpr int kUmmaBeams = 16;
-constexpr int kUmmaThreads = 288;
 constexpr int kUmmaMaxBins = 4096;  // 32 blocks of 128 bins x 16 beams = 512 TMEM columns
 cudaError_t prepare_umma(int kind, bool bf16, size_t smem);
 cudaError_t launch_umma(int kind, bool bf16, size_t smem, const FootprintArgs &a, cudaStream_t s);
