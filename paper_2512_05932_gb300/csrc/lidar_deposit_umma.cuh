@@ -142,7 +142,7 @@ __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity)
 {
     for (long i = 0; i < kUWait; ++i) {
         if (um_try(bar, parity)) return true;
-        if (i >= 1024) __nanosleep(64);
+        if (i >= 8) __nanosleep(32);
     }
     return false;
 }
@@ -275,7 +275,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                     if (*(volatile int *)&S.prod_done && *(volatile int *)&S.seq_total == seq) break;
                     if (*(volatile int *)&S.abort) break;
                     if (++polls > kUWait) { um_fail(S, 1, seq); break; }
-                    if (polls > 1024) __nanosleep(64);
+                    if (polls > 8) __nanosleep(32);
                     continue;
                 }
                 polls = 0;
@@ -422,7 +422,7 @@ __device__ void footprint_umma_group(const FootprintArgs &A, const int group, un
                         long w = 0;
                         while (*(volatile int *)&S.issued <= seq - kUS && !*(volatile int *)&S.abort) {
                             if (++w > kUWait) break;
-                            if (w > 1024) __nanosleep(64);
+                            if (w > 8) __nanosleep(32);
                         }
                         __threadfence_block();
                         if (*(volatile int *)&S.issued <= seq - kUS) {
