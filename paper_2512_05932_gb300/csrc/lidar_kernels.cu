@@ -967,6 +967,142 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
     return amb_acc;
 }
 
+// Phase 1, lean form of the atomic deposit, for groups whose union box needs
+// neither the panorama wrap nor the front-hemisphere test. The box's columns
+// are widened to whole warp steps inside the G-buffer: a column outside a
+// beam's own box lies outside its profile's support, where the profile weight
+// is exactly 0, so no sample needs a bounds or activity test. A lane whose
+// beam slot is empty evaluates its profile far outside any support (weight 0).
+// Lane (j, q) takes beam j on columns q, q + CQ, ... of each step of CQ *
+// kSamples columns; its loads use fixed offsets from two pointers advanced
+// once per step. A record's first word alone identifies its deposit (the bin
+// positions of a narrow record differ by 1 or 2, the end bins of a wide one by
+// at least 3), so one compare decides whether a deposit joins the lane's
+// accumulated one.
+template <int KIND, int G>
+__device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layout &Ly, float *hbuf, float2 *tab,
+                                             const float2 *rtab, const float *ctab, int *uctr, const BeamParam *bp,
+                                             int gcount, int R0, int R1, int C0, int C1, bool use_rtab)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nb = A.n_bins, pad = Ly.pad;
+    constexpr int CQ = kWarp / G;
+    constexpr int kStep = CQ * kSamples;                // columns per warp step
+    constexpr int kStripe = (kTC - 1) / kStep * kStep;  // columns per offset-table stripe
+    const int j = lane % G;
+    const int q = lane / G;
+    const BeamParam P = bp[j];
+    const float t2max = P.pad0 ? A.core2 : A.trunc2;
+    const bool jok = (j < gcount) && P.valid;
+    float *hj = hbuf + j * Ly.HB;
+    uint32_t k0 = kNoDeposit, k1 = kNoDeposit;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, ac = 0.f;
+    float amb_acc = 0.f;
+    for (int cs = C0; cs <= C1; cs += kStripe) {
+        const int ce = min(C1, cs + kStripe - 1);
+        const int ncs = ce - cs + 1;  // a multiple of kStep
+        __syncthreads();  // previous stripe's table no longer read
+        for (int i = tid; i < G * ncs; i += blockDim.x) {
+            int jj = i / ncs, cc = i - jj * ncs;
+            const BeamParam &Q = bp[jj];
+            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
+            float sD, vers;
+            if (fabsf(dAz) <= 0.1f) {
+                float z2 = dAz * dAz;
+                sD = dAz * fmaf(-z2 * (1.f / 6.f), fmaf(-z2, 1.f / 20.f, 1.f), 1.f);
+                vers = 0.5f * z2 * fmaf(-z2 * (1.f / 12.f), fmaf(-z2, 1.f / 30.f, 1.f), 1.f);
+            } else {
+                float cD;
+                sincosf(dAz, &sD, &cD);
+                vers = 1.f - cD;
+            }
+            tab[jj * kTC + cc] = make_float2(sD, vers);
+        }
+        if (tid == 0) *uctr = nwarps;
+        __syncthreads();
+        if (R0 > R1) continue;
+        const float2 *tjc = tab + j * kTC - cs;
+        // segments of whole steps, at most kSeg (rounded up to a step) wide
+        const int nseg = (ncs + kSeg - 1) / kSeg;
+        const int segw = ((ncs + nseg - 1) / nseg + kStep - 1) / kStep * kStep;
+        const int nunits = (R1 - R0 + 1) * nseg;
+        for (int unit = warp; unit < nunits;) {
+            const int row = R0 + unit / nseg;
+            const int seg = unit - (unit / nseg) * nseg;
+            const int c_lo = cs + seg * segw;
+            const int c_hi = min(ce, c_lo + segw - 1);
+            const int nsteps = c_hi >= c_lo ? (c_hi - c_lo + 1) / kStep : 0;
+            float cosEl, sdEl, cdEl;
+            if (use_rtab) {
+                const float2 rt = rtab[j * kRT + (row - R0)];
+                sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
+            } else {
+                cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
+                float dEl = ((float)(row - P.ri) - P.rf) * A.del;
+                sincosf(dEl, &sdEl, &cdEl);
+            }
+            (void)cdEl;
+            const float Kv = P.sin_elb * cosEl;
+            float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
+            float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
+            if (!jok) {
+                // (x, y) = (3, 0): far outside every profile's support
+                ax = 0.f; bx = 0.f; cx = 3.f; ay = 0.f; by = 0.f; cy = 0.f;
+            }
+            const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(c_lo + q));
+            const float2 *tp = tjc + c_lo + q;
+            for (int st = 0; st < nsteps; ++st) {
+                float4 r0[kSamples], r1s[kSamples];
+                float2 t[kSamples];
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    r0[u] = __ldg(rp + 2 * CQ * u);
+                    r1s[u] = __ldg(rp + 2 * CQ * u + 1);
+                    t[u] = tp[CQ * u];
+                }
+                rp += 2 * kStep;
+                tp += kStep;
+                // a record with neither a deposit nor ambient light adds nothing
+                uint32_t live = 0u;
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u)
+                    live |= (__float_as_uint(r0[u].x) + 1u) | __float_as_uint(r0[u].y);
+                if (!__any_sync(0xffffffffu, live != 0u)) continue;
+                ProfFetch pf[kSamples];
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    const float x = fmaf(ax, t[u].x, fmaf(bx, t[u].y, cx));
+                    const float y = fmaf(ay, t[u].x, fmaf(by, t[u].y, cy));
+                    pf[u] = profile_fetch<KIND>(A, x, y, true, t2max);
+                }
+#pragma unroll
+                for (int u = 0; u < kSamples; ++u) {
+                    // records without a deposit carry zero weights, and a zero
+                    // profile weight adds zeros: only the key switch is tested
+                    const float Pw = profile_finish<KIND>(A, pf[u]);
+                    amb_acc = fmaf(Pw, r0[u].y, amb_acc);
+                    const uint32_t kab = __float_as_uint(r0[u].x);
+                    if (Pw > 0.f && kab != k0 && kab != kNoDeposit) {
+                        if (k0 != kNoDeposit) dep_flush(hj, k0, k1, a0, a1, a2, a3, ac, pad, nb);
+                        k0 = kab; k1 = __float_as_uint(r1s[u].x);
+                        a0 = 0.f; a1 = 0.f; a2 = 0.f; a3 = 0.f; ac = 0.f;
+                    }
+                    a0 = fmaf(Pw, r0[u].z, a0);
+                    a1 = fmaf(Pw, r0[u].w, a1);
+                    a2 = fmaf(Pw, r1s[u].y, a2);
+                    a3 = fmaf(Pw, r1s[u].z, a3);
+                    ac = fmaf(Pw, r1s[u].w, ac);
+                }
+            }
+            int nu = 0;
+            if (lane == 0) nu = atomicAdd(uctr, 1);
+            unit = __shfl_sync(0xffffffffu, nu, 0);
+        }
+    }
+    if (k0 != kNoDeposit) dep_flush(hj, k0, k1, a0, a1, a2, a3, ac, pad, nb);
+    return amb_acc;
+}
+
 // Phases 2-4 of a group whose histograms are in hbuf (G slots; slot jj for
 // beam slot b0 + jj, jj < gcount): window edges and support, pulse convolution +
 // ambient with the waveform written out, echo extraction. Every thread of the
@@ -1433,7 +1569,26 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
             const float de = fmaxf(fabsf((float)(Q.row0 - Q.ri) - Q.rf), fabsf((float)(Q.row1 - Q.ri) - Q.rf)) * A.del;
             checked = !(da <= 0.78f && de <= 0.78f);
         }
-        if (checked)
+        // lean form: the union box widened to whole warp steps within the
+        // G-buffer, every beam still within 45 degrees of every column of it
+        constexpr int kStepL = (kWarp / G) * kSamples;
+        bool lean = G >= 4 && !checked && R0 <= R1;
+        int C0w = C0, C1w = C1;
+        if (lean) {
+            const int Wp = (C1 - C0 + kStepL) / kStepL * kStepL;
+            lean = Wp <= A.U;
+            C0w = min(C0, A.U - Wp);
+            C1w = C0w + Wp - 1;
+            for (int jj = 0; jj < gcount && lean; ++jj) {
+                const BeamParam &Q = bp[jj];
+                if (!Q.valid) continue;
+                const float da = fmaxf(fabsf((float)(C0w - Q.ci) - Q.cf), fabsf((float)(C1w - Q.ci) - Q.cf)) * A.daz;
+                lean = da <= 0.78f;
+            }
+        }
+        if (lean)
+            amb_acc = phase1_lean<KIND, G>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0w, C1w, use_rtab);
+        else if (checked)
             amb_acc = phase1_atomic<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
                                                    use_rtab);
         else
