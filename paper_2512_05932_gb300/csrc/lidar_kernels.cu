@@ -975,10 +975,13 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
 // beam slot is empty evaluates its profile far outside any support (weight 0).
 // Lane (j, q) takes beam j on columns q, q + CQ, ... of each step of CQ *
 // kSamples columns; its loads use fixed offsets from two pointers advanced
-// once per step. A record's first word alone identifies its deposit (the bin
-// positions of a narrow record differ by 1 or 2, the end bins of a wide one by
-// at least 3), so one compare decides whether a deposit joins the lane's
-// accumulated one.
+// once per step (the offset table is stored [column][beam], so that a warp
+// reads 32 consecutive entries). A record's first word alone identifies its
+// deposit (the bin positions of a narrow record differ by 1 or 2, the end bins
+// of a wide one by at least 3), so one compare decides whether a deposit joins
+// the lane's accumulated one. Accumulating a lane's successive deposits that
+// share their bins also keeps the FP32 sums of a bin that thousands of samples
+// reach (a plane facing the sensor) short.
 template <int KIND, int G>
 __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layout &Ly, float *hbuf, float2 *tab,
                                              const float2 *rtab, const float *ctab, int *uctr, const BeamParam *bp,
@@ -1003,7 +1006,7 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
         const int ncs = ce - cs + 1;  // a multiple of kStep
         __syncthreads();  // previous stripe's table no longer read
         for (int i = tid; i < G * ncs; i += blockDim.x) {
-            int jj = i / ncs, cc = i - jj * ncs;
+            const int cc = i / G, jj = i - cc * G;
             const BeamParam &Q = bp[jj];
             float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
             float sD, vers;
@@ -1016,12 +1019,11 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
                 sincosf(dAz, &sD, &cD);
                 vers = 1.f - cD;
             }
-            tab[jj * kTC + cc] = make_float2(sD, vers);
+            tab[i] = make_float2(sD, vers);
         }
         if (tid == 0) *uctr = nwarps;
         __syncthreads();
         if (R0 > R1) continue;
-        const float2 *tjc = tab + j * kTC - cs;
         // segments of whole steps, at most kSeg (rounded up to a step) wide
         const int nseg = (ncs + kSeg - 1) / kSeg;
         const int segw = ((ncs + nseg - 1) / nseg + kStep - 1) / kStep * kStep;
@@ -1050,7 +1052,7 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
                 ax = 0.f; bx = 0.f; cx = 3.f; ay = 0.f; by = 0.f; cy = 0.f;
             }
             const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(c_lo + q));
-            const float2 *tp = tjc + c_lo + q;
+            const float2 *tp = tab + (c_lo - cs) * G + lane;
             for (int st = 0; st < nsteps; ++st) {
                 float4 r0[kSamples], r1s[kSamples];
                 float2 t[kSamples];
@@ -1058,10 +1060,10 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
                 for (int u = 0; u < kSamples; ++u) {
                     r0[u] = __ldg(rp + 2 * CQ * u);
                     r1s[u] = __ldg(rp + 2 * CQ * u + 1);
-                    t[u] = tp[CQ * u];
+                    t[u] = tp[kWarp * u];
                 }
                 rp += 2 * kStep;
-                tp += kStep;
+                tp += kWarp * kSamples;
                 // a record with neither a deposit nor ambient light adds nothing
                 uint32_t live = 0u;
 #pragma unroll
