@@ -53,7 +53,9 @@ def parse():
                     help="frame workloads: echoes nearest first (up to 3) or the single strongest return")
     ap.add_argument("--echo-only", action="store_true",
                     help="frame workload through lidar_simulate_echoes (echoes and counts, no waveform output)")
-    ap.add_argument("--cpu-beams", type=int, default=1024, help="oracle beam sample for the CPU baseline (about 20 s of CPU work on 16 cores)")
+    ap.add_argument("--cpu-beams", type=int, default=None,
+                    help="oracle beam sample for the CPU baseline and the parity check: 1024 evenly spaced beams "
+                         "(about 20 s of CPU work on 16 cores), 2000 (the 1 %% subsample) on the wide-tail frame")
     ap.add_argument("--deposit", default="atomic", choices=["atomic", "tc_split", "tc_bf16", "tcgen05_bf16",
                                                              "tcgen05_fp16"],
                     help="deposit form of the footprint kernel (lidar_set_deposit)")
@@ -81,7 +83,10 @@ def parse():
                          "split, 64-frame batch)")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2512_05932_gb300", "weights", "tailnet_wide.bin"),
                     help="network weights of --tail net")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.cpu_beams is None:
+        args.cpu_beams = 2000 if args.workload in ("wide", "split") else 1024
+    return args
 
 
 WORKLOAD = "frame"
