@@ -967,12 +967,31 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
     return amb_acc;
 }
 
-// Phase 1, lean form of the atomic deposit, for groups whose union box needs
-// neither the panorama wrap nor the front-hemisphere test. The box's columns
-// are widened to whole warp steps inside the G-buffer: a column outside a
-// beam's own box lies outside its profile's support, where the profile weight
-// is exactly 0, so no sample needs a bounds or activity test. A lane whose
-// beam slot is empty evaluates its profile far outside any support (weight 0).
+// The box a lean phase 1 walks for each beam of a group: the group's union
+// box (all beams share the origin (C0, R0)), or, for beams too far apart for
+// their boxes to overlap much, each beam's own box widened to the common
+// size Wb x Hb and shifted inside the G-buffer where it reaches an edge.
+struct LeanBox {
+    int pb;        // 1: per-beam boxes, 0: the union box
+    int R0, C0;    // origin of the union box
+    int Hb, Wb;    // rows and columns walked for every beam (Wb a multiple of the warp step)
+};
+
+__device__ __forceinline__ int2 lean_origin(const BeamParam &Q, const LeanBox &B, int U, int V)
+{
+    if (!B.pb) return make_int2(B.C0, B.R0);
+    if (!Q.valid) return make_int2(0, 0);
+    return make_int2(min(Q.col0, U - B.Wb), min(Q.row0, V - B.Hb));
+}
+
+// Phase 1, lean form of the atomic deposit, for groups whose boxes need
+// neither the panorama wrap nor the front-hemisphere test. Every beam's box
+// (the group's union box, or the beam's own box for a group of beams too far
+// apart to share much of it) is widened to whole warp steps inside the
+// G-buffer: a column outside a beam's own box lies outside its profile's
+// support, where the profile weight is exactly 0, so no sample needs a bounds
+// or activity test. A lane whose beam slot is empty evaluates its profile far
+// outside any support (weight 0).
 // Lane (j, q) takes beam j on columns q, q + CQ, ... of each step of CQ *
 // kSamples columns; its loads use fixed offsets from two pointers advanced
 // once per step (the offset table is stored [column][beam], so that a warp
@@ -982,10 +1001,10 @@ __device__ __forceinline__ float phase1_atomic(const FootprintArgs &A, const Lay
 // the lane's accumulated one. Accumulating a lane's successive deposits that
 // share their bins also keeps the FP32 sums of a bin that thousands of samples
 // reach (a plane facing the sensor) short.
-template <int KIND, int G>
+template <int KIND, int G, bool PB>
 __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layout &Ly, float *hbuf, float2 *tab,
-                                             const float2 *rtab, const float *ctab, int *uctr, const BeamParam *bp,
-                                             int gcount, int R0, int R1, int C0, int C1, bool use_rtab)
+                                             float2 *rtab, float *ctab, int *uctr, const BeamParam *bp,
+                                             int gcount, const LeanBox &B)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int nb = A.n_bins, pad = Ly.pad;
@@ -997,18 +1016,37 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
     const BeamParam P = bp[j];
     const float t2max = P.pad0 ? A.core2 : A.trunc2;
     const bool jok = (j < gcount) && P.valid;
+    // this lane's box origin (the same in every lane for the union box)
+    const int2 org = PB ? lean_origin(P, B, A.U, A.V) : make_int2(B.C0, B.R0);
     float *hj = hbuf + j * Ly.HB;
     uint32_t k0 = kNoDeposit, k1 = kNoDeposit;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, ac = 0.f;
     float amb_acc = 0.f;
-    for (int cs = C0; cs <= C1; cs += kStripe) {
-        const int ce = min(C1, cs + kStripe - 1);
-        const int ncs = ce - cs + 1;  // a multiple of kStep
-        __syncthreads();  // previous stripe's table no longer read
+    // per (beam, row of its box): sin of the elevation offset, and cos(el) of
+    // the row (per row in ctab for the union box, beside the sine otherwise)
+    const bool use_rtab = B.Hb <= kRT;
+    if (use_rtab) {
+        for (int i = tid; i < G * B.Hb; i += blockDim.x) {
+            const int rr = i / G, jj = i - rr * G;
+            const BeamParam &Q = bp[jj];
+            const int row = (PB ? lean_origin(Q, B, A.U, A.V).y : B.R0) + rr;
+            const float dEl = ((float)(row - Q.ri) - Q.rf) * A.del;
+            if (PB) {
+                rtab[jj * kRT + rr] = make_float2(sinf(dEl), cosf(A.el0 + ((float)row + 0.5f) * A.del));
+            } else {
+                rtab[jj * kRT + rr].x = sinf(dEl);
+                if (jj == 0) ctab[rr] = cosf(A.el0 + ((float)row + 0.5f) * A.del);
+            }
+        }
+    }
+    for (int cs = 0; cs < B.Wb; cs += kStripe) {
+        const int ncs = min(B.Wb - cs, kStripe);  // a multiple of kStep
+        __syncthreads();  // previous stripe's table no longer read (and the row table is written)
         for (int i = tid; i < G * ncs; i += blockDim.x) {
             const int cc = i / G, jj = i - cc * G;
             const BeamParam &Q = bp[jj];
-            float dAz = ((float)(cs + cc - Q.ci) - Q.cf) * A.daz;
+            const int col = (PB ? lean_origin(Q, B, A.U, A.V).x : B.C0) + cs + cc;
+            float dAz = ((float)(col - Q.ci) - Q.cf) * A.daz;
             float sD, vers;
             if (fabsf(dAz) <= 0.1f) {
                 float z2 = dAz * dAz;
@@ -1023,27 +1061,25 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
         }
         if (tid == 0) *uctr = nwarps;
         __syncthreads();
-        if (R0 > R1) continue;
         // segments of whole steps, at most kSeg (rounded up to a step) wide
         const int nseg = (ncs + kSeg - 1) / kSeg;
         const int segw = ((ncs + nseg - 1) / nseg + kStep - 1) / kStep * kStep;
-        const int nunits = (R1 - R0 + 1) * nseg;
+        const int nunits = B.Hb * nseg;
         for (int unit = warp; unit < nunits;) {
-            const int row = R0 + unit / nseg;
-            const int seg = unit - (unit / nseg) * nseg;
-            const int c_lo = cs + seg * segw;
-            const int c_hi = min(ce, c_lo + segw - 1);
-            const int nsteps = c_hi >= c_lo ? (c_hi - c_lo + 1) / kStep : 0;
-            float cosEl, sdEl, cdEl;
+            const int rr = unit / nseg;
+            const int seg = unit - rr * nseg;
+            const int c_lo = seg * segw;  // relative to the stripe
+            const int nsteps = max(0, min(ncs - c_lo, segw)) / kStep;
+            const int row = org.y + rr;
+            float cosEl, sdEl;
             if (use_rtab) {
-                const float2 rt = rtab[j * kRT + (row - R0)];
-                sdEl = rt.x; cdEl = rt.y; cosEl = ctab[row - R0];
+                const float2 rt = rtab[j * kRT + rr];
+                sdEl = rt.x;
+                cosEl = PB ? rt.y : ctab[rr];
             } else {
                 cosEl = cosf(A.el0 + ((float)row + 0.5f) * A.del);
-                float dEl = ((float)(row - P.ri) - P.rf) * A.del;
-                sincosf(dEl, &sdEl, &cdEl);
+                sdEl = sinf(((float)(row - P.ri) - P.rf) * A.del);
             }
-            (void)cdEl;
             const float Kv = P.sin_elb * cosEl;
             float ax = P.cg * cosEl, bx = P.sg * Kv, cx = P.sg * sdEl;
             float ay = -P.sg * cosEl, by = P.cg * Kv, cy = P.cg * sdEl;
@@ -1051,8 +1087,8 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
                 // (x, y) = (3, 0): far outside every profile's support
                 ax = 0.f; bx = 0.f; cx = 3.f; ay = 0.f; by = 0.f; cy = 0.f;
             }
-            const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(c_lo + q));
-            const float2 *tp = tab + (c_lo - cs) * G + lane;
+            const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(org.x + cs + c_lo + q));
+            const float2 *tp = tab + c_lo * G + lane;
             for (int st = 0; st < nsteps; ++st) {
                 float4 r0[kSamples], r1s[kSamples];
                 float2 t[kSamples];
@@ -1533,16 +1569,48 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
         }
     }
     __syncthreads();
-    int R0 = 1 << 30, R1 = -(1 << 30), C0 = 1 << 30, C1 = -(1 << 30);
-    for (int j = 0; j < gcount; ++j) {
-        const BeamParam &P = bp[j];
-        if (!P.valid) continue;
-        R0 = min(R0, P.row0); R1 = max(R1, P.row1);
-        C0 = min(C0, P.col0); C1 = max(C1, P.col1);
+    // Box extents and the tests below, one beam per lane (G <= 16), reduced
+    // across the warp: every warp computes them, no barrier needed.
+    const unsigned full = 0xffffffffu;
+    const BeamParam &Ql = bp[min(lane, G - 1)];
+    const bool vl = lane < gcount && Ql.valid;
+    const int R0 = __reduce_min_sync(full, vl ? Ql.row0 : (1 << 30));
+    const int R1 = __reduce_max_sync(full, vl ? Ql.row1 : -(1 << 30));
+    const int C0 = __reduce_min_sync(full, vl ? Ql.col0 : (1 << 30));
+    const int C1 = __reduce_max_sync(full, vl ? Ql.col1 : -(1 << 30));
+    // Boxes that wrap around a panorama or reach beyond 45 degrees from a
+    // beam's axis need the per-sample wrap and front-hemisphere tests
+    // (within 45 degrees in both offsets, d.a >= cos 45 - (1 - cos 45) > 0)
+    bool checked = A.panorama != 0;
+    {
+        const float da = fmaxf(fabsf((float)(Ql.col0 - Ql.ci) - Ql.cf), fabsf((float)(Ql.col1 - Ql.ci) - Ql.cf)) * A.daz;
+        const float de = fmaxf(fabsf((float)(Ql.row0 - Ql.ri) - Ql.rf), fabsf((float)(Ql.row1 - Ql.ri) - Ql.rf)) * A.del;
+        checked = checked || __any_sync(full, vl && !(da <= 0.78f && de <= 0.78f));
+    }
+    // Lean form (atomic deposit): the union box, or each beam's own box when
+    // that walks at most 4/5 of the union's samples (the union lets lanes on
+    // one pixel share its record load), widened to whole warp steps inside
+    // the G-buffer; every beam must stay within 45 degrees of every pixel of
+    // the box it walks.
+    LeanBox LB{};
+    bool lean = false;
+    if (!TC && G >= 4 && !checked && R0 <= R1) {
+        constexpr int kStepL = (kWarp / G) * kSamples;
+        const int Wu = (C1 - C0 + kStepL) / kStepL * kStepL;
+        const int Hm = __reduce_max_sync(full, vl ? Ql.row1 - Ql.row0 + 1 : 0);
+        const int Wm = (__reduce_max_sync(full, vl ? Ql.col1 - Ql.col0 + 1 : 0) + kStepL - 1) / kStepL * kStepL;
+        const bool pb = (long)Hm * Wm * 5 < (long)(R1 - R0 + 1) * Wu * 4 && Wm <= A.U && Hm <= A.V;
+        if (pb) LB = LeanBox{1, 0, 0, Hm, Wm};
+        else LB = LeanBox{0, R0, min(C0, A.U - Wu), R1 - R0 + 1, Wu};
+        const int2 o = lean_origin(Ql, LB, A.U, A.V);
+        const float da = fmaxf(fabsf((float)(o.x - Ql.ci) - Ql.cf), fabsf((float)(o.x + LB.Wb - 1 - Ql.ci) - Ql.cf)) * A.daz;
+        const float de = fmaxf(fabsf((float)(o.y - Ql.ri) - Ql.rf), fabsf((float)(o.y + LB.Hb - 1 - Ql.ri) - Ql.rf)) * A.del;
+        lean = LB.Wb <= A.U && __all_sync(full, !vl || (da <= 0.78f && de <= 0.78f));
     }
     // per-(beam, row) sin and cos of the elevation offset and per-row cos(el)
+    // (the lean form fills its own table)
     const bool use_rtab = R0 <= R1 && R1 - R0 + 1 <= kRT;
-    if (use_rtab) {
+    if (use_rtab && !lean) {
         const int nr = R1 - R0 + 1;
         for (int i = tid; i < G * nr; i += blockDim.x) {
             int jj = i / nr, rr = i - jj * nr;
@@ -1560,36 +1628,10 @@ __device__ __forceinline__ void footprint_group(const FootprintArgs &A, const in
     if constexpr (TC) {
         amb_acc = phase1_tc<KIND, G>(A, Ly, hbuf, tab, bp, gcount, R0, R1, C0, C1);
     } else {
-        // Boxes that wrap around a panorama or reach beyond 45 degrees from a
-        // beam's axis need the per-sample wrap and front-hemisphere tests
-        // (within 45 degrees in both offsets, d.a >= cos 45 - (1 - cos 45) > 0)
-        bool checked = A.panorama != 0;
-        for (int jj = 0; jj < gcount && !checked; ++jj) {
-            const BeamParam &Q = bp[jj];
-            if (!Q.valid) continue;
-            const float da = fmaxf(fabsf((float)(Q.col0 - Q.ci) - Q.cf), fabsf((float)(Q.col1 - Q.ci) - Q.cf)) * A.daz;
-            const float de = fmaxf(fabsf((float)(Q.row0 - Q.ri) - Q.rf), fabsf((float)(Q.row1 - Q.ri) - Q.rf)) * A.del;
-            checked = !(da <= 0.78f && de <= 0.78f);
-        }
-        // lean form: the union box widened to whole warp steps within the
-        // G-buffer, every beam still within 45 degrees of every column of it
-        constexpr int kStepL = (kWarp / G) * kSamples;
-        bool lean = G >= 4 && !checked && R0 <= R1;
-        int C0w = C0, C1w = C1;
-        if (lean) {
-            const int Wp = (C1 - C0 + kStepL) / kStepL * kStepL;
-            lean = Wp <= A.U;
-            C0w = min(C0, A.U - Wp);
-            C1w = C0w + Wp - 1;
-            for (int jj = 0; jj < gcount && lean; ++jj) {
-                const BeamParam &Q = bp[jj];
-                if (!Q.valid) continue;
-                const float da = fmaxf(fabsf((float)(C0w - Q.ci) - Q.cf), fabsf((float)(C1w - Q.ci) - Q.cf)) * A.daz;
-                lean = da <= 0.78f;
-            }
-        }
-        if (lean)
-            amb_acc = phase1_lean<KIND, G>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0w, C1w, use_rtab);
+        if (lean && LB.pb)
+            amb_acc = phase1_lean<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, LB);
+        else if (lean)
+            amb_acc = phase1_lean<KIND, G, false>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, LB);
         else if (checked)
             amb_acc = phase1_atomic<KIND, G, true>(A, Ly, hbuf, tab, rtab, ctab, uctr, bp, gcount, R0, R1, C0, C1,
                                                    use_rtab);

@@ -29,8 +29,8 @@ struct TailState {
     int box_off = 0;
     int G_core = 4;                 // beams per CTA of the core pass (the sensor's)
     size_t smem_core = 0;
-    int G_fb = 1;                   // beams per CTA of the exact re-run: one, since the re-run beams are
-    size_t smem_fb = 0;             // scattered (a CTA walks the union of its beams' pixel boxes)
+    int G_fb = 4;                   // beams per CTA of the exact re-run; the re-run beams are scattered,
+    size_t smem_fb = 0;             // so each of a CTA's beams walks its own pixel box (lean phase 1)
     float4 *mip_s[kMipLevels] = {};
     float2 *mip_r[kMipLevels] = {};
     size_t mip_cap[kMipLevels] = {};
@@ -177,6 +177,12 @@ lidar_status_t lidar_tail_configure(lidar_t *l, double core_deg, int32_t n_coars
         box[x + t->box_off] = (float)(acc / cf);
     }
     t->G_core = l->G;
+    {
+        // four re-run beams per CTA where their histograms fit, else one
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, l->device);
+        if ((long)gbl::footprint_smem_bytes(4, model_args(l)) > optin) t->G_fb = 1;
+    }
     t->smem_fb = gbl::footprint_smem_bytes(t->G_fb, model_args(l));
     t->smem_core = gbl::footprint_smem_bytes(t->G_core, model_args(l));
     if ((e = gbl::prepare_footprint(l->kind, t->G_fb, false, t->smem_fb)) != cudaSuccess ||
