@@ -368,3 +368,28 @@ def test_wide_tail_frame_sampled_beams():
     beams = np.sort(S.rng(2000).choice(n, 2000, replace=False)).astype(np.int32)
     st = check_workload(w, beams=beams, strict=True)
     assert st["echoes"] >= 1000, st
+
+
+def test_spread_beams_walk_their_own_boxes():
+    """A coarse grid of 3 200 beams whose footprints (radial profile cut at
+    0.5 deg: boxes about 21 pixels wide) lie 13 pixels apart: a group of 8
+    neighbouring beams shares little of its union box, so each beam walks its
+    own box, shifted inside the G-buffer where it reaches an edge. The corner
+    and edge beams and a random sample against the oracle."""
+    pitch = 0.05 * DEG
+    U, V = 1024, 512
+    n = np.array([-1.0, 0.3, 0.2])
+    n /= np.linalg.norm(n)
+    patch = S.Rect(np.array([8.0, 0.5, 0.3]), np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0]),
+                   0.4, 0.3, rho_d=0.3, retro=100.0)
+    scene = S.Scene(planes=[S.Plane(n, -9.0, 0.4, 0.0)], rects=[patch], ambient="uniform",
+                    ambient_level=0.01)
+    gb = S.raycast(scene, U, V, -U * pitch / 2, -V * pitch / 2, pitch, pitch)
+    dirs = S.grid_pattern(80, 40, U * pitch, V * pitch)
+    w = S.Workload("spread_grid_1024x512_3200beams", gb, dirs, S.radial_profile(trunc_deg=0.5),
+                   S.pulse(1024, 0.1e-9), S.calib(1e-5, 1e-4, 3, True))
+    g = S.rng(21)
+    edges = [0, 1, 79, 80, 3119, 3120, 3198, 3199] + list(range(0, 3200, 80)) + list(range(79, 3200, 80))
+    beams = np.unique(np.concatenate([edges, g.choice(3200, 120, replace=False)])).astype(np.int32)
+    st = check_workload(w, beams=beams)
+    assert st["echoes"] >= 100
