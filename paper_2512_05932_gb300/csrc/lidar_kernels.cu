@@ -384,6 +384,7 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t s)
 // --------------------------------------------------------------------------
 
 constexpr int kSeg = 64;     // columns per work unit (one row)
+constexpr int kSegLean = 256; // columns per work unit of the lean phase 1 (longer units: fewer per-row set-ups)
 constexpr int kBlk = 256;    // waveform bins per convolution work item (8 per lane)
 
 // Per-beam histogram buffer: bins [-pad, n_bins + pad) at positions
@@ -1061,8 +1062,8 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
         }
         if (tid == 0) *uctr = nwarps;
         __syncthreads();
-        // segments of whole steps, at most kSeg (rounded up to a step) wide
-        const int nseg = (ncs + kSeg - 1) / kSeg;
+        // segments of whole steps, at most kSegLean (rounded up to a step) wide
+        const int nseg = (ncs + kSegLean - 1) / kSegLean;
         const int segw = ((ncs + nseg - 1) / nseg + kStep - 1) / kStep * kStep;
         const int nunits = B.Hb * nseg;
         for (int unit = warp; unit < nunits;) {
