@@ -994,9 +994,10 @@ __device__ __forceinline__ int2 lean_origin(const BeamParam &Q, const LeanBox &B
 // or activity test. A lane whose beam slot is empty evaluates its profile far
 // outside any support (weight 0).
 // Lane (j, q) takes beam j on columns q, q + CQ, ... of each step of CQ *
-// kSamples columns; its loads use fixed offsets from two pointers advanced
-// once per step (the offset table is stored [column][beam], so that a warp
-// reads 32 consecutive entries). A record's first word alone identifies its
+// kSamples columns (or, with 4 or fewer beams per CTA, a contiguous run of
+// columns); its loads use fixed offsets from two pointers advanced once per
+// step (the offset table is stored [column][beam], so that a warp reads
+// consecutive entries). A record's first word alone identifies its
 // deposit (the bin positions of a narrow record differ by 1 or 2, the end bins
 // of a wide one by at least 3), so one compare decides whether a deposit joins
 // the lane's accumulated one. Accumulating a lane's successive deposits that
@@ -1012,6 +1013,14 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
     constexpr int CQ = kWarp / G;
     constexpr int kStep = CQ * kSamples;                // columns per warp step
     constexpr int kStripe = (kTC - 1) / kStep * kStep;  // columns per offset-table stripe
+    // With 8 or more column phases (4 or fewer beams per CTA) a lane walks a
+    // contiguous run of columns: its successive deposits then share their bins
+    // far more often (a surface at slowly varying range), which saves flushes;
+    // with fewer phases the columns are interleaved (q, q + CQ, ...), which
+    // keeps a warp's record loads within one or two cache lines.
+    constexpr bool kContig = CQ >= 8;
+    constexpr int kDu = kContig ? 1 : CQ;                // columns between a lane's samples of a step
+    constexpr int kAdv = kContig ? kSamples : kStep;     // columns a lane advances per step
     const int j = lane % G;
     const int q = lane / G;
     const BeamParam P = bp[j];
@@ -1088,19 +1097,22 @@ __device__ __forceinline__ float phase1_lean(const FootprintArgs &A, const Layou
                 // (x, y) = (3, 0): far outside every profile's support
                 ax = 0.f; bx = 0.f; cx = 3.f; ay = 0.f; by = 0.f; cy = 0.f;
             }
-            const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(org.x + cs + c_lo + q));
-            const float2 *tp = tab + c_lo * G + lane;
+            // lane (j, q) starts at column q (interleaved: q + CQ u) or at q Lq
+            // (contiguous: Lq columns per lane, Lq = nsteps kSamples)
+            const int q0 = kContig ? q * nsteps * kSamples : q;
+            const float4 *rp = A.rec + 2 * ((size_t)row * A.U + (size_t)(org.x + cs + c_lo + q0));
+            const float2 *tp = tab + (c_lo + q0) * G + j;
             for (int st = 0; st < nsteps; ++st) {
                 float4 r0[kSamples], r1s[kSamples];
                 float2 t[kSamples];
 #pragma unroll
                 for (int u = 0; u < kSamples; ++u) {
-                    r0[u] = __ldg(rp + 2 * CQ * u);
-                    r1s[u] = __ldg(rp + 2 * CQ * u + 1);
-                    t[u] = tp[kWarp * u];
+                    r0[u] = __ldg(rp + 2 * kDu * u);
+                    r1s[u] = __ldg(rp + 2 * kDu * u + 1);
+                    t[u] = tp[G * kDu * u];
                 }
-                rp += 2 * kStep;
-                tp += kWarp * kSamples;
+                rp += 2 * kAdv;
+                tp += G * kAdv;
                 // a record with neither a deposit nor ambient light adds nothing
                 uint32_t live = 0u;
 #pragma unroll
